@@ -1,0 +1,533 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numbers
+printed in the paper, closed forms stated in its proofs, invariants of the
+theorems, independent libraries (numpy, scipy, mpmath) and brute force.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _trunc_sig(x, sig):
+    """Truncate toward zero to `sig` significant figures."""
+    if x == 0:
+        return 0.0
+    e = math.floor(math.log10(abs(x))) - sig + 1
+    return math.trunc(x / 10.0 ** e) * 10.0 ** e
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_w64_matches_numpy(orc):
+    """The word-size-generic Philox, instantiated at W=64, equals numpy's
+    independent Philox4x64-10 (numpy bumps the counter before each block)."""
+    cases = [([0, 0, 0, 0], [0, 0]), ([5, 7, 9, 11], [123, 456]),
+             ([2**64 - 1, 3, 0, 2**63], [2**64 - 1, 17])]
+    for ctr, key in cases:
+        bg = np.random.Philox(counter=np.array(ctr, dtype=np.uint64), key=np.array(key, dtype=np.uint64))
+        ref = bg.random_raw(4)
+        nxt = list(ctr)
+        nxt[0] = (nxt[0] + 1) % 2**64
+        if nxt[0] == 0:
+            nxt[1] = (nxt[1] + 1) % 2**64
+        got = orc.philox4(nxt, key, wbits=64)
+        assert [int(x) for x in got] == [int(x) for x in ref], (ctr, key)
+
+
+def test_philox_w32_uniformity(orc):
+    """Philox4x32-10 words: chi-square on 256 bins and bit balance."""
+    u = orc.uniforms(seed=0, offset=0, n=1 << 16)
+    hist, _ = np.histogram(u, bins=256, range=(0.0, 1.0))
+    e = u.size / 256
+    chi2 = ((hist - e) ** 2 / e).sum()
+    # 255 dof: mean 255, sd ~22.6; 6 sigma band
+    assert 120 < chi2 < 390, chi2
+    assert abs(u.mean() - 0.5) < 5 * (1 / math.sqrt(12 * u.size))
+
+
+def test_philox_stream_mapping(orc):
+    """Sample i of the standalone stream is word i%4 of block i//4."""
+    u = orc.uniforms(seed=0x1234_5678_9ABC, offset=8, n=8)
+    for i in range(8):
+        j = (8 + i) // 4
+        w = orc.philox4([j & 0xFFFFFFFF, j >> 32, 0, 0], [0x5678_9ABC, 0x1234], 32)
+        assert u[i] == np.float32(orc.u01(int(w[(8 + i) % 4])))
+
+
+def test_u01_grid(orc):
+    """Open, symmetric, FP32-exact grid: u(x) + u(~x) = 1, u in [2^-24, 1-2^-24]."""
+    xs = [0, 1, 511, 512, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF, 0x12345678]
+    for x in xs:
+        a, b = orc.u01(x), orc.u01((~x) & 0xFFFFFFFF)
+        assert a + b == 1.0
+        assert float(np.float32(a)) == a and float(np.float32(1.0 - a)) == 1.0 - a
+    assert orc.u01(0) == 2.0 ** -24 and orc.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+
+
+# ---------------------------------------------------------------- Phi^-1
+def test_phiinv_against_scipy_and_mpmath(orc):
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(0)
+    u = np.concatenate([rng.random(4000), 10.0 ** -rng.uniform(1, 40, 500),
+                        [2.0 ** -24, 0.5 - 2.0 ** -24, 0.25, 0.75]]).astype(np.float32)
+    u = u[(u > 0) & (u < 1)]
+    z = orc.phiinv(u)
+    ref = sp.ndtri(u.astype(np.float64))
+    assert np.allclose(z, ref, rtol=2e-14, atol=0), np.max(np.abs(z - ref) / np.abs(ref))
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 90   # erfinv(1 - 2u) loses digits as u -> 0: carry plenty
+    for uu in [2.0 ** -24, 1e-30, 0.02, 0.3, 0.5 - 2.0 ** -24, 0.9]:
+        exact = float(-mpmath.sqrt(2) * mpmath.erfinv(1 - 2 * mpmath.mpf(uu)))
+        assert abs(orc.phiinv_f64(uu) - exact) <= 4e-16 * abs(exact)
+
+
+def test_phiinv_symmetry_and_roundtrip(orc):
+    from scipy.special import ndtr
+    k = np.arange(0, 1 << 23, 4099, dtype=np.int64)
+    u = ((2 * k + 1) * 2.0 ** -24).astype(np.float32)
+    z = orc.phiinv(u)
+    zr = orc.phiinv((1.0 - u.astype(np.float64)).astype(np.float32))
+    assert np.array_equal(zr, -z)          # exact antisymmetry on the grid
+    lo = u < 0.5
+    assert np.allclose(ndtr(z[lo]), u[lo].astype(np.float64), rtol=1e-14)
+    assert orc.phiinv_f64(0.5) == 0.0
+    assert orc.phiinv_f64(0.0) == -math.inf and orc.phiinv_f64(1.0) == math.inf
+
+
+# ---------------------------------------------------------------- PWC table
+def test_pwc_listing_values(orc):
+    """The listing's printed table entries are Z^E truncated to one decimal."""
+    q = orc.pwc_table(1024, 0)
+    for idx, val in _read_golden("pwc_listing_values.txt"):
+        assert math.trunc(q[int(idx)] * 10) / 10 == pytest.approx(float(val), abs=1e-12)
+
+
+def test_pwc_conditional_mean_by_quadrature(orc):
+    """Z^E_k = N * int_{I_k} Phi^{-1}(u) du, checked by independent quadrature."""
+    from scipy.integrate import quad
+    from scipy.special import ndtri
+    n = 1024
+    q = orc.pwc_table(n, 0)
+    for k in [0, 1, 100, 511, 512, 900, 1022, 1023]:
+        val, err = quad(lambda t: ndtri(t), k / n, (k + 1) / n, epsabs=1e-14, epsrel=1e-13, limit=200)
+        assert q[k] == pytest.approx(n * val, rel=1e-9, abs=1e-12), k
+
+
+def test_pwc_theorem21_conditions(orc):
+    """Conditions (symmetry, intermediate values, bounded growth) of Theorem 2.1,
+    and the tail bound Q_K <= z_K + 1.25 q^{-1/2} of Corollary 2.3 (q >= 10)."""
+    from scipy.special import ndtri
+    for q_exp in [10, 11, 12, 13]:
+        n = 2 ** q_exp
+        for cons in (0, 1, 2):
+            Q = orc.pwc_table(n, cons)
+            assert np.allclose(Q, -Q[::-1], atol=1e-12)
+            u = np.arange(n + 1) / n
+            z = ndtri(u)
+            assert np.all(Q[1:-1] >= z[1:-2] - 1e-12) and np.all(Q[1:-1] <= z[2:-1] + 1e-12)
+            zK = z[n - 1]
+            assert zK - 1e-12 <= Q[-1] <= zK + 1.25 / math.sqrt(q_exp)
+        QE, QC, QI = (orc.pwc_table(n, c) for c in (0, 1, 2))
+        up = slice(n // 2, n)
+        assert np.all(QE[up] >= QC[up] - 1e-12) and np.all(QC[up] >= QI[up] - 1e-12)
+
+
+def test_pwc_l2_error_and_rate(orc):
+    """RMSE of 1024 intervals is about 1e-2 (Section 2.2 / Section 4.1), the
+    closed form agrees with quadrature, and ||Q - Phi^{-1}||_p^p / (2^-q q^{-p/2})
+    stays bounded as q grows (Theorem 2.1, p = 2 and 4)."""
+    from numpy.polynomial.legendre import leggauss
+    from scipy.special import ndtri
+    from scipy.integrate import quad
+    q1024 = orc.pwc_table(1024, 0)
+    rmse = math.sqrt(orc.pwc_l2err2(q1024))
+    assert 0.005 < rmse < 0.02
+    xg, wg = leggauss(24)
+
+    def lpp(n, p):
+        Q = orc.pwc_table(n, 0)
+        z = ndtri(np.arange(n + 1) / n)
+        tot = 0.0
+        # interior intervals in z-space: int |Q_k - z|^p phi(z) dz (Gauss-Legendre)
+        a, b = z[1:-2], z[2:-1]
+        Qi = Q[1:-1]
+        zz = 0.5 * (b - a)[:, None] * xg[None, :] + 0.5 * (a + b)[:, None]
+        f = np.abs(Qi[:, None] - zz) ** p * np.exp(-0.5 * zz ** 2) / math.sqrt(2 * math.pi)
+        tot += (0.5 * (b - a) * (f * wg[None, :]).sum(axis=1)).sum()
+        # the two singular end intervals by adaptive quadrature
+        for k, (lo, hi) in ((0, (-np.inf, z[1])), (n - 1, (z[n - 1], np.inf))):
+            tot += quad(lambda t: abs(Q[k] - t) ** p * math.exp(-0.5 * t * t) / math.sqrt(2 * math.pi),
+                        lo, hi, epsabs=1e-16, limit=200)[0]
+        return tot
+
+    assert lpp(1024, 2) == pytest.approx(rmse ** 2, rel=1e-6)
+    for p in (2, 4):
+        ratios = [lpp(2 ** q, p) / (2.0 ** -q * q ** (-p / 2)) for q in (6, 8, 10, 12)]
+        assert max(ratios) / min(ratios) < 4.0, ratios
+        assert ratios[-1] <= ratios[0] * 1.5, ratios
+
+
+# ---------------------------------------------------------------- PWL table
+def test_pwl_listing_coefficients(orc):
+    a, b = orc.pwl_table(15, 0.5)
+    for idx, av, bv in _read_golden("pwl_listing_coefficients.txt"):
+        i = int(idx)
+        assert _trunc_sig(a[i], 2) == pytest.approx(float(av), abs=1e-9), (i, a[i])
+        assert _trunc_sig(b[i], 2) == pytest.approx(float(bv), rel=1e-9, abs=1e-9), (i, b[i])
+
+
+def test_pwl_singular_interval_closed_form(orc):
+    """alpha = 2 phi(z_b)/b - 3 Phi(sqrt2 z_b)/(b^2 sqrt pi),
+    beta = 6/b^3 (Phi(sqrt2 z_b)/sqrt pi - b phi(z_b))  (proof of Theorem 2.4)."""
+    from scipy.special import ndtri, ndtr
+    for K in (8, 15, 16, 20):
+        a, b = orc.pwl_table(K, 0.5)
+        bb = 2.0 ** -K
+        zb = ndtri(bb)
+        ph = math.exp(-0.5 * zb * zb) / math.sqrt(2 * math.pi)
+        P2 = ndtr(math.sqrt(2) * zb)
+        alpha = 2 * ph / bb - 3 * P2 / (bb * bb * math.sqrt(math.pi))
+        beta = 6 / bb ** 3 * (P2 / math.sqrt(math.pi) - bb * ph)
+        assert a[K] == pytest.approx(alpha, rel=1e-9)
+        assert b[K] == pytest.approx(beta, rel=1e-9)
+        assert b[K] == pytest.approx(-3 / (bb * zb), rel=0.35)   # beta ~ -3/(b z_b)
+
+
+def test_pwl_normal_equations_mpmath(orc):
+    """Coefficients solve the L2 normal equations, integrals by mpmath quadrature."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    a, b = orc.pwl_table(15, 0.5)
+    finv = lambda t: -mpmath.sqrt(2) * mpmath.erfinv(1 - 2 * t)
+    for k in (1, 2, 7, 14, 15):
+        hi = mpmath.mpf(2) ** -k
+        lo = mpmath.mpf(0) if k == 15 else hi / 2
+        m0 = mpmath.quad(finv, [lo, hi])
+        m1 = mpmath.quad(lambda t: t * finv(t), [lo, hi])
+        s11, s12, s22 = hi - lo, (hi ** 2 - lo ** 2) / 2, (hi ** 3 - lo ** 3) / 3
+        det = s11 * s22 - s12 * s12
+        al = (m0 * s22 - m1 * s12) / det
+        be = (s11 * m1 - s12 * m0) / det
+        assert a[k] == pytest.approx(float(al), rel=1e-11), k
+        assert b[k] == pytest.approx(float(be), rel=1e-11), k
+
+
+def test_pwl_l2_error(orc):
+    """RMSE of 15 dyadic intervals is ~1e-2 and plateaus (Section 2.3): the
+    closed form agrees with quadrature, and more intervals barely help."""
+    from numpy.polynomial.legendre import leggauss
+    from scipy.special import ndtri
+    a, b = orc.pwl_table(15, 0.5)
+    e2 = orc.pwl_l2err2(a, b)
+    assert 0.003 < math.sqrt(e2) < 0.02
+    xg, wg = leggauss(60)
+    tot = 0.0
+    for k in range(1, 16):
+        hi = 2.0 ** -k
+        lo = 0.0 if k == 15 else hi / 2
+        if k == 15:  # singular interval: integrate in z-space
+            zl, zh = -40.0, ndtri(hi)
+            zz = 0.5 * (zh - zl) * xg + 0.5 * (zh + zl)
+            from scipy.special import ndtr
+            uu = ndtr(zz)
+            f = (a[k] + b[k] * uu - zz) ** 2 * np.exp(-0.5 * zz ** 2) / math.sqrt(2 * math.pi)
+            tot += 0.5 * (zh - zl) * (f * wg).sum()
+        else:
+            uu = 0.5 * (hi - lo) * xg + 0.5 * (hi + lo)
+            f = (a[k] + b[k] * uu - ndtri(uu)) ** 2
+            tot += 0.5 * (hi - lo) * (f * wg).sum()
+    assert 2 * tot == pytest.approx(e2, rel=1e-5)
+    e_inf = orc.pwl_l2err2(*orc.pwl_table(40, 0.5))
+    prev = None
+    for K in range(4, 25):
+        eK = orc.pwl_l2err2(*orc.pwl_table(K, 0.5))
+        assert eK >= e_inf - 1e-15
+        assert eK - e_inf <= 2.0 ** -(K - 1)          # tail term o(r^{K-1})
+        if prev is not None:
+            assert eK <= prev + 1e-15
+        prev = eK
+    assert math.sqrt(orc.pwl_l2err2(*orc.pwl_table(16, 0.5))) == pytest.approx(math.sqrt(e2), rel=0.01)
+
+
+def test_pwl_rate_in_r(orc):
+    """Central term O((1-r)^{2p}) of Theorem 2.4 for p = 2: with the tail made
+    negligible, log ||D-Phi^{-1}||_2^2 against log(1-r) has slope ~4."""
+    rs = [0.7, 0.8, 0.9]
+    errs = []
+    for r in rs:
+        K = int(math.ceil(math.log(1e-13) / math.log(r))) + 1
+        errs.append(orc.pwl_l2err2(*orc.pwl_table(K, r), r=r))
+    slope = np.polyfit(np.log([1 - r for r in rs]), np.log(errs), 1)[0]
+    assert 3.3 < slope < 4.7, (slope, errs)
+
+
+def test_pwl_peano_bound(orc):
+    """max_a -6 a^2 (Phi^{-1})''(a) ~ 2.59 at a ~ 0.177, with
+    (Phi^{-1})''(u) = z / phi(z)^2, and the pointwise error on the
+    non-singular dyadic intervals stays below 2.59 ((1-r)/r)^2."""
+    a_grid = np.linspace(0.05, 0.45, 40001)
+    z = np.array([orc.phiinv_f64(t) for t in a_grid])
+    phi = np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    g = -6 * a_grid ** 2 * z / phi ** 2
+    i = int(np.argmax(g))
+    assert g[i] == pytest.approx(2.5845, abs=2e-3)
+    assert a_grid[i] == pytest.approx(0.177, abs=2e-3)
+    al, be = orc.pwl_table(15, 0.5)
+    for k in range(1, 15):
+        hi = 2.0 ** -k
+        uu = np.linspace(hi / 2, hi, 200, endpoint=False)
+        err = np.abs(al[k] + be[k] * uu - np.array([orc.phiinv_f64(t) for t in uu]))
+        assert err.max() <= 2.59
+
+
+# ---------------------------------------------------------------- samplers
+def test_samplers_bruteforce_grid(orc):
+    """Every point of the uniform grid near every interval edge: the PWL index
+    equals ceil(-log2 v) - 1 capped at 15 (Section 3.3), the PWC index equals
+    floor(N u) (Section 3.2), and values are the table formulas."""
+    a, b = orc.pwl_table(15, 0.5)
+    a32, b32 = a.astype(np.float32), b.astype(np.float32)
+    q32 = orc.pwc_table(1024, 0).astype(np.float32)
+    edges = [2.0 ** -k for k in range(1, 24)] + [m / 1024 for m in range(1025)]
+    ks = set()
+    for e in edges:
+        c = int(round(e * 2 ** 24))
+        for d in range(-7, 8, 2):
+            m = c + d
+            if 0 < m < 2 ** 24 and m % 2 == 1:
+                ks.add(m)
+                ks.add(2 ** 24 - m)
+    m = np.array(sorted(ks), dtype=np.int64)
+    u = (m * 2.0 ** -24).astype(np.float32)
+    z, idx = orc.sample_pwl(a32, b32, u)
+    ud = u.astype(np.float64)
+    v = np.where(ud < 0.5, ud, 1.0 - ud)
+    _, ex = np.frexp(v)                       # v = f 2^ex, f in [1/2, 1)
+    want_idx = np.minimum(-ex, 15)            # ceil(-log2 v) - 1 for v in (0, 1/2]
+    want_idx = np.where(v == 0.5, 0, want_idx)
+    assert np.array_equal(idx, want_idx)
+    zz = a32[want_idx].astype(np.float64) + b32[want_idx].astype(np.float64) * v
+    assert np.array_equal(z, np.where(ud < 0.5, zz, -zz))
+    zc, ic = orc.sample_pwc(q32, u)
+    assert np.array_equal(ic, np.minimum(np.floor(ud * 1024).astype(np.int64), 1023))
+    assert np.array_equal(zc, q32[ic].astype(np.float64))
+
+
+def test_samplers_edge_cases(orc):
+    a, b = orc.pwl_table(15, 0.5)
+    a32, b32 = a.astype(np.float32), b.astype(np.float32)
+    u = np.array([0.5, 0.0, 1.0, np.nan, -0.25, 1.5, 2.0 ** -140], dtype=np.float32)
+    z, idx = orc.sample_pwl(a32, b32, u)
+    assert z[0] == 0.0 and math.copysign(1.0, z[0]) == -1.0    # u = 1/2 -> -0
+    assert z[1] == a32[15] and z[2] == -a32[15]
+    assert np.isnan(z[3]) and np.isnan(z[4]) and np.isnan(z[5])
+    assert idx[6] == 15
+    q32 = orc.pwc_table(1024, 0).astype(np.float32)
+    zc, ic = orc.sample_pwc(q32, u)
+    assert list(ic[:3]) == [512, 0, 1023] and np.isnan(zc[3:6]).all()
+
+
+def test_pwc_exact_discrete_law(orc):
+    """On the 2^23-point grid every PWC value has probability exactly 1/N, so the
+    sampled distribution is the discrete law of Q (Section 2.2)."""
+    k = np.arange(1 << 23, dtype=np.int64)
+    u = ((2 * k + 1) * 2.0 ** -24).astype(np.float32)
+    q32 = orc.pwc_table(1024, 0).astype(np.float32)
+    _, ic = orc.sample_pwc(q32, u)
+    assert np.array_equal(np.bincount(ic, minlength=1024), np.full(1024, 8192))
+
+
+# ---------------------------------------------------------------- MLMC
+def _gbm(orc, payoff, scheme=0, approx=0):
+    return orc.sde_params(model=orc.MODEL_GBM, scheme=scheme, payoff=payoff, approx=approx,
+                          X0=1.0, T=1.0, K=1.0, mu=0.05, sigma=0.2, discount=1.0)
+
+
+def test_mlmc_em_exact_moments(orc):
+    """E[X_N] = X0 (1 + mu dt)^N for exact and approximate variates (both have
+    zero mean), and E[X_N^2] = ((1 + mu dt)^2 + sigma^2 dt E[Z^2])^N  (Section 4)."""
+    a, b = orc.pwl_table(15, 0.5)
+    tab = (a, b)
+    # E[Z~^2] = int D^2 = 2 sum_k int_{I_k} (alpha + beta u)^2 du
+    sq = 0.0
+    for k in range(1, 16):
+        hi = 2.0 ** -k
+        lo = 0.0 if k == 15 else hi / 2
+        sq += a[k] ** 2 * (hi - lo) + a[k] * b[k] * (hi * hi - lo * lo) + b[k] ** 2 * (hi ** 3 - lo ** 3) / 3
+    EZ2a = 2 * sq
+    prm = _gbm(orc, orc.PAYOFF_X)
+    n = 40000
+    for level in (0, 3):
+        N = 2 ** level
+        dt = 1.0 / N
+        for kind, ez2 in ((orc.KIND_PLAIN, 1.0), (orc.KIND_PLAIN_APPROX, EZ2a)):
+            y = orc.mlmc_paths(prm, tab, level, kind, n, seed=11, tag=7)
+            m1 = (1 + 0.05 * dt) ** N
+            m2 = ((1 + 0.05 * dt) ** 2 + 0.04 * dt * ez2) ** N
+            se1 = y.std() / math.sqrt(n)
+            se2 = (y ** 2).std() / math.sqrt(n)
+            assert abs(y.mean() - m1) < 4.5 * se1
+            assert abs((y ** 2).mean() - m2) < 4.5 * se2
+
+
+def test_mlmc_telescoping_black_scholes(orc):
+    """Nested MLMC sum over levels of APPROX2 + CORR4 means matches the
+    Black-Scholes call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1) within the
+    Euler-Maruyama weak bias plus sampling error (Section 4, Section 4.1)."""
+    from scipy.stats import norm
+    r, s = 0.05, 0.2
+    d1 = (r + 0.5 * s * s) / s
+    bs = norm.cdf(d1) - math.exp(-r) * norm.cdf(d1 - s)
+    assert bs == pytest.approx(0.1045058357, abs=1e-9)
+    a, b = orc.pwl_table(15, 0.5)
+    prm = orc.sde_params(payoff=orc.PAYOFF_CALL, mu=r, sigma=s)
+    est, var = 0.0, 0.0
+    for level, n2, n4 in ((0, 200000, 4000), (1, 100000, 4000), (2, 60000, 4000), (3, 40000, 4000),
+                          (4, 20000, 2000), (5, 10000, 2000)):
+        s2 = orc.mlmc_level(prm, (a, b), level, orc.KIND_APPROX2, n2, seed=3, tag=100 + level)
+        s4 = orc.mlmc_level(prm, (a, b), level, orc.KIND_CORR4, n4, seed=3, tag=200 + level)
+        for (S1, S2, N) in (s2, s4):
+            m = S1 / N
+            est += m
+            var += (S2 / N - m * m) / N
+    bias_bound = 0.1045 * 2.0 ** -5 * 2   # EM weak error is O(dt); generous constant
+    assert abs(est - bs) < 4 * math.sqrt(var) + bias_bound
+
+
+def test_mlmc_cir_mean_exact(orc):
+    """Truncated Euler-Maruyama for CIR has E[X_N] = theta + (X0 - theta)(1 - kappa dt)^N
+    exactly, because the noise term has zero mean given X_n."""
+    prm = orc.sde_params(model=orc.MODEL_CIR, payoff=orc.PAYOFF_X, X0=0.04, T=1.0,
+                         sigma=0.3, kappa=0.5, theta=0.04, discount=1.0)
+    prm.X0 = 0.09
+    a, b = orc.pwl_table(15, 0.5)
+    for level in (2, 5):
+        N = 2 ** level
+        y = orc.mlmc_paths(prm, (a, b), level, orc.KIND_PLAIN, 30000, seed=5, tag=9)
+        want = 0.04 + (0.09 - 0.04) * (1 - 0.5 / N) ** N
+        assert abs(y.mean() - want) < 4.5 * y.std() / math.sqrt(y.size)
+
+
+def test_mlmc_variance_structure(orc):
+    """Fig. 3 / Table 2 shape: two-way exact variance decays ~2^-l (strong order
+    1/2), the four-way variance is ~2^-13..2^-14 of it for PWC/PWL, flat in l."""
+    prm_l = _gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWL)
+    prm_c = _gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWC)
+    a, b = orc.pwl_table(15, 0.5)
+    q = orc.pwc_table(1024, 0)
+    v2, rl, rc = [], [], []
+    for level in (2, 4, 6):
+        n = 20000
+        y2 = orc.mlmc_paths(prm_l, (a, b), level, orc.KIND_EXACT2, n, seed=1, tag=1)
+        y4 = orc.mlmc_paths(prm_l, (a, b), level, orc.KIND_CORR4, n, seed=1, tag=1)
+        y4c = orc.mlmc_paths(prm_c, q, level, orc.KIND_CORR4, n, seed=1, tag=1)
+        v2.append(y2.var())
+        rl.append(math.log2(y4.var() / y2.var()))
+        rc.append(math.log2(y4c.var() / y2.var()))
+    slope = (math.log2(v2[2]) - math.log2(v2[0])) / 4
+    assert -1.25 < slope < -0.75, v2
+    assert all(abs(x - (-14)) < 1.5 for x in rl), rl
+    assert all(abs(x - (-13)) < 2.0 for x in rc), rc
+    assert max(rl) - min(rl) < 1.0 and max(rc) - min(rc) < 1.0
+
+
+def test_cost_model_tables(orc):
+    """Table 2 and Table 6 speed-ups follow from the allocation formulas of
+    Section 4.1 with C~ = c^ + c~ and v~ = v^."""
+    for name, lv, cr, sp, eff, mm, mM in _read_golden("savings_tables.txt"):
+        lv, cr, sp, eff, mm = float(lv), float(cr), float(sp), float(eff), float(mm)
+        vhat, chat, ctil = 1.0, cr, 1.0
+        Vt, Ct = 2.0 ** lv, chat + ctil
+        eps = 1e-3
+        That, mhat = orc.mlmc_alloc([vhat], [chat], eps)
+        Ttil, mtil = orc.mlmc_alloc([vhat, Vt], [ctil, Ct], eps)
+        speed = That / Ttil
+        assert speed == pytest.approx(sp, abs=1.0 if cr > 100 else 0.006), name
+        assert 100 * speed / cr == pytest.approx(eff, abs=0.06), name
+        assert mtil[0] / mhat[0] == pytest.approx(mm, abs=0.011), name
+        if mM != "nan":
+            assert mtil[0] / mtil[1] == pytest.approx(float(mM), rel=0.025), name
+
+
+# ---------------------------------------------------------------- NCX2
+def test_gammp_against_scipy(orc):
+    from scipy.special import gammainc
+    for a in (0.1, 0.5, 1.0, 2.5, 10.0, 57.3, 400.0):
+        for x in (1e-3, 0.3, 1.0, 3.0, 9.5, 50.0, 380.0, 500.0):
+            assert orc.gammp(a, x) == pytest.approx(gammainc(a, x), rel=1e-12, abs=1e-15)
+
+
+def test_ncx2_closed_forms_and_scipy(orc):
+    from scipy.stats import ncx2
+    for u in (1e-6, 0.1, 0.5, 0.9, 0.999999):
+        # the quantile is found from F = 1 - Q, so near u -> 1 its error is
+        # ~1e-16 / f(x) in absolute terms: allow that conditioning
+        x = -2 * math.log1p(-u)
+        cond = 1e-15 / (0.5 * math.exp(-0.5 * x))
+        assert orc.ncx2_ppf(u, 2.0, 0.0) == pytest.approx(x, rel=1e-12, abs=cond)
+    for nu, lam in ((0.8889, 1.37), (1.0, 10.0), (5.0, 0.5), (2.0, 113.0), (10.0, 200.0)):
+        for u in (0.001, 0.2, 0.5, 0.8, 0.999):
+            assert orc.ncx2_ppf(u, nu, lam) == pytest.approx(ncx2.ppf(u, nu, lam), rel=1e-8)
+        for x in (0.05, 1.0, nu + lam):
+            assert orc.ncx2_cdf(x, nu, lam) == pytest.approx(ncx2.cdf(x, nu, lam), rel=1e-9, abs=1e-14)
+
+
+def test_ncx2_moments_by_quadrature(orc):
+    """mean nu + lambda and variance 2(nu + 2 lambda) of the quantile function."""
+    from numpy.polynomial.legendre import leggauss
+    xg, wg = leggauss(400)
+    u = 0.5 * (xg + 1)
+    for nu, lam in ((1.0, 5.0), (4.0, 2.0)):
+        x = np.array([orc.ncx2_ppf(t, nu, lam) for t in u])
+        m = 0.5 * (wg * x).sum()
+        v = 0.5 * (wg * x * x).sum() - m * m
+        assert m == pytest.approx(nu + lam, rel=2e-3)
+        assert v == pytest.approx(2 * (nu + 2 * lam), rel=2e-2)
+
+
+def test_ncx2_P_limits(orc):
+    """P_x(U; y) -> Phi^{-1}(U) as y -> 0 and -> C_x^{-1}(U)/(2 sqrt x) - sqrt(x)/2
+    as y -> 1 (Section 5.1)."""
+    from scipy.stats import chi2
+    for u in (0.05, 0.3, 0.7, 0.95):
+        assert orc.ncx2_P(u, 1.0, 1e-5) == pytest.approx(orc.phiinv_f64(u), abs=0.01)
+        y1 = orc.ncx2_P(u, 3.0, 1.0 - 1e-9)
+        assert y1 == pytest.approx(chi2.ppf(u, 3.0) / (2 * math.sqrt(3.0)) - math.sqrt(3.0) / 2, abs=1e-6)
+
+
+# ---------------------------------------------------------------- MLP
+def test_mlp_gradient_finite_differences(orc):
+    rng = np.random.default_rng(4)
+    H = 8
+    p = {"W1": rng.normal(size=(H, 2)), "b1": rng.normal(size=H) * 0.1,
+         "W2": rng.normal(size=(H, H)) / math.sqrt(H), "b2": rng.normal(size=H) * 0.1,
+         "w3": rng.normal(size=H) / math.sqrt(H), "b3": np.array([0.05])}
+    x = rng.normal(size=(17, 2))
+    t = rng.normal(size=17)
+    loss, g = orc.mlp_grad(p, x, t)
+    assert loss == pytest.approx(np.mean((orc.mlp_forward(p, x) - t) ** 2), rel=1e-13)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for j in range(min(flat.size, 6)):
+            old = flat[j]
+            flat[j] = old + h
+            lp = np.mean((orc.mlp_forward(p, x) - t) ** 2)
+            flat[j] = old - h
+            lm = np.mean((orc.mlp_forward(p, x) - t) ** 2)
+            flat[j] = old
+            assert g[name].reshape(-1)[j] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-9)
