@@ -1,0 +1,179 @@
+/*
+ * aicdf.h -- C ABI of libaicdf, a GB300 (sm_103a) library for approximate
+ * random variables produced from cheap approximations to the inverse
+ * cumulative distribution function, after Giles & Sheridan-Methven,
+ * "Approximating inverse cumulative distribution functions to produce
+ * approximate random variables" (arXiv 2012.09715).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers; *_host are host pointers.
+ *     The caller owns every buffer and stream; the library owns handles.
+ *   - Calls that take a stream are asynchronous on it unless stated.
+ *   - Errors are returned as aicdf_status; nothing throws across the ABI.
+ *     Arguments are checked before anything is launched.  A CUDA error from a
+ *     launch is reported as AICDF_ERR_CUDA (aicdf_last_cuda_error() gives the
+ *     cudaError_t value).
+ *   - Uniforms.  Where the library draws uniforms itself it uses
+ *     Philox4x32-10 (Salmon et al., SC'11) with key (seed mod 2^32, seed>>32)
+ *     and maps a 32-bit word x to u = (2*(x>>9)+1) * 2^-24, the midpoint of
+ *     one of 2^23 equal cells: u lies in [2^-24, 1-2^-24], and u and 1-u are
+ *     both exact in FP32.
+ */
+#ifndef AICDF_H
+#define AICDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (binary compatible with cudaStream_t); NULL = legacy stream. */
+typedef struct CUstream_st *aicdf_stream_t;
+
+typedef enum {
+  AICDF_OK = 0,
+  AICDF_ERR_ARG = 1,          /* bad argument (null, size, alignment, range)   */
+  AICDF_ERR_CUDA = 2,         /* a CUDA runtime call or launch failed          */
+  AICDF_ERR_NOCONVERGE = 3,   /* an iteration hit its cap                      */
+  AICDF_ERR_DOMAIN = 4,       /* parameters outside the model's domain         */
+  AICDF_ERR_STATE = 5,        /* handle in the wrong state                     */
+  AICDF_ERR_NOMEM = 6,        /* host allocation failed                        */
+  AICDF_ERR_UNSUPPORTED = 7   /* valid request that this build does not serve  */
+} aicdf_status;
+
+const char *aicdf_status_str(aicdf_status s);
+int aicdf_last_cuda_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int aicdf_version(void);
+
+/* ===================================================================== */
+/* Approximation tables (host objects; built in FP64)                     */
+/* ===================================================================== */
+typedef enum { AICDF_PWC = 0, AICDF_PWL = 1, AICDF_EXACT = 2, AICDF_EXACT_LIB = 3 } aicdf_method;
+typedef enum { AICDF_Z_E = 0, AICDF_Z_C = 1, AICDF_Z_I = 2 } aicdf_construction;
+typedef struct aicdf_table_s *aicdf_table;
+
+/* Build an approximation table on the host in FP64.
+ *
+ * AICDF_PWC (Section 2.2, Theorem 2.1, Corollary 2.3): n equal intervals
+ *   [m/n, (m+1)/n), n a power of two in [2, 4096]; constants by construction
+ *   Z^E (conditional mean E(Z | Phi(Z) in I_m), the paper's choice),
+ *   Z^C (Phi^{-1} of the interval centre) or Z^I (the endpoint nearest 1/2).
+ * AICDF_PWL (Section 2.3, Theorem 2.4 with the dyadic rate r = 1/2,
+ *   Section 3.3): n = K intervals in (0, 1/2), I_k = [2^-(k+1), 2^-k) for
+ *   k < K and I_K = (0, 2^-K), K in [1, 31]; each line is the L2-optimal fit
+ *   on its interval (the normal equations of the proof of Theorem 2.4).  The
+ *   table holds K+1 rows; row 0 is zero so that u = 1/2 maps to 0 (Section
+ *   3.3).  construction must be AICDF_Z_E (ignored).
+ * On success *out owns the table; release it with aicdf_table_destroy. */
+aicdf_status aicdf_table_build(int method, int n, int construction, aicdf_table *out);
+void aicdf_table_destroy(aicdf_table t);
+/* Copy the FP64 coefficients to the host.  PWC: c0 = the n constants, c1
+ * unused (may be NULL).  PWL: c0 = intercepts alpha[0..K], c1 = gradients
+ * beta[0..K].  cap = capacity of each array; *n_out = entries written. */
+aicdf_status aicdf_table_get(aicdf_table t, double *c0, double *c1, int cap, int *n_out);
+/* method (AICDF_PWC / AICDF_PWL) and size (n or K) of a table */
+aicdf_status aicdf_table_info(aicdf_table t, int *method, int *n);
+
+/* ===================================================================== */
+/* Sampling (Section 3: the inverse transform with Q, D or exact Phi^{-1}) */
+/* ===================================================================== */
+typedef enum { AICDF_F32 = 0, AICDF_F16 = 1 } aicdf_dtype;
+
+/* out_dev[i] = approx(u_i) for i < n, where
+ *   method AICDF_PWC : Q(u) = table[min(floor(n_table u), n_table-1)]  (Section 3.2)
+ *   method AICDF_PWL : Algorithm 1 -- reflect about 1/2, interval index from
+ *                      the FP32 exponent bits, one FMA, restore the sign
+ *                      (u = 1/2 gives -0, as the listing does)
+ *   method AICDF_EXACT     : the library's FP32 Phi^{-1} (max rel. error < 1e-6)
+ *   method AICDF_EXACT_LIB : CUDA's normcdfinvf, for comparison
+ * Uniforms: if u_dev != NULL, u_i = u_dev[i] (FP32, any value; u outside
+ * [0, 1] or NaN gives NaN; u = 0 / 1 give the end values: -inf / +inf for the
+ * exact methods, the end constants for PWC/PWL).  If u_dev == NULL, u_i is
+ * the library's Philox uniform for sample index offset + i: Philox call
+ * j = (offset+i)/4 with counter (j mod 2^32, j>>32, 0, 0), word (offset+i)%4.
+ * table must be NULL for the exact methods and a table of the matching method
+ * otherwise.  out_dtype: AICDF_F32, or AICDF_F16 (round-to-nearest-even of
+ * the FP32 result).  out_dev must be aligned to its element size; 16-byte
+ * alignment enables the vectorised path.  Asynchronous on stream. */
+aicdf_status aicdf_sample(aicdf_table table, int method, const float *u_dev, uint64_t seed,
+                          uint64_t offset, size_t n, void *out_dev, int out_dtype,
+                          aicdf_stream_t stream);
+
+/* Same samples as aicdf_sample with u_dev == NULL, delivered to HOST memory:
+ * the library generates chunks into the caller's device staging buffer
+ * (staging_bytes >= 2 MiB, split in two halves) and overlaps generation of
+ * one chunk with the device-to-host copy of the previous one.  host_out
+ * should be pinned for full speed.  Synchronous: returns when host_out is
+ * complete. */
+aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint64_t seed,
+                                  uint64_t offset, size_t n, void *host_out, int out_dtype,
+                                  void *staging_dev, size_t staging_bytes,
+                                  aicdf_stream_t stream);
+
+/* ===================================================================== */
+/* Multilevel Monte Carlo levels (Section 4, Section 4.1)                 */
+/* ===================================================================== */
+typedef enum { AICDF_MODEL_GBM = 0, AICDF_MODEL_CIR = 1 } aicdf_model;
+typedef enum { AICDF_SCHEME_EM = 0, AICDF_SCHEME_MILSTEIN = 1 } aicdf_scheme;
+typedef enum { AICDF_PAYOFF_X = 0, AICDF_PAYOFF_CALL = 1 } aicdf_payoff;
+/* Level estimator kinds.  With P^ (exact variates) and P~ (approximate
+ * variates from the same uniforms), fine level l and coarse level l-1
+ * (P_{-1} := 0):
+ *   APPROX2      Y = P~_l - P~_{l-1}                     (two-way, approximate)
+ *   CORR4        Y = P^_l - P^_{l-1} - P~_l + P~_{l-1}   (four-way correction)
+ *   EXACT2       Y = P^_l - P^_{l-1}                     (regular MLMC)
+ *   PLAIN        Y = P^_l                                (plain Monte Carlo)
+ *   PLAIN_APPROX Y = P~_l                                                     */
+typedef enum {
+  AICDF_KIND_APPROX2 = 0, AICDF_KIND_CORR4 = 1, AICDF_KIND_EXACT2 = 2,
+  AICDF_KIND_PLAIN = 3, AICDF_KIND_PLAIN_APPROX = 4
+} aicdf_kind;
+
+typedef struct {
+  int model;        /* aicdf_model                                         */
+  int scheme;       /* aicdf_scheme                                        */
+  int payoff;       /* aicdf_payoff: P = discount * X_T or discount*(X_T-K)^+ */
+  int reserved;
+  double X0, T, K;  /* initial value, horizon, strike                      */
+  double mu;        /* GBM drift                                           */
+  double sigma;     /* volatility (GBM) / diffusion coefficient (CIR)      */
+  double kappa;     /* CIR mean-reversion rate                             */
+  double theta;     /* CIR mean-reversion level                            */
+  double discount;  /* payoff multiplier, e.g. exp(-rT)                    */
+} aicdf_sde_params;
+
+/* Sum over paths p = path_offset .. path_offset+n_paths-1 of Y and Y^2 for the
+ * level estimator `kind` at `level` (2^level fine steps of size T/2^level;
+ * the coarse path takes 2^(level-1) steps with the pairwise sums of the fine
+ * Brownian increments, Section 4.1).  Fine step s of path p draws its uniform
+ * from Philox4x32-10 with counter (s/4, p mod 2^32, p>>32, tag), word s%4,
+ * key from seed; the exact and approximate variates of a step use that same
+ * uniform (Section 4.1).  approx: a PWL (K <= 15) or PWC (n <= 1024) table.
+ * Models: GBM dX = mu X dt + sigma X dW; CIR dX = kappa(theta-X)dt +
+ * sigma sqrt(X) dW with sqrt(|X|) (truncated scheme).  Schemes: Euler-
+ * Maruyama (Section 4) or Milstein.
+ * Writes sums_dev[0] = sum Y, sums_dev[1] = sum Y^2, sums_dev[2] = n (FP64).
+ * workspace_dev: caller-owned device scratch of at least
+ * aicdf_mlmc_level_workspace_bytes() bytes (per-block partial sums), not
+ * shared with a concurrent call.  Deterministic: the same arguments give
+ * bit-identical sums on the same GPU model.  Asynchronous on stream. */
+size_t aicdf_mlmc_level_workspace_bytes(void);
+aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_table approx, int level,
+                              int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                              uint32_t tag, double *sums_dev, void *workspace_dev,
+                              size_t workspace_bytes, aicdf_stream_t stream);
+
+/* Optimal sample allocation (Section 4.1): for nterms estimator terms with
+ * variances v[i] and costs c[i] and target RMSE eps, the Lagrange-optimal
+ * counts m[i] = eps^-1 sqrt(2 T v_i / c_i) with total time
+ * T = 2 eps^-2 (sum_i sqrt(v_i c_i))^2; returns T in *total.  Host only. */
+aicdf_status aicdf_mlmc_allocate(int nterms, const double *v, const double *c, double eps,
+                                 double *m, double *total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AICDF_H */

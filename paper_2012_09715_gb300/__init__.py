@@ -1,0 +1,211 @@
+"""Python binding of libaicdf (approximate inverse-CDF random variables on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libaicdf.so`` built in-tree by ``build.py`` (``__graft_entry__.build()``).
+There is no CPU fallback; if the library is missing every call raises.
+
+Functions mirror the C ABI in ``include/aicdf.h`` (without the ``aicdf_``
+prefix).  Device buffers are torch CUDA tensors (or raw integer pointers);
+streams default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaicdf.so")
+
+# enums (include/aicdf.h)
+OK, ERR_ARG, ERR_CUDA, ERR_NOCONVERGE, ERR_DOMAIN, ERR_STATE, ERR_NOMEM, ERR_UNSUPPORTED = range(8)
+PWC, PWL, EXACT, EXACT_LIB = 0, 1, 2, 3
+Z_E, Z_C, Z_I = 0, 1, 2
+F32, F16 = 0, 1
+MODEL_GBM, MODEL_CIR = 0, 1
+SCHEME_EM, SCHEME_MILSTEIN = 0, 1
+PAYOFF_X, PAYOFF_CALL = 0, 1
+KIND_APPROX2, KIND_CORR4, KIND_EXACT2, KIND_PLAIN, KIND_PLAIN_APPROX = range(5)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AicdfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.aicdf_status_str(status).decode() if _lib is not None else str(status)
+        if status == ERR_CUDA and _lib is not None:
+            msg += f" (cudaError {_lib.aicdf_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+class SdeParams(C.Structure):
+    _fields_ = [("model", C.c_int), ("scheme", C.c_int), ("payoff", C.c_int), ("reserved", C.c_int),
+                ("X0", C.c_double), ("T", C.c_double), ("K", C.c_double), ("mu", C.c_double),
+                ("sigma", C.c_double), ("kappa", C.c_double), ("theta", C.c_double),
+                ("discount", C.c_double)]
+
+
+# name -> (restype, argtypes); every entry point of include/aicdf.h
+_P, _I, _U32, _U64, _SZ, _D = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_size_t, C.c_double
+SIGNATURES = {
+    "aicdf_status_str": (C.c_char_p, [_I]),
+    "aicdf_last_cuda_error": (_I, []),
+    "aicdf_version": (_I, []),
+    "aicdf_table_build": (_I, [_I, _I, _I, C.POINTER(_P)]),
+    "aicdf_table_destroy": (None, [_P]),
+    "aicdf_table_get": (_I, [_P, _P, _P, _I, C.POINTER(_I)]),
+    "aicdf_table_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+    "aicdf_sample": (_I, [_P, _I, _P, _U64, _U64, _SZ, _P, _I, _P]),
+    "aicdf_sample_to_host": (_I, [_P, _I, _U64, _U64, _SZ, _P, _I, _P, _SZ, _P]),
+    "aicdf_mlmc_level_workspace_bytes": (_SZ, []),
+    "aicdf_mlmc_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P]),
+    "aicdf_mlmc_allocate": (_I, [_I, _P, _P, _D, _P, _P]),
+}
+
+
+def lib():
+    """Load libaicdf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise AicdfError(status, where)
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, numpy array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Table:
+    """Owning handle of an aicdf_table (host FP64 coefficients)."""
+
+    def __init__(self, method: int, n: int, construction: int = Z_E):
+        L = lib()
+        h = C.c_void_p()
+        _check(L.aicdf_table_build(method, n, construction, C.byref(h)), "table_build")
+        self.handle = h
+        self.method = method
+        self.n = n
+
+    def coefficients(self):
+        import numpy as np
+        cnt = self.n if self.method == PWC else self.n + 1
+        c0 = np.zeros(cnt, dtype=np.float64)
+        c1 = np.zeros(cnt, dtype=np.float64)
+        got = C.c_int()
+        _check(lib().aicdf_table_get(self.handle, c0.ctypes.data, c1.ctypes.data, cnt, C.byref(got)),
+               "table_get")
+        return (c0,) if self.method == PWC else (c0, c1)
+
+    def info(self):
+        m, n = C.c_int(), C.c_int()
+        _check(lib().aicdf_table_info(self.handle, C.byref(m), C.byref(n)), "table_info")
+        return m.value, n.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.aicdf_table_destroy(h)
+            self.handle = None
+
+
+def table_build(method: int, n: int, construction: int = Z_E) -> Table:
+    return Table(method, n, construction)
+
+
+def _th(table):
+    return None if table is None else table.handle
+
+
+def sample(table, method: int, out, u=None, seed: int = 0, offset: int = 0, n: int | None = None,
+           out_dtype: int | None = None, stream=None):
+    """aicdf_sample: fill device buffer `out` (torch float32/float16 tensor)."""
+    if n is None:
+        n = out.numel()
+    if out_dtype is None:
+        import torch
+        out_dtype = F16 if out.dtype == torch.float16 else F32
+    _check(lib().aicdf_sample(_th(table), method, _ptr(u), seed, offset, n, _ptr(out), out_dtype,
+                              _stream(stream)), "sample")
+    return out
+
+
+def sample_to_host(table, method: int, host_out, staging, seed: int = 0, offset: int = 0,
+                   n: int | None = None, out_dtype: int | None = None, stream=None):
+    """aicdf_sample_to_host: generate into `staging` (device) and copy to `host_out`."""
+    if n is None:
+        n = host_out.numel()
+    if out_dtype is None:
+        import torch
+        out_dtype = F16 if host_out.dtype == torch.float16 else F32
+    nbytes = staging.numel() * staging.element_size()
+    _check(lib().aicdf_sample_to_host(_th(table), method, seed, offset, n, _ptr(host_out), out_dtype,
+                                      _ptr(staging), nbytes, _stream(stream)), "sample_to_host")
+    return host_out
+
+
+def sde_params(model=MODEL_GBM, scheme=SCHEME_EM, payoff=PAYOFF_CALL, X0=1.0, T=1.0, K=1.0,
+               mu=0.05, sigma=0.2, kappa=0.0, theta=0.0, discount=None) -> SdeParams:
+    import math
+    if discount is None:
+        discount = math.exp(-mu * T) if (model == MODEL_GBM and payoff == PAYOFF_CALL) else 1.0
+    return SdeParams(model, scheme, payoff, 0, X0, T, K, mu, sigma, kappa, theta, discount)
+
+
+def mlmc_level_workspace_bytes() -> int:
+    return lib().aicdf_mlmc_level_workspace_bytes()
+
+
+def mlmc_level(params: SdeParams, table: Table, level: int, kind: int, n_paths: int, sums,
+               workspace, path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
+    """aicdf_mlmc_level: sums (device float64[3]) <- [sum Y, sum Y^2, n]."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().aicdf_mlmc_level(C.byref(params), table.handle, level, kind, n_paths, path_offset,
+                                  seed, tag, _ptr(sums), _ptr(workspace), nbytes, _stream(stream)),
+           "mlmc_level")
+    return sums
+
+
+def mlmc_allocate(v, c, eps: float):
+    """aicdf_mlmc_allocate (host): optimal path counts and total time."""
+    import numpy as np
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m = np.zeros(v.size, dtype=np.float64)
+    tot = C.c_double()
+    _check(lib().aicdf_mlmc_allocate(v.size, v.ctypes.data, c.ctypes.data, eps, m.ctypes.data,
+                                     C.byref(tot)), "mlmc_allocate")
+    return tot.value, m

@@ -1,0 +1,28 @@
+// Host-side internals of libaicdf (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/aicdf.h"
+
+struct aicdf_table_s {
+  uint32_t magic;
+  int method;                 // AICDF_PWC or AICDF_PWL
+  int n;                      // PWC: number of intervals; PWL: K
+  int construction;           // PWC constant construction
+  std::vector<double> c0, c1; // FP64 coefficients (PWC: constants; PWL: alpha, beta)
+  std::vector<float> f0, f1;  // the same rounded to FP32 (what the kernels use)
+};
+
+constexpr uint32_t AICDF_TABLE_MAGIC = 0x41494344u;  // "AICD"
+
+namespace aicdf {
+// Set by the launch wrappers; read by aicdf_last_cuda_error().
+void set_cuda_error(int e);
+bool table_ok(const aicdf_table_s *t);
+// SM count of the current device (cached per device).
+int sm_count();
+// Host FP64 inverse Gaussian CDF used for the table build.
+double host_phiinv(double p);
+}  // namespace aicdf

@@ -1,0 +1,137 @@
+// Device primitives shared by the sampling and path kernels.
+//
+//  * Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed on
+//    the host: the key schedule is the same for every thread of a launch, so
+//    the xor with the round key reads a kernel-parameter (constant bank) word.
+//  * u01: the 32-bit word -> (2*(x>>9)+1) 2^-24 map, exact in FP32.
+//  * pwl_eval: Algorithm 1 (Section 3.3) with the 2 x 16 coefficients held in
+//    registers across the warp and fetched by __shfl_sync -- the GPU form of
+//    keeping the table in one 512-bit vector register (Section 3.3).
+//  * pwc_eval: the lookup of Section 3.2, table staged in shared memory.
+//  * phiinv_f32: exact FP32 inverse Gaussian CDF (Giles' erfinv formulation,
+//    coefficients fitted by fit_phiinv.py), FP64 branch in the far tail.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+
+#include "phiinv_coefs.h"
+
+namespace aicdf {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u;
+constexpr uint32_t PHILOX_M1 = 0xCD9E8D57u;
+constexpr uint32_t PHILOX_W0 = 0x9E3779B9u;
+constexpr uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+// Round keys of Philox4x32-10 for one seed: k0[r] = lo(seed) + r*W0,
+// k1[r] = hi(seed) + r*W1 (mod 2^32).
+struct PhiloxKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline PhiloxKeys make_keys(uint64_t seed) {
+  PhiloxKeys k;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = a;
+    k.k1[r] = b;
+    a += PHILOX_W0;
+    b += PHILOX_W1;
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = PHILOX_M0 * c.x, hi0 = __umulhi(PHILOX_M0, c.x);
+    const uint32_t lo1 = PHILOX_M1 * c.z, hi1 = __umulhi(PHILOX_M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.k0[r], lo1, hi0 ^ c.w ^ k.k1[r], lo0);
+  }
+  return c;
+}
+
+// (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = x >> 9: both steps exact.
+__device__ __forceinline__ float u01(uint32_t x) {
+  return __uint_as_float(0x3F800000u | (x >> 9)) - 0x1.fffffep-1f;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1.  Lane L of every warp holds the coefficients of row (L & 15);
+// lanes 0..15 hold them negated (used for u >= 1/2), lanes 16..31 as they are
+// (u < 1/2), so the sign restore is folded into the row choice.
+struct PwlLane {
+  float a, b;
+};
+
+__device__ __forceinline__ PwlLane pwl_lane_coefs(const float *alpha, const float *beta) {
+  const int lane = threadIdx.x & 31;
+  PwlLane c;
+  c.a = alpha[lane & 15];
+  c.b = beta[lane & 15];
+  if (lane < 16) {
+    c.a = -c.a;
+    c.b = -c.b;
+  }
+  return c;
+}
+
+// Must be called by all 32 lanes of the warp (the shuffles are warp-wide).
+__device__ __forceinline__ float pwl_eval(float u, const PwlLane &c, unsigned kmax) {
+  const bool lower = u < 0.5f;                           // predicate
+  const float v = lower ? u : 1.0f - u;                  // reflect (exact)
+  const uint32_t e = __float_as_uint(v) >> 23;           // exponent bits
+  uint32_t idx = min(126u - e, kmax);                    // bias offset, cap
+  idx |= lower ? 16u : 0u;                               // sign via the row
+  const float a = __shfl_sync(FULL_MASK, c.a, idx);
+  const float b = __shfl_sync(FULL_MASK, c.b, idx);
+  return fmaf(b, v, a);                                  // one FMA
+}
+
+// Piecewise constant: n a power of two, table in shared memory.
+__device__ __forceinline__ float pwc_eval(float u, const float *s_tab, float nf, int nmax) {
+  const int m = min(__float2int_rz(u * nf), nmax);       // floor(n u), capped
+  return s_tab[max(m, 0)];
+}
+
+// ---------------------------------------------------------------------------
+// Exact inverse Gaussian CDF in FP32.  With v = min(u, 1-u), x = 2v-1 and
+// w = -ln(4v(1-v)), Phi^{-1}(v) = x g(w); g is a fitted polynomial in w (w < W0)
+// or in sqrt(w) (W0 <= w <= W1).  Below v ~ 1.7e-8 (and for v = 0, NaN) an
+// FP64 branch runs three Newton steps on ln Phi(z) = ln v.
+static __device__ __noinline__ float phiinv_far_tail_f64(float vf) {
+  const double v = (double)vf;
+  if (!(v > 0.0)) return v == 0.0 ? -__int_as_float(0x7f800000) : __int_as_float(0x7fc00000);
+  const double L = -2.0 * log(v);
+  double z = -sqrt(L - log(6.283185307179586 * L));      // asymptotic start
+#pragma unroll 1
+  for (int it = 0; it < 3; ++it) {
+    const double P = 0.5 * erfc(-z * 0.7071067811865476);
+    const double d = 0.3989422804014327 * exp(-0.5 * z * z);
+    z -= (log(P) - log(v)) * P / d;
+  }
+  return (float)z;
+}
+
+__device__ __forceinline__ float phiinv_f32(float u) {
+  const bool lower = u < 0.5f;
+  const float v = lower ? u : 1.0f - u;
+  const float x = fmaf(2.0f, v, -1.0f);
+  const float w = -__logf(4.0f * v * (1.0f - v));
+  float z;
+  if (w < AICDF_PHIINV_W0) {
+    z = x * aicdf_phiinv_poly_central(w - AICDF_PHIINV_WC);
+  } else if (w <= AICDF_PHIINV_W1) {
+    z = x * aicdf_phiinv_poly_tail(sqrtf(w) - AICDF_PHIINV_S0);
+  } else {
+    z = phiinv_far_tail_f64(v);
+  }
+  return lower ? z : -z;
+}
+
+__device__ __forceinline__ bool in_unit(float u) { return u >= 0.0f && u <= 1.0f; }
+
+}  // namespace aicdf

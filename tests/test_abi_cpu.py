@@ -1,0 +1,146 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/*.h, and its host-side logic (table build, allocation,
+argument validation) agrees with the oracle and the header's contract."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2012_09715_gb300 import build as b
+    b.build()
+    import paper_2012_09715_gb300 as P
+    P.lib()
+    return P
+
+
+def _declared_symbols():
+    syms = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(aicdf_[a-z0-9_]+)\s*\(", text):
+            syms.add(m.group(1))
+    return syms
+
+
+def test_library_exports_every_declared_symbol(P):
+    syms = _declared_symbols()
+    assert len(syms) >= 10
+    L = C.CDLL(P.LIB_PATH)
+    missing = [s for s in sorted(syms) if not hasattr(L, s)]
+    assert not missing, missing
+    # and the binding wraps every one of them
+    assert syms <= set(P.SIGNATURES), sorted(syms - set(P.SIGNATURES))
+
+
+def test_status_strings_and_version(P):
+    L = P.lib()
+    for s in range(8):
+        assert L.aicdf_status_str(s)
+    assert L.aicdf_version() >= 100
+
+
+def test_table_build_matches_oracle(P, orc):
+    """The library's FP64 table build (its own inverse CDF, centred-basis
+    normal equations, expm1 form of Z^E) agrees with the oracle's."""
+    for K in (1, 4, 15, 16, 24):
+        t = P.table_build(P.PWL, K)
+        a, b = t.coefficients()
+        oa, ob = orc.pwl_table(K, 0.5)
+        # both sides are within ~2e-12 of mpmath: the moments M1 - m M0 lose
+        # a few digits to cancellation in FP64
+        assert np.allclose(a, oa, rtol=5e-12, atol=1e-14)
+        assert np.allclose(b, ob, rtol=5e-12, atol=1e-14)
+        assert t.info() == (P.PWL, K)
+    for n in (2, 8, 1024, 4096):
+        for cons in (P.Z_E, P.Z_C, P.Z_I):
+            q = P.table_build(P.PWC, n, cons).coefficients()[0]
+            oq = orc.pwc_table(n, cons)
+            # the oracle's plain form n (phi(z_k) - phi(z_{k+1})) cancels near
+            # u = 1/2: its absolute error is ~ n * 1e-16 (mpmath confirms the
+            # library side to 1e-15 there)
+            assert np.allclose(q, oq, rtol=1e-11, atol=n * 2e-16), (n, cons)
+            assert np.array_equal(q.astype(np.float32), oq.astype(np.float32)), (n, cons)
+    # the FP32 tables the kernels use are identical on both sides
+    t = P.table_build(P.PWL, 15)
+    a, b = t.coefficients()
+    oa, ob = orc.pwl_table(15, 0.5)
+    assert np.array_equal(a.astype(np.float32), oa.astype(np.float32))
+    assert np.array_equal(b.astype(np.float32), ob.astype(np.float32))
+    q = P.table_build(P.PWC, 1024).coefficients()[0]
+    assert np.array_equal(q.astype(np.float32), orc.pwc_table(1024, 0).astype(np.float32))
+
+
+def test_table_build_rejects_bad_arguments(P):
+    L = P.lib()
+    h = C.c_void_p()
+    for m, n, c in ((P.PWC, 1000, 0), (P.PWC, 1, 0), (P.PWC, 8192, 0), (P.PWC, 64, 7),
+                    (P.PWL, 0, 0), (P.PWL, 32, 0), (9, 15, 0)):
+        assert L.aicdf_table_build(m, n, c, C.byref(h)) == P.ERR_ARG
+    assert L.aicdf_table_build(P.PWL, 15, 0, None) == P.ERR_ARG
+
+
+def test_allocation_matches_oracle(P, orc):
+    rng = np.random.default_rng(0)
+    v = rng.random(9) * 1e-3
+    c = 2.0 ** np.arange(9)
+    T, m = P.mlmc_allocate(v, c, 1e-4)
+    To, mo = orc.mlmc_alloc(v, c, 1e-4)
+    assert T == pytest.approx(To, rel=1e-14)
+    assert np.allclose(m, mo, rtol=1e-14)
+    with pytest.raises(P.AicdfError):
+        P.mlmc_allocate([1.0], [0.0], 1e-3)
+    with pytest.raises(P.AicdfError):
+        P.mlmc_allocate([1.0], [1.0], 0.0)
+
+
+def test_sample_argument_validation_without_gpu(P):
+    """Invalid requests are refused before anything touches the device."""
+    L = P.lib()
+    t = P.table_build(P.PWL, 15)
+    tc = P.table_build(P.PWC, 1024)
+    fake = 1 << 40
+    # wrong table for the method, table given to an exact method, bad dtype/method
+    assert L.aicdf_sample(tc.handle, P.PWL, None, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample(t.handle, P.EXACT, None, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample(t.handle, P.PWL, None, 0, 0, 16, fake, 5, None) == P.ERR_ARG
+    assert L.aicdf_sample(t.handle, 11, None, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    # misaligned output / input, null output
+    assert L.aicdf_sample(t.handle, P.PWL, None, 0, 0, 16, fake + 2, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample(t.handle, P.PWL, fake + 1, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample(t.handle, P.PWL, None, 0, 0, 16, None, P.F32, None) == P.ERR_ARG
+    # n = 0 is a no-op
+    assert L.aicdf_sample(t.handle, P.PWL, None, 0, 0, 0, None, P.F32, None) == P.OK
+    # tables too large for the kernels are refused, not truncated
+    big = P.table_build(P.PWL, 20)
+    assert L.aicdf_sample(big.handle, P.PWL, None, 0, 0, 16, fake, P.F32, None) == P.ERR_UNSUPPORTED
+    # host pipeline: staging too small
+    assert L.aicdf_sample_to_host(t.handle, P.PWL, 0, 0, 16, fake, P.F32, fake, 1024, None) == P.ERR_ARG
+
+
+def test_mlmc_argument_validation_without_gpu(P):
+    L = P.lib()
+    t = P.table_build(P.PWL, 15)
+    prm = P.sde_params()
+    ws_bytes = P.mlmc_level_workspace_bytes()
+    fake = 1 << 40
+    call = lambda prm, lvl, kind, n, sums=fake, ws=fake, wsb=ws_bytes: L.aicdf_mlmc_level(
+        C.byref(prm), t.handle, lvl, kind, n, 0, 0, 1, sums, ws, wsb, None)
+    assert call(prm, -1, P.KIND_CORR4, 10) == P.ERR_ARG
+    assert call(prm, 3, 9, 10) == P.ERR_ARG
+    assert call(prm, 3, P.KIND_CORR4, 0) == P.ERR_ARG
+    assert call(prm, 3, P.KIND_CORR4, 10, wsb=16) == P.ERR_ARG
+    assert call(prm, 3, P.KIND_CORR4, 10, sums=fake + 4) == P.ERR_ARG
+    bad = P.sde_params(sigma=float("nan"))
+    assert call(bad, 3, P.KIND_CORR4, 10) == P.ERR_DOMAIN
+    bad = P.sde_params(T=0.0)
+    assert call(bad, 3, P.KIND_CORR4, 10) == P.ERR_DOMAIN
+    assert L.aicdf_mlmc_level(None, t.handle, 3, 1, 10, 0, 0, 1, fake, fake, ws_bytes, None) == P.ERR_ARG
