@@ -79,8 +79,8 @@ void or_philox4(int w, int rounds, const uint64_t ctr[4], const uint64_t key[2],
 }
 
 double or_u01(uint32_t x) {
-  /* midpoint of the k-th of 2^23 equal cells, k = top 23 bits of x */
-  return ((double)(x >> 9) + 0.5) / 8388608.0;
+  /* midpoint of the k-th of 2^23 equal cells, k = low 23 bits of x */
+  return ((double)(x & 0x7FFFFFu) + 0.5) / 8388608.0;
 }
 
 void or_uniforms(uint64_t seed, uint64_t offset, int64_t n, float *u) {

@@ -26,7 +26,7 @@ extern "C" {
 /* ---- uniforms: Philox4xW-R (Salmon et al., SC'11), W in {32, 64} ---------- */
 void or_philox4(int wbits, int rounds, const uint64_t ctr[4], const uint64_t key[2],
                 uint64_t out[4]);
-/* u = (2*(x>>9)+1) * 2^-24 : 2^23-point midpoint grid, open and symmetric. */
+/* u = (2*(x & 0x7FFFFF)+1) * 2^-24 : 2^23-point midpoint grid, open and symmetric. */
 double or_u01(uint32_t x);
 /* Standalone sampling stream: sample i uses Philox call j=(offset+i)/4 with
  * ctr=(j mod 2^32, j>>32, 0, 0), key=(seed mod 2^32, seed>>32), word (offset+i)%4. */

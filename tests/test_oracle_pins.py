@@ -69,13 +69,15 @@ def test_philox_stream_mapping(orc):
 
 
 def test_u01_grid(orc):
-    """Open, symmetric, FP32-exact grid: u(x) + u(~x) = 1, u in [2^-24, 1-2^-24]."""
-    xs = [0, 1, 511, 512, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF, 0x12345678]
+    """Open, symmetric, FP32-exact grid from the low 23 bits: u(x) + u(~x) = 1,
+    u in [2^-24, 1-2^-24], and the top 9 bits are ignored."""
+    xs = [0, 1, 511, 512, 0x7FFFFF, 0x800000, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF, 0x12345678]
     for x in xs:
         a, b = orc.u01(x), orc.u01((~x) & 0xFFFFFFFF)
         assert a + b == 1.0
         assert float(np.float32(a)) == a and float(np.float32(1.0 - a)) == 1.0 - a
     assert orc.u01(0) == 2.0 ** -24 and orc.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    assert orc.u01(0xFF800000) == 2.0 ** -24 and orc.u01(0x0000_1235) == (2 * 0x1235 + 1) * 2.0 ** -24
 
 
 # ---------------------------------------------------------------- Phi^-1
