@@ -164,6 +164,32 @@ def cpu_baseline(budget_s: float = 12.0, chunk: int = 1 << 20):
                       f"arithmetic), single thread, {t:.1f} s"}
 
 
+def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
+    """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
+    wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
+    (exact variates) and plain Monte Carlo with exact variates at the finest
+    level the nested run chose -- all on this GPU, through aicdf_mlmc_run."""
+    import torch
+    ws = torch.empty(P.mlmc_run_workspace_bytes(), dtype=torch.uint8, device=dev)
+    prm = P.sde_params()
+    P.mlmc_run(prm, tl, 1e-3, ws, estimator=P.EST_NESTED, seed=99)   # warm-up
+    res = {}
+    nested = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_NESTED, seed=1)
+    regular = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_REGULAR, seed=2)
+    L = nested.L
+    plain = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=L, seed=3)
+    for name, r in (("nested", nested), ("regular", regular), ("plain_exact", plain)):
+        res[name] = {"estimate": r.estimate, "rmse_est": (r.variance + r.bias ** 2) ** 0.5,
+                     "L": r.L, "wall_ms": r.wall_ms, "gpu_ms": r.gpu_ms, "launches": r.launches,
+                     "converged": bool(r.converged)}
+    res["eps"] = eps
+    res["speedup_vs_plain_exact_wall"] = plain.wall_ms / nested.wall_ms
+    res["speedup_vs_regular_mlmc_wall"] = regular.wall_ms / nested.wall_ms
+    res["speedup_vs_plain_exact_gpu"] = plain.gpu_ms / nested.gpu_ms
+    res["speedup_vs_regular_mlmc_gpu"] = regular.gpu_ms / nested.gpu_ms
+    return res
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -289,6 +315,7 @@ def main():
         tot, _ = _time_device(lambda: P.sample(tc, P.PWC, small, seed=seed, stream=stream), 50, 5, stream)
         extras["pwc_2p20_gsamples_per_s"] = (1 << 20) * 50 / (tot / 1e3) / 1e9
         del out16, small
+        extras["mlmc"] = mlmc_time_to_rmse(P, tl, dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

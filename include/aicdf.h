@@ -15,9 +15,9 @@
  *     cudaError_t value).
  *   - Uniforms.  Where the library draws uniforms itself it uses
  *     Philox4x32-10 (Salmon et al., SC'11) with key (seed mod 2^32, seed>>32)
- *     and maps a 32-bit word x to u = (2*(x>>9)+1) * 2^-24, the midpoint of
- *     one of 2^23 equal cells: u lies in [2^-24, 1-2^-24], and u and 1-u are
- *     both exact in FP32.
+ *     and maps a 32-bit word x to u = (2*(x mod 2^23)+1) * 2^-24 (its low 23
+ *     bits), the midpoint of one of 2^23 equal cells: u lies in
+ *     [2^-24, 1-2^-24], and u and 1-u are both exact in FP32.
  */
 #ifndef AICDF_H
 #define AICDF_H
@@ -172,6 +172,115 @@ aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_table approx
  * T = 2 eps^-2 (sum_i sqrt(v_i c_i))^2; returns T in *total.  Host only. */
 aicdf_status aicdf_mlmc_allocate(int nterms, const double *v, const double *c, double eps,
                                  double *m, double *total);
+
+
+/* ===================================================================== */
+/* Batched MLMC terms in one persistent launch                            */
+/* ===================================================================== */
+/* One estimator term: `n_paths` paths (indices path_offset ...) of kind
+ * `kind` at `level` for parameter set `set`, Philox stream `tag`.  Its sums
+ * are defined exactly as for aicdf_mlmc_level with the same arguments. */
+typedef struct {
+  uint32_t set;
+  int32_t level;
+  int32_t kind;
+  uint32_t tag;
+  uint64_t n_paths;
+  uint64_t path_offset;
+} aicdf_batch_term;
+
+/* Launch schedule: terms are cut into tiles of tile_paths paths (a multiple
+ * of 32, >= block_threads); each CTA of block_threads threads (64/128/256)
+ * takes tiles from a shared counter, largest first; blocks_per_sm = 0 uses
+ * the occupancy maximum.  var16 = 1 rounds every approximate variate to FP16
+ * before it drives a path (FP16 approximate variates); exact variates stay FP32. */
+typedef struct {
+  int tile_paths;
+  int block_threads;
+  int blocks_per_sm;
+  int var16;
+} aicdf_schedule;
+
+typedef struct aicdf_batch_s *aicdf_batch;
+
+/* Describe a batch: n_sets parameter sets and n_terms terms over them, one
+ * approximation table (PWL K <= 15 or PWC n <= 1024) and one seed.  Host only. */
+aicdf_status aicdf_batch_create(const aicdf_sde_params *sets, int n_sets,
+                                const aicdf_batch_term *terms, int n_terms, aicdf_table approx,
+                                uint64_t seed, aicdf_batch *out);
+void aicdf_batch_destroy(aicdf_batch b);
+/* Device workspace a schedule needs (0 for an invalid schedule). */
+size_t aicdf_batch_workspace_bytes(aicdf_batch b, const aicdf_schedule *s);
+/* Run every term: sums_dev[3t .. 3t+2] = (sum Y, sum Y^2, n) of term t (FP64).
+ * The first run with a given (schedule, workspace, sums) uploads the tile
+ * list into the workspace and captures the counter reset, the persistent
+ * kernel and the per-term reduction into a CUDA graph; later runs replay it.
+ * The workspace must stay untouched between runs of the same batch.
+ * Deterministic: sums do not depend on which CTA ran which tile.
+ * Asynchronous on stream (the first run synchronises it once). */
+aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, double *sums_dev,
+                             void *workspace_dev, size_t workspace_bytes, aicdf_stream_t stream);
+/* Tiles and grid of the last run of schedule s. */
+aicdf_status aicdf_batch_info(aicdf_batch b, const aicdf_schedule *s, int *n_items, int *grid);
+/* Time candidate schedules (block 128/256 x tile 2..128 blocks) that fit the
+ * workspace on this GPU and return the fastest (median of 3 graph replays).
+ * If cache_path is given, a result cached there for this GPU model and batch
+ * is returned without timing, and a new result is appended to it. */
+aicdf_status aicdf_batch_autotune(aicdf_batch b, int var16, double *sums_dev,
+                                  void *workspace_dev, size_t workspace_bytes,
+                                  aicdf_stream_t stream, const char *cache_path,
+                                  aicdf_schedule *best, double *best_ms);
+
+/* ===================================================================== */
+/* MLMC driver (Section 4.1): estimate E[P] to a target RMSE               */
+/* ===================================================================== */
+typedef enum {
+  AICDF_EST_NESTED = 0,   /* theta~ : per level APPROX2 + CORR4 terms (independent streams) */
+  AICDF_EST_REGULAR = 1,  /* theta^ : per level EXACT2 terms                              */
+  AICDF_EST_PLAIN = 2     /* plain Monte Carlo with exact variates at the finest level     */
+} aicdf_estimator;
+
+#define AICDF_MAX_LEVELS 24
+
+typedef struct {
+  double eps;             /* target RMSE: variance eps^2/2 and bias^2 <= eps^2/2        */
+  int estimator;          /* aicdf_estimator                                              */
+  int L_min, L_max;       /* first and last admissible finest level                      */
+  int fixed_L;            /* >= 0: use exactly this finest level (no bias test)           */
+  uint64_t n_pilot;       /* pilot paths per new term                                     */
+  uint64_t seed;
+  double weak_order;      /* alpha in the bias estimate |E Y_L| / (2^alpha - 1)           */
+} aicdf_mlmc_opts;
+
+typedef struct {
+  double estimate;        /* sum over terms of the sample means                          */
+  double variance;        /* estimated variance of the estimator                         */
+  double bias;            /* bias estimate from the finest level                          */
+  double gpu_ms;          /* device time of all path launches (CUDA events)               */
+  double wall_ms;         /* host wall time of the whole run                              */
+  int L;                  /* finest level used                                            */
+  int converged;          /* 1 if the bias test passed (or fixed_L was given)             */
+  int n_terms;            /* terms per level: 2 (nested) or 1                            */
+  int launches;           /* path-kernel launches issued                                  */
+  /* per level l and term t (t = 0: APPROX2 / EXACT2 / PLAIN, t = 1: CORR4) */
+  uint64_t paths[AICDF_MAX_LEVELS][2];
+  double mean[AICDF_MAX_LEVELS][2];
+  double var[AICDF_MAX_LEVELS][2];
+  double cost_ns[AICDF_MAX_LEVELS][2];  /* measured device ns per path                     */
+} aicdf_mlmc_result;
+
+/* Run one estimator to RMSE opts->eps.  Each term draws uniforms from its own
+ * Philox stream (tag = 1 + 64*estimator + 2*l + t), extending the stream with
+ * path_offset as more paths are added, so the result is reproducible from the
+ * seed.  Path counts follow the optimal allocation of Section 4.1 from the
+ * measured variances and per-path device times.  Levels are added while the
+ * bias estimate exceeds eps/sqrt(2) (up to L_max; converged = 0 if it is
+ * reached).  workspace_dev: at least aicdf_mlmc_run_workspace_bytes().
+ * Synchronous on stream. */
+size_t aicdf_mlmc_run_workspace_bytes(void);
+aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_table approx,
+                            const aicdf_mlmc_opts *opts, aicdf_mlmc_result *result,
+                            void *workspace_dev, size_t workspace_bytes, aicdf_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -47,6 +47,47 @@ class SdeParams(C.Structure):
                 ("discount", C.c_double)]
 
 
+EST_NESTED, EST_REGULAR, EST_PLAIN = 0, 1, 2
+MAX_LEVELS = 24
+
+
+class MlmcOpts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("estimator", C.c_int), ("L_min", C.c_int), ("L_max", C.c_int),
+                ("fixed_L", C.c_int), ("n_pilot", C.c_uint64), ("seed", C.c_uint64),
+                ("weak_order", C.c_double)]
+
+
+class MlmcResult(C.Structure):
+    _fields_ = [("estimate", C.c_double), ("variance", C.c_double), ("bias", C.c_double),
+                ("gpu_ms", C.c_double), ("wall_ms", C.c_double), ("L", C.c_int),
+                ("converged", C.c_int), ("n_terms", C.c_int), ("launches", C.c_int),
+                ("paths", (C.c_uint64 * 2) * MAX_LEVELS), ("mean", (C.c_double * 2) * MAX_LEVELS),
+                ("var", (C.c_double * 2) * MAX_LEVELS), ("cost_ns", (C.c_double * 2) * MAX_LEVELS)]
+
+    def as_dict(self):
+        L, t = self.L, self.n_terms
+        lv = range(L + 1) if t == 2 or self.paths[0][0] else [L]
+        return {"estimate": self.estimate, "variance": self.variance, "bias": self.bias,
+                "gpu_ms": self.gpu_ms, "wall_ms": self.wall_ms, "L": L, "converged": bool(self.converged),
+                "launches": self.launches,
+                "levels": [{"l": l, "paths": list(self.paths[l])[:t], "mean": list(self.mean[l])[:t],
+                            "var": list(self.var[l])[:t], "cost_ns": list(self.cost_ns[l])[:t]}
+                           for l in lv]}
+
+
+class BatchTerm(C.Structure):
+    _fields_ = [("set", C.c_uint32), ("level", C.c_int32), ("kind", C.c_int32), ("tag", C.c_uint32),
+                ("n_paths", C.c_uint64), ("path_offset", C.c_uint64)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("tile_paths", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
+                ("var16", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # name -> (restype, argtypes); every entry point of include/aicdf.h
 _P, _I, _U32, _U64, _SZ, _D = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_size_t, C.c_double
 SIGNATURES = {
@@ -62,6 +103,14 @@ SIGNATURES = {
     "aicdf_mlmc_level_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "aicdf_mlmc_allocate": (_I, [_I, _P, _P, _D, _P, _P]),
+    "aicdf_batch_create": (_I, [_P, _I, _P, _I, _P, _U64, C.POINTER(_P)]),
+    "aicdf_batch_destroy": (None, [_P]),
+    "aicdf_batch_workspace_bytes": (_SZ, [_P, _P]),
+    "aicdf_batch_run": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "aicdf_batch_info": (_I, [_P, _P, C.POINTER(_I), C.POINTER(_I)]),
+    "aicdf_batch_autotune": (_I, [_P, _I, _P, _P, _SZ, _P, C.c_char_p, _P, C.POINTER(_D)]),
+    "aicdf_mlmc_run_workspace_bytes": (_SZ, []),
+    "aicdf_mlmc_run": (_I, [_P, _P, _P, _P, _P, _SZ, _P]),
 }
 
 
@@ -209,3 +258,62 @@ def mlmc_allocate(v, c, eps: float):
     _check(lib().aicdf_mlmc_allocate(v.size, v.ctypes.data, c.ctypes.data, eps, m.ctypes.data,
                                      C.byref(tot)), "mlmc_allocate")
     return tot.value, m
+
+
+def mlmc_run_workspace_bytes() -> int:
+    return lib().aicdf_mlmc_run_workspace_bytes()
+
+
+def mlmc_run(params: SdeParams, table: Table, eps: float, workspace, estimator: int = EST_NESTED,
+             L_min: int = 2, L_max: int = 20, fixed_L: int = -1, n_pilot: int = 10000, seed: int = 0,
+             weak_order: float = 1.0, stream=None) -> MlmcResult:
+    """aicdf_mlmc_run: estimate E[P] to RMSE eps (synchronous)."""
+    o = MlmcOpts(eps, estimator, L_min, L_max, fixed_L, n_pilot, seed, weak_order)
+    r = MlmcResult()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().aicdf_mlmc_run(C.byref(params), table.handle, C.byref(o), C.byref(r), _ptr(workspace),
+                                nbytes, _stream(stream)), "mlmc_run")
+    return r
+
+
+class Batch:
+    """Owning handle of an aicdf_batch: many MLMC terms in one persistent launch."""
+
+    def __init__(self, sets, terms, table: Table, seed: int = 0):
+        L = lib()
+        self._sets = (SdeParams * len(sets))(*sets)
+        self._terms = (BatchTerm * len(terms))(*terms)
+        self.n_terms = len(terms)
+        h = C.c_void_p()
+        _check(L.aicdf_batch_create(self._sets, len(sets), self._terms, len(terms), table.handle, seed,
+                                    C.byref(h)), "batch_create")
+        self.handle = h
+
+    def workspace_bytes(self, sched: Schedule) -> int:
+        return lib().aicdf_batch_workspace_bytes(self.handle, C.byref(sched))
+
+    def run(self, sched: Schedule, sums, workspace, stream=None):
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().aicdf_batch_run(self.handle, C.byref(sched), _ptr(sums), _ptr(workspace), nbytes,
+                                     _stream(stream)), "batch_run")
+        return sums
+
+    def info(self, sched: Schedule):
+        n, g = C.c_int(), C.c_int()
+        _check(lib().aicdf_batch_info(self.handle, C.byref(sched), C.byref(n), C.byref(g)), "batch_info")
+        return n.value, g.value
+
+    def autotune(self, sums, workspace, var16: int = 0, cache_path: str | None = None, stream=None):
+        best = Schedule()
+        ms = C.c_double()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().aicdf_batch_autotune(self.handle, var16, _ptr(sums), _ptr(workspace), nbytes,
+                                          _stream(stream), cache_path.encode() if cache_path else None,
+                                          C.byref(best), C.byref(ms)), "batch_autotune")
+        return best, ms.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.aicdf_batch_destroy(h)
+            self.handle = None

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libaicdf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["sample.cu", "mlmc.cu"]
-CPP_SOURCES = ["tables.cpp", "abi.cpp"]
+CPP_SOURCES = ["tables.cpp", "abi.cpp", "driver.cpp"]
 
 
 def _cuda_home() -> str:

@@ -4,7 +4,9 @@
 
 #include <atomic>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "aicdf_internal.h"
 
@@ -29,6 +31,24 @@ int sm_count() {
     cache[dev] = n;
   }
   return cache[dev];
+}
+
+int resident_blocks(const void *kernel, int threads) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void *, int, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(kernel, threads, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  cache[key] = n;
+  return n;
 }
 
 }  // namespace aicdf

@@ -23,6 +23,9 @@ void set_cuda_error(int e);
 bool table_ok(const aicdf_table_s *t);
 // SM count of the current device (cached per device).
 int sm_count();
+// Resident blocks per SM of `kernel` at `threads` per block (occupancy API,
+// cached per kernel and device; at least 1).
+int resident_blocks(const void *kernel, int threads);
 // Host FP64 inverse Gaussian CDF used for the table build.
 double host_phiinv(double p);
 }  // namespace aicdf

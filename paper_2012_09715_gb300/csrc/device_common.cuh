@@ -54,9 +54,45 @@ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &k) {
   return c;
 }
 
-// (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = x >> 9: both steps exact.
+// (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = low 23 bits of x: both
+// steps exact (one logic op and one add).
 __device__ __forceinline__ float u01(uint32_t x) {
-  return __uint_as_float(0x3F800000u | (x >> 9)) - 0x1.fffffep-1f;
+  return __uint_as_float(0x3F800000u | (x & 0x7FFFFFu)) - 0x1.fffffep-1f;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 for uniforms on the 2^-24 grid (the library's own uniforms).
+// On the grid, u - 1/2 and 1/2 - |u - 1/2| are exact, so v = min(u, 1-u) costs
+// two adds; v >= 2^-24 bounds the row index 126 - e by 23, so lane L holds
+// row min(L, K) and no cap is needed; the sign is restored by one xor with
+// the complement of the sign of u - 1/2 (u = 1/2 gives -0, as in the listing).
+struct PwlRows {
+  float a, b;
+};
+
+__device__ __forceinline__ PwlRows pwl_lane_rows(const float *alpha, const float *beta, int K) {
+  const int r = min((int)(threadIdx.x & 31), K);
+  PwlRows c;
+  c.a = alpha[r];
+  c.b = beta[r];
+  return c;
+}
+
+// Must be called by all 32 lanes of the warp.
+__device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) {
+  const float t = u - 0.5f;
+  const float v = 0.5f - fabsf(t);
+  const uint32_t idx = 126u - (__float_as_uint(v) >> 23);
+  const float a = __shfl_sync(0xffffffffu, c.a, idx);
+  const float b = __shfl_sync(0xffffffffu, c.b, idx);
+  const float z = fmaf(b, v, a);
+  return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
+}
+
+// Piecewise constant with n = 2^q intervals for a grid uniform from word x:
+// floor(n u) = floor((2m+1) 2^-(24-q)) = m >> (23 - q), m = low 23 bits.
+__device__ __forceinline__ uint32_t pwc_index_from_word(uint32_t x, uint32_t shift) {
+  return (x & 0x7FFFFFu) >> shift;
 }
 
 // ---------------------------------------------------------------------------

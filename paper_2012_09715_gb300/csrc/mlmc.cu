@@ -1,20 +1,36 @@
-// Fused nested-MLMC level kernel (Section 4, Section 4.1).
+// Fused nested-MLMC kernels (Section 4, Section 4.1).
 //
-// One thread simulates one path at a time, entirely in registers: every fine
-// step draws one Philox uniform U, and from that same U the exact variate
-// Z = Phi^{-1}(U) and/or the approximate variate Z~ = D(U) (or Q(U)); the fine
-// exact and approximate states advance with Z and Z~, and every second step
-// the coarse states advance with the pairwise sums (Section 4.1: coarse
-// Wiener increments are pairwise sums of the fine ones).  The payoff
-// difference Y of the requested estimator kind is accumulated per thread in
-// FP32 over a chunk of paths and flushed to FP64; warps reduce in FP64 by
-// shuffles, blocks write one FP64 partial each, and a second one-block
-// kernel adds the partials in a fixed order, so sums are deterministic.
+// Level kernel: one thread simulates one path at a time, entirely in
+// registers: every fine step draws one Philox uniform U, and from that same U
+// the exact variate Z = Phi^{-1}(U) and/or the approximate variate Z~ = D(U)
+// (or Q(U)); the fine exact and approximate states advance with Z and Z~,
+// and every second step the coarse states advance with the pairwise sums
+// (Section 4.1: coarse Wiener increments are pairwise sums of the fine
+// ones).  The payoff difference Y of the requested estimator kind is
+// accumulated per thread in FP32 over a chunk of paths and flushed to FP64
+// (FP64 issues at a small fraction of the FP32 rate on this GPU); warps
+// reduce in FP64 by shuffles, blocks write one FP64 partial each, and a
+// second one-block kernel adds the partials in a fixed order, so the sums
+// are deterministic.
+//
+// Batched kernel: many estimator terms (parameter sets x levels x kinds,
+// each with its own path count) in one persistent launch.  Terms are cut into
+// tiles of paths; CTAs take tiles from an atomic counter, largest tiles
+// first; each tile's FP64 partial lands in its own slot, and a second kernel
+// adds each term's slots in a fixed order, so the result does not depend on
+// which CTA ran which tile.  The three launches (counter reset, persistent
+// kernel, reduction) are captured once per schedule in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
 
 #include "aicdf_internal.h"
 #include "device_common.cuh"
@@ -26,13 +42,14 @@ constexpr int kLevelThreads = 256;
 constexpr int kMaxLevelBlocks = 4096;
 constexpr int kFlushEvery = 16;  // paths per FP32 chunk before the FP64 flush
 
-template <bool NE, bool NA, int AP, int MODEL, int SCHEME>
+// ============================================================== level kernel
+template <bool NE, bool NA, int AP, int MODEL>
 __global__ void __launch_bounds__(kLevelThreads)
     k_mlmc_level(const __grid_constant__ LevelArgs a, double2 *__restrict__ partials) {
   __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
   __shared__ double2 s_red[kLevelThreads / 32];
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
-  const PathConsts pc = make_path_consts(a);
+  const PathConsts pc = make_path_consts(a.ps);
   const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   float f1 = 0.f, f2 = 0.f;
@@ -41,8 +58,7 @@ __global__ void __launch_bounds__(kLevelThreads)
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n_paths;
        base += stride) {
     const uint64_t i = base + lane;
-    const uint64_t p = a.path_offset + i;
-    const float y = path_y<NE, NA, AP, MODEL, SCHEME>(a, pc, ap, p);
+    const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
     if (i < a.n_paths) {
       f1 += y;
       f2 = fmaf(y, y, f2);
@@ -81,89 +97,100 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double2 *__restri
 using LevelFn = void (*)(LevelArgs, double2 *);
 
 template <bool NE, bool NA, int AP>
-LevelFn pick_ms(int model, int scheme) {
-  if (model == AICDF_MODEL_GBM)
-    return scheme == AICDF_SCHEME_EM ? (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_GBM, AICDF_SCHEME_EM>
-                                     : (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_GBM, AICDF_SCHEME_MILSTEIN>;
-  return scheme == AICDF_SCHEME_EM ? (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_CIR, AICDF_SCHEME_EM>
-                                   : (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_CIR, AICDF_SCHEME_MILSTEIN>;
+LevelFn pick_model(int model) {
+  return model == AICDF_MODEL_GBM ? (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_GBM>
+                                  : (LevelFn)k_mlmc_level<NE, NA, AP, AICDF_MODEL_CIR>;
 }
 
 template <bool NE, bool NA>
-LevelFn pick_ap(int ap, int model, int scheme) {
-  return ap == AICDF_PWL ? pick_ms<NE, NA, AICDF_PWL>(model, scheme) : pick_ms<NE, NA, AICDF_PWC>(model, scheme);
+LevelFn pick_ap(int ap, int model) {
+  return ap == AICDF_PWL ? pick_model<NE, NA, AICDF_PWL>(model) : pick_model<NE, NA, AICDF_PWC>(model);
 }
 
-static LevelFn select_level_kernel(int kind, int ap, int model, int scheme) {
+static LevelFn select_level_kernel(int kind, int ap, int model) {
   const bool ne = kind_needs_exact(kind), na = kind_needs_approx(kind);
-  if (ne && na) return pick_ap<true, true>(ap, model, scheme);
-  if (ne) return pick_ap<true, false>(ap, model, scheme);
-  return pick_ap<false, true>(ap, model, scheme);
+  if (ne && na) return pick_ap<true, true>(ap, model);
+  if (ne) return pick_ap<true, false>(ap, model);
+  return pick_ap<false, true>(ap, model);
 }
 
-aicdf_status prepare_level_args(const aicdf_sde_params *prm, aicdf_table approx, int level,
-                                int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
-                                uint32_t tag, LevelArgs *a) {
-  if (!prm || !table_ok(approx)) return AICDF_ERR_ARG;
+aicdf_status make_path_spec(const aicdf_sde_params *prm, int level, int kind, uint32_t tag,
+                            PathSpec *ps) {
+  if (!prm) return AICDF_ERR_ARG;
   if (level < 0 || level > 20) return AICDF_ERR_ARG;
   if (kind < AICDF_KIND_APPROX2 || kind > AICDF_KIND_PLAIN_APPROX) return AICDF_ERR_ARG;
   if (prm->model != AICDF_MODEL_GBM && prm->model != AICDF_MODEL_CIR) return AICDF_ERR_ARG;
   if (prm->scheme != AICDF_SCHEME_EM && prm->scheme != AICDF_SCHEME_MILSTEIN) return AICDF_ERR_ARG;
   if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL) return AICDF_ERR_ARG;
-  if (n_paths == 0) return AICDF_ERR_ARG;
-  if (path_offset + n_paths < path_offset) return AICDF_ERR_ARG;  // wraps
   const double vals[] = {prm->X0, prm->T, prm->K, prm->mu, prm->sigma, prm->kappa, prm->theta,
                          prm->discount};
   for (double v : vals)
     if (!std::isfinite(v)) return AICDF_ERR_DOMAIN;
   if (!(prm->T > 0.0) || prm->sigma < 0.0) return AICDF_ERR_DOMAIN;
   if (prm->model == AICDF_MODEL_CIR && (prm->kappa < 0.0 || prm->theta < 0.0)) return AICDF_ERR_DOMAIN;
-  std::memset(a, 0, sizeof(*a));
-  a->keys = make_keys(seed);
-  a->n_paths = n_paths;
-  a->path_offset = path_offset;
-  a->tag = tag;
-  a->level = level;
-  a->kind = kind;
-  a->model = prm->model;
-  a->scheme = prm->scheme;
-  a->payoff = prm->payoff;
-  a->approx = approx->method;
-  a->X0 = (float)prm->X0;
-  a->K = (float)prm->K;
-  a->discount = (float)prm->discount;
-  a->mu = (float)prm->mu;
-  a->sigma = (float)prm->sigma;
-  a->kappa = (float)prm->kappa;
-  a->theta = (float)prm->theta;
-  a->dt = (float)(prm->T / std::ldexp(1.0, level));
-  if (approx->method == AICDF_PWL) {
-    if (approx->n > 15) return AICDF_ERR_UNSUPPORTED;
-    for (int i = 0; i < 16; ++i) {
-      const int r = std::min(i, approx->n);
-      a->tab[i] = approx->f0[r];
-      a->tab[16 + i] = approx->f1[r];
-    }
-  } else {
-    if (approx->n > 1024) return AICDF_ERR_UNSUPPORTED;
-    for (int i = 0; i < approx->n; ++i) a->tab[i] = approx->f0[i];
-    a->nf = (float)approx->n;
-  }
-  a->ntab = approx->n;
+  std::memset(ps, 0, sizeof(*ps));
+  ps->tag = tag;
+  ps->level = level;
+  ps->kind = kind;
+  ps->model = prm->model;
+  ps->scheme = prm->scheme;
+  ps->payoff = prm->payoff;
+  ps->X0 = (float)prm->X0;
+  ps->K = (float)prm->K;
+  ps->discount = (float)prm->discount;
+  ps->mu = (float)prm->mu;
+  ps->sigma = (float)prm->sigma;
+  ps->kappa = (float)prm->kappa;
+  ps->theta = (float)prm->theta;
+  ps->dt = (float)(prm->T / std::ldexp(1.0, level));
   return AICDF_OK;
 }
 
-int level_grid(uint64_t n_paths) {
+aicdf_status pack_table(aicdf_table approx, float *tab, int *ntab) {
+  if (!table_ok(approx)) return AICDF_ERR_ARG;
+  if (approx->method == AICDF_PWL) {
+    if (approx->n > 15) return AICDF_ERR_UNSUPPORTED;  // 16 rows fit one half-warp
+    for (int i = 0; i < 16; ++i) {
+      const int r = std::min(i, approx->n);  // rows past K repeat row K (never indexed)
+      tab[i] = approx->f0[r];
+      tab[16 + i] = approx->f1[r];
+    }
+  } else {
+    if (approx->n > 1024) return AICDF_ERR_UNSUPPORTED;
+    for (int i = 0; i < approx->n; ++i) tab[i] = approx->f0[i];
+  }
+  *ntab = approx->n;
+  return AICDF_OK;
+}
+
+aicdf_status prepare_level_args(const aicdf_sde_params *prm, aicdf_table approx, int level,
+                                int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                uint32_t tag, LevelArgs *a) {
+  if (!table_ok(approx)) return AICDF_ERR_ARG;
+  if (n_paths == 0) return AICDF_ERR_ARG;
+  if (path_offset + n_paths < path_offset) return AICDF_ERR_ARG;  // wraps
+  std::memset(a, 0, sizeof(*a));
+  aicdf_status s = make_path_spec(prm, level, kind, tag, &a->ps);
+  if (s != AICDF_OK) return s;
+  s = pack_table(approx, a->tab, &a->ntab);
+  if (s != AICDF_OK) return s;
+  a->keys = make_keys(seed);
+  a->n_paths = n_paths;
+  a->path_offset = path_offset;
+  a->approx = approx->method;
+  return AICDF_OK;
+}
+
+int level_grid(uint64_t n_paths, const void *kernel) {
   const uint64_t want = (n_paths + kLevelThreads - 1) / kLevelThreads;
-  const uint64_t cap = (uint64_t)sm_count() * (2048 / kLevelThreads);
+  const uint64_t cap = (uint64_t)sm_count() * resident_blocks(kernel, kLevelThreads);
   uint64_t g = std::min<uint64_t>(want, std::min<uint64_t>(cap, kMaxLevelBlocks));
   return (int)std::max<uint64_t>(g, 1);
 }
 
-aicdf_status launch_level(const LevelArgs &a, int kind, double *sums_dev, void *ws,
-                          cudaStream_t st) {
-  LevelFn k = select_level_kernel(kind, a.approx, a.model, a.scheme);
-  const int grid = level_grid(a.n_paths);
+aicdf_status launch_level(const LevelArgs &a, double *sums_dev, void *ws, cudaStream_t st) {
+  LevelFn k = select_level_kernel(a.ps.kind, a.approx, a.ps.model);
+  const int grid = level_grid(a.n_paths, (const void *)k);
   double2 *parts = reinterpret_cast<double2 *>(ws);
   k<<<grid, kLevelThreads, 0, st>>>(a, parts);
   k_reduce_partials<<<1, 256, 0, st>>>(parts, grid, (double)a.n_paths, sums_dev);
@@ -175,10 +202,454 @@ aicdf_status launch_level(const LevelArgs &a, int kind, double *sums_dev, void *
   return AICDF_OK;
 }
 
+// ============================================================ batched kernel
+struct BatchItem {
+  uint32_t term;   // index into specs
+  uint32_t slot;   // partial-sum slot (slots of one term are contiguous)
+  uint64_t begin;  // first path index (absolute, includes the term's offset)
+  uint32_t count;  // paths in this tile
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  PhiloxKeys keys;
+  const BatchItem *items;
+  const PathSpec *specs;
+  int *counter;
+  double2 *partials;
+  int n_items, approx, ntab;
+  float tab[1024];
+};
+
+template <int AP, bool V16>
+__global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ BatchArgs a) {
+  __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
+  __shared__ double2 s_red[256 / 32];
+  __shared__ int s_item;
+  const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();  // everyone has read s_item before thread 0 may overwrite it
+    if (it >= a.n_items) break;
+    const BatchItem item = a.items[it];
+    const PathSpec ps = a.specs[item.term];
+    const PathConsts pc = make_path_consts(ps);
+    float f1 = 0.f, f2 = 0.f;
+    double d1 = 0.0, d2 = 0.0;
+    int chunk = 0;
+    for (uint32_t base = threadIdx.x & ~31u; base < item.count; base += blockDim.x) {
+      const uint32_t i = base + lane;
+      const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
+      if (i < item.count) {
+        f1 += y;
+        f2 = fmaf(y, y, f2);
+      }
+      if (++chunk == kFlushEvery) {
+        d1 += (double)f1;
+        d2 += (double)f2;
+        f1 = f2 = 0.f;
+        chunk = 0;
+      }
+    }
+    d1 += (double)f1;
+    d2 += (double)f2;
+    const double2 t = block_reduce2(d1, d2, s_red);
+    if (threadIdx.x == 0) a.partials[item.slot] = t;
+  }
+}
+
+// sums[3 t + {0,1,2}] = (sum Y, sum Y^2, n) of term t from its slots, in slot order.
+__global__ void k_reduce_terms(const double2 *__restrict__ partials, const int *__restrict__ slot_begin,
+                               const double *__restrict__ counts, int n_terms,
+                               double *__restrict__ sums) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_terms) return;
+  double d1 = 0.0, d2 = 0.0;
+  for (int s = slot_begin[t]; s < slot_begin[t + 1]; ++s) {
+    d1 += partials[s].x;
+    d2 += partials[s].y;
+  }
+  sums[3 * t + 0] = d1;
+  sums[3 * t + 1] = d2;
+  sums[3 * t + 2] = counts[t];
+}
+
+using BatchFn = void (*)(BatchArgs);
+
+static BatchFn select_batch_kernel(int ap, bool v16) {
+  if (ap == AICDF_PWL) return v16 ? (BatchFn)k_mlmc_batch<AICDF_PWL, true> : (BatchFn)k_mlmc_batch<AICDF_PWL, false>;
+  return v16 ? (BatchFn)k_mlmc_batch<AICDF_PWC, true> : (BatchFn)k_mlmc_batch<AICDF_PWC, false>;
+}
+
 }  // namespace aicdf
 
 using namespace aicdf;
 
+// ---------------------------------------------------------------- batch plans
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+  aicdf_schedule sched;
+  std::vector<BatchItem> items;  // dispatch order (largest tiles first)
+  std::vector<int> slot_begin;   // n_terms + 1
+  // workspace layout (byte offsets)
+  size_t off_counter, off_items, off_specs, off_slots, off_counts, off_partials, bytes;
+  // device state this plan was uploaded to / captured with
+  void *uploaded_ws = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void *graph_ws = nullptr;
+  double *graph_sums = nullptr;
+  int grid = 0;
+};
+
+bool same_sched(const aicdf_schedule &a, const aicdf_schedule &b) {
+  return a.tile_paths == b.tile_paths && a.block_threads == b.block_threads &&
+         a.blocks_per_sm == b.blocks_per_sm && a.var16 == b.var16;
+}
+
+}  // namespace
+
+struct aicdf_batch_s {
+  uint32_t magic;
+  std::vector<PathSpec> specs;
+  std::vector<aicdf_batch_term> terms;
+  std::vector<double> counts;
+  BatchArgs base;  // keys + table (pointers filled per plan)
+  uint64_t fingerprint;
+  std::vector<Plan *> plans;
+};
+
+constexpr uint32_t kBatchMagic = 0x42415443u;
+
+static bool batch_ok(const aicdf_batch_s *b) { return b && b->magic == kBatchMagic; }
+
+static aicdf_status check_schedule(const aicdf_schedule *s) {
+  if (!s) return AICDF_ERR_ARG;
+  if (s->block_threads != 64 && s->block_threads != 128 && s->block_threads != 256) return AICDF_ERR_ARG;
+  if (s->tile_paths < s->block_threads || s->tile_paths % 32 || s->tile_paths > (1 << 24)) return AICDF_ERR_ARG;
+  if (s->blocks_per_sm < 0 || s->blocks_per_sm > 32) return AICDF_ERR_ARG;
+  if (s->var16 != 0 && s->var16 != 1) return AICDF_ERR_ARG;
+  return AICDF_OK;
+}
+
+static Plan *get_plan(aicdf_batch_s *b, const aicdf_schedule &s) {
+  for (Plan *p : b->plans)
+    if (same_sched(p->sched, s)) return p;
+  Plan *p = new (std::nothrow) Plan();
+  if (!p) return nullptr;
+  p->sched = s;
+  const int nt = (int)b->terms.size();
+  struct Tile {
+    double cost;
+    BatchItem it;
+  };
+  std::vector<Tile> tiles;
+  p->slot_begin.assign(nt + 1, 0);
+  uint32_t slot = 0;
+  for (int t = 0; t < nt; ++t) {
+    p->slot_begin[t] = (int)slot;
+    const aicdf_batch_term &tm = b->terms[t];
+    const double step_cost = (double)(1u << tm.level) * (tm.kind == AICDF_KIND_CORR4 ? 2.0 : 1.0);
+    for (uint64_t off = 0; off < tm.n_paths; off += (uint64_t)s.tile_paths) {
+      BatchItem it;
+      it.term = (uint32_t)t;
+      it.slot = slot++;
+      it.begin = tm.path_offset + off;
+      it.count = (uint32_t)std::min<uint64_t>((uint64_t)s.tile_paths, tm.n_paths - off);
+      it.pad = 0;
+      tiles.push_back({step_cost * (double)it.count, it});
+    }
+  }
+  p->slot_begin[nt] = (int)slot;
+  std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &x, const Tile &y) { return x.cost > y.cost; });
+  p->items.reserve(tiles.size());
+  for (auto &x : tiles) p->items.push_back(x.it);
+  size_t off = 0;
+  p->off_counter = off;
+  off = align256(off + sizeof(int));
+  p->off_items = off;
+  off = align256(off + sizeof(BatchItem) * p->items.size());
+  p->off_specs = off;
+  off = align256(off + sizeof(PathSpec) * b->specs.size());
+  p->off_slots = off;
+  off = align256(off + sizeof(int) * p->slot_begin.size());
+  p->off_counts = off;
+  off = align256(off + sizeof(double) * b->counts.size());
+  p->off_partials = off;
+  off = align256(off + sizeof(double2) * p->items.size());
+  p->bytes = off;
+  b->plans.push_back(p);
+  return p;
+}
+
+static void drop_graph(Plan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  p->exec = nullptr;
+  p->graph_ws = nullptr;
+  p->graph_sums = nullptr;
+}
+
+extern "C" aicdf_status aicdf_batch_create(const aicdf_sde_params *sets, int n_sets,
+                                           const aicdf_batch_term *terms, int n_terms,
+                                           aicdf_table approx, uint64_t seed, aicdf_batch *out) {
+  if (!out) return AICDF_ERR_ARG;
+  *out = nullptr;
+  if (!sets || n_sets <= 0 || !terms || n_terms <= 0 || n_terms > (1 << 22)) return AICDF_ERR_ARG;
+  if (!table_ok(approx)) return AICDF_ERR_ARG;
+  aicdf_batch_s *b = new (std::nothrow) aicdf_batch_s();
+  if (!b) return AICDF_ERR_NOMEM;
+  b->magic = kBatchMagic;
+  std::memset(&b->base, 0, sizeof(b->base));
+  aicdf_status s = pack_table(approx, b->base.tab, &b->base.ntab);
+  if (s != AICDF_OK) {
+    delete b;
+    return s;
+  }
+  b->base.approx = approx->method;
+  b->base.keys = make_keys(seed);
+  uint64_t fp = 1469598103934665603ull ^ seed;
+  auto mix = [&fp](uint64_t v) { fp = (fp ^ v) * 1099511628211ull; };
+  mix((uint64_t)approx->method);
+  mix((uint64_t)approx->n);
+  for (int t = 0; t < n_terms; ++t) {
+    const aicdf_batch_term &tm = terms[t];
+    if (tm.set >= (uint32_t)n_sets || tm.n_paths == 0 || tm.n_paths > (1ull << 40) ||
+        tm.path_offset + tm.n_paths < tm.path_offset) {
+      delete b;
+      return AICDF_ERR_ARG;
+    }
+    PathSpec ps;
+    s = make_path_spec(&sets[tm.set], tm.level, tm.kind, tm.tag, &ps);
+    if (s != AICDF_OK) {
+      delete b;
+      return s;
+    }
+    b->specs.push_back(ps);
+    b->terms.push_back(tm);
+    b->counts.push_back((double)tm.n_paths);
+    mix(tm.set);
+    mix((uint64_t)tm.level << 8 | (uint64_t)tm.kind);
+    mix(tm.n_paths);
+    mix(tm.path_offset);
+    mix(tm.tag);
+  }
+  for (int i = 0; i < n_sets; ++i) {
+    uint64_t w[8];
+    std::memcpy(w, &sets[i].X0, sizeof(w));
+    for (uint64_t v : w) mix(v);
+    mix((uint64_t)sets[i].model << 16 | (uint64_t)sets[i].scheme << 8 | (uint64_t)sets[i].payoff);
+  }
+  b->fingerprint = fp;
+  *out = b;
+  return AICDF_OK;
+}
+
+extern "C" void aicdf_batch_destroy(aicdf_batch b) {
+  if (!batch_ok(b)) return;
+  for (Plan *p : b->plans) {
+    drop_graph(p);
+    delete p;
+  }
+  b->magic = 0;
+  delete b;
+}
+
+extern "C" size_t aicdf_batch_workspace_bytes(aicdf_batch b, const aicdf_schedule *s) {
+  if (!batch_ok(b) || check_schedule(s) != AICDF_OK) return 0;
+  Plan *p = get_plan(b, *s);
+  return p ? p->bytes : 0;
+}
+
+static aicdf_status record_batch(aicdf_batch_s *b, Plan *p, void *ws, double *sums, cudaStream_t st) {
+  char *w = (char *)ws;
+  BatchArgs a = b->base;
+  a.items = reinterpret_cast<const BatchItem *>(w + p->off_items);
+  a.specs = reinterpret_cast<const PathSpec *>(w + p->off_specs);
+  a.counter = reinterpret_cast<int *>(w + p->off_counter);
+  a.partials = reinterpret_cast<double2 *>(w + p->off_partials);
+  a.n_items = (int)p->items.size();
+  BatchFn k = select_batch_kernel(a.approx, p->sched.var16 != 0);
+  const int threads = p->sched.block_threads;
+  int bps = resident_blocks((const void *)k, threads);
+  if (p->sched.blocks_per_sm > 0) bps = std::min(bps, p->sched.blocks_per_sm);
+  const int grid = std::max(1, std::min(sm_count() * bps, a.n_items));
+  p->grid = grid;
+  cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  k<<<grid, threads, 0, st>>>(a);
+  const int nt = (int)b->terms.size();
+  k_reduce_terms<<<(nt + 255) / 256, 256, 0, st>>>(a.partials, reinterpret_cast<const int *>(w + p->off_slots),
+                                                   reinterpret_cast<const double *>(w + p->off_counts), nt, sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error((int)e);
+    return AICDF_ERR_CUDA;
+  }
+  return AICDF_OK;
+}
+
+extern "C" aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, double *sums_dev,
+                                        void *workspace_dev, size_t workspace_bytes,
+                                        aicdf_stream_t stream) {
+  if (!batch_ok(b)) return AICDF_ERR_ARG;
+  aicdf_status st = check_schedule(s);
+  if (st != AICDF_OK) return st;
+  if (!sums_dev || ((uintptr_t)sums_dev % 8) || !workspace_dev || ((uintptr_t)workspace_dev % 256))
+    return AICDF_ERR_ARG;
+  Plan *p = get_plan(b, *s);
+  if (!p) return AICDF_ERR_NOMEM;
+  if (workspace_bytes < p->bytes) return AICDF_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  char *w = (char *)workspace_dev;
+  if (p->uploaded_ws != workspace_dev) {
+    // the plan's tables live in the workspace; upload once per workspace
+    if (cudaMemcpyAsync(w + p->off_items, p->items.data(), sizeof(BatchItem) * p->items.size(),
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_specs, b->specs.data(), sizeof(PathSpec) * b->specs.size(),
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_slots, p->slot_begin.data(), sizeof(int) * p->slot_begin.size(),
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_counts, b->counts.data(), sizeof(double) * b->counts.size(),
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess) {
+      set_cuda_error((int)cudaGetLastError());
+      return AICDF_ERR_CUDA;
+    }
+    p->uploaded_ws = workspace_dev;
+  }
+  if (!p->exec || p->graph_ws != workspace_dev || p->graph_sums != sums_dev) {
+    drop_graph(p);
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+      set_cuda_error((int)cudaGetLastError());
+      return AICDF_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    aicdf_status rs = AICDF_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rs = AICDF_ERR_CUDA;
+    } else {
+      rs = record_batch(b, p, workspace_dev, sums_dev, cap);
+      cudaError_t e = cudaStreamEndCapture(cap, &g);
+      if (rs == AICDF_OK && e != cudaSuccess) rs = AICDF_ERR_CUDA;
+    }
+    if (rs == AICDF_OK && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) rs = AICDF_ERR_CUDA;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rs != AICDF_OK) {
+      set_cuda_error((int)cudaGetLastError());
+      p->exec = nullptr;
+      return rs;
+    }
+    p->graph_ws = workspace_dev;
+    p->graph_sums = sums_dev;
+  }
+  if (cudaGraphLaunch(p->exec, cs) != cudaSuccess) {
+    set_cuda_error((int)cudaGetLastError());
+    return AICDF_ERR_CUDA;
+  }
+  return AICDF_OK;
+}
+
+extern "C" aicdf_status aicdf_batch_info(aicdf_batch b, const aicdf_schedule *s, int *n_items,
+                                         int *grid) {
+  if (!batch_ok(b) || check_schedule(s) != AICDF_OK) return AICDF_ERR_ARG;
+  Plan *p = get_plan(b, *s);
+  if (!p) return AICDF_ERR_NOMEM;
+  if (n_items) *n_items = (int)p->items.size();
+  if (grid) *grid = p->grid;
+  return AICDF_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+static std::string tune_key(aicdf_batch_s *b, int var16) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char &c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "/%016llx/v%d", (unsigned long long)b->fingerprint, var16);
+  return name + buf;
+}
+
+extern "C" aicdf_status aicdf_batch_autotune(aicdf_batch b, int var16, double *sums_dev,
+                                             void *workspace_dev, size_t workspace_bytes,
+                                             aicdf_stream_t stream, const char *cache_path,
+                                             aicdf_schedule *best, double *best_ms) {
+  if (!batch_ok(b) || !best || (var16 != 0 && var16 != 1)) return AICDF_ERR_ARG;
+  const std::string key = tune_key(b, var16);
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream is(line);
+      std::string k;
+      aicdf_schedule s{};
+      double ms = 0.0;
+      if (is >> k >> s.tile_paths >> s.block_threads >> s.blocks_per_sm >> s.var16 >> ms && k == key &&
+          check_schedule(&s) == AICDF_OK) {
+        *best = s;
+        if (best_ms) *best_ms = ms;
+        return AICDF_OK;
+      }
+    }
+  }
+  std::vector<aicdf_schedule> cands;
+  for (int threads : {128, 256})
+    for (int tile_mult : {2, 8, 32, 128}) cands.push_back({threads * tile_mult, threads, 0, var16});
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_t = 1e300;
+  aicdf_status rc = AICDF_OK;
+  for (const aicdf_schedule &s : cands) {
+    Plan *p = get_plan(b, s);
+    if (!p) {
+      rc = AICDF_ERR_NOMEM;
+      break;
+    }
+    if (p->bytes > workspace_bytes) continue;  // this schedule does not fit the workspace
+    rc = aicdf_batch_run(b, &s, sums_dev, workspace_dev, workspace_bytes, stream);  // warm + capture
+    if (rc != AICDF_OK) break;
+    std::vector<double> ts;
+    for (int rep = 0; rep < 3 && rc == AICDF_OK; ++rep) {
+      cudaEventRecord(e0, cs);
+      rc = aicdf_batch_run(b, &s, sums_dev, workspace_dev, workspace_bytes, stream);
+      cudaEventRecord(e1, cs);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ts.push_back(ms);
+    }
+    if (rc != AICDF_OK) break;
+    std::sort(ts.begin(), ts.end());
+    if (ts[1] < best_t) {
+      best_t = ts[1];
+      *best = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != AICDF_OK) return rc;
+  if (best_t >= 1e300) return AICDF_ERR_ARG;  // no candidate fits the workspace
+  if (best_ms) *best_ms = best_t;
+  if (cache_path) {
+    std::ofstream out(cache_path, std::ios::app);
+    out << key << " " << best->tile_paths << " " << best->block_threads << " " << best->blocks_per_sm
+        << " " << best->var16 << " " << best_t << "\n";
+  }
+  return AICDF_OK;
+}
+
+// ---------------------------------------------------------------- level ABI
 extern "C" size_t aicdf_mlmc_level_workspace_bytes(void) {
   return sizeof(double2) * (size_t)kMaxLevelBlocks;
 }
@@ -195,5 +666,5 @@ extern "C" aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_t
   if (!sums_dev || ((uintptr_t)sums_dev % 8)) return AICDF_ERR_ARG;
   if (!workspace_dev || ((uintptr_t)workspace_dev % 16)) return AICDF_ERR_ARG;
   if (workspace_bytes < aicdf_mlmc_level_workspace_bytes()) return AICDF_ERR_ARG;
-  return launch_level(a, kind, sums_dev, workspace_dev, (cudaStream_t)stream);
+  return launch_level(a, sums_dev, workspace_dev, (cudaStream_t)stream);
 }

@@ -1,25 +1,31 @@
 // One coupled MLMC path (Section 4): Euler-Maruyama or Milstein for GBM or
 // CIR, driven by exact and/or approximate variates from the same uniforms;
-// plus the argument block and FP64 block reduction used by the level and
-// batched kernels.
+// plus the per-term specification and the FP64 block reduction shared by the
+// level kernel and the batched persistent kernel.
 #pragma once
 
 #include <cstdint>
+
+#include <cuda_fp16.h>
 
 #include "aicdf_internal.h"
 #include "device_common.cuh"
 
 namespace aicdf {
 
+// Everything one estimator term needs besides the approximation table.
+struct PathSpec {
+  uint32_t tag;                       // Philox counter word 3
+  int level, kind, model, scheme, payoff;
+  float X0, K, discount;
+  float mu, sigma, kappa, theta, dt;  // dt = T / 2^level (fine step)
+};
+
 struct LevelArgs {
   PhiloxKeys keys;
   uint64_t n_paths, path_offset;
-  uint32_t tag;
-  int level, kind, model, scheme, payoff, approx, ntab;
-  float nf;
-  float X0, K, discount;
-  // per-step coefficients (fine step dt, coarse step 2 dt), see make_path_consts
-  float mu, sigma, kappa, theta, dt;
+  PathSpec ps;
+  int approx, ntab;
   float tab[1024];  // PWC constants | PWL alpha[0..15], beta[16..31]
 };
 
@@ -30,66 +36,67 @@ inline bool kind_needs_approx(int kind) {
   return kind == AICDF_KIND_CORR4 || kind == AICDF_KIND_APPROX2 || kind == AICDF_KIND_PLAIN_APPROX;
 }
 
-// Approximation evaluator used inside path loops.
+// Approximation evaluator used inside path loops.  Path uniforms always come
+// from the library's Philox words, so both forms use the grid shortcuts:
+// (x, u) = (the word, its uniform u01(x)).
 template <int AP>
 struct ApproxTable;
 
 template <>
 struct ApproxTable<AICDF_PWL> {
-  PwlLane c;
-  unsigned kmax;
+  PwlRows rows;
   __device__ ApproxTable(const float *tab, int ntab, float *) {
-    c = pwl_lane_coefs(tab, tab + 16);
-    kmax = (unsigned)ntab;
+    rows = pwl_lane_rows(tab, tab + 16, ntab);
   }
-  __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
+  __device__ __forceinline__ float operator()(uint32_t, float u) const { return pwl_eval_grid(u, rows); }
 };
 
 template <>
 struct ApproxTable<AICDF_PWC> {
   const float *s;
-  float nf;
-  int nmax;
+  uint32_t shift;
   __device__ ApproxTable(const float *tab, int ntab, float *smem) {
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) smem[i] = tab[i];
     __syncthreads();
     s = smem;
-    nf = (float)ntab;
-    nmax = ntab - 1;
+    shift = 23u - (31u - __clz(ntab));  // ntab = 2^q: floor(ntab u) = m >> (23 - q)
   }
-  __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
+  __device__ __forceinline__ float operator()(uint32_t x, float) const {
+    return s[pwc_index_from_word(x, shift)];
+  }
 };
 
-// Step multipliers.  GBM, with Z the standard normal of one step of size h:
-//   EM:       X <- X (1 + mu h + sigma sqrt(h) Z)
-//   Milstein: X <- X (1 + mu h + sigma sqrt(h) Z + sigma^2 h (Z^2 - 1) / 2)
+// Steps are written as X <- X + increment so that FP32 rounding of the
+// constant factors never biases every step the same way: rounding 1 + mu dt
+// to FP32 once would shift the drift by up to 2^-24 per step, a bias that
+// grows like 2^l.  GBM, with Z the standard normal of one step of size h:
+//   EM:       X <- X + X (mu h + sigma sqrt(h) Z)
+//   Milstein: X <- X + X (mu h + sigma sqrt(h) Z + sigma^2 h (Z^2 - 1) / 2)
 // For the coarse step (h = 2 dt) the increment is sqrt(dt) (Z1 + Z2) = sqrt(dt) S,
 // so with S in place of Z the same polynomial holds with sqrt(dt) and 2 dt.
 // CIR (truncated):   X <- X + kappa (theta - X) h + sigma sqrt(|X|) dW
 //                         [+ sigma^2 (dW^2 - h) / 4  for Milstein]
 struct PathConsts {
-  // GBM: fine multiplier g0 + g1 Z + g2 Z^2, coarse c0 + c1 S + c2 S^2
+  // GBM: fine increment factor g0 + g1 Z + g2 Z^2, coarse c0 + c1 S + c2 S^2
   float g0, g1, g2, c0, c1, c2;
-  // CIR: fine  X (1 - kappa dt) + kappa theta dt + sig_sdt sqrt|X| Z + m (Z^2 - 1)
-  //      coarse X (1 - 2 kappa dt) + 2 kappa theta dt + sig_sdt sqrt|X| S + m (S^2 - 2)
-  float a1f, a0f, a1c, a0c, sig_sdt, mq;
+  // CIR: fine   kdt (theta - X) + sig_sdt sqrt|X| Z + mq (Z^2 - 1)
+  //      coarse 2 kdt (theta - X) + sig_sdt sqrt|X| S + mq (S^2 - 2)
+  float kdt, theta, sig_sdt, mq;
 };
 
-__device__ __forceinline__ PathConsts make_path_consts(const LevelArgs &a) {
+__device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   PathConsts p;
   const float dt = a.dt, sdt = sqrtf(dt);
   const bool mil = a.scheme == AICDF_SCHEME_MILSTEIN;
   const float hs2 = 0.5f * a.sigma * a.sigma * dt;
-  p.g0 = 1.0f + a.mu * dt - (mil ? hs2 : 0.f);
+  p.g0 = a.mu * dt - (mil ? hs2 : 0.f);
   p.g1 = a.sigma * sdt;
   p.g2 = mil ? hs2 : 0.f;
-  p.c0 = 1.0f + 2.0f * a.mu * dt - (mil ? 2.0f * hs2 : 0.f);
+  p.c0 = 2.0f * a.mu * dt - (mil ? 2.0f * hs2 : 0.f);
   p.c1 = a.sigma * sdt;
   p.c2 = mil ? hs2 : 0.f;
-  p.a1f = 1.0f - a.kappa * dt;
-  p.a0f = a.kappa * a.theta * dt;
-  p.a1c = 1.0f - 2.0f * a.kappa * dt;
-  p.a0c = 2.0f * a.kappa * a.theta * dt;
+  p.kdt = a.kappa * dt;
+  p.theta = a.theta;
   p.sig_sdt = a.sigma * sdt;
   p.mq = mil ? 0.25f * a.sigma * a.sigma * dt : 0.f;
   return p;
@@ -97,34 +104,38 @@ __device__ __forceinline__ PathConsts make_path_consts(const LevelArgs &a) {
 
 template <int MODEL>
 __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p) {
-  if (MODEL == AICDF_MODEL_GBM) return x * fmaf(fmaf(p.g2, z, p.g1), z, p.g0);
+  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.g2, z, p.g1), z, p.g0), x);
   const float r = sqrtf(fabsf(x));
-  return fmaf(p.a1f, x, p.a0f) + fmaf(p.sig_sdt * r, z, p.mq * fmaf(z, z, -1.0f));
+  const float inc = fmaf(p.kdt, p.theta - x, fmaf(p.sig_sdt * r, z, p.mq * fmaf(z, z, -1.0f)));
+  return x + inc;
 }
 
 template <int MODEL>
 __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts &p) {
-  if (MODEL == AICDF_MODEL_GBM) return x * fmaf(fmaf(p.c2, s, p.c1), s, p.c0);
+  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.c2, s, p.c1), s, p.c0), x);
   const float r = sqrtf(fabsf(x));
-  return fmaf(p.a1c, x, p.a0c) + fmaf(p.sig_sdt * r, s, p.mq * fmaf(s, s, -2.0f));
+  const float inc = fmaf(2.0f * p.kdt, p.theta - x, fmaf(p.sig_sdt * r, s, p.mq * fmaf(s, s, -2.0f)));
+  return x + inc;
 }
 
-__device__ __forceinline__ float payoff(const LevelArgs &a, float x) {
+__device__ __forceinline__ float payoff(const PathSpec &a, float x) {
   return a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf(x - a.K, 0.0f) : a.discount * x;
 }
 
 // Y of one path.  All 32 lanes of a warp must call it together (the PWL
-// approximation shuffles across the warp).
-template <bool NE, bool NA, int AP, int MODEL, int SCHEME>
-__device__ __forceinline__ float path_y(const LevelArgs &a, const PathConsts &pc,
-                                        const ApproxTable<AP> &ap, uint64_t p) {
+// approximation shuffles across the warp).  V16: the approximate variate is
+// rounded to FP16 before use (FP16 approximate variates).
+template <bool NE, bool NA, int AP, int MODEL, bool V16 = false>
+__device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
+                                        const ApproxTable<AP> &ap, const PhiloxKeys &keys,
+                                        uint64_t p) {
   const int nfine = 1 << a.level;
   const bool coarse = a.level > 0;
   float xfe = a.X0, xce = a.X0, xfa = a.X0, xca = a.X0;
   float se = 0.f, sa = 0.f;  // pair sums of fine variates
   const uint32_t plo = (uint32_t)p, phi = (uint32_t)(p >> 32);
   for (int s4 = 0; s4 < nfine; s4 += 4) {
-    const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), plo, phi, a.tag), a.keys);
+    const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), plo, phi, a.tag), keys);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -136,7 +147,8 @@ __device__ __forceinline__ float path_y(const LevelArgs &a, const PathConsts &pc
           se += ze;
         }
         if (NA) {
-          const float za = ap(u);
+          float za = ap(w[t], u);
+          if (V16) za = __half2float(__float2half_rn(za));
           xfa = step_fine<MODEL>(xfa, za, pc);
           sa += za;
         }
@@ -161,7 +173,29 @@ __device__ __forceinline__ float path_y(const LevelArgs &a, const PathConsts &pc
   }
 }
 
-// FP64 block reduction of two values; result valid in thread 0.
+// Runtime dispatch on (kind, model) for kernels that mix terms; the branch is
+// uniform across the block, outside the path loop.
+template <int AP, bool V16>
+__device__ __forceinline__ float path_y_any(const PathSpec &a, const PathConsts &pc,
+                                            const ApproxTable<AP> &ap, const PhiloxKeys &keys,
+                                            uint64_t p) {
+  const bool gbm = a.model == AICDF_MODEL_GBM;
+  switch (a.kind) {
+    case AICDF_KIND_CORR4:
+      return gbm ? path_y<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+    case AICDF_KIND_EXACT2:
+    case AICDF_KIND_PLAIN:
+      return gbm ? path_y<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+    default:
+      return gbm ? path_y<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+  }
+}
+
+// FP64 block reduction of two values; result valid in thread 0.  Ends with a
+// barrier so that s_red may be reused right away.
 template <int NW>
 __device__ __forceinline__ double2 block_reduce2(double d1, double d2, double2 (&s_red)[NW]) {
 #pragma unroll
@@ -174,17 +208,20 @@ __device__ __forceinline__ double2 block_reduce2(double d1, double d2, double2 (
   __syncthreads();
   double2 t = make_double2(0.0, 0.0);
   if (threadIdx.x == 0) {
-    for (int w = 0; w < NW; ++w) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = 0; w < nw; ++w) {
       t.x += s_red[w].x;
       t.y += s_red[w].y;
     }
   }
+  __syncthreads();
   return t;
 }
 
-// Validate parameters and fill the argument block (host).
-aicdf_status prepare_level_args(const aicdf_sde_params *params, aicdf_table approx, int level,
-                                int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
-                                uint32_t tag, LevelArgs *a);
+// Validate SDE parameters and fill a PathSpec (host).
+aicdf_status make_path_spec(const aicdf_sde_params *prm, int level, int kind, uint32_t tag,
+                            PathSpec *ps);
+// Copy an approximation table into the kernel-parameter layout (host).
+aicdf_status pack_table(aicdf_table approx, float *tab, int *ntab);
 
 }  // namespace aicdf

@@ -27,48 +27,59 @@ struct SampleArgs {
   PhiloxKeys keys;
   int ntab;            // PWC: intervals; PWL: K (rows 0..K)
   float nf;            // PWC: (float)ntab
+  uint32_t pwc_shift;  // PWC: 23 - log2(ntab)
   float tab[1024];     // PWC constants | PWL alpha[0..15], beta[16..31]
 };
 
 // Per-thread evaluator for one method.  Construction stages the table.
-template <int METHOD>
+// word(x): the sample for the library's uniform from Philox word x (on the
+// 2^-24 grid); operator()(u): the sample for any FP32 u (caller uniforms).
+template <int METHOD, int SRC>
 struct Approx;
 
-template <>
-struct Approx<AICDF_PWC> {
+template <int SRC>
+struct Approx<AICDF_PWC, SRC> {
   const float *s;
   float nf;
   int nmax;
+  uint32_t shift;
   __device__ Approx(const SampleArgs &a, float *smem) {
     for (int i = threadIdx.x; i < a.ntab; i += blockDim.x) smem[i] = a.tab[i];
     __syncthreads();
     s = smem;
     nf = a.nf;
     nmax = a.ntab - 1;
+    shift = a.pwc_shift;
   }
+  __device__ __forceinline__ float word(uint32_t x) const { return s[pwc_index_from_word(x, shift)]; }
   __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
 };
 
-template <>
-struct Approx<AICDF_PWL> {
-  PwlLane c;
+template <int SRC>
+struct Approx<AICDF_PWL, SRC> {
+  PwlLane c;     // general inputs: capped index, sign folded into the row
+  PwlRows rows;  // grid inputs: 32 rows, sign by xor
   unsigned kmax;
   __device__ Approx(const SampleArgs &a, float *) {
-    c = pwl_lane_coefs(a.tab, a.tab + 16);
+    if (SRC == SRC_PHILOX) rows = pwl_lane_rows(a.tab, a.tab + 16, a.ntab);
+    else c = pwl_lane_coefs(a.tab, a.tab + 16);
     kmax = (unsigned)a.ntab;
   }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_grid(u01(x), rows); }
   __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
 };
 
-template <>
-struct Approx<AICDF_EXACT> {
+template <int SRC>
+struct Approx<AICDF_EXACT, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
+  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }
   __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
 };
 
-template <>
-struct Approx<AICDF_EXACT_LIB> {
+template <int SRC>
+struct Approx<AICDF_EXACT_LIB, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
+  __device__ __forceinline__ float word(uint32_t x) const { return normcdfinvf(u01(x)); }
   __device__ __forceinline__ float operator()(float u) const { return normcdfinvf(u); }
 };
 
@@ -106,7 +117,7 @@ __device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ SampleArgs a) {
   __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
-  const Approx<METHOD> f(a, smem);
+  const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
   constexpr int E = OutVec<OUT>::kElems;
@@ -124,10 +135,10 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
       for (int h = 0; h < E / 4; ++h) {
         const uint64_t j = (a.offset >> 2) + v * (E / 4) + h;
         const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
-        z[4 * h + 0] = f(u01(r.x));
-        z[4 * h + 1] = f(u01(r.y));
-        z[4 * h + 2] = f(u01(r.z));
-        z[4 * h + 3] = f(u01(r.w));
+        z[4 * h + 0] = f.word(r.x);
+        z[4 * h + 1] = f.word(r.y);
+        z[4 * h + 2] = f.word(r.z);
+        z[4 * h + 3] = f.word(r.w);
       }
     } else {
 #pragma unroll
@@ -162,7 +173,7 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ SampleArgs a) {
   __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
-  const Approx<METHOD> f(a, smem);
+  const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -170,18 +181,18 @@ __global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ S
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n;
        base += stride) {
     const uint64_t e = base + lane;
-    float u;
+    float y;
     if constexpr (SRC == SRC_PHILOX) {
       const uint64_t s = a.offset + e;
       const uint64_t j = s >> 2;
       const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
       const uint32_t w = (s & 3) == 0 ? r.x : (s & 3) == 1 ? r.y : (s & 3) == 2 ? r.z : r.w;
-      u = u01(w);
+      y = f.word(w);
     } else {
-      u = (e < a.n) ? a.u[e] : 0.5f;
+      const float u = (e < a.n) ? a.u[e] : 0.5f;
+      y = f(u);
+      if (!in_unit(u)) y = __int_as_float(0x7fc00000);
     }
-    float y = f(u);
-    if (SRC == SRC_INPUT && !in_unit(u)) y = __int_as_float(0x7fc00000);
     if (e < a.n) store_one(out, e, y);
   }
 }
@@ -219,6 +230,9 @@ aicdf_status prepare_sample_args(aicdf_table table, int method, SampleArgs *a) {
       for (int i = 0; i < table->n; ++i) a->tab[i] = table->f0[i];
       a->ntab = table->n;
       a->nf = (float)table->n;
+      int q = 0;
+      while ((1 << q) < table->n) ++q;
+      a->pwc_shift = (uint32_t)(23 - q);
     } else {
       if (table->n > 15) return AICDF_ERR_UNSUPPORTED;  // 16 rows fit one half-warp
       for (int i = 0; i < 16; ++i) {
@@ -242,9 +256,9 @@ aicdf_status launch_sample(const SampleArgs &a, int method, int out_dtype, int s
   const int E = vec ? (out_dtype == AICDF_F32 ? 4 : 8) : 1;
   const uint64_t units = (a.n + E - 1) / E;
   const int threads = 256;
-  const int sms = sm_count();
+  // one full wave: SMs x resident blocks of this kernel (grid-stride inside)
+  const uint64_t cap = (uint64_t)sm_count() * resident_blocks((const void *)k, threads);
   uint64_t blocks = (units + threads - 1) / threads;
-  const uint64_t cap = (uint64_t)sms * 8;  // 8 x 256 threads = 2048 per SM
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k<<<(unsigned)blocks, threads, 0, stream>>>(a);

@@ -104,8 +104,11 @@ def test_determinism_and_additivity(P, orc, env):
     for off, m in parts:
         tot += _level(P, env, gp, env["tl"], 4, 1, m, off=off, seed=8, tag=2)
     assert tot[2] == n
-    assert tot[0] == pytest.approx(s1[0], rel=1e-9, abs=1e-10)
-    assert tot[1] == pytest.approx(s1[1], rel=1e-9, abs=1e-12)
+    # a different split regroups the per-thread FP32 chunks: the sums agree to
+    # the chunk rounding, ~1e-6 of sum |Y| <= 1e-6 sqrt(n sum Y^2)
+    scale = math.sqrt(n * s1[1])
+    assert abs(tot[0] - s1[0]) <= 1e-6 * scale
+    assert tot[1] == pytest.approx(s1[1], rel=1e-6)
 
 
 def test_full_size_gbm_config(P, orc, env):

@@ -73,7 +73,8 @@ def test_pwl_philox_parity(P, tabs, orc, n, offset):
     ref, _ = orc.sample_pwl(a, b, u)
     z = _gpu_sample(P, tl, P.PWL, n, seed=7, offset=offset)
     _assert_pwl(z, ref)
-    assert np.mean(z == ref) > 0.999   # one correctly rounded FMA: nearly always bit-equal
+    # one correctly rounded FMA: nearly always bit-equal to the FP32-rounded oracle value
+    assert np.mean(z == ref.astype(np.float32).astype(np.float64)) > 0.999
 
 
 @pytest.mark.parametrize("n", [5, 4099, (1 << 18) + 3])
