@@ -212,10 +212,12 @@ void aicdf_batch_destroy(aicdf_batch b);
 /* Device workspace a schedule needs (0 for an invalid schedule). */
 size_t aicdf_batch_workspace_bytes(aicdf_batch b, const aicdf_schedule *s);
 /* Run every term: sums_dev[3t .. 3t+2] = (sum Y, sum Y^2, n) of term t (FP64).
- * The first run with a given (schedule, workspace, sums) uploads the tile
- * list into the workspace and captures the counter reset, the persistent
- * kernel and the per-term reduction into a CUDA graph; later runs replay it.
- * The workspace must stay untouched between runs of the same batch.
+ * The tile list of the schedule is uploaded into the workspace whenever
+ * another schedule or batch used that workspace since (or never), and the
+ * counter reset, the persistent kernel and the per-term reduction are
+ * captured into a CUDA graph on the first run with a given (schedule,
+ * workspace, sums); later runs replay it.  Only the library may write the
+ * workspace between runs.
  * Deterministic: sums do not depend on which CTA ran which tile.
  * Asynchronous on stream (the first run synchronises it once). */
 aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, double *sums_dev,
@@ -230,6 +232,92 @@ aicdf_status aicdf_batch_autotune(aicdf_batch b, int var16, double *sums_dev,
                                   void *workspace_dev, size_t workspace_bytes,
                                   aicdf_stream_t stream, const char *cache_path,
                                   aicdf_schedule *best, double *best_ms);
+
+/* ===================================================================== */
+/* Non-central chi-squared (Section 5)                                     */
+/* ===================================================================== */
+/* Exact quantiles C^{-1}_nu(u_i; lambda_i) in FP64 for i < n: root finding on
+ * the CDF written as the Poisson mixture of central chi-squared CDFs
+ * (Section 5), Newton steps inside a bracket from Sankaran's approximation
+ * (Section 5.1).  Every loop is capped; a cap that is hit ORs 1 into
+ * *status_dev (device int, caller-cleared).  u outside (0, 1): 0 or +inf. */
+aicdf_status aicdf_ncx2_ppf(const float *u_dev, const double *lam_dev, double nu, size_t n,
+                            double *out_dev, int *status_dev, aicdf_stream_t stream);
+/* Training targets for the surrogate: sample i takes u and ln(lambda) ~
+ * U(loglam_lo, loglam_hi) from words 0 and 1 of Philox block i (counter
+ * (i mod 2^32, i>>32, 0, tag)) and the exact rescaled quantile
+ * P = (C^{-1}_nu(u; lambda) - lambda - nu) / (2 sqrt(lambda + nu)), i.e.
+ * P_nu(u; nu/(lambda+nu)) of Section 5.1.  Writes u, lambda, P (FP32). */
+aicdf_status aicdf_ncx2_targets(double nu, float loglam_lo, float loglam_hi, uint64_t seed,
+                                uint32_t tag, size_t n, float *u_dev, float *lam_dev, float *p_dev,
+                                int *status_dev, aicdf_stream_t stream);
+
+/* ===================================================================== */
+/* Learned surrogate of P_nu(U; y) (Section 5.1 rescaling)                 */
+/* ===================================================================== */
+/* A 2 -> 64 -> 64 -> 1 tanh network P~(u, lambda) for one fixed nu, inputs
+ * x0 = s(u)/3 with s(u) = sign(u-1/2) sqrt(-2 ln(2 min(u,1-u))) and
+ * x1 = clamp(ln(lambda)/4, -1, 1); then
+ * C~^{-1}_nu(u; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~(u, lambda).
+ * The 64 x 64 layer runs on the tensor cores in BF16 with FP32 accumulation;
+ * FP32 master weights.  The handle owns its device buffers (allocated at
+ * create).  Parameter blob layout (FP32): W1[64][2] | b1[64] | W2[64 out][64 in]
+ * | b2[64] | w3[64] | b3, aicdf_surrogate_param_count() floats. */
+typedef struct aicdf_surrogate_s *aicdf_surrogate;
+aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_surrogate *out);
+void aicdf_surrogate_destroy(aicdf_surrogate s);
+int aicdf_surrogate_param_count(void);
+aicdf_status aicdf_surrogate_get_params(aicdf_surrogate s, float *host, int cap);
+/* Replaces the weights and resets the optimiser state. */
+aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const float *host, int n);
+/* p_out_dev[i] = P~(u_dev[i], lam_dev[i]). */
+aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                  size_t n, float *p_out_dev, aicdf_stream_t stream);
+/* Gradient of L = mean_i (P~_i - target_i)^2 over the n samples, into
+ * grad_dev[0 .. param_count) (same layout as the parameters), with the loss
+ * sum at grad_dev[param_count]; n <= 2^24. */
+aicdf_status aicdf_surrogate_grad(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                  const float *target_dev, size_t n, float *grad_dev,
+                                  aicdf_stream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch; writes the
+ * batch's mean squared error to *loss_dev if loss_dev is not NULL. */
+aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                        const float *target_dev, size_t n, float lr,
+                                        float *loss_dev, aicdf_stream_t stream);
+/* epochs passes over n samples in batches of `batch` (the tail that does not
+ * fill a batch is skipped), step size decaying geometrically from lr to
+ * lr_final; the last batch's loss goes to *loss_dev. */
+aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                   const float *target_dev, size_t n, size_t batch, int epochs,
+                                   float lr, float lr_final, float *loss_dev, aicdf_stream_t stream);
+
+/* ===================================================================== */
+/* CIR with exact and approximate non-central chi-squared steps (Section 5.2) */
+/* ===================================================================== */
+/* Kinds of Y for one path of 2^level steps of size h = T/2^level; every step
+ * draws one uniform U (Philox counter (s/4, p mod 2^32, p>>32, tag), word
+ * s%4) and both sides use the same U:
+ *   EXACT       P(X^_T), X^' = c C^{-1}_nu(U; X^ e^{-kappa h}/c)  (FP64 root finder)
+ *   SURROGATE   P(X~_T), X~' = c max(C~^{-1}_nu(U; lambda~), 0)   (learned P~)
+ *   DIFF        P(X^_T) - P(X~_T)                                  (same steps)
+ *   GAUSS       as SURROGATE with P~ replaced by Phi^{-1}(U), the y -> 0
+ *               limit of P (Section 5.1): the approximation without the network
+ *   DIFF_GAUSS  P(X^_T) - P(X~_T) for GAUSS
+ * with c = sigma^2 (1 - e^{-kappa h}) / (4 kappa), nu = 4 kappa theta / sigma^2. */
+typedef enum {
+  AICDF_CIR_EXACT = 0, AICDF_CIR_SURROGATE = 1, AICDF_CIR_DIFF = 2,
+  AICDF_CIR_GAUSS = 3, AICDF_CIR_DIFF_GAUSS = 4
+} aicdf_cir_kind;
+
+/* Sums of Y and Y^2 (FP64) over paths path_offset .. path_offset+n_paths-1 of
+ * a CIR model (params->model = AICDF_MODEL_CIR, payoff X or call; level <=
+ * 12).  sur: a surrogate trained for this nu (required by SURROGATE and
+ * DIFF, else may be NULL).  workspace: as for aicdf_mlmc_level.  Root-finder
+ * caps hit OR 1 into *status_dev.  Asynchronous on stream. */
+aicdf_status aicdf_cir_level(const aicdf_sde_params *params, aicdf_surrogate sur, int level,
+                             int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                             uint32_t tag, double *sums_dev, void *workspace_dev,
+                             size_t workspace_bytes, int *status_dev, aicdf_stream_t stream);
 
 /* ===================================================================== */
 /* MLMC driver (Section 4.1): estimate E[P] to a target RMSE               */

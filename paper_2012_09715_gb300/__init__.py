@@ -109,6 +109,18 @@ SIGNATURES = {
     "aicdf_batch_run": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "aicdf_batch_info": (_I, [_P, _P, C.POINTER(_I), C.POINTER(_I)]),
     "aicdf_batch_autotune": (_I, [_P, _I, _P, _P, _SZ, _P, C.c_char_p, _P, C.POINTER(_D)]),
+    "aicdf_ncx2_ppf": (_I, [_P, _P, _D, _SZ, _P, _P, _P]),
+    "aicdf_ncx2_targets": (_I, [_D, C.c_float, C.c_float, _U64, _U32, _SZ, _P, _P, _P, _P, _P]),
+    "aicdf_surrogate_create": (_I, [_D, _U64, C.POINTER(_P)]),
+    "aicdf_surrogate_destroy": (None, [_P]),
+    "aicdf_surrogate_param_count": (_I, []),
+    "aicdf_surrogate_get_params": (_I, [_P, _P, _I]),
+    "aicdf_surrogate_set_params": (_I, [_P, _P, _I]),
+    "aicdf_surrogate_eval": (_I, [_P, _P, _P, _SZ, _P, _P]),
+    "aicdf_surrogate_grad": (_I, [_P, _P, _P, _P, _SZ, _P, _P]),
+    "aicdf_surrogate_train_step": (_I, [_P, _P, _P, _P, _SZ, C.c_float, _P, _P]),
+    "aicdf_surrogate_train": (_I, [_P, _P, _P, _P, _SZ, _SZ, _I, C.c_float, C.c_float, _P, _P]),
+    "aicdf_cir_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P, _P]),
     "aicdf_mlmc_run_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_run": (_I, [_P, _P, _P, _P, _P, _SZ, _P]),
 }
@@ -317,3 +329,85 @@ class Batch:
         if h is not None and _lib is not None:
             _lib.aicdf_batch_destroy(h)
             self.handle = None
+
+
+# ------------------------------------------------------------------ NCX2, surrogate, CIR
+CIR_EXACT, CIR_SURROGATE, CIR_DIFF, CIR_GAUSS, CIR_DIFF_GAUSS = range(5)
+MLP_OFFSETS = {"W1": (0, (64, 2)), "b1": (128, (64,)), "W2": (192, (64, 64)), "b2": (4288, (64,)),
+               "w3": (4352, (64,)), "b3": (4416, (1,))}
+
+
+def ncx2_ppf(u, lam, nu: float, out, status, stream=None):
+    """aicdf_ncx2_ppf: out[i] = C^{-1}_nu(u[i]; lam[i]) (u float32, lam/out float64, device)."""
+    _check(lib().aicdf_ncx2_ppf(_ptr(u), _ptr(lam), nu, u.numel(), _ptr(out), _ptr(status),
+                                _stream(stream)), "ncx2_ppf")
+    return out
+
+
+def ncx2_targets(nu: float, n: int, u, lam, p, status, seed: int = 0, tag: int = 1,
+                 loglam_lo: float = -4.0, loglam_hi: float = 4.0, stream=None):
+    """aicdf_ncx2_targets: exact training targets P_nu(u; nu/(lam+nu)) (device float32)."""
+    _check(lib().aicdf_ncx2_targets(nu, loglam_lo, loglam_hi, seed, tag, n, _ptr(u), _ptr(lam), _ptr(p),
+                                    _ptr(status), _stream(stream)), "ncx2_targets")
+
+
+class Surrogate:
+    """Owning handle of the learned P_nu(U; y) surrogate (device weights)."""
+
+    def __init__(self, nu: float, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().aicdf_surrogate_create(nu, seed, C.byref(h)), "surrogate_create")
+        self.handle = h
+        self.nu = nu
+        self.n_params = lib().aicdf_surrogate_param_count()
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(4420, dtype=np.float32)
+        _check(lib().aicdf_surrogate_get_params(self.handle, p.ctypes.data, p.size), "surrogate_get_params")
+        return p[: self.n_params]
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().aicdf_surrogate_set_params(self.handle, p.ctypes.data, p.size), "surrogate_set_params")
+
+    def params_dict(self):
+        p = self.get_params().astype("float64")
+        return {k: p[o:o + int(__import__("numpy").prod(s))].reshape(s) for k, (o, s) in MLP_OFFSETS.items()}
+
+    def eval(self, u, lam, out, stream=None):
+        _check(lib().aicdf_surrogate_eval(self.handle, _ptr(u), _ptr(lam), u.numel(), _ptr(out),
+                                          _stream(stream)), "surrogate_eval")
+        return out
+
+    def grad(self, u, lam, target, grad_out, stream=None):
+        _check(lib().aicdf_surrogate_grad(self.handle, _ptr(u), _ptr(lam), _ptr(target), u.numel(),
+                                          _ptr(grad_out), _stream(stream)), "surrogate_grad")
+        return grad_out
+
+    def train_step(self, u, lam, target, lr: float, loss=None, stream=None):
+        _check(lib().aicdf_surrogate_train_step(self.handle, _ptr(u), _ptr(lam), _ptr(target), u.numel(),
+                                                lr, _ptr(loss), _stream(stream)), "surrogate_train_step")
+
+    def train(self, u, lam, target, batch: int, epochs: int, lr: float, lr_final: float, loss=None,
+              stream=None):
+        _check(lib().aicdf_surrogate_train(self.handle, _ptr(u), _ptr(lam), _ptr(target), u.numel(), batch,
+                                           epochs, lr, lr_final, _ptr(loss), _stream(stream)),
+               "surrogate_train")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.aicdf_surrogate_destroy(h)
+            self.handle = None
+
+
+def cir_level(params: SdeParams, surrogate, level: int, kind: int, n_paths: int, sums, workspace, status,
+              path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
+    """aicdf_cir_level: sums <- [sum Y, sum Y^2, n] for a CIR kind (see aicdf.h)."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().aicdf_cir_level(C.byref(params), None if surrogate is None else surrogate.handle, level,
+                                 kind, n_paths, path_offset, seed, tag, _ptr(sums), _ptr(workspace), nbytes,
+                                 _ptr(status), _stream(stream)), "cir_level")
+    return sums

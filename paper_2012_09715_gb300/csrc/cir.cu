@@ -1,0 +1,170 @@
+// CIR paths with exact non-central chi-squared transitions vs approximate ones
+// driven by the same uniforms (Section 5.2).
+//
+// Over a step h the CIR law is X' = c chi'^2_nu(lambda) with c = sigma^2 (1 - e^{-kappa h}) /
+// (4 kappa), nu = 4 kappa theta / sigma^2 and lambda = X e^{-kappa h} / c (the
+// horizon-T law of Section 5.2 applied per step).  Exact: X' = c C^{-1}_nu(U; lambda)
+// by the FP64 root finder.  Approximate: X' = c max(C~^{-1}_nu(U; lambda), 0) with
+// C~^{-1} = lambda + nu + 2 sqrt(lambda + nu) P~ and P~ either the learned
+// surrogate (tensor-core MLP, one warp = 32 paths) or, for comparison, the
+// limit P -> Phi^{-1}(U) of Section 5.1.  As in the paper's CIR experiment the
+// two-way difference uses the same time step on both sides.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "aicdf_internal.h"
+#include "device_common.cuh"
+#include "mlmc_path.cuh"
+#include "mlp_device.cuh"
+#include "ncx2.cuh"
+
+namespace aicdf {
+
+constexpr int kCirThreads = 256;
+
+struct CirArgs {
+  PhiloxKeys keys;
+  const float *params;  // surrogate weights (may be null for kinds without it)
+  uint64_t n_paths, path_offset;
+  uint32_t tag;
+  int level, kind, payoff;
+  double nu, c, e;      // chi^2 scale, degrees of freedom, e^{-kappa h}
+  float X0, K, discount;
+};
+
+template <bool EXACT, int APPROX>  // APPROX: 0 none, 1 surrogate, 2 Gaussian limit
+__global__ void __launch_bounds__(kCirThreads)
+    k_cir(const __grid_constant__ CirArgs a, double2 *__restrict__ partials, int *__restrict__ status) {
+  __shared__ __align__(16) MlpSmem s;
+  __shared__ __align__(16) __nv_bfloat16 hs[APPROX == 1 ? kCirThreads / 32 : 1][32 * kHPad];
+  __shared__ double2 s_red[kCirThreads / 32];
+  if (APPROX == 1) {
+    mlp_stage(a.params, s);
+    __syncthreads();
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nsteps = 1 << a.level;
+  const float cf = (float)a.c, nuf = (float)a.nu, ratio = (float)(a.e / a.c);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int st = 0;
+  double d1 = 0.0, d2 = 0.0;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n_paths;
+       base += stride) {
+    const uint64_t i = base + lane;
+    const uint64_t p = a.path_offset + i;
+    double xe = a.X0;
+    float xa = a.X0;
+    for (int s4 = 0; s4 < nsteps; s4 += 4) {
+      const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), (uint32_t)p, (uint32_t)(p >> 32), a.tag), a.keys);
+      const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (s4 + t < nsteps) {
+          const float u = u01(w[t]);
+          if (EXACT) {
+            const double lam = xe * a.e / a.c;
+            xe = a.c * ncx2_ppf((double)u, a.nu, lam, &st);
+          }
+          if (APPROX != 0) {
+            const float lam = fmaxf(xa, 0.f) * ratio;
+            float pt;
+            if (APPROX == 1) pt = mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_lam(lam), hs[warp]);
+            else pt = phiinv_f32(u);
+            const float h = lam + nuf;
+            xa = cf * fmaxf(fmaf(2.0f * sqrtf(h), pt, h), 0.f);
+          }
+        }
+      }
+    }
+    float y;
+    const float pe = a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf((float)xe - a.K, 0.f)
+                                                   : a.discount * (float)xe;
+    const float pa = a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf(xa - a.K, 0.f) : a.discount * xa;
+    if (EXACT && APPROX != 0) y = pe - pa;
+    else if (EXACT) y = pe;
+    else y = pa;
+    if (i < a.n_paths) {
+      d1 += (double)y;
+      d2 += (double)y * (double)y;
+    }
+  }
+  const double2 tot = block_reduce2(d1, d2, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  if (st) atomicOr(status, st);
+}
+
+using CirFn = void (*)(CirArgs, double2 *, int *);
+
+static CirFn select_cir(int kind) {
+  switch (kind) {
+    case AICDF_CIR_EXACT: return k_cir<true, 0>;
+    case AICDF_CIR_SURROGATE: return k_cir<false, 1>;
+    case AICDF_CIR_DIFF: return k_cir<true, 1>;
+    case AICDF_CIR_GAUSS: return k_cir<false, 2>;
+    default: return k_cir<true, 2>;
+  }
+}
+
+const float *surrogate_params(aicdf_surrogate s);
+double surrogate_nu(aicdf_surrogate s);
+bool surrogate_ok(aicdf_surrogate s);
+
+}  // namespace aicdf
+
+using namespace aicdf;
+
+extern "C" aicdf_status aicdf_cir_level(const aicdf_sde_params *prm, aicdf_surrogate sur, int level, int kind,
+                                        uint64_t n_paths, uint64_t path_offset, uint64_t seed, uint32_t tag,
+                                        double *sums_dev, void *workspace_dev, size_t workspace_bytes,
+                                        int *status_dev, aicdf_stream_t stream) {
+  if (!prm || prm->model != AICDF_MODEL_CIR) return AICDF_ERR_ARG;
+  if (level < 0 || level > 12 || kind < AICDF_CIR_EXACT || kind > AICDF_CIR_DIFF_GAUSS) return AICDF_ERR_ARG;
+  if (n_paths == 0 || path_offset + n_paths < path_offset) return AICDF_ERR_ARG;
+  if (!sums_dev || ((uintptr_t)sums_dev % 8) || !status_dev) return AICDF_ERR_ARG;
+  if (!workspace_dev || ((uintptr_t)workspace_dev % 16) || workspace_bytes < aicdf_mlmc_level_workspace_bytes())
+    return AICDF_ERR_ARG;
+  if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL) return AICDF_ERR_ARG;
+  if (!(prm->kappa > 0.0) || !(prm->theta > 0.0) || !(prm->sigma > 0.0) || !(prm->T > 0.0) ||
+      !(prm->X0 >= 0.0) || !std::isfinite(prm->X0 + prm->T + prm->K + prm->discount))
+    return AICDF_ERR_DOMAIN;
+  const bool needs_sur = kind == AICDF_CIR_SURROGATE || kind == AICDF_CIR_DIFF;
+  CirArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const double nu = 4.0 * prm->kappa * prm->theta / (prm->sigma * prm->sigma);
+  if (needs_sur) {
+    if (!surrogate_ok(sur)) return AICDF_ERR_ARG;
+    if (std::fabs(surrogate_nu(sur) - nu) > 1e-9 * nu) return AICDF_ERR_DOMAIN;  // trained for another nu
+    a.params = surrogate_params(sur);
+  }
+  const double h = prm->T / std::ldexp(1.0, level);
+  a.keys = make_keys(seed);
+  a.n_paths = n_paths;
+  a.path_offset = path_offset;
+  a.tag = tag;
+  a.level = level;
+  a.kind = kind;
+  a.payoff = prm->payoff;
+  a.nu = nu;
+  a.e = std::exp(-prm->kappa * h);
+  a.c = prm->sigma * prm->sigma * (-std::expm1(-prm->kappa * h)) / (4.0 * prm->kappa);
+  a.X0 = (float)prm->X0;
+  a.K = (float)prm->K;
+  a.discount = (float)prm->discount;
+  CirFn k = select_cir(kind);
+  const uint64_t want = (n_paths + kCirThreads - 1) / kCirThreads;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
+      want, std::min<uint64_t>((uint64_t)sm_count() * resident_blocks((const void *)k, kCirThreads), 4096)));
+  double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  k<<<grid, kCirThreads, 0, st>>>(a, parts, status_dev);
+  launch_reduce_partials(parts, grid, (double)n_paths, sums_dev, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error((int)e);
+    return AICDF_ERR_CUDA;
+  }
+  return AICDF_OK;
+}

@@ -27,6 +27,8 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
@@ -92,6 +94,11 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double2 *__restri
     sums[1] = t.y;
     sums[2] = count;
   }
+}
+
+void launch_reduce_partials(const double2 *partials, int nparts, double count, double *sums,
+                            cudaStream_t st) {
+  k_reduce_partials<<<1, 256, 0, st>>>(partials, nparts, count, sums);
 }
 
 using LevelFn = void (*)(LevelArgs, double2 *);
@@ -186,6 +193,10 @@ int level_grid(uint64_t n_paths, const void *kernel) {
   const uint64_t cap = (uint64_t)sm_count() * resident_blocks(kernel, kLevelThreads);
   uint64_t g = std::min<uint64_t>(want, std::min<uint64_t>(cap, kMaxLevelBlocks));
   return (int)std::max<uint64_t>(g, 1);
+}
+
+int level_launch_grid(const LevelArgs &a) {
+  return level_grid(a.n_paths, (const void *)select_level_kernel(a.ps.kind, a.approx, a.ps.model));
 }
 
 aicdf_status launch_level(const LevelArgs &a, double *sums_dev, void *ws, cudaStream_t st) {
@@ -299,8 +310,7 @@ struct Plan {
   std::vector<int> slot_begin;   // n_terms + 1
   // workspace layout (byte offsets)
   size_t off_counter, off_items, off_specs, off_slots, off_counts, off_partials, bytes;
-  // device state this plan was uploaded to / captured with
-  void *uploaded_ws = nullptr;
+  // graph captured for this plan and the pointers it was captured with
   cudaGraphExec_t exec = nullptr;
   void *graph_ws = nullptr;
   double *graph_sums = nullptr;
@@ -323,6 +333,12 @@ struct aicdf_batch_s {
   uint64_t fingerprint;
   std::vector<Plan *> plans;
 };
+
+// Which plan's tile list currently sits in each workspace.  Plans (of one
+// batch or of several) may share a workspace, and each upload overwrites the
+// previous one, so a plan re-uploads whenever it is not the resident one.
+static std::mutex g_resident_mu;
+static std::map<void *, const Plan *> g_resident;
 
 constexpr uint32_t kBatchMagic = 0x42415443u;
 
@@ -451,6 +467,13 @@ extern "C" aicdf_status aicdf_batch_create(const aicdf_sde_params *sets, int n_s
 
 extern "C" void aicdf_batch_destroy(aicdf_batch b) {
   if (!batch_ok(b)) return;
+  {
+    std::lock_guard<std::mutex> lock(g_resident_mu);
+    for (auto it = g_resident.begin(); it != g_resident.end();) {
+      if (std::find(b->plans.begin(), b->plans.end(), it->second) != b->plans.end()) it = g_resident.erase(it);
+      else ++it;
+    }
+  }
   for (Plan *p : b->plans) {
     drop_graph(p);
     delete p;
@@ -505,8 +528,11 @@ extern "C" aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, 
   if (workspace_bytes < p->bytes) return AICDF_ERR_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
   char *w = (char *)workspace_dev;
-  if (p->uploaded_ws != workspace_dev) {
-    // the plan's tables live in the workspace; upload once per workspace
+  std::lock_guard<std::mutex> lock(g_resident_mu);
+  auto res = g_resident.find(workspace_dev);
+  if (res == g_resident.end() || res->second != p) {
+    // the plan's tables live in the workspace; upload them unless this plan's
+    // copy is the one currently there
     if (cudaMemcpyAsync(w + p->off_items, p->items.data(), sizeof(BatchItem) * p->items.size(),
                         cudaMemcpyHostToDevice, cs) != cudaSuccess ||
         cudaMemcpyAsync(w + p->off_specs, b->specs.data(), sizeof(PathSpec) * b->specs.size(),
@@ -517,9 +543,10 @@ extern "C" aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, 
                         cudaMemcpyHostToDevice, cs) != cudaSuccess ||
         cudaStreamSynchronize(cs) != cudaSuccess) {
       set_cuda_error((int)cudaGetLastError());
+      g_resident.erase(workspace_dev);
       return AICDF_ERR_CUDA;
     }
-    p->uploaded_ws = workspace_dev;
+    g_resident[workspace_dev] = p;
   }
   if (!p->exec || p->graph_ws != workspace_dev || p->graph_sums != sums_dev) {
     drop_graph(p);

@@ -223,5 +223,18 @@ aicdf_status make_path_spec(const aicdf_sde_params *prm, int level, int kind, ui
                             PathSpec *ps);
 // Copy an approximation table into the kernel-parameter layout (host).
 aicdf_status pack_table(aicdf_table approx, float *tab, int *ntab);
+// Validate the arguments of one level call and fill its kernel arguments (host).
+aicdf_status prepare_level_args(const aicdf_sde_params *prm, aicdf_table approx, int level,
+                                int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                uint32_t tag, LevelArgs *a);
+// Thread blocks launch_level will use for these arguments (= partial-sum slots).
+int level_launch_grid(const LevelArgs &a);
+// Launch the level kernel (one FP64 partial per block into ws) and the
+// fixed-order reduction into sums_dev (host).
+aicdf_status launch_level(const LevelArgs &a, double *sums_dev, void *ws, cudaStream_t st);
+// Launch the one-block fixed-order sum of per-block partials into
+// sums[0..2] = (sum Y, sum Y^2, count) (host).
+void launch_reduce_partials(const double2 *partials, int nparts, double count, double *sums,
+                            cudaStream_t st);
 
 }  // namespace aicdf

@@ -1,0 +1,570 @@
+// Learned surrogate for the non-central chi-squared inverse CDF (Section 5.1):
+// P~(U; lambda) ~ P_nu(U; nu / (lambda + nu)), so that
+// C~^{-1}_nu(U; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~.
+//
+// Kernels: batched evaluation, a fused forward + backward training step (the
+// three 64 x 64 products -- layer 2, dH1 = dZ2 W2 and dW2 = dZ2^T H1 -- on
+// the tensor cores in BF16 with FP32 accumulation), a fixed-order reduction
+// of the per-block gradients with an Adam update of FP32 master weights, and
+// the generation of exact training targets with the FP64 root finder.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <vector>
+
+#include "aicdf_internal.h"
+#include "device_common.cuh"
+#include "mlp_device.cuh"
+#include "ncx2.cuh"
+
+namespace aicdf {
+
+constexpr int kMlpThreads = 256;               // 8 warps = 256 samples per block
+constexpr int kMlpWarps = kMlpThreads / 32;
+constexpr int kGradSlots = kMlpParams;         // per-block partial: params + loss at kLossSlot
+constexpr int kLossSlot = kOffB3 + 1;          // 4417
+// dynamic shared-memory layout of the training kernel (16-byte aligned parts)
+constexpr size_t kTileBytes = sizeof(__nv_bfloat16) * 32 * kHPad;
+constexpr size_t kTrainOffH = (sizeof(MlpSmem) + 15) & ~(size_t)15;
+constexpr size_t kTrainOffDZ = kTrainOffH + kMlpWarps * kTileBytes;
+constexpr size_t kTrainOffW = kTrainOffDZ + kMlpWarps * kTileBytes;
+constexpr size_t kTrainSmem = kTrainOffW + sizeof(float) * kMlpWarps * (4 * kH + 2);
+
+// ------------------------------------------------------------------ evaluation
+__global__ void __launch_bounds__(kMlpThreads)
+    k_mlp_eval(const float *__restrict__ params, const float *__restrict__ u,
+               const float *__restrict__ lam, float *__restrict__ out, uint64_t n) {
+  __shared__ __align__(16) MlpSmem s;
+  __shared__ __align__(16) __nv_bfloat16 hs[kMlpWarps][32 * kHPad];
+  mlp_stage(params, s);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const uint64_t i = base + lane;
+    const bool ok = i < n;
+    const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
+    const float x1 = ok ? mlp_feature_lam(lam[i]) : 0.f;
+    const float y = mlp_forward_warp(s, x0, x1, hs[warp]);
+    if (ok) out[i] = y;
+  }
+}
+
+// ------------------------------------------------------------------ training
+// One block = 256 consecutive samples of the batch.  Writes the block's
+// gradient of sum_i (y_i - t_i)^2 * scale and its loss sum to partial[blockIdx].
+__global__ void __launch_bounds__(kMlpThreads)
+    k_mlp_train(const float *__restrict__ params, const float *__restrict__ u,
+                const float *__restrict__ lam, const float *__restrict__ target, uint64_t begin,
+                uint64_t count, float scale, float *__restrict__ partial) {
+  // dynamic shared memory (> 48 KB): MlpSmem | H1 tiles | dZ2 tiles | per-warp partials
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
+  auto hs = reinterpret_cast<__nv_bfloat16(*)[32 * kHPad]>(smem_raw + kTrainOffH);    // H1 (BF16)
+  auto dzs = reinterpret_cast<__nv_bfloat16(*)[32 * kHPad]>(smem_raw + kTrainOffDZ);  // dZ2 (BF16)
+  auto wpart = reinterpret_cast<float(*)[4 * kH + 2]>(smem_raw + kTrainOffW);          // gw3 gb2 gb1 gW1 ...
+  mlp_stage(params, s);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const uint64_t i = begin + (uint64_t)blockIdx.x * kMlpThreads + threadIdx.x;
+  const bool ok = (uint64_t)blockIdx.x * kMlpThreads + threadIdx.x < count;
+  const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
+  const float x1 = ok ? mlp_feature_lam(lam[i]) : 0.f;
+  const float tg = ok ? target[i] : 0.f;
+  __nv_bfloat16 *hw = hs[warp], *dw = dzs[warp];
+  // ---- forward
+  mlp_layer1(s, x0, x1, hw);
+  __syncwarp();
+  float acc[2][8][4];
+  mlp_layer2_mma(s, hw, acc);
+  float part[4];
+  mlp_layer3_partial(s, acc, part);  // acc now holds h2
+  const float y = mlp_gather_output(s, part);
+  const float err = ok ? y - tg : 0.f;
+  const float dy = 2.0f * err * scale;
+  // dy, x0, x1 of the four rows this lane holds in fragment layout
+  float dyr[4], x0r[4], x1r[4];
+#pragma unroll
+  for (int ri = 0; ri < 4; ++ri) {
+    const int r = 16 * (ri >> 1) + g + 8 * (ri & 1);
+    dyr[ri] = __shfl_sync(0xffffffffu, dy, r);
+    x0r[ri] = __shfl_sync(0xffffffffu, x0, r);
+    x1r[ri] = __shfl_sync(0xffffffffu, x1, r);
+  }
+  // ---- layer 3 and activation 2: gw3, gb2, dZ2
+  float gw3[8][2], gb2[8][2];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) gw3[nt][j] = gb2[nt][j] = 0.f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int ri = 2 * mt + hh;
+        const int r = 16 * mt + g + 8 * hh;
+        const int c = 8 * nt + 2 * t;
+        const float h0 = acc[mt][nt][2 * hh], h1 = acc[mt][nt][2 * hh + 1];
+        gw3[nt][0] = fmaf(dyr[ri], h0, gw3[nt][0]);
+        gw3[nt][1] = fmaf(dyr[ri], h1, gw3[nt][1]);
+        const float d0 = dyr[ri] * s.w3[c] * (1.f - h0 * h0);
+        const float d1 = dyr[ri] * s.w3[c + 1] * (1.f - h1 * h1);
+        gb2[nt][0] += d0;
+        gb2[nt][1] += d1;
+        *reinterpret_cast<uint32_t *>(dw + r * kHPad + c) = pack_bf16(d0, d1);
+      }
+    }
+  __syncwarp();
+  // ---- dH1 = dZ2 W2 (tensor cores), B fragments from W2 by transposed ldmatrix
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    uint32_t a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const __nv_bfloat16 *p = dw + (16 * mt + (lane & 15)) * kHPad + 16 * ks + (lane >> 4) * 8;
+      ldsm_x4(smem_addr(p), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+    }
+#pragma unroll
+    for (int np = 0; np < 4; ++np) {
+      const int nrow = 16 * ks + (lane & 7) + ((lane >> 3) & 1) * 8;   // W2 row = contraction index
+      const int kcol = 16 * np + (lane >> 4) * 8;                       // W2 col = output index
+      uint32_t b0, b1, b2, b3;
+      ldsm_x4_t(smem_addr(s.w2 + nrow * kHPad + kcol), b0, b1, b2, b3);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+        mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+      }
+    }
+  }
+  // ---- activation 1: dZ1 = dH1 (1 - h1^2); gb1, gW1
+  float gb1[8][2], gw1a[8][2], gw1b[8][2];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) gb1[nt][j] = gw1a[nt][j] = gw1b[nt][j] = 0.f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int ri = 2 * mt + hh;
+        const int r = 16 * mt + g + 8 * hh;
+        const int c = 8 * nt + 2 * t;
+        const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162 *>(hw + r * kHPad + c);
+        const float h0 = __bfloat162float(hv.x), h1 = __bfloat162float(hv.y);
+        const float d0 = acc[mt][nt][2 * hh] * (1.f - h0 * h0);
+        const float d1 = acc[mt][nt][2 * hh + 1] * (1.f - h1 * h1);
+        gb1[nt][0] += d0;
+        gb1[nt][1] += d1;
+        gw1a[nt][0] = fmaf(d0, x0r[ri], gw1a[nt][0]);
+        gw1a[nt][1] = fmaf(d1, x0r[ri], gw1a[nt][1]);
+        gw1b[nt][0] = fmaf(d0, x1r[ri], gw1b[nt][0]);
+        gw1b[nt][1] = fmaf(d1, x1r[ri], gw1b[nt][1]);
+      }
+  // reduce the per-lane column partials over the 8 groups (lanes with equal t)
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        gw3[nt][j] += __shfl_xor_sync(0xffffffffu, gw3[nt][j], o);
+        gb2[nt][j] += __shfl_xor_sync(0xffffffffu, gb2[nt][j], o);
+        gb1[nt][j] += __shfl_xor_sync(0xffffffffu, gb1[nt][j], o);
+        gw1a[nt][j] += __shfl_xor_sync(0xffffffffu, gw1a[nt][j], o);
+        gw1b[nt][j] += __shfl_xor_sync(0xffffffffu, gw1b[nt][j], o);
+      }
+  float* wp = wpart[warp];
+  if (g == 0) {
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int c = 8 * nt + 2 * t + j;
+        wp[c] = gw3[nt][j];
+        wp[kH + c] = gb2[nt][j];
+        wp[2 * kH + c] = gb1[nt][j];
+        // gW1 stored after the block-level reduction (two values per column)
+        wp[3 * kH + c] = gw1a[nt][j];
+      }
+  }
+  // gW1[c][1] and the loss need more room: reuse the dy row slots via shuffles
+  float loss = err * err, sdy = dy;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
+  }
+  if (lane == 0) {
+    wp[4 * kH] = sdy;
+    wp[4 * kH + 1] = loss;
+  }
+  __syncthreads();  // all warps' dZ2 and H1 tiles and partials are in shared memory
+  float *out = partial + (size_t)blockIdx.x * kGradSlots;
+  // fixed-order block sums of the small gradients
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
+    float a3 = 0.f, a2 = 0.f, a1 = 0.f, aw = 0.f;
+    for (int w = 0; w < kMlpWarps; ++w) {
+      a3 += wpart[w][c];
+      a2 += wpart[w][kH + c];
+      a1 += wpart[w][2 * kH + c];
+      aw += wpart[w][3 * kH + c];
+    }
+    out[kOffW3 + c] = a3;
+    out[kOffB2 + c] = a2;
+    out[kOffB1 + c] = a1;
+    out[kOffW1 + 2 * c] = aw;
+  }
+  if (threadIdx.x == 0) {
+    float a = 0.f, l = 0.f;
+    for (int w = 0; w < kMlpWarps; ++w) {
+      a += wpart[w][4 * kH];
+      l += wpart[w][4 * kH + 1];
+    }
+    out[kOffB3] = a;
+    out[kLossSlot] = l;
+  }
+  __syncthreads();  // wpart reused below for gW1[c][1]
+  if (g == 0) {
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) wpart[warp][8 * nt + 2 * t + j] = gw1b[nt][j];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
+    float aw = 0.f;
+    for (int w = 0; w < kMlpWarps; ++w) aw += wpart[w][c];
+    out[kOffW1 + 2 * c + 1] = aw;
+  }
+  // ---- dW2[n][k] = sum_s dZ2[s][n] H1[s][k] over the block's 256 samples
+  // warp w: n rows 16 (w>>1) .. +15, k cols 32 (w&1) .. +31 (4 n-tiles)
+  {
+    const int mtn = warp >> 1, kb = 32 * (warp & 1);
+    float d[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[q][e] = 0.f;
+    for (int ks = 0; ks < kMlpThreads / 16; ++ks) {
+      const __nv_bfloat16 *dt = dzs[ks >> 1] + (ks & 1) * 16 * kHPad;   // 16 samples
+      const __nv_bfloat16 *ht = hs[ks >> 1] + (ks & 1) * 16 * kHPad;
+      uint32_t a0, a1, a2, a3;
+      {
+        const int srow = (lane & 7) + ((lane >> 4) << 3);
+        const int ncol = 16 * mtn + ((lane >> 3) & 1) * 8;
+        ldsm_x4_t(smem_addr(dt + srow * kHPad + ncol), a0, a1, a2, a3);
+      }
+#pragma unroll
+      for (int p2 = 0; p2 < 2; ++p2) {
+        const int srow = (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int kcol = kb + 16 * p2 + (lane >> 4) * 8;
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(smem_addr(ht + srow * kHPad + kcol), b0, b1, b2, b3);
+        mma_bf16(d[2 * p2], a0, a1, a2, a3, b0, b1);
+        mma_bf16(d[2 * p2 + 1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n0 = 16 * mtn + g, k0 = kb + 8 * q + 2 * t;
+      out[kOffW2 + n0 * kH + k0] = d[q][0];
+      out[kOffW2 + n0 * kH + k0 + 1] = d[q][1];
+      out[kOffW2 + (n0 + 8) * kH + k0] = d[q][2];
+      out[kOffW2 + (n0 + 8) * kH + k0 + 1] = d[q][3];
+    }
+  }
+}
+
+// Sum per-block gradients in block order and take one Adam step.
+__global__ void k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2,
+                           const float *__restrict__ partial, int nblocks, float lr, float b1,
+                           float b2, float eps, float bc1, float bc2, float *__restrict__ loss_out,
+                           float loss_scale) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && loss_out) {
+    float l = 0.f;
+    for (int b = 0; b < nblocks; ++b) l += partial[(size_t)b * kGradSlots + kLossSlot];
+    *loss_out = l * loss_scale;
+  }
+  if (p > kOffB3) return;
+  float gsum = 0.f;
+  for (int b = 0; b < nblocks; ++b) gsum += partial[(size_t)b * kGradSlots + p];
+  const float m = b1 * m1[p] + (1.f - b1) * gsum;
+  const float v = b2 * m2[p] + (1.f - b2) * gsum * gsum;
+  m1[p] = m;
+  m2[p] = v;
+  params[p] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+// Just the gradient (summed over blocks), for the gradient check.
+__global__ void k_mlp_grad_sum(const float *__restrict__ partial, int nblocks, float *__restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > kLossSlot) return;
+  float gsum = 0.f;
+  for (int b = 0; b < nblocks; ++b) gsum += partial[(size_t)b * kGradSlots + p];
+  grad[p] = gsum;
+}
+
+// ------------------------------------------------------------------ exact targets
+// Sample i: u from word 0 and ln(lambda) ~ U(lo, hi) from word 1 of Philox
+// block i (counter (i mod 2^32, i >> 32, 0, tag)); target
+// P = (C^{-1}_nu(u; lambda) - lambda - nu) / (2 sqrt(lambda + nu)).
+__global__ void k_ncx2_targets(PhiloxKeys keys, uint32_t tag, double nu, float loglam_lo,
+                               float loglam_hi, uint64_t n, float *__restrict__ u_out,
+                               float *__restrict__ lam_out, float *__restrict__ p_out,
+                               int *__restrict__ status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int st = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint4 r = philox(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, tag), keys);
+    const float u = u01(r.x);
+    const float ll = loglam_lo + (loglam_hi - loglam_lo) * u01(r.y);
+    const float lam = __expf(ll);
+    const double q = ncx2_ppf((double)u, nu, (double)lam, &st);
+    const double h = (double)lam + nu;
+    u_out[i] = u;
+    lam_out[i] = lam;
+    p_out[i] = (float)((q - h) / (2.0 * sqrt(h)));
+  }
+  if (st) atomicOr(status, st);
+}
+
+// Exact quantiles for caller arrays (FP64 arithmetic, FP32 in/out for u).
+__global__ void k_ncx2_ppf(const float *__restrict__ u, const double *__restrict__ lam, double nu,
+                           uint64_t n, double *__restrict__ out, int *__restrict__ status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int st = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = ncx2_ppf((double)u[i], nu, lam[i], &st);
+  if (st) atomicOr(status, st);
+}
+
+}  // namespace aicdf
+
+using namespace aicdf;
+
+// ------------------------------------------------------------------ handle
+struct aicdf_surrogate_s {
+  uint32_t magic;
+  int device;
+  double nu;
+  float *params = nullptr;   // FP32 master weights [kMlpParams]
+  float *m1 = nullptr, *m2 = nullptr;
+  float *partial = nullptr;  // per-block gradient partials
+  int partial_blocks = 0;
+  int *status = nullptr;
+  long long step = 0;
+};
+
+constexpr uint32_t kSurrogateMagic = 0x53555247u;
+
+static bool sur_ok(const aicdf_surrogate_s *s) { return s && s->magic == kSurrogateMagic; }
+
+static aicdf_status cuda_fail() {
+  set_cuda_error((int)cudaGetLastError());
+  return AICDF_ERR_CUDA;
+}
+
+extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_surrogate *out) {
+  if (!out || !(nu > 0.0) || !std::isfinite(nu)) return AICDF_ERR_ARG;
+  *out = nullptr;
+  aicdf_surrogate_s *s = new (std::nothrow) aicdf_surrogate_s();
+  if (!s) return AICDF_ERR_NOMEM;
+  s->magic = kSurrogateMagic;
+  s->nu = nu;
+  cudaGetDevice(&s->device);
+  if (cudaMalloc(&s->params, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMalloc(&s->m1, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMalloc(&s->m2, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMalloc(&s->status, sizeof(int)) != cudaSuccess) {
+    aicdf_surrogate_destroy(s);
+    return cuda_fail();
+  }
+  // Glorot-uniform weights, zero biases (host RNG, seeded)
+  std::vector<float> p(kMlpParams, 0.f);
+  std::mt19937_64 rng(seed);
+  auto uni = [&](double lim) {
+    return (float)(lim * (2.0 * std::uniform_real_distribution<double>(0.0, 1.0)(rng) - 1.0));
+  };
+  for (int i = 0; i < 2 * kH; ++i) p[kOffW1 + i] = uni(std::sqrt(6.0 / (2 + kH)) * 2.0);
+  for (int i = 0; i < kH * kH; ++i) p[kOffW2 + i] = uni(std::sqrt(6.0 / (2 * kH)));
+  for (int i = 0; i < kH; ++i) p[kOffW3 + i] = uni(std::sqrt(6.0 / (kH + 1)));
+  for (int i = 0; i < kH; ++i) p[kOffB1 + i] = uni(1.0);
+  if (cudaMemcpy(s->params, p.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    aicdf_surrogate_destroy(s);
+    return cuda_fail();
+  }
+  *out = s;
+  return AICDF_OK;
+}
+
+extern "C" void aicdf_surrogate_destroy(aicdf_surrogate s) {
+  if (!sur_ok(s)) return;
+  cudaFree(s->params);
+  cudaFree(s->m1);
+  cudaFree(s->m2);
+  cudaFree(s->partial);
+  cudaFree(s->status);
+  s->magic = 0;
+  delete s;
+}
+
+extern "C" aicdf_status aicdf_surrogate_get_params(aicdf_surrogate s, float *host, int cap) {
+  if (!sur_ok(s) || !host || cap < kMlpParams) return AICDF_ERR_ARG;
+  if (cudaMemcpy(host, s->params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail();
+  return AICDF_OK;
+}
+
+extern "C" aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const float *host, int n) {
+  if (!sur_ok(s) || !host || n < kOffB3 + 1 || n > kMlpParams) return AICDF_ERR_ARG;
+  if (cudaMemcpy(s->params, host, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess)
+    return cuda_fail();
+  s->step = 0;
+  return AICDF_OK;
+}
+
+extern "C" int aicdf_surrogate_param_count(void) { return kOffB3 + 1; }
+
+namespace aicdf {
+const float *surrogate_params(aicdf_surrogate s) { return sur_ok(s) ? s->params : nullptr; }
+double surrogate_nu(aicdf_surrogate s) { return sur_ok(s) ? s->nu : 0.0; }
+bool surrogate_ok(aicdf_surrogate s) { return sur_ok(s); }
+}  // namespace aicdf
+
+extern "C" aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                             size_t n, float *p_out_dev, aicdf_stream_t stream) {
+  if (!sur_ok(s)) return AICDF_ERR_ARG;
+  if (n == 0) return AICDF_OK;
+  if (!u_dev || !lam_dev || !p_out_dev) return AICDF_ERR_ARG;
+  const int cap = sm_count() * resident_blocks((const void *)k_mlp_eval, kMlpThreads);
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + kMlpThreads - 1) / kMlpThreads, cap));
+  k_mlp_eval<<<grid, kMlpThreads, 0, (cudaStream_t)stream>>>(s->params, u_dev, lam_dev, p_out_dev, n);
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+static aicdf_status ensure_partials(aicdf_surrogate_s *s, int blocks) {
+  if (s->partial_blocks >= blocks) return AICDF_OK;
+  cudaFree(s->partial);
+  s->partial = nullptr;
+  s->partial_blocks = 0;
+  if (cudaMalloc(&s->partial, sizeof(float) * (size_t)kGradSlots * blocks) != cudaSuccess) return cuda_fail();
+  s->partial_blocks = blocks;
+  return AICDF_OK;
+}
+
+static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, const float *lam,
+                                      const float *target, uint64_t begin, uint64_t count,
+                                      cudaStream_t st, int *blocks_out) {
+  const int blocks = (int)((count + kMlpThreads - 1) / kMlpThreads);
+  aicdf_status rc = ensure_partials(s, blocks);
+  if (rc != AICDF_OK) return rc;
+  static bool smem_set = false;  // opt in to > 48 KB of dynamic shared memory once
+  if (!smem_set) {
+    if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem) !=
+        cudaSuccess)
+      return cuda_fail();
+    smem_set = true;
+  }
+  k_mlp_train<<<blocks, kMlpThreads, kTrainSmem, st>>>(s->params, u, lam, target, begin, count,
+                                                       1.0f / (float)count, s->partial);
+  *blocks_out = blocks;
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+extern "C" aicdf_status aicdf_surrogate_grad(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                             const float *target_dev, size_t n, float *grad_dev,
+                                             aicdf_stream_t stream) {
+  if (!sur_ok(s) || !u_dev || !lam_dev || !target_dev || !grad_dev || n == 0 || n > (1u << 24))
+    return AICDF_ERR_ARG;
+  int blocks = 0;
+  aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, (cudaStream_t)stream, &blocks);
+  if (rc != AICDF_OK) return rc;
+  k_mlp_grad_sum<<<(kLossSlot + 256) / 256, 256, 0, (cudaStream_t)stream>>>(s->partial, blocks, grad_dev);
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+extern "C" aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const float *u_dev,
+                                                   const float *lam_dev, const float *target_dev,
+                                                   size_t n, float lr, float *loss_dev,
+                                                   aicdf_stream_t stream) {
+  if (!sur_ok(s) || !u_dev || !lam_dev || !target_dev || n == 0 || n > (1u << 24) || !(lr > 0.f))
+    return AICDF_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int blocks = 0;
+  aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, st, &blocks);
+  if (rc != AICDF_OK) return rc;
+  s->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.f - (float)std::pow((double)b1, (double)s->step);
+  const float bc2 = 1.f - (float)std::pow((double)b2, (double)s->step);
+  k_mlp_adam<<<(kOffB3 + 256) / 256, 256, 0, st>>>(s->params, s->m1, s->m2, s->partial, blocks, lr, b1,
+                                                   b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n);
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+extern "C" aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
+                                              const float *target_dev, size_t n, size_t batch,
+                                              int epochs, float lr, float lr_final, float *loss_dev,
+                                              aicdf_stream_t stream) {
+  if (!sur_ok(s) || !u_dev || !lam_dev || !target_dev || n == 0 || batch == 0 || batch > (1u << 24) ||
+      epochs <= 0 || !(lr > 0.f) || !(lr_final > 0.f))
+    return AICDF_ERR_ARG;
+  const size_t steps_per_epoch = n / batch;
+  if (steps_per_epoch == 0) return AICDF_ERR_ARG;
+  const size_t total = steps_per_epoch * (size_t)epochs;
+  size_t k = 0;
+  for (int e = 0; e < epochs; ++e)
+    for (size_t b = 0; b < steps_per_epoch; ++b, ++k) {
+      // geometric decay of the step size from lr to lr_final
+      const float l = lr * std::pow(lr_final / lr, (float)k / (float)std::max<size_t>(total - 1, 1));
+      const bool last = (k + 1 == total);
+      aicdf_status rc = aicdf_surrogate_train_step(s, u_dev + b * batch, lam_dev + b * batch,
+                                                   target_dev + b * batch, batch, l,
+                                                   last ? loss_dev : nullptr, stream);
+      if (rc != AICDF_OK) return rc;
+    }
+  return AICDF_OK;
+}
+
+extern "C" aicdf_status aicdf_ncx2_targets(double nu, float loglam_lo, float loglam_hi, uint64_t seed,
+                                           uint32_t tag, size_t n, float *u_dev, float *lam_dev,
+                                           float *p_dev, int *status_dev, aicdf_stream_t stream) {
+  if (!(nu > 0.0) || !(loglam_hi >= loglam_lo) || !u_dev || !lam_dev || !p_dev || !status_dev)
+    return AICDF_ERR_ARG;
+  if (n == 0) return AICDF_OK;
+  const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sm_count() * 8);
+  k_ncx2_targets<<<grid, 256, 0, (cudaStream_t)stream>>>(make_keys(seed), tag, nu, loglam_lo, loglam_hi,
+                                                          n, u_dev, lam_dev, p_dev, status_dev);
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+extern "C" aicdf_status aicdf_ncx2_ppf(const float *u_dev, const double *lam_dev, double nu, size_t n,
+                                       double *out_dev, int *status_dev, aicdf_stream_t stream) {
+  if (!(nu > 0.0) || !u_dev || !lam_dev || !out_dev || !status_dev) return AICDF_ERR_ARG;
+  if (n == 0) return AICDF_OK;
+  const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sm_count() * 8);
+  k_ncx2_ppf<<<grid, 256, 0, (cudaStream_t)stream>>>(u_dev, lam_dev, nu, n, out_dev, status_dev);
+  return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}

@@ -1,0 +1,198 @@
+// Small MLP surrogate y = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3  (2 -> 64 -> 64 -> 1)
+// for the rescaled non-central chi-squared quantile P_nu(U; y) of Section 5.1.
+//
+// One warp evaluates 32 samples (lane = sample).  Layers 1 and 3 and the
+// activations run on the FP32 pipes; the 64 x 64 layer runs on the tensor
+// cores as BF16 mma.sync m16n8k16 with FP32 accumulation: the warp's
+// activations H (32 x 64, BF16) go through shared memory into A fragments
+// (ldmatrix), W2 (BF16, [out][in]) supplies the B fragments, giving
+// 2 m-tiles x 8 n-tiles x 4 k-steps = 64 MMAs per 32 samples.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+namespace aicdf {
+
+constexpr int kH = 64;           // hidden width
+constexpr int kHPad = kH + 8;    // row pitch (BF16 elements) of smem tiles: avoids bank conflicts
+constexpr int kMlpParams = 4420; // FP32 parameter blob (4417 used)
+// offsets into the FP32 parameter blob
+constexpr int kOffW1 = 0;        // [64][2]
+constexpr int kOffB1 = 128;      // [64]
+constexpr int kOffW2 = 192;      // [64 out][64 in]
+constexpr int kOffB2 = 192 + 4096;
+constexpr int kOffW3 = kOffB2 + 64;
+constexpr int kOffB3 = kOffW3 + 64;
+
+// Parameters staged in shared memory for one block.
+struct MlpSmem {
+  __nv_bfloat16 w2[kH * kHPad];  // W2 [out n][in k], k contiguous
+  float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
+};
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Input features: x0 = s(u)/3 with the tail stretch s(u) = sign(u - 1/2)
+// sqrt(-2 ln(2 min(u, 1-u))) (smooth, monotone, s(1/2) = 0), x1 = ln(lambda)/4
+// clamped to the trained range [-1, 1].
+__device__ __forceinline__ float mlp_feature_u(float u) {
+  const float v = fminf(u, 1.0f - u);
+  const float s = sqrtf(fmaxf(-2.0f * __logf(2.0f * v), 0.0f));
+  return (u < 0.5f ? -s : s) * (1.0f / 3.0f);
+}
+__device__ __forceinline__ float mlp_feature_lam(float lam) {
+  return fminf(fmaxf(__logf(fmaxf(lam, 1e-30f)) * 0.25f, -1.0f), 1.0f);
+}
+
+// Stage FP32 parameters (global) into shared memory; W2 rounded to BF16.
+__device__ __forceinline__ void mlp_stage(const float *__restrict__ p, MlpSmem &s) {
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const int n = i / kH, k = i % kH;
+    s.w2[n * kHPad + k] = __float2bfloat16_rn(p[kOffW2 + i]);
+  }
+  for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) s.w1[i] = p[kOffW1 + i];
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    s.b1[i] = p[kOffB1 + i];
+    s.b2[i] = p[kOffB2 + i];
+    s.w3[i] = p[kOffW3 + i];
+  }
+  if (threadIdx.x == 0) s.b3 = p[kOffB3];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Layer 1 for this lane's sample: writes h1 (BF16) into row `lane` of the
+// warp's tile hs [32][kHPad].  Returns nothing; caller __syncwarp()s.
+__device__ __forceinline__ void mlp_layer1(const MlpSmem &s, float x0, float x1, __nv_bfloat16 *hs) {
+  const int lane = threadIdx.x & 31;
+  uint32_t *row = reinterpret_cast<uint32_t *>(hs + lane * kHPad);
+#pragma unroll 8
+  for (int k = 0; k < kH; k += 2) {
+    const float a = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
+    const float b = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
+    row[k >> 1] = pack_bf16(a, b);
+  }
+}
+
+// z2 = H W2^T for the warp's 32 samples: acc[mt][nt][4] in m16n8 D-fragment
+// layout (rows g, g+8 of m-tile mt; cols 2t, 2t+1 of n-tile nt; g = lane/4,
+// t = lane%4).
+__device__ __forceinline__ void mlp_layer2_mma(const MlpSmem &s, const __nv_bfloat16 *hs,
+                                               float (&acc)[2][8][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    uint32_t a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      // matrices: rows 0-7 / 8-15 x cols 0-7 / 8-15 of the 16x16 A tile
+      const __nv_bfloat16 *p = hs + (16 * mt + (lane & 15)) * kHPad + 16 * ks + (lane >> 4) * 8;
+      ldsm_x4(smem_addr(p), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+    }
+#pragma unroll
+    for (int np = 0; np < 4; ++np) {
+      // two n-tiles (16 outputs) x 16 k: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+      const int n = 16 * np + (lane & 7) + ((lane >> 4) << 3);
+      const int k = 16 * ks + ((lane >> 3) & 1) * 8;
+      uint32_t b0, b1, b2, b3;
+      ldsm_x4(smem_addr(s.w2 + n * kHPad + k), b0, b1, b2, b3);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+        mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+      }
+    }
+  }
+}
+
+// h2 = tanh(z2 + b2) in place; returns this lane's partial dot products with
+// w3 for its four rows r = 16 mt + g + 8 h (index 2 mt + h).
+__device__ __forceinline__ void mlp_layer3_partial(const MlpSmem &s, float (&acc)[2][8][4], float (&part)[4]) {
+  const int t = threadIdx.x & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) part[i] = 0.f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = 8 * nt + 2 * t + (i & 1);
+        const float h = tanh_fast(acc[mt][nt][i] + s.b2[c]);
+        acc[mt][nt][i] = h;
+        part[2 * mt + (i >> 1)] = fmaf(s.w3[c], h, part[2 * mt + (i >> 1)]);
+      }
+}
+
+// Sum the partial dots over the 4 lanes of a group and hand each lane the
+// output of its own sample.
+__device__ __forceinline__ float mlp_gather_output(const MlpSmem &s, float (&part)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    part[i] += __shfl_xor_sync(0xffffffffu, part[i], 1);
+    part[i] += __shfl_xor_sync(0xffffffffu, part[i], 2);
+  }
+  // sample `lane` sits in m-tile lane>>4, half (lane>>3)&1, group lane&7
+  const int src = (lane & 7) << 2;
+  const float v0 = __shfl_sync(0xffffffffu, part[0], src);
+  const float v1 = __shfl_sync(0xffffffffu, part[1], src);
+  const float v2 = __shfl_sync(0xffffffffu, part[2], src);
+  const float v3 = __shfl_sync(0xffffffffu, part[3], src);
+  const int idx = 2 * (lane >> 4) + ((lane >> 3) & 1);
+  const float v = idx == 0 ? v0 : idx == 1 ? v1 : idx == 2 ? v2 : v3;
+  return v + s.b3;
+}
+
+// Full forward for the warp: lane's sample (x0, x1) -> output.  hs: this
+// warp's [32][kHPad] BF16 tile in shared memory.  All 32 lanes must call.
+__device__ __forceinline__ float mlp_forward_warp(const MlpSmem &s, float x0, float x1, __nv_bfloat16 *hs) {
+  mlp_layer1(s, x0, x1, hs);
+  __syncwarp();
+  float acc[2][8][4];
+  mlp_layer2_mma(s, hs, acc);
+  float part[4];
+  mlp_layer3_partial(s, acc, part);
+  const float y = mlp_gather_output(s, part);
+  __syncwarp();  // hs may be overwritten by the next call
+  return y;
+}
+
+}  // namespace aicdf

@@ -1,0 +1,191 @@
+// Exact non-central chi-squared quantile on the GPU, FP64 (Section 5).
+//
+// C_nu(x; lambda) = sum_j Pois(j; lambda/2) P(nu/2 + j, x/2)   (Poisson mixture of
+// central chi-squared CDFs), and the upper tail Q = 1 - C the same with the
+// regularised upper gamma Q(s, y).  With y = x/2, s_j = nu/2 + j and
+// g_j = y^{s_j} e^-y / Gamma(s_j + 1):
+//   P(s_j - 1, y) = P(s_j, y) + g_{j-1},   g_{j-1} = g_j s_j / y     (downward, adds)
+//   Q(s_j + 1, y) = Q(s_j, y) + g_j,       g_{j+1} = g_j y / (s_j + 1) (upward, adds)
+// so the lower CDF is summed downward from the top of the Poisson range and
+// the upper tail upward from its bottom: every recurrence step adds positive
+// terms.  Only one incomplete gamma is evaluated directly (series below
+// s + 1, continued fraction above, each giving the small one of P and Q).  The
+// density is sum_j p_j g_{j-1} / 2.  The quantile solves C = u for u <= 1/2 and
+// Q = 1 - u above (1 - u is exact for FP32 u >= 1/2), by Newton steps kept
+// inside a bracket, started from Sankaran's approximation (Section 5.1).
+// Every loop has a fixed cap; hitting one sets the returned status bit.
+#pragma once
+
+#include <cstdint>
+
+namespace aicdf {
+
+constexpr int kNcx2NoConverge = 1;
+
+// log Gamma(s), s > 0: shift to s >= 12 (one log of the product), then the
+// Stirling series through the s^-11 term (truncation error < 1e-16).
+__device__ __forceinline__ double lgamma_pos(double s) {
+  double prod = 1.0;
+  while (s < 12.0) {  // at most 12 iterations for s > 0
+    prod *= s;
+    s += 1.0;
+  }
+  const double r = 1.0 / s, r2 = r * r;
+  const double series =
+      r * (1.0 / 12.0 -
+           r2 * (1.0 / 360.0 -
+                 r2 * (1.0 / 1260.0 - r2 * (1.0 / 1680.0 - r2 * (1.0 / 1188.0 - r2 * (691.0 / 360360.0))))));
+  return (s - 0.5) * log(s) - s + 0.91893853320467274178 + series - log(prod);
+}
+
+// P(s, y), Q(s, y) and g(s) = y^s e^-y / Gamma(s+1): the series for y < s + 1
+// (gives P), the continued fraction for Q otherwise (modified Lentz).
+__device__ __forceinline__ void gamma_pq(double s, double y, double *P, double *Q, double *g, int *status) {
+  const double lg = s * log(y) - y - lgamma_pos(s + 1.0);
+  *g = exp(lg);
+  if (y < s + 1.0) {
+    double term = 1.0, sum = 1.0, d = s;
+    int it = 0;
+    for (; it < 2000; ++it) {
+      d += 1.0;
+      term *= y / d;
+      sum += term;
+      if (term < sum * 1e-17) break;
+    }
+    if (it == 2000) *status |= kNcx2NoConverge;
+    *P = fmin(*g * sum, 1.0);
+    *Q = 1.0 - *P;
+    return;
+  }
+  const double tiny = 1e-300;
+  double b = y + 1.0 - s, c = 1.0 / tiny, dd = 1.0 / b, h = dd;
+  int i = 1;
+  for (; i < 2000; ++i) {
+    const double an = -i * (i - s);
+    b += 2.0;
+    dd = an * dd + b;
+    if (fabs(dd) < tiny) dd = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    dd = 1.0 / dd;
+    const double del = dd * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  if (i == 2000) *status |= kNcx2NoConverge;
+  *Q = fmin((*g) * s * h, 1.0);  // e^-y y^s / Gamma(s) = g s
+  *P = 1.0 - *Q;
+}
+
+// Lower CDF (upper = false) or upper tail (upper = true) of chi'^2_nu(lambda)
+// at x, and the density.
+__device__ __forceinline__ void ncx2_tail_pdf(double x, double nu, double lam, bool upper, double *T, double *f,
+                                              int *status) {
+  if (x <= 0.0) {
+    *T = upper ? 1.0 : 0.0;
+    *f = 0.0;
+    return;
+  }
+  const double y = 0.5 * x, a = 0.5 * nu, m = 0.5 * lam;
+  // Poisson range [jlo, jhi] holding all but ~1e-20 of the mass, walked from the mode
+  int jlo = 0, jhi = 0;
+  double plo = 1.0, phi = 1.0;
+  if (m > 0.0) {
+    const int j0 = (int)floor(m);
+    const double p0 = exp(-m + j0 * log(m) - lgamma_pos(j0 + 1.0));
+    double p = p0;
+    int j = j0, it = 0;
+    for (; j > 0 && p > 1e-20 && it < 100000; ++it) {
+      p *= (double)j / m;
+      --j;
+    }
+    if (it == 100000) *status |= kNcx2NoConverge;
+    jlo = j;
+    plo = p;
+    p = p0;
+    j = j0;
+    for (it = 0; p > 1e-20 && it < 100000; ++it) {
+      p *= m / (double)(j + 1);
+      ++j;
+    }
+    if (it == 100000) *status |= kNcx2NoConverge;
+    jhi = j;
+    phi = p;
+  }
+  double acc = 0.0, dens = 0.0;
+  if (!upper) {
+    double P, Q, g;
+    gamma_pq(a + jhi, y, &P, &Q, &g, status);
+    double p = phi;
+    acc = p * P;
+    dens = p * g * (a + jhi) / (2.0 * y);
+    for (int j = jhi; j > jlo; --j) {
+      g = g * (a + j) / y;  // g_{j-1}
+      P += g;               // P(s_{j-1})
+      p *= (double)j / m;   // p_{j-1}
+      acc += p * P;
+      dens += p * g * (a + j - 1) / (2.0 * y);
+    }
+  } else {
+    double P, Q, g;
+    gamma_pq(a + jlo, y, &P, &Q, &g, status);
+    double p = plo;
+    acc = p * Q;
+    dens = p * g * (a + jlo) / (2.0 * y);
+    for (int j = jlo; j < jhi; ++j) {
+      Q += g;                    // Q(s_{j+1})
+      g = g * y / (a + j + 1);   // g_{j+1}
+      p *= m / (double)(j + 1);  // p_{j+1}
+      acc += p * Q;
+      dens += p * g * (a + j + 1) / (2.0 * y);
+    }
+  }
+  *T = fmin(acc, 1.0);
+  *f = dens;
+}
+
+// Sankaran's approximation of the quantile (Section 5.1; with sqrt(2 c2) in
+// the normal term), used as the start.
+__device__ __forceinline__ double ncx2_sankaran(double u, double nu, double lam) {
+  const double k = nu, h0 = k + lam, h2 = k + 2.0 * lam;
+  const double c1 = 1.0 - (2.0 / 3.0) * h0 * (k + 3.0 * lam) / (h2 * h2);
+  const double c2 = h2 / (h0 * h0);
+  const double c3 = (c1 - 1.0) * (1.0 - 3.0 * c1);
+  const double z = normcdfinv(u);
+  const double base = 1.0 + c1 * c2 * (c1 - 1.0 + 0.5 * (2.0 - c1) * c2 * c3) +
+                      c1 * sqrt(2.0 * c2) * (1.0 + 0.5 * c2 * c3) * z;
+  if (!(base > 0.0) || !(fabs(c1) > 1e-3)) return h0;  // outside its range: start at the mean
+  const double r = h0 * pow(base, 1.0 / c1);
+  return (r > 0.0 && isfinite(r)) ? r : h0;
+}
+
+// Quantile C^{-1}_nu(u; lambda) for 0 < u < 1 (FP64).
+__device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int *status) {
+  if (!(u > 0.0)) return 0.0;
+  if (!(u < 1.0)) return __longlong_as_double(0x7ff0000000000000ll);
+  const bool upper = u > 0.5;
+  const double target = upper ? 1.0 - u : u;
+  double T, f;
+  double x = ncx2_sankaran(u, nu, lam);
+  double lo = 0.0, hi = -1.0;  // hi < 0: no upper bound yet
+  int it = 0;
+  for (; it < 100; ++it) {
+    ncx2_tail_pdf(x, nu, lam, upper, &T, &f, status);
+    const double r = upper ? target - T : T - target;  // = C(x) - u, > 0 when x is too large
+    if (r > 0.0) hi = x;
+    else lo = x;
+    double xn = (f > 0.0) ? x - r / f : -1.0;
+    if (hi < 0.0) {
+      if (!(xn > lo)) xn = 2.0 * x + 1.0;
+    } else if (!(xn > lo && xn < hi)) {
+      xn = 0.5 * (lo + hi);
+    }
+    const double dx = fabs(xn - x);
+    x = xn;
+    if (dx <= 1e-13 * x || (hi > 0.0 && hi - lo <= 1e-14 * hi)) break;
+  }
+  if (it == 100) *status |= kNcx2NoConverge;
+  return x;
+}
+
+}  // namespace aicdf

@@ -121,50 +121,62 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
   constexpr int E = OutVec<OUT>::kElems;
+  // Each warp takes chunks of 2 x 32 consecutive 16-byte vectors; lane L
+  // computes vectors L and L + 32 of the chunk, so its two independent
+  // Philox chains overlap and both stores stay fully coalesced.
+  constexpr int VECS = 2;
   const uint64_t nvec = (a.n + E - 1) / E;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t nchunk = (nvec + 32 * VECS - 1) / (32 * VECS);
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   // warp-uniform loop: every lane runs every iteration (shuffles need all 32)
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nvec;
-       base += stride) {
-    const uint64_t v = base + lane;
-    const uint64_t e0 = v * E;
-    float z[E];
-    if constexpr (SRC == SRC_PHILOX) {
+  for (uint64_t chunk = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk;
+       chunk += warps) {
+    float z[VECS][E];
 #pragma unroll
-      for (int h = 0; h < E / 4; ++h) {
-        const uint64_t j = (a.offset >> 2) + v * (E / 4) + h;
-        const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
-        z[4 * h + 0] = f.word(r.x);
-        z[4 * h + 1] = f.word(r.y);
-        z[4 * h + 2] = f.word(r.z);
-        z[4 * h + 3] = f.word(r.w);
-      }
-    } else {
+    for (int hv = 0; hv < VECS; ++hv) {
+      const uint64_t v = chunk * (32 * VECS) + 32 * hv + lane;
+      const uint64_t e0 = v * E;
+      if constexpr (SRC == SRC_PHILOX) {
 #pragma unroll
-      for (int h = 0; h < E / 4; ++h) {
-        float4 uu = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
-        if (e0 + 4 * h + 3 < a.n) {
-          uu = __ldcs(reinterpret_cast<const float4 *>(a.u + e0 + 4 * h));
-        } else {
-          if (e0 + 4 * h + 0 < a.n) uu.x = a.u[e0 + 4 * h + 0];
-          if (e0 + 4 * h + 1 < a.n) uu.y = a.u[e0 + 4 * h + 1];
-          if (e0 + 4 * h + 2 < a.n) uu.z = a.u[e0 + 4 * h + 2];
+        for (int h = 0; h < E / 4; ++h) {
+          const uint64_t j = (a.offset >> 2) + v * (E / 4) + h;
+          const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
+          z[hv][4 * h + 0] = f.word(r.x);
+          z[hv][4 * h + 1] = f.word(r.y);
+          z[hv][4 * h + 2] = f.word(r.z);
+          z[hv][4 * h + 3] = f.word(r.w);
         }
-        const float us[4] = {uu.x, uu.y, uu.z, uu.w};
+      } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          float y = f(us[t]);
-          z[4 * h + t] = in_unit(us[t]) ? y : __int_as_float(0x7fc00000);
+        for (int h = 0; h < E / 4; ++h) {
+          float4 uu = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
+          if (e0 + 4 * h + 3 < a.n) {
+            uu = __ldcs(reinterpret_cast<const float4 *>(a.u + e0 + 4 * h));
+          } else {
+            if (e0 + 4 * h + 0 < a.n) uu.x = a.u[e0 + 4 * h + 0];
+            if (e0 + 4 * h + 1 < a.n) uu.y = a.u[e0 + 4 * h + 1];
+            if (e0 + 4 * h + 2 < a.n) uu.z = a.u[e0 + 4 * h + 2];
+          }
+          const float us[4] = {uu.x, uu.y, uu.z, uu.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            float y = f(us[t]);
+            z[hv][4 * h + t] = in_unit(us[t]) ? y : __int_as_float(0x7fc00000);
+          }
         }
       }
     }
-    if (e0 + E <= a.n) {
-      store_vec(out, e0, z);
-    } else if (e0 < a.n) {
 #pragma unroll
-      for (int t = 0; t < E; ++t)
-        if (e0 + t < a.n) store_one(out, e0 + t, z[t]);
+    for (int hv = 0; hv < VECS; ++hv) {
+      const uint64_t e0 = (chunk * (32 * VECS) + 32 * hv + lane) * E;
+      if (e0 + E <= a.n) {
+        store_vec(out, e0, z[hv]);
+      } else if (e0 < a.n) {
+#pragma unroll
+        for (int t = 0; t < E; ++t)
+          if (e0 + t < a.n) store_one(out, e0 + t, z[hv][t]);
+      }
     }
   }
 }
