@@ -166,6 +166,34 @@ aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_table approx
                               uint32_t tag, double *sums_dev, void *workspace_dev,
                               size_t workspace_bytes, aicdf_stream_t stream);
 
+/* aicdf_mlmc_level for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a library convenience.
+ *
+ * Who needs it: code that must not call cudaMalloc -- for example a plugin
+ * running inside a host application that owns all device memory through its
+ * own pool and does not let components allocate outside it, or a latency-
+ * critical loop that cannot afford cudaMalloc/cudaFree and the device
+ * synchronisation they imply.  Such callers cannot provide the scratch
+ * workspace that aicdf_mlmc_level asks for.
+ *
+ * Same arguments and results as aicdf_mlmc_level, without the workspace: the
+ * per-block partial sums go to a fixed array inside the library (2048 FP64
+ * pairs, 32 KiB, held on every GPU that loads the library until the process
+ * exits).  The caller still passes the output sums_dev.  The call allocates
+ * nothing.  Its first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  A launch that would need more than 2048 thread blocks is
+ * refused with AICDF_ERR_UNSUPPORTED (the library sizes the grid itself; this
+ * does not happen on GPUs with up to 256 SMs).  All calls share the one
+ * array: two calls that can run at the same time on the GPU (different
+ * streams, no ordering between them) race and give wrong sums; serialise
+ * them.  Nothing carries over between calls: every slot a call reads it has
+ * written first.  Asynchronous on stream. */
+aicdf_status aicdf_mlmc_level_noalloc(const aicdf_sde_params *params, aicdf_table approx,
+                                      int level, int kind, uint64_t n_paths, uint64_t path_offset,
+                                      uint64_t seed, uint32_t tag, double *sums_dev,
+                                      aicdf_stream_t stream);
+
 /* Optimal sample allocation (Section 4.1): for nterms estimator terms with
  * variances v[i] and costs c[i] and target RMSE eps, the Lagrange-optimal
  * counts m[i] = eps^-1 sqrt(2 T v_i / c_i) with total time

@@ -103,6 +103,7 @@ SIGNATURES = {
     "aicdf_mlmc_level_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "aicdf_mlmc_allocate": (_I, [_I, _P, _P, _D, _P, _P]),
+    "aicdf_mlmc_level_noalloc": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P]),
     "aicdf_batch_create": (_I, [_P, _I, _P, _I, _P, _U64, C.POINTER(_P)]),
     "aicdf_batch_destroy": (None, [_P]),
     "aicdf_batch_workspace_bytes": (_SZ, [_P, _P]),
@@ -257,6 +258,17 @@ def mlmc_level(params: SdeParams, table: Table, level: int, kind: int, n_paths: 
     _check(lib().aicdf_mlmc_level(C.byref(params), table.handle, level, kind, n_paths, path_offset,
                                   seed, tag, _ptr(sums), _ptr(workspace), nbytes, _stream(stream)),
            "mlmc_level")
+    return sums
+
+
+def mlmc_level_noalloc(params: SdeParams, table: Table, level: int, kind: int, n_paths: int, sums,
+                       path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
+    """aicdf_mlmc_level_noalloc: like mlmc_level, for callers that cannot
+    allocate device memory; the scratch lives in a fixed array inside the
+    library, shared by all calls (serialise calls that could overlap)."""
+    _check(lib().aicdf_mlmc_level_noalloc(C.byref(params), table.handle, level, kind, n_paths,
+                                          path_offset, seed, tag, _ptr(sums), _stream(stream)),
+           "mlmc_level_noalloc")
     return sums
 
 
