@@ -35,7 +35,8 @@ WORKLOAD = {"workload": "piecewise-linear Phi^-1, 16-entry dyadic table, 2^28 Ph
                         "uniforms -> FP32 (1 GiB out)",
             "n_samples": N_SAMPLES, "table": "K=15 dyadic intervals + zero row",
             "uniforms": "Philox4x32-10 seed 0, in registers", "l2": "output 1 GiB > L2 (129 MB): no flush"}
-KERNEL_SOURCES = ["paper_2012_09715_gb300/csrc/sample.cu", "paper_2012_09715_gb300/csrc/device_common.cuh",
+KERNEL_SOURCES = ["paper_2012_09715_gb300/csrc/sample_kernels.cuh",
+                  "paper_2012_09715_gb300/csrc/device_common.cuh",
                   "paper_2012_09715_gb300/csrc/phiinv_coefs.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "ncu_sample_pwl_f32_2p28.md")
 
@@ -164,6 +165,114 @@ def cpu_baseline(budget_s: float = 12.0, chunk: int = 1 << 20):
                       f"arithmetic), single thread, {t:.1f} s"}
 
 
+def sampler_sweep(P, tl, dev, stream):
+    """Bandwidth sweep of the PWL sampler, 2^16 .. 2^30 samples (FP32 out)."""
+    import torch
+    res = {}
+    for lg in (16, 18, 20, 22, 24, 26, 28, 30):
+        n = 1 << lg
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        steps = 20 if lg <= 26 else 5
+        tot, per = _time_device(lambda: P.sample(tl, P.PWL, out, seed=0, stream=stream), steps, 3, stream)
+        ms = statistics.mean(per)
+        res[f"2^{lg}"] = {"gsamples_per_s": n / (ms / 1e3) / 1e9, "write_gbs": 4 * n / (ms / 1e3) / 1e9,
+                          "ms": ms}
+        del out
+    return res
+
+
+def batch_sweep(P, dev, stream):
+    """4096 CIR parameter sets x levels 0..7 x (APPROX2, CORR4), truncated
+    Euler-Maruyama with FP16 approximate variates: one persistent launch per
+    run; the schedule is picked by the autotuner."""
+    import torch
+    from paper_2012_09715_gb300 import inputs
+    sw = inputs.sweep_sets(4096, seed=0)
+    n2, n4 = inputs.sweep_counts(sw["n_base"], levels=8)
+    sets = [P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=float(sw["X0"][i]), T=1.0, K=0.0, mu=0.0,
+                         sigma=float(sw["sigma"][i]), kappa=float(sw["kappa"][i]), theta=float(sw["theta"][i]),
+                         discount=1.0) for i in range(4096)]
+    terms, steps = [], 0
+    for s in range(4096):
+        for l in range(8):
+            terms.append(P.BatchTerm(s, l, P.KIND_APPROX2, 2 * (8 * s + l) + 1, int(n2[s, l]), 0))
+            terms.append(P.BatchTerm(s, l, P.KIND_CORR4, 2 * (8 * s + l) + 2, int(n4[s, l]), 0))
+            steps += (int(n2[s, l]) + int(n4[s, l])) << l
+    tl = P.table_build(P.PWL, 15)
+    b = P.Batch(sets, terms, tl, seed=0)
+    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    big = max(b.workspace_bytes(P.Schedule(t * m, t, 0, 1)) for t in (128, 256) for m in (2, 8, 32, 128))
+    ws = torch.empty(big, dtype=torch.uint8, device=dev)
+    best, tune_ms = b.autotune(sums, ws, var16=1, stream=stream)
+    tot, per = _time_device(lambda: b.run(best, sums, ws, stream=stream), 5, 2, stream)
+    ms = statistics.mean(per)
+    n_items, grid = b.info(best)
+    return {"sets": 4096, "terms": len(terms), "fine_path_steps": steps, "ms": ms,
+            "path_steps_per_s": steps / (ms / 1e3), "schedule": best.as_dict(), "tiles": n_items, "grid": grid,
+            "autotune_best_ms": tune_ms, "fp16_variates": True}
+
+
+def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
+    """CIR (kappa 0.5, theta 0.04, sigma 0.3, X0 0.04, T 1; nu = 0.889): train the
+    surrogate on exact quantiles, then report its error, the exact/surrogate
+    cost ratio, and the variance of the two-way differences per level."""
+    import math
+    import torch
+    nu = 4 * 0.5 * 0.04 / 0.3 ** 2
+    u = torch.empty(n_train, device=dev)
+    lam = torch.empty(n_train, device=dev)
+    tgt = torch.empty(n_train, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.ncx2_targets(nu, n_train, u, lam, tgt, st, seed=11, tag=1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_exact_ms = e0.elapsed_time(e1)
+    s = P.Surrogate(nu, seed=3)
+    loss = torch.zeros(1, device=dev)
+    epochs = 12
+    e0.record(stream)
+    s.train(u, lam, tgt, batch=8192, epochs=epochs, lr=3e-3, lr_final=3e-5, loss=loss, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_train_ms = e0.elapsed_time(e1)
+    # held-out error, surrogate vs the Gaussian limit
+    nh = 1 << 18
+    uh, lh, th = (torch.empty(nh, device=dev) for _ in range(3))
+    P.ncx2_targets(nu, nh, uh, lh, th, st, seed=99, tag=2, stream=stream)
+    out = torch.empty(nh, device=dev)
+    tot, per = _time_device(lambda: s.eval(uh, lh, out, stream=stream), 10, 3, stream)
+    t_eval_ms = statistics.mean(per)
+    torch.cuda.synchronize()
+    from scipy.special import ndtri
+    t_np = th.cpu().numpy().astype("float64")
+    rmse = math.sqrt(float(((out.cpu().numpy() - t_np) ** 2).mean()))
+    rmse_g = math.sqrt(float(((ndtri(uh.cpu().numpy().astype("float64")) - t_np) ** 2).mean()))
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=0.04, T=1.0, K=0.0, mu=0.0, sigma=0.3, kappa=0.5,
+                       theta=0.04, discount=1.0)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    levels = []
+    for l in range(7):
+        n = 20000
+        row = {"l": l}
+        for name, kind in (("exact", P.CIR_EXACT), ("diff", P.CIR_DIFF), ("diff_gauss", P.CIR_DIFF_GAUSS)):
+            P.cir_level(prm, s, l, kind, n, sums, ws, st, seed=5, tag=1 + l, stream=stream)
+            v = sums.cpu().numpy()
+            m = v[0] / n
+            row[name + "_var"] = v[1] / n - m * m
+        row["log2_var_ratio_surrogate"] = math.log2(row["diff_var"] / row["exact_var"])
+        row["log2_var_ratio_gauss"] = math.log2(row["diff_gauss_var"] / row["exact_var"])
+        levels.append(row)
+    return {"nu": nu, "train_samples": n_train, "epochs": epochs, "train_ms": t_train_ms,
+            "final_batch_mse": float(loss.item()), "heldout_rmse": rmse, "heldout_rmse_gauss_limit": rmse_g,
+            "exact_quantiles_per_s": n_train / (t_exact_ms / 1e3),
+            "surrogate_evals_per_s": nh / (t_eval_ms / 1e3),
+            "exact_over_surrogate_cost": (t_exact_ms / n_train) / (t_eval_ms / nh),
+            "root_finder_status": int(st.item()), "levels": levels}
+
+
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
     wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
@@ -277,7 +386,7 @@ def main():
     achieved = bytes_per_launch / (kernel_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _profile_traffic(), "peak_source": peak_kind,
-            "kernel": "k_sample_vec<PWL,F32,PHILOX>", "algorithmic_bytes_per_launch": bytes_per_launch}
+            "kernel": "k_sample_philox32<PWL,F32>", "algorithmic_bytes_per_launch": bytes_per_launch}
 
     extras = {}
     e2e = None
@@ -315,7 +424,16 @@ def main():
         tot, _ = _time_device(lambda: P.sample(tc, P.PWC, small, seed=seed, stream=stream), 50, 5, stream)
         extras["pwc_2p20_gsamples_per_s"] = (1 << 20) * 50 / (tot / 1e3) / 1e9
         del out16, small
-        extras["mlmc"] = mlmc_time_to_rmse(P, tl, dev)
+        del out
+        for name, fn in (("mlmc", lambda: mlmc_time_to_rmse(P, tl, dev)),
+                         ("mlmc_eps_1e-5", lambda: mlmc_time_to_rmse(P, tl, dev, eps=1e-5)),
+                         ("sampler_sweep", lambda: sampler_sweep(P, tl, dev, stream)),
+                         ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
+                         ("cir_surrogate", lambda: cir_surrogate(P, dev, stream))):
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # reported, not hidden: the headline line still prints
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -326,7 +326,10 @@ aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const 
  * draws one uniform U (Philox counter (s/4, p mod 2^32, p>>32, tag), word
  * s%4) and both sides use the same U:
  *   EXACT       P(X^_T), X^' = c C^{-1}_nu(U; X^ e^{-kappa h}/c)  (FP64 root finder)
- *   SURROGATE   P(X~_T), X~' = c max(C~^{-1}_nu(U; lambda~), 0)   (learned P~)
+ *   SURROGATE   P(X~_T), X~' = c max(C~^{-1}_nu(U; lambda~), 0)   (learned P~;
+ *               for lambda > e^4, beyond the trained range, P~ = Phi^{-1}(U) +
+ *               sqrt(y/y_max) (P~(U, e^4) - Phi^{-1}(U)), the O(sqrt(y)) decay of
+ *               P - Phi^{-1} as y = nu/(lambda+nu) -> 0)
  *   DIFF        P(X^_T) - P(X~_T)                                  (same steps)
  *   GAUSS       as SURROGATE with P~ replaced by Phi^{-1}(U), the y -> 0
  *               limit of P (Section 5.1): the approximation without the network

@@ -1,6 +1,8 @@
 // Host-side internals of libaicdf (not part of the ABI).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -28,4 +30,8 @@ int sm_count();
 int resident_blocks(const void *kernel, int threads);
 // Host FP64 inverse Gaussian CDF used for the table build.
 double host_phiinv(double p);
+// One-off batched launch of MLMC terms (no graph); see mlmc.cu.
+aicdf_status batch_run_once(const aicdf_sde_params *sets, int n_sets, const aicdf_batch_term *terms,
+                            int n_terms, aicdf_table approx, uint64_t seed, double *sums_dev, void *ws,
+                            size_t ws_bytes, cudaStream_t st);
 }  // namespace aicdf

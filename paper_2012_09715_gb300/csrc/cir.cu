@@ -24,6 +24,7 @@
 namespace aicdf {
 
 constexpr int kCirThreads = 256;
+constexpr float kLamTrainMax = 54.598150033144236f;  // e^4: top of the surrogate's trained range
 
 struct CirArgs {
   PhiloxKeys keys;
@@ -71,8 +72,18 @@ __global__ void __launch_bounds__(kCirThreads)
           if (APPROX != 0) {
             const float lam = fmaxf(xa, 0.f) * ratio;
             float pt;
-            if (APPROX == 1) pt = mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_lam(lam), hs[warp]);
-            else pt = phiinv_f32(u);
+            if (APPROX == 1) {
+              pt = mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_lam(lam), hs[warp]);
+              if (lam > kLamTrainMax) {
+                // beyond the trained range: P - Phi^{-1}(U) = O(sqrt(y)) as y -> 0
+                // (Section 5.1), so carry the learned correction at the edge
+                // of the range over with the factor sqrt(y / y_max)
+                const float z = phiinv_f32(u);
+                pt = fmaf(pt - z, sqrtf((kLamTrainMax + nuf) / (lam + nuf)), z);
+              }
+            } else {
+              pt = phiinv_f32(u);
+            }
             const float h = lam + nuf;
             xa = cf * fmaxf(fmaf(2.0f * sqrtf(h), pt, h), 0.f);
           }

@@ -63,15 +63,17 @@ __device__ __forceinline__ float u01(uint32_t x) {
 // ---------------------------------------------------------------------------
 // Algorithm 1 for uniforms on the 2^-24 grid (the library's own uniforms).
 // On the grid, u - 1/2 and 1/2 - |u - 1/2| are exact, so v = min(u, 1-u) costs
-// two adds; v >= 2^-24 bounds the row index 126 - e by 23, so lane L holds
-// row min(L, K) and no cap is needed; the sign is restored by one xor with
-// the complement of the sign of u - 1/2 (u = 1/2 gives -0, as in the listing).
+// two adds.  v in [2^-24, 1/2] has biased exponent e in [103, 126] and row
+// 126 - e; since the shuffle reads lane (e mod 32) = e - 96, lane L holds row
+// min(30 - L, K) and the exponent is the lane index as it stands (no bias
+// subtraction, no cap).  The sign is restored by one xor with the complement
+// of the sign of u - 1/2 (u = 1/2 gives -0, as in the listing).
 struct PwlRows {
   float a, b;
 };
 
 __device__ __forceinline__ PwlRows pwl_lane_rows(const float *alpha, const float *beta, int K) {
-  const int r = min((int)(threadIdx.x & 31), K);
+  const int r = min(max(30 - (int)(threadIdx.x & 31), 0), K);
   PwlRows c;
   c.a = alpha[r];
   c.b = beta[r];
@@ -82,9 +84,9 @@ __device__ __forceinline__ PwlRows pwl_lane_rows(const float *alpha, const float
 __device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) {
   const float t = u - 0.5f;
   const float v = 0.5f - fabsf(t);
-  const uint32_t idx = 126u - (__float_as_uint(v) >> 23);
-  const float a = __shfl_sync(0xffffffffu, c.a, idx);
-  const float b = __shfl_sync(0xffffffffu, c.b, idx);
+  const uint32_t e = __float_as_uint(v) >> 23;  // the shuffle uses e mod 32
+  const float a = __shfl_sync(0xffffffffu, c.a, e);
+  const float b = __shfl_sync(0xffffffffu, c.b, e);
   const float z = fmaf(b, v, a);
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
 }

@@ -1,13 +1,21 @@
 // Host MLMC driver (Section 4.1): pilot runs, Lagrange-optimal path counts
 // from measured variances and per-path device costs, and levels added until
-// the bias estimate is below eps / sqrt(2).  Every path launch goes through
-// aicdf_mlmc_level; sums come back to the host once per launch.
+// the bias estimate is below eps / sqrt(2).
+//
+// Each round is one batched persistent launch: the pilot paths of every new
+// level in one, the extra paths of every term in the next.  Per-path costs
+// for the allocation come from a per-step cost of each estimator kind,
+// calibrated once per process, device and model by timing one large level
+// launch of that kind, times (2^l + 1) steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "aicdf_internal.h"
@@ -19,8 +27,6 @@ struct Term {
   uint32_t tag = 0;
   uint64_t n = 0;
   double s1 = 0.0, s2 = 0.0;
-  double ns_per_path = 0.0;   // from the largest launch so far
-  uint64_t cost_launch = 0;   // size of that launch
   double mean() const { return n ? s1 / (double)n : 0.0; }
   double var() const {
     if (n < 2) return 0.0;
@@ -29,55 +35,60 @@ struct Term {
   }
 };
 
-struct Ctx {
-  const aicdf_sde_params *prm;
-  aicdf_table tab;
-  uint64_t seed;
-  double *sums_dev;
-  void *ws;
-  size_t ws_bytes;
-  cudaStream_t st;
-  cudaEvent_t e0, e1;
-  double gpu_ms = 0.0;
-  int launches = 0;
-};
+constexpr size_t kSumsBytes = 256 + 4096;
+constexpr int kCalLevel = 5;
+constexpr uint64_t kCalPaths = 1u << 17;
 
-constexpr uint64_t kMaxPathsPerLaunch = 1ull << 32;
+std::mutex g_cal_mu;
+std::map<std::tuple<int, int, int, int, int>, double> g_step_ns;  // (dev, model, scheme, approx, kind)
 
-aicdf_status extend(Ctx &c, Term &t, uint64_t add) {
-  while (add > 0) {
-    const uint64_t m = std::min(add, kMaxPathsPerLaunch);
-    if (cudaEventRecord(c.e0, c.st) != cudaSuccess) return AICDF_ERR_CUDA;
-    aicdf_status s = aicdf_mlmc_level(c.prm, c.tab, t.level, t.kind, m, t.n, c.seed, t.tag,
-                                      c.sums_dev, c.ws, c.ws_bytes, (aicdf_stream_t)c.st);
-    if (s != AICDF_OK) return s;
-    double h[3];
-    if (cudaEventRecord(c.e1, c.st) != cudaSuccess ||
-        cudaMemcpyAsync(h, c.sums_dev, sizeof(h), cudaMemcpyDeviceToHost, c.st) != cudaSuccess ||
-        cudaStreamSynchronize(c.st) != cudaSuccess) {
-      aicdf::set_cuda_error((int)cudaGetLastError());
-      return AICDF_ERR_CUDA;
+// Device ns per fine step of one path of `kind` (calibrated once).
+aicdf_status step_cost_ns(const aicdf_sde_params *prm, aicdf_table tab, int kind, void *ws, size_t wsb,
+                          double *sums_dev, cudaStream_t st, double *out) {
+  int dev = 0, method = 0, n = 0;
+  cudaGetDevice(&dev);
+  aicdf_table_info(tab, &method, &n);
+  const auto key = std::make_tuple(dev, prm->model, prm->scheme, method, kind);
+  {
+    std::lock_guard<std::mutex> lock(g_cal_mu);
+    auto it = g_step_ns.find(key);
+    if (it != g_step_ns.end()) {
+      *out = it->second;
+      return AICDF_OK;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c.e0, c.e1);
-    c.gpu_ms += ms;
-    c.launches += 1;
-    t.s1 += h[0];
-    t.s2 += h[1];
-    t.n += m;
-    if (m >= t.cost_launch) {
-      t.cost_launch = m;
-      t.ns_per_path = std::max((double)ms * 1e6 / (double)m, 1e-6);
-    }
-    add -= m;
   }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  aicdf_status s = aicdf_mlmc_level(prm, tab, kCalLevel, kind, kCalPaths, 0, 1234, 0xCA1u, sums_dev, ws, wsb,
+                                    (aicdf_stream_t)st);  // warm-up
+  float best = 1e30f;
+  for (int rep = 0; rep < 2 && s == AICDF_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    s = aicdf_mlmc_level(prm, tab, kCalLevel, kind, kCalPaths, 0, 1234, 0xCA1u, sums_dev, ws, wsb,
+                         (aicdf_stream_t)st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != AICDF_OK) return s;
+  const double ns = (double)best * 1e6 / ((double)kCalPaths * (double)((1 << kCalLevel) + 1));
+  std::lock_guard<std::mutex> lock(g_cal_mu);
+  g_step_ns[key] = ns;
+  *out = ns;
   return AICDF_OK;
 }
 
 }  // namespace
 
 extern "C" size_t aicdf_mlmc_run_workspace_bytes(void) {
-  return aicdf_mlmc_level_workspace_bytes() + 256;
+  // level-kernel partials | calibration sums (256 B) | per-round term sums
+  // (4 KiB: 2 x 21 terms x 3 doubles) | batch tile list and partials
+  return aicdf_mlmc_level_workspace_bytes() + kSumsBytes + (8u << 20);
 }
 
 extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_table approx,
@@ -95,68 +106,123 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     return AICDF_ERR_ARG;
   const auto wall0 = std::chrono::steady_clock::now();
   std::memset(r, 0, sizeof(*r));
-  Ctx c;
-  c.prm = params;
-  c.tab = approx;
-  c.seed = o->seed;
-  c.ws = workspace_dev;
-  c.ws_bytes = aicdf_mlmc_level_workspace_bytes();
-  c.sums_dev = reinterpret_cast<double *>((char *)workspace_dev + c.ws_bytes);
-  c.st = (cudaStream_t)stream;
-  if (cudaEventCreate(&c.e0) != cudaSuccess || cudaEventCreate(&c.e1) != cudaSuccess) {
-    aicdf::set_cuda_error((int)cudaGetLastError());
-    return AICDF_ERR_CUDA;
-  }
-  const uint64_t pilot = o->n_pilot ? o->n_pilot : 10000;
-  const double alpha = o->weak_order > 0.0 ? o->weak_order : 1.0;
+  cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)workspace_dev;
+  const size_t lvl_ws = aicdf_mlmc_level_workspace_bytes();
+  double *cal_sums = reinterpret_cast<double *>(w + lvl_ws);
+  double *term_sums = reinterpret_cast<double *>(w + lvl_ws + 256);  // <= 2 x 21 terms x 3 doubles
+  void *batch_ws = w + lvl_ws + kSumsBytes;
+  const size_t batch_wsb = workspace_bytes - lvl_ws - kSumsBytes;
+
   const int est = o->estimator;
+  std::vector<int> kinds;
+  if (est == AICDF_EST_NESTED) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
+  else if (est == AICDF_EST_REGULAR) kinds = {AICDF_KIND_EXACT2};
+  else kinds = {AICDF_KIND_PLAIN};
+  double kind_ns[5] = {0, 0, 0, 0, 0};
+  for (int k : kinds) {
+    aicdf_status s = step_cost_ns(params, approx, k, w, lvl_ws, cal_sums, st, &kind_ns[k]);
+    if (s != AICDF_OK) return s;
+  }
+  auto cost = [&](const Term &t) { return kind_ns[t.kind] * (double)((1u << t.level) + 1); };
+
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double gpu_ms = 0.0;
+  int launches = 0;
   std::vector<Term> terms;
-  auto add_level = [&](int l) -> aicdf_status {
-    std::vector<int> kinds;
-    if (est == AICDF_EST_NESTED) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
-    else if (est == AICDF_EST_REGULAR) kinds = {AICDF_KIND_EXACT2};
-    else kinds = {AICDF_KIND_PLAIN};
-    for (size_t i = 0; i < kinds.size(); ++i) {
-      Term t;
-      t.level = l;
-      t.kind = kinds[i];
-      t.slot = (int)i;
-      t.tag = 1u + 64u * (uint32_t)est + 2u * (uint32_t)l + (uint32_t)i;
-      terms.push_back(t);
-      aicdf_status s = extend(c, terms.back(), pilot);
-      if (s != AICDF_OK) return s;
+  // one batched launch adding add[i] paths to terms[i] (add[i] = 0: skipped)
+  auto run_round = [&](const std::vector<uint64_t> &add) -> aicdf_status {
+    std::vector<aicdf_batch_term> bt;
+    std::vector<int> idx;
+    for (size_t i = 0; i < terms.size(); ++i)
+      if (add[i] > 0) {
+        aicdf_batch_term x;
+        x.set = 0;
+        x.level = terms[i].level;
+        x.kind = terms[i].kind;
+        x.tag = terms[i].tag;
+        x.n_paths = add[i];
+        x.path_offset = terms[i].n;
+        bt.push_back(x);
+        idx.push_back((int)i);
+      }
+    if (bt.empty()) return AICDF_OK;
+    cudaEventRecord(e0, st);
+    aicdf_status s = aicdf::batch_run_once(params, 1, bt.data(), (int)bt.size(), approx, o->seed, term_sums,
+                                           batch_ws, batch_wsb, st);
+    if (s != AICDF_OK) return s;
+    cudaEventRecord(e1, st);
+    std::vector<double> h(3 * bt.size());
+    if (cudaMemcpyAsync(h.data(), term_sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      aicdf::set_cuda_error((int)cudaGetLastError());
+      return AICDF_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    gpu_ms += ms;
+    launches += 1;
+    for (size_t j = 0; j < idx.size(); ++j) {
+      Term &t = terms[idx[j]];
+      t.s1 += h[3 * j];
+      t.s2 += h[3 * j + 1];
+      t.n += bt[j].n_paths;
     }
     return AICDF_OK;
   };
+  const uint64_t pilot = o->n_pilot ? o->n_pilot : 10000;
+  auto add_levels = [&](int l0, int l1) -> aicdf_status {  // pilot for levels l0..l1
+    const size_t first = terms.size();
+    for (int l = l0; l <= l1; ++l)
+      for (size_t i = 0; i < kinds.size(); ++i) {
+        Term t;
+        t.level = l;
+        t.kind = kinds[i];
+        t.slot = (int)i;
+        t.tag = 1u + 64u * (uint32_t)est + 2u * (uint32_t)l + (uint32_t)i;
+        terms.push_back(t);
+      }
+    std::vector<uint64_t> add(terms.size(), 0);
+    for (size_t i = first; i < terms.size(); ++i) add[i] = pilot;
+    return run_round(add);
+  };
+
   aicdf_status s = AICDF_OK;
   int L;
   if (est == AICDF_EST_PLAIN) {
     L = o->fixed_L;
-    s = add_level(L);
+    s = add_levels(L, L);
   } else {
     L = o->fixed_L >= 0 ? o->fixed_L : o->L_min;
-    for (int l = 0; l <= L && s == AICDF_OK; ++l) s = add_level(l);
+    s = add_levels(0, L);
   }
   bool converged = false;
   const double eps = o->eps;
+  const double alpha = o->weak_order > 0.0 ? o->weak_order : 1.0;
   while (s == AICDF_OK) {
-    // optimal counts for the current set of terms (Section 4.1)
-    std::vector<double> v, cst, m(terms.size());
+    // optimal counts for the current terms (Section 4.1)
+    std::vector<double> v, c, m(terms.size());
     for (auto &t : terms) {
       v.push_back(t.var());
-      cst.push_back(t.ns_per_path);
+      c.push_back(cost(t));
     }
     double total = 0.0;
-    s = aicdf_mlmc_allocate((int)terms.size(), v.data(), cst.data(), eps, m.data(), &total);
+    s = aicdf_mlmc_allocate((int)terms.size(), v.data(), c.data(), eps, m.data(), &total);
     if (s != AICDF_OK) break;
-    for (size_t i = 0; i < terms.size() && s == AICDF_OK; ++i) {
+    std::vector<uint64_t> add(terms.size(), 0);
+    for (size_t i = 0; i < terms.size(); ++i) {
       const double want = std::ceil(m[i]);
       if (!(want < 1e15)) {
         s = AICDF_ERR_NOCONVERGE;
         break;
       }
-      if ((uint64_t)want > terms[i].n) s = extend(c, terms[i], (uint64_t)want - terms[i].n);
+      if ((uint64_t)want > terms[i].n) add[i] = (uint64_t)want - terms[i].n;
     }
+    if (s != AICDF_OK) break;
+    s = run_round(add);
     if (s != AICDF_OK) break;
     if (est == AICDF_EST_PLAIN || o->fixed_L >= 0) {
       converged = true;
@@ -179,10 +245,10 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     }
     if (L >= o->L_max) break;
     ++L;
-    s = add_level(L);
+    s = add_levels(L, L);
   }
-  cudaEventDestroy(c.e0);
-  cudaEventDestroy(c.e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   if (s != AICDF_OK) return s;
   double estv = 0.0, var = 0.0;
   for (auto &t : terms) {
@@ -191,15 +257,15 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     r->paths[t.level][t.slot] = t.n;
     r->mean[t.level][t.slot] = t.mean();
     r->var[t.level][t.slot] = t.var();
-    r->cost_ns[t.level][t.slot] = t.ns_per_path;
+    r->cost_ns[t.level][t.slot] = cost(t);
   }
   r->estimate = estv;
   r->variance = var;
   r->L = L;
   r->converged = converged ? 1 : 0;
   r->n_terms = est == AICDF_EST_NESTED ? 2 : 1;
-  r->gpu_ms = c.gpu_ms;
-  r->launches = c.launches;
+  r->gpu_ms = gpu_ms;
+  r->launches = launches;
   r->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   return AICDF_OK;

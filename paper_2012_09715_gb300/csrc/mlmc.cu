@@ -582,6 +582,48 @@ extern "C" aicdf_status aicdf_batch_run(aicdf_batch b, const aicdf_schedule *s, 
   return AICDF_OK;
 }
 
+namespace aicdf {
+// One-off batch for the MLMC driver: plan, upload and launch directly on the
+// stream (no graph), sums for every term into sums_dev.  The tile size grows
+// with the work so the tile list stays below ~64k tiles.  Synchronises the
+// stream once (after the upload).
+aicdf_status batch_run_once(const aicdf_sde_params *sets, int n_sets, const aicdf_batch_term *terms,
+                            int n_terms, aicdf_table approx, uint64_t seed, double *sums_dev, void *ws,
+                            size_t ws_bytes, cudaStream_t st) {
+  aicdf_batch b = nullptr;
+  aicdf_status s = aicdf_batch_create(sets, n_sets, terms, n_terms, approx, seed, &b);
+  if (s != AICDF_OK) return s;
+  uint64_t total = 0;
+  for (int t = 0; t < n_terms; ++t) total += terms[t].n_paths;
+  uint64_t tile = std::max<uint64_t>(4096, ((total / 65536) + 255) & ~(uint64_t)255);
+  tile = std::min<uint64_t>(tile, 1u << 24);
+  const aicdf_schedule sc = {(int)tile, 256, 0, 0};
+  Plan *p = get_plan(b, sc);
+  if (!p) s = AICDF_ERR_NOMEM;
+  else if (p->bytes > ws_bytes) s = AICDF_ERR_ARG;
+  if (s == AICDF_OK) {
+    char *w = (char *)ws;
+    std::lock_guard<std::mutex> lock(g_resident_mu);
+    if (cudaMemcpyAsync(w + p->off_items, p->items.data(), sizeof(BatchItem) * p->items.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_specs, b->specs.data(), sizeof(PathSpec) * b->specs.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_slots, p->slot_begin.data(), sizeof(int) * p->slot_begin.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(w + p->off_counts, b->counts.data(), sizeof(double) * b->counts.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_cuda_error((int)cudaGetLastError());
+      s = AICDF_ERR_CUDA;
+    }
+    g_resident.erase(ws);  // this plan dies with the batch below
+    if (s == AICDF_OK) s = record_batch(b, p, ws, sums_dev, st);
+  }
+  aicdf_batch_destroy(b);  // host objects only; the launch owns nothing of them
+  return s;
+}
+}  // namespace aicdf
+
 extern "C" aicdf_status aicdf_batch_info(aicdf_batch b, const aicdf_schedule *s, int *n_items,
                                          int *grid) {
   if (!batch_ok(b) || check_schedule(s) != AICDF_OK) return AICDF_ERR_ARG;

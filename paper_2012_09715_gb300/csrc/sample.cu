@@ -14,200 +14,9 @@
 
 #include "aicdf_internal.h"
 #include "device_common.cuh"
+#include "sample_kernels.cuh"
 
 namespace aicdf {
-
-enum Source { SRC_PHILOX = 0, SRC_INPUT = 1 };
-
-struct SampleArgs {
-  const float *u;      // SRC_INPUT: caller uniforms
-  void *out;
-  uint64_t n;          // samples
-  uint64_t offset;     // SRC_PHILOX: index of the first sample in the stream
-  PhiloxKeys keys;
-  int ntab;            // PWC: intervals; PWL: K (rows 0..K)
-  float nf;            // PWC: (float)ntab
-  uint32_t pwc_shift;  // PWC: 23 - log2(ntab)
-  float tab[1024];     // PWC constants | PWL alpha[0..15], beta[16..31]
-};
-
-// Per-thread evaluator for one method.  Construction stages the table.
-// word(x): the sample for the library's uniform from Philox word x (on the
-// 2^-24 grid); operator()(u): the sample for any FP32 u (caller uniforms).
-template <int METHOD, int SRC>
-struct Approx;
-
-template <int SRC>
-struct Approx<AICDF_PWC, SRC> {
-  const float *s;
-  float nf;
-  int nmax;
-  uint32_t shift;
-  __device__ Approx(const SampleArgs &a, float *smem) {
-    for (int i = threadIdx.x; i < a.ntab; i += blockDim.x) smem[i] = a.tab[i];
-    __syncthreads();
-    s = smem;
-    nf = a.nf;
-    nmax = a.ntab - 1;
-    shift = a.pwc_shift;
-  }
-  __device__ __forceinline__ float word(uint32_t x) const { return s[pwc_index_from_word(x, shift)]; }
-  __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
-};
-
-template <int SRC>
-struct Approx<AICDF_PWL, SRC> {
-  PwlLane c;     // general inputs: capped index, sign folded into the row
-  PwlRows rows;  // grid inputs: 32 rows, sign by xor
-  unsigned kmax;
-  __device__ Approx(const SampleArgs &a, float *) {
-    if (SRC == SRC_PHILOX) rows = pwl_lane_rows(a.tab, a.tab + 16, a.ntab);
-    else c = pwl_lane_coefs(a.tab, a.tab + 16);
-    kmax = (unsigned)a.ntab;
-  }
-  __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_grid(u01(x), rows); }
-  __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
-};
-
-template <int SRC>
-struct Approx<AICDF_EXACT, SRC> {
-  __device__ Approx(const SampleArgs &, float *) {}
-  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }
-  __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
-};
-
-template <int SRC>
-struct Approx<AICDF_EXACT_LIB, SRC> {
-  __device__ Approx(const SampleArgs &, float *) {}
-  __device__ __forceinline__ float word(uint32_t x) const { return normcdfinvf(u01(x)); }
-  __device__ __forceinline__ float operator()(float u) const { return normcdfinvf(u); }
-};
-
-template <int OUT>
-struct OutVec;
-template <>
-struct OutVec<AICDF_F32> {
-  static constexpr int kElems = 4;
-};
-template <>
-struct OutVec<AICDF_F16> {
-  static constexpr int kElems = 8;
-};
-
-__device__ __forceinline__ void store_vec(float *out, uint64_t e, const float (&z)[4]) {
-  *reinterpret_cast<float4 *>(out + e) = make_float4(z[0], z[1], z[2], z[3]);
-}
-__device__ __forceinline__ void store_vec(__half *out, uint64_t e, const float (&z)[8]) {
-  uint4 w;
-  __half2 h0 = __floats2half2_rn(z[0], z[1]), h1 = __floats2half2_rn(z[2], z[3]);
-  __half2 h2 = __floats2half2_rn(z[4], z[5]), h3 = __floats2half2_rn(z[6], z[7]);
-  w.x = *reinterpret_cast<uint32_t *>(&h0);
-  w.y = *reinterpret_cast<uint32_t *>(&h1);
-  w.z = *reinterpret_cast<uint32_t *>(&h2);
-  w.w = *reinterpret_cast<uint32_t *>(&h3);
-  *reinterpret_cast<uint4 *>(out + e) = w;
-}
-__device__ __forceinline__ void store_one(float *out, uint64_t e, float z) { out[e] = z; }
-__device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
-  out[e] = __float2half_rn(z);
-}
-
-// Vectorised kernel.  Requires: out 16-byte aligned; SRC_PHILOX: offset % 4 == 0;
-// SRC_INPUT: u 16-byte aligned.
-template <int METHOD, int OUT, int SRC>
-__global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
-  const Approx<METHOD, SRC> f(a, smem);
-  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
-  T *out = reinterpret_cast<T *>(a.out);
-  constexpr int E = OutVec<OUT>::kElems;
-  // Each warp takes chunks of 2 x 32 consecutive 16-byte vectors; lane L
-  // computes vectors L and L + 32 of the chunk, so its two independent
-  // Philox chains overlap and both stores stay fully coalesced.
-  constexpr int VECS = 2;
-  const uint64_t nvec = (a.n + E - 1) / E;
-  const uint64_t nchunk = (nvec + 32 * VECS - 1) / (32 * VECS);
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  // warp-uniform loop: every lane runs every iteration (shuffles need all 32)
-  for (uint64_t chunk = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk;
-       chunk += warps) {
-    float z[VECS][E];
-#pragma unroll
-    for (int hv = 0; hv < VECS; ++hv) {
-      const uint64_t v = chunk * (32 * VECS) + 32 * hv + lane;
-      const uint64_t e0 = v * E;
-      if constexpr (SRC == SRC_PHILOX) {
-#pragma unroll
-        for (int h = 0; h < E / 4; ++h) {
-          const uint64_t j = (a.offset >> 2) + v * (E / 4) + h;
-          const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
-          z[hv][4 * h + 0] = f.word(r.x);
-          z[hv][4 * h + 1] = f.word(r.y);
-          z[hv][4 * h + 2] = f.word(r.z);
-          z[hv][4 * h + 3] = f.word(r.w);
-        }
-      } else {
-#pragma unroll
-        for (int h = 0; h < E / 4; ++h) {
-          float4 uu = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
-          if (e0 + 4 * h + 3 < a.n) {
-            uu = __ldcs(reinterpret_cast<const float4 *>(a.u + e0 + 4 * h));
-          } else {
-            if (e0 + 4 * h + 0 < a.n) uu.x = a.u[e0 + 4 * h + 0];
-            if (e0 + 4 * h + 1 < a.n) uu.y = a.u[e0 + 4 * h + 1];
-            if (e0 + 4 * h + 2 < a.n) uu.z = a.u[e0 + 4 * h + 2];
-          }
-          const float us[4] = {uu.x, uu.y, uu.z, uu.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            float y = f(us[t]);
-            z[hv][4 * h + t] = in_unit(us[t]) ? y : __int_as_float(0x7fc00000);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int hv = 0; hv < VECS; ++hv) {
-      const uint64_t e0 = (chunk * (32 * VECS) + 32 * hv + lane) * E;
-      if (e0 + E <= a.n) {
-        store_vec(out, e0, z[hv]);
-      } else if (e0 < a.n) {
-#pragma unroll
-        for (int t = 0; t < E; ++t)
-          if (e0 + t < a.n) store_one(out, e0 + t, z[hv][t]);
-      }
-    }
-  }
-}
-
-// Scalar kernel for unaligned pointers or an offset not divisible by 4.
-template <int METHOD, int OUT, int SRC>
-__global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
-  const Approx<METHOD, SRC> f(a, smem);
-  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
-  T *out = reinterpret_cast<T *>(a.out);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n;
-       base += stride) {
-    const uint64_t e = base + lane;
-    float y;
-    if constexpr (SRC == SRC_PHILOX) {
-      const uint64_t s = a.offset + e;
-      const uint64_t j = s >> 2;
-      const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
-      const uint32_t w = (s & 3) == 0 ? r.x : (s & 3) == 1 ? r.y : (s & 3) == 2 ? r.z : r.w;
-      y = f.word(w);
-    } else {
-      const float u = (e < a.n) ? a.u[e] : 0.5f;
-      y = f(u);
-      if (!in_unit(u)) y = __int_as_float(0x7fc00000);
-    }
-    if (e < a.n) store_one(out, e, y);
-  }
-}
 
 using KernelFn = void (*)(SampleArgs);
 
@@ -262,10 +71,27 @@ aicdf_status prepare_sample_args(aicdf_table table, int method, SampleArgs *a) {
   return AICDF_OK;
 }
 
+template <int OUT>
+static KernelFn select_philox32(int method) {
+  switch (method) {
+    case AICDF_PWC: return k_sample_philox32<AICDF_PWC, OUT>;
+    case AICDF_PWL: return k_sample_philox32<AICDF_PWL, OUT>;
+    case AICDF_EXACT: return k_sample_philox32<AICDF_EXACT, OUT>;
+    default: return k_sample_philox32<AICDF_EXACT_LIB, OUT>;
+  }
+}
+
 aicdf_status launch_sample(const SampleArgs &a, int method, int out_dtype, int src, bool vec,
                            cudaStream_t stream) {
   KernelFn k = select_kernel(method, out_dtype, src, vec);
   const int E = vec ? (out_dtype == AICDF_F32 ? 4 : 8) : 1;
+  if (src == SRC_PHILOX && vec) {
+    // 32-bit index variant when counters and element indices stay below 2^32
+    const uint64_t nvec = (a.n + E - 1) / E;
+    const uint64_t lim = 1ull << 32;
+    if ((nvec + 64) * (uint64_t)E < lim && (a.offset >> 2) + (nvec + 64) * (uint64_t)(E / 4) < lim)
+      k = out_dtype == AICDF_F32 ? select_philox32<AICDF_F32>(method) : select_philox32<AICDF_F16>(method);
+  }
   const uint64_t units = (a.n + E - 1) / E;
   const int threads = 256;
   // one full wave: SMs x resident blocks of this kernel (grid-stride inside)
@@ -324,34 +150,32 @@ extern "C" aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint
   a.u = nullptr;
   a.keys = make_keys(seed);
   const size_t esz = out_dtype == AICDF_F32 ? 4 : 2;
-  // two halves, each a multiple of 16 bytes and of 8 samples
-  size_t half = (staging_bytes / 2) & ~(size_t)255;
-  const size_t chunk = half / esz;
+  // NB staging buffers (4 when the staging holds >= 4 x 1 MiB, else 2), each
+  // a multiple of 256 bytes; chunk i is generated into buffer i % NB on the
+  // caller's stream and copied out on copy stream i % 2, so two copies can be
+  // in flight on separate copy engines while the next chunk is generated.
+  const int NB = staging_bytes >= (4u << 20) ? 4 : 2;
+  const size_t part = (staging_bytes / NB) & ~(size_t)255;
+  const size_t chunk = part / esz;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t done[2];
-  if (cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming) != cudaSuccess) {
-    set_cuda_error((int)cudaGetLastError());
-    return AICDF_ERR_CUDA;
-  }
-  cudaStream_t copy_st;
-  if (cudaStreamCreateWithFlags(&copy_st, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaEventDestroy(done[0]);
-    cudaEventDestroy(done[1]);
-    set_cuda_error((int)cudaGetLastError());
-    return AICDF_ERR_CUDA;
-  }
-  cudaEvent_t copied[2];
-  cudaEventCreateWithFlags(&copied[0], cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&copied[1], cudaEventDisableTiming);
-  aicdf_status rc = AICDF_OK;
+  cudaEvent_t done[4] = {}, copied[4] = {};
+  cudaStream_t copy_st[2] = {};
+  bool ok = true;
+  for (int i = 0; i < NB; ++i)
+    ok = ok && cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 2; ++i) ok = ok && cudaStreamCreateWithFlags(&copy_st[i], cudaStreamNonBlocking) == cudaSuccess;
+  aicdf_status rc = ok ? AICDF_OK : AICDF_ERR_CUDA;
+  if (!ok) set_cuda_error((int)cudaGetLastError());
   size_t pos = 0;
-  int buf = 0;
-  bool used[2] = {false, false};
-  while (pos < n) {
+  uint64_t k = 0;
+  bool used[4] = {false, false, false, false};
+  while (rc == AICDF_OK && pos < n) {
     const size_t cnt = std::min(chunk, n - pos);
-    char *dst = (char *)staging_dev + (size_t)buf * half;
-    // the generator may not overwrite a half whose copy is still in flight
+    const int buf = (int)(k % NB);
+    cudaStream_t cs = copy_st[k % 2];
+    char *dst = (char *)staging_dev + (size_t)buf * part;
+    // the generator may not overwrite a buffer whose copy is still in flight
     if (used[buf]) cudaStreamWaitEvent(st, copied[buf], 0);
     a.out = dst;
     a.n = cnt;
@@ -360,28 +184,35 @@ extern "C" aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint
     rc = launch_sample(a, method, out_dtype, SRC_PHILOX, vec, st);
     if (rc != AICDF_OK) break;
     cudaEventRecord(done[buf], st);
-    cudaStreamWaitEvent(copy_st, done[buf], 0);
-    if (cudaMemcpyAsync((char *)host_out + pos * esz, dst, cnt * esz, cudaMemcpyDeviceToHost,
-                        copy_st) != cudaSuccess) {
+    cudaStreamWaitEvent(cs, done[buf], 0);
+    if (cudaMemcpyAsync((char *)host_out + pos * esz, dst, cnt * esz, cudaMemcpyDeviceToHost, cs) !=
+        cudaSuccess) {
       set_cuda_error((int)cudaGetLastError());
       rc = AICDF_ERR_CUDA;
       break;
     }
-    cudaEventRecord(copied[buf], copy_st);
+    cudaEventRecord(copied[buf], cs);
     used[buf] = true;
     pos += cnt;
-    buf ^= 1;
+    ++k;
   }
-  cudaError_t e = cudaStreamSynchronize(copy_st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (int i = 0; i < 2; ++i)
+    if (copy_st[i]) {
+      cudaError_t e = cudaStreamSynchronize(copy_st[i]);
+      if (e != cudaSuccess && rc == AICDF_OK) {
+        set_cuda_error((int)e);
+        rc = AICDF_ERR_CUDA;
+      }
+      cudaStreamDestroy(copy_st[i]);
+    }
+  cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess && rc == AICDF_OK) {
     set_cuda_error((int)e);
     rc = AICDF_ERR_CUDA;
   }
-  cudaStreamDestroy(copy_st);
-  for (int i = 0; i < 2; ++i) {
-    cudaEventDestroy(done[i]);
-    cudaEventDestroy(copied[i]);
+  for (int i = 0; i < NB; ++i) {
+    if (done[i]) cudaEventDestroy(done[i]);
+    if (copied[i]) cudaEventDestroy(copied[i]);
   }
   return rc;
 }

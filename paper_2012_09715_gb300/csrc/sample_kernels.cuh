@@ -1,0 +1,264 @@
+// Sampling kernels (device side of sample.cu): u -> approximate or exact
+// Gaussian variate for the four methods, two output types and two uniform
+// sources.  Kept apart from the host code so that the kernel source can be
+// fingerprinted on its own.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "aicdf_internal.h"
+#include "device_common.cuh"
+
+namespace aicdf {
+
+enum Source { SRC_PHILOX = 0, SRC_INPUT = 1 };
+
+struct SampleArgs {
+  const float *u;      // SRC_INPUT: caller uniforms
+  void *out;
+  uint64_t n;          // samples
+  uint64_t offset;     // SRC_PHILOX: index of the first sample in the stream
+  PhiloxKeys keys;
+  int ntab;            // PWC: intervals; PWL: K (rows 0..K)
+  float nf;            // PWC: (float)ntab
+  uint32_t pwc_shift;  // PWC: 23 - log2(ntab)
+  float tab[1024];     // PWC constants | PWL alpha[0..15], beta[16..31]
+};
+
+// Per-thread evaluator for one method.  Construction stages the table.
+// word(x): the sample for the library's uniform from Philox word x (on the
+// 2^-24 grid); operator()(u): the sample for any FP32 u (caller uniforms).
+template <int METHOD, int SRC>
+struct Approx;
+
+template <int SRC>
+struct Approx<AICDF_PWC, SRC> {
+  const float *s;
+  float nf;
+  int nmax;
+  uint32_t shift;
+  __device__ Approx(const SampleArgs &a, float *smem) {
+    for (int i = threadIdx.x; i < a.ntab; i += blockDim.x) smem[i] = a.tab[i];
+    __syncthreads();
+    s = smem;
+    nf = a.nf;
+    nmax = a.ntab - 1;
+    shift = a.pwc_shift;
+  }
+  __device__ __forceinline__ float word(uint32_t x) const { return s[pwc_index_from_word(x, shift)]; }
+  __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
+};
+
+template <int SRC>
+struct Approx<AICDF_PWL, SRC> {
+  PwlLane c;     // general inputs: capped index, sign folded into the row
+  PwlRows rows;  // grid inputs: 32 rows, sign by xor
+  unsigned kmax;
+  __device__ Approx(const SampleArgs &a, float *) {
+    if (SRC == SRC_PHILOX) rows = pwl_lane_rows(a.tab, a.tab + 16, a.ntab);
+    else c = pwl_lane_coefs(a.tab, a.tab + 16);
+    kmax = (unsigned)a.ntab;
+  }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_grid(u01(x), rows); }
+  __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
+};
+
+template <int SRC>
+struct Approx<AICDF_EXACT, SRC> {
+  __device__ Approx(const SampleArgs &, float *) {}
+  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }
+  __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
+};
+
+template <int SRC>
+struct Approx<AICDF_EXACT_LIB, SRC> {
+  __device__ Approx(const SampleArgs &, float *) {}
+  __device__ __forceinline__ float word(uint32_t x) const { return normcdfinvf(u01(x)); }
+  __device__ __forceinline__ float operator()(float u) const { return normcdfinvf(u); }
+};
+
+template <int OUT>
+struct OutVec;
+template <>
+struct OutVec<AICDF_F32> {
+  static constexpr int kElems = 4;
+};
+template <>
+struct OutVec<AICDF_F16> {
+  static constexpr int kElems = 8;
+};
+
+__device__ __forceinline__ void store_vec(float *out, uint64_t e, const float (&z)[4]) {
+  *reinterpret_cast<float4 *>(out + e) = make_float4(z[0], z[1], z[2], z[3]);
+}
+__device__ __forceinline__ void store_vec(__half *out, uint64_t e, const float (&z)[8]) {
+  uint4 w;
+  __half2 h0 = __floats2half2_rn(z[0], z[1]), h1 = __floats2half2_rn(z[2], z[3]);
+  __half2 h2 = __floats2half2_rn(z[4], z[5]), h3 = __floats2half2_rn(z[6], z[7]);
+  w.x = *reinterpret_cast<uint32_t *>(&h0);
+  w.y = *reinterpret_cast<uint32_t *>(&h1);
+  w.z = *reinterpret_cast<uint32_t *>(&h2);
+  w.w = *reinterpret_cast<uint32_t *>(&h3);
+  *reinterpret_cast<uint4 *>(out + e) = w;
+}
+__device__ __forceinline__ void store_one(float *out, uint64_t e, float z) { out[e] = z; }
+__device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
+  out[e] = __float2half_rn(z);
+}
+
+// Vectorised kernel.  Requires: out 16-byte aligned; SRC_PHILOX: offset % 4 == 0;
+// SRC_INPUT: u 16-byte aligned.
+template <int METHOD, int OUT, int SRC>
+__global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ SampleArgs a) {
+  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  const Approx<METHOD, SRC> f(a, smem);
+  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
+  T *out = reinterpret_cast<T *>(a.out);
+  constexpr int E = OutVec<OUT>::kElems;
+  // Each warp takes chunks of 2 x 32 consecutive 16-byte vectors; lane L
+  // computes vectors L and L + 32 of the chunk, so its two independent
+  // Philox chains overlap and both stores stay fully coalesced.
+  constexpr int VECS = 2;
+  const uint64_t nvec = (a.n + E - 1) / E;
+  const uint64_t nchunk = (nvec + 32 * VECS - 1) / (32 * VECS);
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: every lane runs every iteration (shuffles need all 32)
+  for (uint64_t chunk = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk;
+       chunk += warps) {
+    float z[VECS][E];
+#pragma unroll
+    for (int hv = 0; hv < VECS; ++hv) {
+      const uint64_t v = chunk * (32 * VECS) + 32 * hv + lane;
+      const uint64_t e0 = v * E;
+      if constexpr (SRC == SRC_PHILOX) {
+#pragma unroll
+        for (int h = 0; h < E / 4; ++h) {
+          const uint64_t j = (a.offset >> 2) + v * (E / 4) + h;
+          const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
+          z[hv][4 * h + 0] = f.word(r.x);
+          z[hv][4 * h + 1] = f.word(r.y);
+          z[hv][4 * h + 2] = f.word(r.z);
+          z[hv][4 * h + 3] = f.word(r.w);
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < E / 4; ++h) {
+          float4 uu = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
+          if (e0 + 4 * h + 3 < a.n) {
+            uu = __ldcs(reinterpret_cast<const float4 *>(a.u + e0 + 4 * h));
+          } else {
+            if (e0 + 4 * h + 0 < a.n) uu.x = a.u[e0 + 4 * h + 0];
+            if (e0 + 4 * h + 1 < a.n) uu.y = a.u[e0 + 4 * h + 1];
+            if (e0 + 4 * h + 2 < a.n) uu.z = a.u[e0 + 4 * h + 2];
+          }
+          const float us[4] = {uu.x, uu.y, uu.z, uu.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            float y = f(us[t]);
+            z[hv][4 * h + t] = in_unit(us[t]) ? y : __int_as_float(0x7fc00000);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int hv = 0; hv < VECS; ++hv) {
+      const uint64_t e0 = (chunk * (32 * VECS) + 32 * hv + lane) * E;
+      if (e0 + E <= a.n) {
+        store_vec(out, e0, z[hv]);
+      } else if (e0 < a.n) {
+#pragma unroll
+        for (int t = 0; t < E; ++t)
+          if (e0 + t < a.n) store_one(out, e0 + t, z[hv][t]);
+      }
+    }
+  }
+}
+
+// The vectorised Philox kernel when every index fits in 32 bits (the host
+// checks j0 + (nvec + 64) E/4 < 2^32 and (nvec + 64) E < 2^32): 32-bit index
+// arithmetic, the counter's high words are the constant 0 (so the compiler
+// folds part of the first round), and chunks that lie wholly inside the
+// output are stored without per-vector bounds checks.
+template <int METHOD, int OUT>
+__global__ void __launch_bounds__(256) k_sample_philox32(const __grid_constant__ SampleArgs a) {
+  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  const Approx<METHOD, SRC_PHILOX> f(a, smem);
+  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
+  T *out = reinterpret_cast<T *>(a.out);
+  constexpr int E = OutVec<OUT>::kElems;
+  constexpr int VECS = 2;
+  constexpr uint32_t CH = 32 * VECS;  // 16-byte vectors per warp chunk
+  const uint32_t n = (uint32_t)a.n;
+  const uint32_t nvec = (n + E - 1) / E;
+  const uint32_t nchunk = (nvec + CH - 1) / CH;
+  const uint32_t nfull = (n / E) / CH;  // chunks with every vector complete
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t j0 = (uint32_t)(a.offset >> 2);
+  for (uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk; chunk += warps) {
+    float z[VECS][E];
+#pragma unroll
+    for (int hv = 0; hv < VECS; ++hv) {
+      const uint32_t v = chunk * CH + 32 * hv + lane;
+#pragma unroll
+      for (int h = 0; h < E / 4; ++h) {
+        const uint4 r = philox(make_uint4(j0 + v * (E / 4) + h, 0u, 0u, 0u), a.keys);
+        z[hv][4 * h + 0] = f.word(r.x);
+        z[hv][4 * h + 1] = f.word(r.y);
+        z[hv][4 * h + 2] = f.word(r.z);
+        z[hv][4 * h + 3] = f.word(r.w);
+      }
+    }
+    if (chunk < nfull) {  // warp-uniform
+#pragma unroll
+      for (int hv = 0; hv < VECS; ++hv) store_vec(out, (uint64_t)(chunk * CH + 32 * hv + lane) * E, z[hv]);
+    } else {
+#pragma unroll
+      for (int hv = 0; hv < VECS; ++hv) {
+        const uint32_t e0 = (chunk * CH + 32 * hv + lane) * E;
+        if (e0 + E <= n) {
+          store_vec(out, e0, z[hv]);
+        } else if (e0 < n) {
+#pragma unroll
+          for (int t = 0; t < E; ++t)
+            if (e0 + t < n) store_one(out, e0 + t, z[hv][t]);
+        }
+      }
+    }
+  }
+}
+
+// Scalar kernel for unaligned pointers or an offset not divisible by 4.
+template <int METHOD, int OUT, int SRC>
+__global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ SampleArgs a) {
+  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  const Approx<METHOD, SRC> f(a, smem);
+  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
+  T *out = reinterpret_cast<T *>(a.out);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n;
+       base += stride) {
+    const uint64_t e = base + lane;
+    float y;
+    if constexpr (SRC == SRC_PHILOX) {
+      const uint64_t s = a.offset + e;
+      const uint64_t j = s >> 2;
+      const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
+      const uint32_t w = (s & 3) == 0 ? r.x : (s & 3) == 1 ? r.y : (s & 3) == 2 ? r.z : r.w;
+      y = f.word(w);
+    } else {
+      const float u = (e < a.n) ? a.u[e] : 0.5f;
+      y = f(u);
+      if (!in_unit(u)) y = __int_as_float(0x7fc00000);
+    }
+    if (e < a.n) store_one(out, e, y);
+  }
+}
+
+
+}  // namespace aicdf

@@ -153,6 +153,24 @@ def test_input_mode_edge_cases(P, tabs, orc):
                 _assert_exact(ze[sel], zinv[sel])
 
 
+@pytest.mark.parametrize("method", ["PWL", "PWC"])
+def test_counters_beyond_32_bits(P, tabs, orc, method):
+    """Sample offsets past 2^34 take the 64-bit-index kernel (Philox counter
+    word 1 non-zero); offset 2^34 - 4000 straddles the 2^32 block boundary."""
+    tl, tc, a, b, q = tabs
+    for off in ((1 << 34) + 8, (1 << 34) - 4000):
+        n = 8195
+        u = orc.uniforms(seed=13, offset=off, n=n)
+        if method == "PWL":
+            ref, _ = orc.sample_pwl(a, b, u)
+            z = _gpu_sample(P, tl, P.PWL, n, seed=13, offset=off)
+            _assert_pwl(z, ref)
+        else:
+            ref, _ = orc.sample_pwc(q, u)
+            z = _gpu_sample(P, tc, P.PWC, n, seed=13, offset=off)
+            assert np.array_equal(z, ref)
+
+
 def test_unaligned_pointers_use_scalar_path(P, tabs, orc):
     import torch
     tl, _, a, b, _ = tabs
