@@ -255,3 +255,28 @@ def mlp_grad(params: dict, x: np.ndarray, t: np.ndarray):
     loss = lib().or_mlp_grad(H, *[_p(a) for a in arrs], _p(x), _p(t), x.shape[0],
                              *[_p(g) for g in grads])
     return loss, dict(zip(names, grads))
+
+
+# ---------------------------------------------------------------- piecewise polynomials
+def pwp_table(K: int = 15, deg: int = 3):
+    """Piecewise polynomial table (rows 0..K x 4 coefficients in the local
+    variable s) and its squared L2 error."""
+    L = lib()
+    if not getattr(L, "_pwp_sig", False):
+        L.or_pwp_table.restype = C.c_double
+        L.or_pwp_table.argtypes = [C.c_int, C.c_int, C.c_void_p]
+        L.or_sample_pwp.restype = None
+        L.or_sample_pwp.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]
+        L._pwp_sig = True
+    c = np.zeros(4 * (K + 1), dtype=np.float64)
+    e2 = L.or_pwp_table(K, deg, _p(c))
+    return c.reshape(K + 1, 4), e2
+
+
+def sample_pwp(coef_f32, u):
+    pwp_table(1, 1)  # binds the signatures
+    c = np.ascontiguousarray(coef_f32, dtype=np.float32).reshape(-1)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    out = np.empty(u.size, dtype=np.float64)
+    lib().or_sample_pwp(_p(c), c.size // 4 - 1, _p(u), u.size, _p(out))
+    return out

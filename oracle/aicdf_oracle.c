@@ -256,6 +256,130 @@ int or_pwl_index(double v, int K, double r) {
 }
 
 /* ========================================================================== */
+/* Piecewise polynomials on the dyadic intervals (Section 2.3, "best L2       */
+/* polynomial on each interval"): normal equations in the local variable s,   */
+/* moments by Gauss-Legendre quadrature.                                      */
+/* ========================================================================== */
+#define OR_GL 48
+static void gauss_legendre(int n, double *x, double *w) {
+  /* nodes on [-1, 1]: Newton on P_n from the Chebyshev-like start */
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* M_j = int_{I_k} s^j Phi^{-1}(u) du, j = 0..3 */
+static void pwp_moments(int k, int K, double *M) {
+  double x[OR_GL], w[OR_GL];
+  gauss_legendre(OR_GL, x, w);
+  for (int j = 0; j < 4; ++j) M[j] = 0.0;
+  const double b = ldexp(1.0, -k);
+  if (k < K) {
+    const double a = 0.5 * b, h = b - a;
+    for (int i = 0; i < OR_GL; ++i) {
+      const double s = 0.5 * (x[i] + 1.0), u = a + h * s, f = or_phiinv(u), wi = 0.5 * w[i] * h;
+      double sp = 1.0;
+      for (int j = 0; j < 4; ++j) {
+        M[j] += wi * sp * f;
+        sp *= s;
+      }
+    }
+  } else {
+    /* singular interval: u = Phi(z), z in (-38, z_b], 16 equal panels */
+    const double zb = or_phiinv(b), zl = -38.0;
+    const int panels = 16;
+    for (int p = 0; p < panels; ++p) {
+      const double z0 = zl + (zb - zl) * p / panels, z1 = zl + (zb - zl) * (p + 1) / panels;
+      for (int i = 0; i < OR_GL; ++i) {
+        const double z = 0.5 * (z1 - z0) * x[i] + 0.5 * (z1 + z0);
+        const double s = or_Phi(z) / b, wi = 0.5 * (z1 - z0) * w[i] * z * or_phi(z);
+        double sp = 1.0;
+        for (int j = 0; j < 4; ++j) {
+          M[j] += wi * sp;
+          sp *= s;
+        }
+      }
+    }
+  }
+}
+
+double or_pwp_table(int K, int deg, double *coef) {
+  if (K < 1 || deg < 1 || deg > 3) return NAN;
+  for (int i = 0; i < 4 * (K + 1); ++i) coef[i] = 0.0;
+  double proj = 0.0;
+  for (int k = 1; k <= K; ++k) {
+    const double b = ldexp(1.0, -k);
+    const double h = (k < K) ? 0.5 * b : b;
+    double M[4], G[4][5];
+    pwp_moments(k, K, M);
+    const int n = deg + 1;
+    /* Gram matrix: int_{I_k} s^i s^j du = h / (i + j + 1) */
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) G[i][j] = h / (i + j + 1.0);
+      G[i][n] = M[i];
+    }
+    /* Gaussian elimination with partial pivoting */
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (fabs(G[r][c]) > fabs(G[piv][c])) piv = r;
+      for (int j = 0; j <= n; ++j) {
+        double t = G[c][j];
+        G[c][j] = G[piv][j];
+        G[piv][j] = t;
+      }
+      for (int r = c + 1; r < n; ++r) {
+        double f = G[r][c] / G[c][c];
+        for (int j = c; j <= n; ++j) G[r][j] -= f * G[c][j];
+      }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      double s = G[r][n];
+      for (int j = r + 1; j < n; ++j) s -= G[r][j] * coef[4 * k + j];
+      coef[4 * k + r] = s / G[r][r];
+    }
+    for (int j = 0; j < n; ++j) proj += coef[4 * k + j] * M[j];
+  }
+  /* projection: int D Phi^{-1} = int D^2 per interval; both halves */
+  return 1.0 - 2.0 * proj;
+}
+
+void or_sample_pwp(const float *coef, int K, const float *u, int64_t n, double *out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double x = (double)u[i];
+    if (!(x >= 0.0 && x <= 1.0)) {
+      out[i] = NAN;
+      continue;
+    }
+    int lower = x < 0.5;
+    double v = lower ? x : 1.0 - x;
+    int k = or_pwl_index(v, K, 0.5);
+    double s = 0.0;
+    if (k > 0) {
+      const double b = ldexp(1.0, -k);
+      s = (k < K) ? (v - 0.5 * b) / (0.5 * b) : v / b;
+    }
+    double z = 0.0;
+    for (int j = 3; j >= 0; --j) z = z * s + (double)coef[4 * k + j];
+    out[i] = lower ? z : -z;
+  }
+}
+
+/* ========================================================================== */
 /* Samplers (Section 3.2 piecewise constant; Section 3.3 / Algorithm 1)       */
 /* ========================================================================== */
 void or_sample_pwc(const float *table, int n_table, const float *u, int64_t n,

@@ -48,6 +48,14 @@ double or_pwl_l2err2(int K, double r, const double *alpha, const double *beta);
 /* interval index of v in (0,1/2] for decay rate r (0 for v = 1/2) */
 int    or_pwl_index(double v, int K, double r);
 
+/* Piecewise polynomials of degree deg (1..3) on the K dyadic intervals of
+ * (0, 1/2) (Section 2.3: the best L2 polynomial on each interval), in the
+ * local variable s in [0, 1): s = (v - a)/(b - a) on I_k = [a, b), k < K, and
+ * s = v / b on I_K = (0, b).  coef[4 k + j] multiplies s^j (rows 1..K; row 0
+ * zero, unused coefficients zero).  Returns ||D - Phi^{-1}||_2^2 over (0, 1). */
+double or_pwp_table(int K, int deg, double *coef);
+void or_sample_pwp(const float *coef, int K, const float *u, int64_t n, double *out);
+
 /* ---- samplers (Section 3.2 listing semantics; Algorithm 1) ---------------- */
 void or_sample_pwc(const float *table, int n_table, const float *u, int64_t n,
                    double *out, int32_t *idx);

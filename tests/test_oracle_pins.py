@@ -296,6 +296,66 @@ def test_pwl_peano_bound(orc):
         assert err.max() <= 2.59
 
 
+# ---------------------------------------------------------------- piecewise polynomials
+def test_pwp_degree1_equals_closed_form_pwl(orc):
+    """The quadrature route of the polynomial tables, at degree 1, reproduces the
+    closed-form L2 lines (proof of Theorem 2.4) in the local variable s."""
+    for K in (8, 15, 16):
+        c, e2 = orc.pwp_table(K, 1)
+        a, b = orc.pwl_table(K, 0.5)
+        for k in range(1, K + 1):
+            hi = 2.0 ** -k
+            lo = 0.0 if k == K else hi / 2
+            assert c[k, 0] == pytest.approx(a[k] + b[k] * lo, rel=1e-11, abs=1e-12)
+            assert c[k, 1] == pytest.approx(b[k] * (hi - lo), rel=1e-10)
+        assert e2 == pytest.approx(orc.pwl_l2err2(a, b), rel=1e-9)
+
+
+def test_pwp_cubic_error_and_orthogonality(orc):
+    """Piecewise cubic on 16 dyadic intervals reaches an L2 error around 1e-4,
+    far below the linear plateau ~1e-2 (Section 2.3, Fig. 2 discussion); the
+    residual is orthogonal to 1, s, s^2, s^3 on every interval (independent
+    adaptive quadrature)."""
+    from scipy.integrate import quad
+    from scipy.special import ndtri
+    c16, e16 = orc.pwp_table(16, 3)
+    l16 = orc.pwl_l2err2(*orc.pwl_table(16, 0.5))
+    assert 5e-5 < math.sqrt(e16) < 5e-4
+    assert math.sqrt(l16) / math.sqrt(e16) > 10
+    c, _ = orc.pwp_table(15, 3)
+    for k in (1, 5, 14):
+        hi = 2.0 ** -k
+        lo = hi / 2
+        for j in range(4):
+            f = lambda u: ((u - lo) / (hi - lo)) ** j * (ndtri(u) - np.polyval(c[k, ::-1], (u - lo) / (hi - lo)))
+            val = quad(f, lo, hi, epsabs=1e-16, epsrel=1e-12, limit=200)[0]
+            assert abs(val) < 1e-12 * (hi - lo) * 10, (k, j, val)
+
+
+def test_pwp_sampler_bruteforce(orc):
+    """Grid uniforms near every interval edge: the sampler evaluates the cubic
+    of the interval containing min(u, 1-u) in its local variable, with the sign
+    restored (Algorithm 1 with Horner's rule)."""
+    c, _ = orc.pwp_table(15, 3)
+    c32 = c.astype(np.float32)
+    ks = []
+    for k in range(1, 24):
+        m = int(2 ** 24 * 2.0 ** -k)
+        for d in (-3, -1, 1, 3):
+            if 0 < m + d < 2 ** 24 and (m + d) % 2:
+                ks += [m + d, 2 ** 24 - (m + d)]
+    u = (np.array(ks) * 2.0 ** -24).astype(np.float32)
+    z = orc.sample_pwp(c32, u)
+    ud = u.astype(np.float64)
+    v = np.where(ud < 0.5, ud, 1 - ud)
+    _, ex = np.frexp(v)
+    k = np.minimum(-ex, 15)
+    b = 2.0 ** -k
+    s = np.where(k < 15, (v - b / 2) / (b / 2), v / b)
+    want = sum(c32[k, j].astype(np.float64) * s ** j for j in range(4))
+    assert np.allclose(z, np.where(ud < 0.5, want, -want), rtol=1e-13, atol=1e-13)
+
+
 # ---------------------------------------------------------------- samplers
 def test_samplers_bruteforce_grid(orc):
     """Every point of the uniform grid near every interval edge: the PWL index
