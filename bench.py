@@ -408,9 +408,11 @@ def main():
         # other methods / dtypes on the same GPU, same workload size
         out16 = torch.empty(N_SAMPLES, dtype=torch.float16, device=dev)
         tc = P.table_build(P.PWC, 1024)
+        tp = P.table_build(P.PWP, 15, 3)
         variants = {
             "pwl_f16": lambda: P.sample(tl, P.PWL, out16, seed=seed, stream=stream),
             "pwc_f32": lambda: P.sample(tc, P.PWC, out, seed=seed, stream=stream),
+            "pwp3_f32": lambda: P.sample(tp, P.PWP, out, seed=seed, stream=stream),
             "exact_f32": lambda: P.sample(None, P.EXACT, out, seed=seed, stream=stream),
             "exact_lib_f32": lambda: P.sample(None, P.EXACT_LIB, out, seed=seed, stream=stream),
         }

@@ -51,7 +51,9 @@ int aicdf_version(void);
 /* ===================================================================== */
 /* Approximation tables (host objects; built in FP64)                     */
 /* ===================================================================== */
-typedef enum { AICDF_PWC = 0, AICDF_PWL = 1, AICDF_EXACT = 2, AICDF_EXACT_LIB = 3 } aicdf_method;
+typedef enum {
+  AICDF_PWC = 0, AICDF_PWL = 1, AICDF_EXACT = 2, AICDF_EXACT_LIB = 3, AICDF_PWP = 4
+} aicdf_method;
 typedef enum { AICDF_Z_E = 0, AICDF_Z_C = 1, AICDF_Z_I = 2 } aicdf_construction;
 typedef struct aicdf_table_s *aicdf_table;
 
@@ -67,6 +69,13 @@ typedef struct aicdf_table_s *aicdf_table;
  *   on its interval (the normal equations of the proof of Theorem 2.4).  The
  *   table holds K+1 rows; row 0 is zero so that u = 1/2 maps to 0 (Section
  *   3.3).  construction must be AICDF_Z_E (ignored).
+ * AICDF_PWP (Section 2.3, the piecewise polynomial generalisation; Fig. 2
+ *   uses cubics): n = K dyadic intervals as for PWL, construction = the
+ *   degree d in 1..3; on each interval the L2-optimal polynomial of degree d
+ *   in the local variable s in [0, 1): s = (v - a)/(b - a) on I_k = [a, b),
+ *   k < K (the fraction of v's FP32 significand), and s = v / b on I_K = (0, b).
+ *   The table holds K+1 rows of 4 coefficients (powers s^0..s^3; row 0 and the
+ *   powers above d are zero).
  * On success *out owns the table; release it with aicdf_table_destroy. */
 aicdf_status aicdf_table_build(int method, int n, int construction, aicdf_table *out);
 void aicdf_table_destroy(aicdf_table t);

@@ -25,7 +25,7 @@ KIND_APPROX2, KIND_CORR4, KIND_EXACT2, KIND_PLAIN, KIND_PLAIN_APPROX = 0, 1, 2, 
 MODEL_GBM, MODEL_CIR = 0, 1
 SCHEME_EM, SCHEME_MILSTEIN = 0, 1
 PAYOFF_X, PAYOFF_CALL = 0, 1
-APPROX_PWL, APPROX_PWC = 0, 1
+APPROX_PWL, APPROX_PWC, APPROX_PWP = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -185,6 +185,9 @@ def _approx_arrays(approx_table):
         b = np.ascontiguousarray(approx_table[1], dtype=np.float32)
         return a, b, a.size - 1
     t = np.ascontiguousarray(approx_table, dtype=np.float32)
+    if t.ndim == 2:  # piecewise polynomial rows 0..K x 4 coefficients
+        t = t.reshape(-1)
+        return t, t, t.size // 4 - 1
     return t, t, t.size
 
 

@@ -426,6 +426,7 @@ static double approx_variate(const or_sde_params *prm, const float *alpha, const
                              int K, float u) {
   double z;
   if (prm->approx == OR_APPROX_PWC) or_sample_pwc(alpha, K, &u, 1, &z, NULL);
+  else if (prm->approx == OR_APPROX_PWP) or_sample_pwp(alpha, K, &u, 1, &z);
   else or_sample_pwl(alpha, beta, K, &u, 1, &z, NULL);
   return z;
 }

@@ -68,7 +68,7 @@ enum { OR_KIND_APPROX2 = 0, OR_KIND_CORR4 = 1, OR_KIND_EXACT2 = 2, OR_KIND_PLAIN
 enum { OR_MODEL_GBM = 0, OR_MODEL_CIR = 1 };
 enum { OR_SCHEME_EM = 0, OR_SCHEME_MILSTEIN = 1 };
 enum { OR_PAYOFF_X = 0, OR_PAYOFF_CALL = 1 };
-enum { OR_APPROX_PWL = 0, OR_APPROX_PWC = 1 };
+enum { OR_APPROX_PWL = 0, OR_APPROX_PWC = 1, OR_APPROX_PWP = 2 };
 
 typedef struct {
   int model, scheme, payoff, approx;
@@ -82,7 +82,8 @@ typedef struct {
  * for the level estimator of the given kind.  sums = {sum Y, sum Y^2, n}.
  * Uniform for fine step s of path p: Philox4x32-10 with
  * ctr = (s/4, p mod 2^32, p>>32, tag), key = (seed mod 2^32, seed>>32), word s%4.
- * approx tables: PWL (alpha, beta, K) or PWC (alpha = table, K = n_table). */
+ * approx tables: PWL (alpha, beta, K), PWC (alpha = table, K = n_table) or
+ * PWP (alpha = (K+1) x 4 polynomial coefficients, K). */
 void or_mlmc_level(const or_sde_params *prm, const float *alpha, const float *beta, int K,
                    int level, int kind, uint64_t n_paths, uint64_t path_offset,
                    uint64_t seed, uint32_t tag, double sums[3]);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libaicdf.so")
 
 # enums (include/aicdf.h)
 OK, ERR_ARG, ERR_CUDA, ERR_NOCONVERGE, ERR_DOMAIN, ERR_STATE, ERR_NOMEM, ERR_UNSUPPORTED = range(8)
-PWC, PWL, EXACT, EXACT_LIB = 0, 1, 2, 3
+PWC, PWL, EXACT, EXACT_LIB, PWP = 0, 1, 2, 3, 4
 Z_E, Z_C, Z_I = 0, 1, 2
 F32, F16 = 0, 1
 MODEL_GBM, MODEL_CIR = 0, 1
@@ -184,12 +184,14 @@ class Table:
 
     def coefficients(self):
         import numpy as np
-        cnt = self.n if self.method == PWC else self.n + 1
+        cnt = {PWC: self.n, PWL: self.n + 1, PWP: 4 * (self.n + 1)}[self.method]
         c0 = np.zeros(cnt, dtype=np.float64)
         c1 = np.zeros(cnt, dtype=np.float64)
         got = C.c_int()
         _check(lib().aicdf_table_get(self.handle, c0.ctypes.data, c1.ctypes.data, cnt, C.byref(got)),
                "table_get")
+        if self.method == PWP:
+            return (c0.reshape(self.n + 1, 4),)
         return (c0,) if self.method == PWC else (c0, c1)
 
     def info(self):

@@ -91,6 +91,54 @@ __device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) {
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
 }
 
+// ---------------------------------------------------------------------------
+// Piecewise polynomial (degree <= 3) on the dyadic intervals, Horner's rule in
+// the local variable s: the fraction of v's significand on I_k = [2^-(k+1),
+// 2^-k) (exactly (v - a)/(b - a)), and v 2^K on the singular interval.  Lane L
+// holds the 4 coefficients of row min(30 - L, K), as for the linear table.
+struct PwpRows {
+  float c0, c1, c2, c3;
+};
+
+__device__ __forceinline__ PwpRows pwp_lane_rows(const float *tab, int K) {  // tab: [4 powers][16 rows]
+  const int r = min(max(30 - (int)(threadIdx.x & 31), 0), K);
+  return PwpRows{tab[r], tab[16 + r], tab[32 + r], tab[48 + r]};
+}
+
+// v in [0, 1/2]; lane = 30 - row; all 32 lanes must call.
+__device__ __forceinline__ float pwp_eval_v(float v, uint32_t lane, bool singular, float scale_k,
+                                            const PwpRows &c) {
+  const float a0 = __shfl_sync(0xffffffffu, c.c0, lane);
+  const float a1 = __shfl_sync(0xffffffffu, c.c1, lane);
+  const float a2 = __shfl_sync(0xffffffffu, c.c2, lane);
+  const float a3 = __shfl_sync(0xffffffffu, c.c3, lane);
+  const float frac = __uint_as_float((__float_as_uint(v) & 0x7FFFFFu) | 0x3F800000u) - 1.0f;
+  const float s = singular ? v * scale_k : frac;
+  return fmaf(fmaf(fmaf(a3, s, a2), s, a1), s, a0);
+}
+
+// Grid uniforms: lane = biased exponent e of v (mod 32), singular when e <= 126 - K.
+__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c, uint32_t e_sing, float scale_k) {
+  const float t = u - 0.5f;
+  const float v = 0.5f - fabsf(t);
+  const uint32_t e = __float_as_uint(v) >> 23;
+  const float z = pwp_eval_v(v, e, e <= e_sing, scale_k, c);
+  return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
+}
+
+// Any FP32 u (caller uniforms): reflection by 1 - u, capped row.  The row is
+// taken in unsigned arithmetic as in pwl_eval: a set sign bit (u = -0, or the
+// NaN / out-of-range inputs whose result the caller discards) wraps 126 - e
+// past K, so -0 lands on the singular row like +0.
+__device__ __forceinline__ float pwp_eval(float u, const PwpRows &c, uint32_t K, float scale_k) {
+  const bool lower = u < 0.5f;
+  const float v = lower ? u : 1.0f - u;
+  const uint32_t e = __float_as_uint(v) >> 23;
+  const uint32_t row = min(126u - e, K);
+  const float z = pwp_eval_v(v, 30u - row, row == K, scale_k, c);
+  return lower ? z : -z;
+}
+
 // Piecewise constant with n = 2^q intervals for a grid uniform from word x:
 // floor(n u) = floor((2m+1) 2^-(24-q)) = m >> (23 - q), m = low 23 bits.
 __device__ __forceinline__ uint32_t pwc_index_from_word(uint32_t x, uint32_t shift) {

@@ -111,7 +111,9 @@ LevelFn pick_model(int model) {
 
 template <bool NE, bool NA>
 LevelFn pick_ap(int ap, int model) {
-  return ap == AICDF_PWL ? pick_model<NE, NA, AICDF_PWL>(model) : pick_model<NE, NA, AICDF_PWC>(model);
+  return ap == AICDF_PWL   ? pick_model<NE, NA, AICDF_PWL>(model)
+         : ap == AICDF_PWP ? pick_model<NE, NA, AICDF_PWP>(model)
+                           : pick_model<NE, NA, AICDF_PWC>(model);
 }
 
 static LevelFn select_level_kernel(int kind, int ap, int model) {
@@ -162,6 +164,10 @@ aicdf_status pack_table(aicdf_table approx, float *tab, int *ntab) {
       tab[i] = approx->f0[r];
       tab[16 + i] = approx->f1[r];
     }
+  } else if (approx->method == AICDF_PWP) {
+    if (approx->n > 15) return AICDF_ERR_UNSUPPORTED;
+    for (int j = 0; j < 4; ++j)
+      for (int r = 0; r < 16; ++r) tab[16 * j + r] = approx->f0[4 * std::min(r, approx->n) + j];
   } else {
     if (approx->n > 1024) return AICDF_ERR_UNSUPPORTED;
     for (int i = 0; i < approx->n; ++i) tab[i] = approx->f0[i];
@@ -292,6 +298,7 @@ using BatchFn = void (*)(BatchArgs);
 
 static BatchFn select_batch_kernel(int ap, bool v16) {
   if (ap == AICDF_PWL) return v16 ? (BatchFn)k_mlmc_batch<AICDF_PWL, true> : (BatchFn)k_mlmc_batch<AICDF_PWL, false>;
+  if (ap == AICDF_PWP) return v16 ? (BatchFn)k_mlmc_batch<AICDF_PWP, true> : (BatchFn)k_mlmc_batch<AICDF_PWP, false>;
   return v16 ? (BatchFn)k_mlmc_batch<AICDF_PWC, true> : (BatchFn)k_mlmc_batch<AICDF_PWC, false>;
 }
 

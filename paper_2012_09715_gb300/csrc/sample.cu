@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "aicdf_internal.h"
@@ -36,6 +37,7 @@ static KernelFn select_kernel(int method, int out, int src, bool vec) {
   switch (method) {
     case AICDF_PWC: return pick2<AICDF_PWC>(out, src, vec);
     case AICDF_PWL: return pick2<AICDF_PWL>(out, src, vec);
+    case AICDF_PWP: return pick2<AICDF_PWP>(out, src, vec);
     case AICDF_EXACT: return pick2<AICDF_EXACT>(out, src, vec);
     default: return pick2<AICDF_EXACT_LIB>(out, src, vec);
   }
@@ -44,9 +46,15 @@ static KernelFn select_kernel(int method, int out, int src, bool vec) {
 // Fill the kernel argument block; validates the method/table pairing.
 aicdf_status prepare_sample_args(aicdf_table table, int method, SampleArgs *a) {
   std::memset(a, 0, sizeof(*a));
-  if (method == AICDF_PWC || method == AICDF_PWL) {
+  if (method == AICDF_PWC || method == AICDF_PWL || method == AICDF_PWP) {
     if (!table_ok(table) || table->method != method) return AICDF_ERR_ARG;
-    if (method == AICDF_PWC) {
+    if (method == AICDF_PWP) {
+      if (table->n > 15) return AICDF_ERR_UNSUPPORTED;
+      for (int j = 0; j < 4; ++j)
+        for (int r = 0; r < 16; ++r) a->tab[16 * j + r] = table->f0[4 * std::min(r, table->n) + j];
+      a->ntab = table->n;
+      a->nf = std::ldexp(1.0f, table->n);  // 2^K: scale of the singular interval
+    } else if (method == AICDF_PWC) {
       if (table->n > 1024) return AICDF_ERR_UNSUPPORTED;
       for (int i = 0; i < table->n; ++i) a->tab[i] = table->f0[i];
       a->ntab = table->n;
@@ -76,6 +84,7 @@ static KernelFn select_philox32(int method) {
   switch (method) {
     case AICDF_PWC: return k_sample_philox32<AICDF_PWC, OUT>;
     case AICDF_PWL: return k_sample_philox32<AICDF_PWL, OUT>;
+    case AICDF_PWP: return k_sample_philox32<AICDF_PWP, OUT>;
     case AICDF_EXACT: return k_sample_philox32<AICDF_EXACT, OUT>;
     default: return k_sample_philox32<AICDF_EXACT_LIB, OUT>;
   }

@@ -67,6 +67,22 @@ struct Approx<AICDF_PWL, SRC> {
 };
 
 template <int SRC>
+struct Approx<AICDF_PWP, SRC> {
+  PwpRows rows;
+  uint32_t K;
+  uint32_t e_sing;
+  float scale_k;
+  __device__ Approx(const SampleArgs &a, float *) {
+    rows = pwp_lane_rows(a.tab, a.ntab);
+    K = (uint32_t)a.ntab;
+    e_sing = 126u - (uint32_t)a.ntab;
+    scale_k = a.nf;  // 2^K
+  }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_grid(u01(x), rows, e_sing, scale_k); }
+  __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K, scale_k); }
+};
+
+template <int SRC>
 struct Approx<AICDF_EXACT, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
   __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }

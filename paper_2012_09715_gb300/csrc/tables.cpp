@@ -105,6 +105,83 @@ static aicdf_status build_pwl(aicdf_table_s *t, int K) {
   return AICDF_OK;
 }
 
+// Piecewise polynomial of degree d on the dyadic intervals (Section 2.3: the
+// best L2 polynomial on each interval) in the local variable s in [0, 1).
+// Projection onto shifted Legendre polynomials L_j(s) (orthogonal on [0,1],
+// int L_j^2 = 1/(2j+1)), so no linear system is solved:
+//   D = sum_j (2j+1) <f, L_j>_s L_j(s),  <f, L_j>_s = (1/h) int_{I_k} L_j(s(u)) f(u) du,
+// then expanded to monomials in s.  Moments: Gauss-Legendre in u on the regular
+// intervals; on the singular interval (0, b) the substitution u = b e^{-w}
+// (s = e^{-w}, w in [0, 80], 40 panels).
+static void gl_nodes(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// shifted Legendre L_0..L_3 on [0, 1] as monomial coefficients [j][power]
+static const double kShiftedLegendre[4][4] = {
+    {1, 0, 0, 0}, {-1, 2, 0, 0}, {1, -6, 6, 0}, {-1, 12, -30, 20}};
+
+static aicdf_status build_pwp(aicdf_table_s *t, int K, int deg) {
+  t->c0.assign(4 * (K + 1), 0.0);  // row-major [row][power]
+  std::vector<double> gx, gw;
+  gl_nodes(40, gx, gw);
+  for (int k = 1; k <= K; ++k) {
+    const double b = std::ldexp(1.0, -k);
+    double proj[4] = {0, 0, 0, 0};  // (1/h) int L_j(s) f du = int_0^1 L_j(s) f(u(s)) ds
+    auto accumulate = [&](double s, double f, double weight) {
+      double Lv[4];
+      for (int j = 0; j < 4; ++j) {
+        const double *c = kShiftedLegendre[j];
+        Lv[j] = ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+        proj[j] += weight * Lv[j] * f;
+      }
+    };
+    if (k < K) {
+      const double a = 0.5 * b, h = b - a;
+      for (size_t i = 0; i < gx.size(); ++i) {
+        const double s = 0.5 * (gx[i] + 1.0);
+        accumulate(s, aicdf::host_phiinv(a + h * s), 0.5 * gw[i]);
+      }
+    } else {
+      // s = e^{-w}, ds = e^{-w} dw
+      const int panels = 40;
+      const double wmax = 80.0;
+      for (int p = 0; p < panels; ++p) {
+        const double w0 = wmax * p / panels, w1 = wmax * (p + 1) / panels;
+        for (size_t i = 0; i < gx.size(); ++i) {
+          const double wv = 0.5 * (w1 - w0) * gx[i] + 0.5 * (w1 + w0);
+          const double s = std::exp(-wv);
+          accumulate(s, aicdf::host_phiinv(b * s), 0.5 * (w1 - w0) * gw[i] * s);
+        }
+      }
+    }
+    for (int j = 0; j <= deg; ++j) {
+      const double dj = (2.0 * j + 1.0) * proj[j];
+      for (int pw = 0; pw < 4; ++pw) t->c0[4 * k + pw] += dj * kShiftedLegendre[j][pw];
+    }
+  }
+  t->c1.clear();
+  return AICDF_OK;
+}
+
 extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, aicdf_table *out) {
   if (!out) return AICDF_ERR_ARG;
   *out = nullptr;
@@ -113,6 +190,8 @@ extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, a
     if (construction < AICDF_Z_E || construction > AICDF_Z_I) return AICDF_ERR_ARG;
   } else if (method == AICDF_PWL) {
     if (n < 1 || n > 31) return AICDF_ERR_ARG;
+  } else if (method == AICDF_PWP) {
+    if (n < 1 || n > 31 || construction < 1 || construction > 3) return AICDF_ERR_ARG;
   } else {
     return AICDF_ERR_ARG;
   }
@@ -122,7 +201,9 @@ extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, a
   t->method = method;
   t->n = n;
   t->construction = construction;
-  aicdf_status s = (method == AICDF_PWC) ? build_pwc(t, n, construction) : build_pwl(t, n);
+  aicdf_status s = (method == AICDF_PWC)   ? build_pwc(t, n, construction)
+                   : (method == AICDF_PWL) ? build_pwl(t, n)
+                                           : build_pwp(t, n, construction);
   if (s != AICDF_OK) {
     delete t;
     return s;

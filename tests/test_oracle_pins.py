@@ -507,6 +507,61 @@ def test_mlmc_variance_structure(orc):
     assert max(rl) - min(rl) < 1.0 and max(rc) - min(rc) < 1.0
 
 
+def test_mlmc_pwp_linear_rows_reproduce_pwl_paths(orc):
+    """A degree-1 polynomial table is the piecewise linear approximation written
+    in the local variable s, so coupled paths driven by it equal the PWL paths up
+    to the FP32 rounding of the two coefficient sets (a wrong row, local
+    variable or sign in the polynomial branch of the path code fails this)."""
+    a, b = orc.pwl_table(15, 0.5)
+    c1, _ = orc.pwp_table(15, 1)
+    for kind in (orc.KIND_APPROX2, orc.KIND_CORR4, orc.KIND_PLAIN_APPROX):
+        yl = orc.mlmc_paths(_gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWL), (a, b), 3, kind, 3000,
+                            seed=2, tag=5)
+        yp = orc.mlmc_paths(_gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWP), c1, 3, kind, 3000,
+                            seed=2, tag=5)
+        # the coefficient rounding moves Y by ~1e-5 of its own scale
+        assert np.max(np.abs(yl - yp)) < 1e-4 * np.max(np.abs(yl)), kind
+        assert np.max(np.abs(yl)) > 0
+
+
+def test_mlmc_cubic_variance_drop(orc):
+    """Fig. 3 / Table 6, with the variance predicted from the table's own error.
+
+    Writing Z~ = Z - e, the first-order effect of e_n cancels between the fine
+    and the coarse path (the coarse increment sums the same two variates); what
+    remains is e_n sigma^2 h Z_(n+-1), so Var(four-way) ~ N delta^2 sigma^4 h^2
+    = 2 delta^2 Var(two-way), delta^2 = E[e^2] the squared L2 error.  PWL (K=15)
+    has delta = 6.5e-3: 2 delta^2 = 2^-13.5 (the paper's 2^-14).  For the cubic,
+    the regular intervals give delta = 1.0e-4 (the paper's ~1e-4): 2^-25.6, the
+    paper's 2^-25; the singular interval adds 93% of delta^2 through rare u near
+    0, so the full expectation is 2^-21.7 and finite-sample estimates lie
+    between the two."""
+    from scipy.integrate import quad
+    from scipy.special import ndtri
+    c3, e2 = orc.pwp_table(15, 3)
+    reg = 0.0
+    for k in range(1, 15):
+        hi = 2.0 ** -k
+        lo = hi / 2
+        reg += 2 * quad(lambda u: (ndtri(u) - np.polyval(c3[k, ::-1], (u - lo) / (hi - lo))) ** 2, lo, hi,
+                        epsabs=1e-20, limit=200)[0]
+    assert 0.9e-4 < math.sqrt(reg) < 1.1e-4 and reg < 0.1 * e2
+    lo_pred, hi_pred = math.log2(2 * reg), math.log2(2 * e2)
+    assert -26 < lo_pred < -25 and -22 < hi_pred < -21.5
+    prm = _gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWP)
+    prm_l = _gbm(orc, orc.PAYOFF_X, approx=orc.APPROX_PWL)
+    a, b = orc.pwl_table(15, 0.5)
+    for level in (2, 3):
+        n = 20000
+        y2 = orc.mlmc_paths(prm, c3, level, orc.KIND_EXACT2, n, seed=1, tag=1)
+        y4 = orc.mlmc_paths(prm, c3, level, orc.KIND_CORR4, n, seed=1, tag=1)
+        y4l = orc.mlmc_paths(prm_l, (a, b), level, orc.KIND_CORR4, n, seed=1, tag=1)
+        r = math.log2(y4.var() / y2.var())
+        rl = math.log2(y4l.var() / y2.var())
+        assert lo_pred - 1.5 < r < hi_pred + 1.0, (level, r)
+        assert r < rl - 8, (level, r, rl)
+
+
 def test_cost_model_tables(orc):
     """Table 2 and Table 6 speed-ups follow from the allocation formulas of
     Section 4.1 with C~ = c^ + c~ and v~ = v^."""
