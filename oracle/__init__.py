@@ -107,6 +107,17 @@ def uniforms(seed: int, offset: int, n: int) -> np.ndarray:
     return u
 
 
+def uniforms_bits(seed: int, offset: int, n: int, bits: int) -> np.ndarray:
+    L = lib()
+    if not getattr(L, "_ubits_sig", False):
+        L.or_uniforms_bits.restype = None
+        L.or_uniforms_bits.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_int, C.c_void_p]
+        L._ubits_sig = True
+    u = np.empty(n, dtype=np.float32)
+    L.or_uniforms_bits(seed, offset, n, bits, _p(u))
+    return u
+
+
 # ---------------------------------------------------------------- Gaussian
 def phiinv(u):
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float32))

@@ -95,6 +95,26 @@ void or_uniforms(uint64_t seed, uint64_t offset, int64_t n, float *u) {
   }
 }
 
+/* Truncated-bit uniforms (Section 1, Section 2.2: a uniform carried to B bits
+ * and offset to its cell midpoint).  Philox call j gives four words; each word
+ * holds F = floor(32/B) B-bit fields.  Sample s of the stream is field h of
+ * word t of call j with s = 4F j + 4h + t, and u = (m + 1/2) 2^-B for the
+ * field value m. */
+void or_uniforms_bits(uint64_t seed, uint64_t offset, int64_t n, int bits, float *u) {
+  const uint64_t key[2] = {seed & 0xffffffffull, seed >> 32};
+  const uint64_t F = (uint64_t)(32 / bits), per = 4 * F;
+  const uint64_t mask = (1ull << bits) - 1;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t s = offset + (uint64_t)i;
+    uint64_t j = s / per, r = s % per, h = r / 4, t = r % 4;
+    uint64_t ctr[4] = {j & 0xffffffffull, j >> 32, 0, 0};
+    uint64_t out[4];
+    or_philox4(32, 10, ctr, key, out);
+    uint64_t m = (out[t] >> (h * (uint64_t)bits)) & mask;
+    u[i] = (float)(((double)m + 0.5) / (double)(1ull << bits));
+  }
+}
+
 /* ========================================================================== */
 /* Gaussian: phi, Phi, and the exact inverse Phi^{-1} (Section 2)             */
 /* ========================================================================== */
@@ -168,9 +188,20 @@ int or_pwc_table(int n, int construction, double *q) {
       if (ulo >= 0.5) q[k] = or_phiinv(ulo);
       else if (uhi < 0.5) q[k] = or_phiinv(uhi);
       else q[k] = 0.0; /* interval straddles 1/2 (only for n = 2): endpoint 1/2 */
+    } else if (construction == 3) {
+      /* Z^V: Z^E rescaled to unit variance (moment matching, Section 1); for
+       * n = 2 the values are +-1, the Rademacher variables. */
+      double pa = (k == 0) ? 0.0 : or_phi(or_phiinv(ulo));
+      double pb = (k == n - 1) ? 0.0 : or_phi(or_phiinv(uhi));
+      q[k] = n * (pa - pb);
     } else {
       return -1;
     }
+  }
+  if (construction == 3) {
+    double m2 = 0.0;
+    for (int k = 0; k < n; ++k) m2 += q[k] * q[k] / n;
+    for (int k = 0; k < n; ++k) q[k] /= sqrt(m2);
   }
   return 0;
 }

@@ -31,6 +31,10 @@ double or_u01(uint32_t x);
 /* Standalone sampling stream: sample i uses Philox call j=(offset+i)/4 with
  * ctr=(j mod 2^32, j>>32, 0, 0), key=(seed mod 2^32, seed>>32), word (offset+i)%4. */
 void or_uniforms(uint64_t seed, uint64_t offset, int64_t n, float *u);
+/* Truncated-bit stream, B = bits in [1, 23]: F = floor(32/B) fields per word;
+ * sample s = 4F j + 4h + t is field h (bits hB..hB+B-1) of word t of call j
+ * (counter and key as above); u = (m + 1/2) 2^-B. */
+void or_uniforms_bits(uint64_t seed, uint64_t offset, int64_t n, int bits, float *u);
 
 /* ---- Gaussian ---------------------------------------------------------------- */
 double or_phi(double z);            /* density */
@@ -39,7 +43,8 @@ double or_phiinv(double u);         /* exact inverse CDF: bisection + Newton on 
 void   or_phiinv_n(const float *u, int64_t n, double *z);
 
 /* ---- tables (Section 2.2, Corollary 2.3; Section 2.3, Theorem 2.4) --------- */
-/* construction: 0 = conditional mean Z^E, 1 = centre Z^C, 2 = inner endpoint Z^I */
+/* construction: 0 = conditional mean Z^E, 1 = centre Z^C, 2 = inner endpoint Z^I,
+ * 3 = Z^E rescaled to unit variance (n = 2: Rademacher +-1) */
 int    or_pwc_table(int n, int construction, double *q);
 double or_pwc_l2err2(int n, const double *q);          /* ||Q - Phi^-1||_2^2 */
 /* K intervals with decay rate r; alpha/beta get K+1 rows, row 0 = (0,0). */

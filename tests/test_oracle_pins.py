@@ -80,6 +80,68 @@ def test_u01_grid(orc):
     assert orc.u01(0xFF800000) == 2.0 ** -24 and orc.u01(0x0000_1235) == (2 * 0x1235 + 1) * 2.0 ** -24
 
 
+@pytest.mark.parametrize("bits", [1, 8, 10, 16])
+def test_truncated_uniform_stream_mapping(orc, bits):
+    """Sample s = 4F j + 4h + t of the B-bit stream is field h of word t of
+    Philox call j, at the midpoint (m + 1/2) 2^-B of its cell."""
+    F = 32 // bits
+    off, n = 4 * F * 3 + 5, 4 * F * 2 + 7
+    seed = 0xABCDEF0123
+    u = orc.uniforms_bits(seed=seed, offset=off, n=n, bits=bits)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(n):
+        s = off + i
+        j, r = divmod(s, 4 * F)
+        h, t = divmod(r, 4)
+        w = int(orc.philox4([j, 0, 0, 0], key, 32)[t])
+        m = (w >> (h * bits)) & ((1 << bits) - 1)
+        assert u[i] == np.float32((m + 0.5) / 2.0 ** bits), (bits, i)
+
+
+def test_truncated_uniforms_equidistributed_and_fields_independent(orc):
+    """8-bit stream: chi-square over the 256 cells, and over 16 x 16 cells of
+    the top nibbles of fields 0 and 1 of the same word."""
+    u = orc.uniforms_bits(seed=3, offset=0, n=1 << 17, bits=8)
+    m = np.floor(u.astype(np.float64) * 256).astype(int)
+    assert np.all((m + 0.5) / 256 == u)
+    hist = np.bincount(m, minlength=256)
+    e = m.size / 256
+    assert 120 < ((hist - e) ** 2 / e).sum() < 390
+    blk = m.reshape(-1, 16)                   # one Philox call = 16 samples
+    a, b = blk[:, 0:4].ravel() >> 4, blk[:, 4:8].ravel() >> 4
+    joint = np.bincount(a * 16 + b, minlength=256)
+    e2 = a.size / 256
+    assert 120 < ((joint - e2) ** 2 / e2).sum() < 390
+
+
+def test_truncated_uniform_inverse_is_midpoint_pwc(orc):
+    """Section 1 / Section 2.2: inverting a B-bit uniform exactly gives the
+    piecewise constant approximation on 2^B equal intervals with the midpoint
+    values Z^C, whose squared L2 error decays like 2^-q / q (Giles et al.)."""
+    for q in (4, 8):
+        u = ((np.arange(2 ** q) + 0.5) / 2 ** q).astype(np.float32)
+        assert np.array_equal(orc.phiinv(u), orc.pwc_table(2 ** q, 1))
+    r = [orc.pwc_l2err2(orc.pwc_table(2 ** q, 1)) * q * 2 ** q for q in (6, 8, 10, 12)]
+    assert max(r) / min(r) < 1.6, r
+    # a PWC table on 2^q <= 2^B intervals reads cell m >> (B - q) of a B-bit uniform
+    t = orc.pwc_table(64, 0).astype(np.float32)
+    u = ((np.arange(256) + 0.5) / 256).astype(np.float32)
+    z, idx = orc.sample_pwc(t, u)
+    assert np.array_equal(idx, np.arange(256) >> 2)
+
+
+def test_unit_variance_construction(orc):
+    """Construction 3 rescales Z^E to unit variance: n = 2 gives the Rademacher
+    values +-1 (Section 1); the mean square is 1 for every n."""
+    q2 = orc.pwc_table(2, 3)
+    assert np.allclose(q2, [-1.0, 1.0], rtol=0, atol=1e-14)
+    for n in (4, 64, 1024):
+        q = orc.pwc_table(n, 3)
+        e = orc.pwc_table(n, 0)
+        assert np.mean(q * q) == pytest.approx(1.0, abs=1e-13)
+        assert np.allclose(q / e, q[0] / e[0], rtol=1e-12)
+
+
 # ---------------------------------------------------------------- Phi^-1
 def test_phiinv_against_scipy_and_mpmath(orc):
     sp = pytest.importorskip("scipy.special")
