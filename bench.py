@@ -409,10 +409,15 @@ def main():
         out16 = torch.empty(N_SAMPLES, dtype=torch.float16, device=dev)
         tc = P.table_build(P.PWC, 1024)
         tp = P.table_build(P.PWP, 15, 3)
+        tc256 = P.table_build(P.PWC, 256)
         variants = {
             "pwl_f16": lambda: P.sample(tl, P.PWL, out16, seed=seed, stream=stream),
             "pwc_f32": lambda: P.sample(tc, P.PWC, out, seed=seed, stream=stream),
             "pwp3_f32": lambda: P.sample(tp, P.PWP, out, seed=seed, stream=stream),
+            # truncated-bit uniforms: 8 (16-bit) or 16 (8-bit) samples per Philox call
+            "pwl_bits16_f32": lambda: P.sample_bits(tl, P.PWL, 16, out, seed=seed, stream=stream),
+            "pwl_bits16_f16": lambda: P.sample_bits(tl, P.PWL, 16, out16, seed=seed, stream=stream),
+            "pwc256_bits8_f16": lambda: P.sample_bits(tc256, P.PWC, 8, out16, seed=seed, stream=stream),
             "exact_f32": lambda: P.sample(None, P.EXACT, out, seed=seed, stream=stream),
             "exact_lib_f32": lambda: P.sample(None, P.EXACT_LIB, out, seed=seed, stream=stream),
         }

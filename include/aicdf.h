@@ -54,7 +54,7 @@ int aicdf_version(void);
 typedef enum {
   AICDF_PWC = 0, AICDF_PWL = 1, AICDF_EXACT = 2, AICDF_EXACT_LIB = 3, AICDF_PWP = 4
 } aicdf_method;
-typedef enum { AICDF_Z_E = 0, AICDF_Z_C = 1, AICDF_Z_I = 2 } aicdf_construction;
+typedef enum { AICDF_Z_E = 0, AICDF_Z_C = 1, AICDF_Z_I = 2, AICDF_Z_V = 3 } aicdf_construction;
 typedef struct aicdf_table_s *aicdf_table;
 
 /* Build an approximation table on the host in FP64.
@@ -62,7 +62,9 @@ typedef struct aicdf_table_s *aicdf_table;
  * AICDF_PWC (Section 2.2, Theorem 2.1, Corollary 2.3): n equal intervals
  *   [m/n, (m+1)/n), n a power of two in [2, 4096]; constants by construction
  *   Z^E (conditional mean E(Z | Phi(Z) in I_m), the paper's choice),
- *   Z^C (Phi^{-1} of the interval centre) or Z^I (the endpoint nearest 1/2).
+ *   Z^C (Phi^{-1} of the interval centre), Z^I (the endpoint nearest 1/2)
+ *   or Z^V (Z^E rescaled to unit mean square, a moment-matched variant as in
+ *   Section 1; n = 2 gives the Rademacher values -1, +1).
  * AICDF_PWL (Section 2.3, Theorem 2.4 with the dyadic rate r = 1/2,
  *   Section 3.3): n = K intervals in (0, 1/2), I_k = [2^-(k+1), 2^-k) for
  *   k < K and I_K = (0, 2^-K), K in [1, 31]; each line is the L2-optimal fit
@@ -81,9 +83,11 @@ aicdf_status aicdf_table_build(int method, int n, int construction, aicdf_table 
 void aicdf_table_destroy(aicdf_table t);
 /* Copy the FP64 coefficients to the host.  PWC: c0 = the n constants, c1
  * unused (may be NULL).  PWL: c0 = intercepts alpha[0..K], c1 = gradients
- * beta[0..K].  cap = capacity of each array; *n_out = entries written. */
+ * beta[0..K].  PWP: c0 = 4(K+1) coefficients, c0[4k + j] multiplying s^j on
+ * interval k; c1 unused.  cap = capacity of each array; *n_out = entries
+ * written. */
 aicdf_status aicdf_table_get(aicdf_table t, double *c0, double *c1, int cap, int *n_out);
-/* method (AICDF_PWC / AICDF_PWL) and size (n or K) of a table */
+/* method (AICDF_PWC / AICDF_PWL / AICDF_PWP) and size (n or K) of a table */
 aicdf_status aicdf_table_info(aicdf_table t, int *method, int *n);
 
 /* ===================================================================== */
@@ -96,6 +100,9 @@ typedef enum { AICDF_F32 = 0, AICDF_F16 = 1 } aicdf_dtype;
  *   method AICDF_PWL : Algorithm 1 -- reflect about 1/2, interval index from
  *                      the FP32 exponent bits, one FMA, restore the sign
  *                      (u = 1/2 gives -0, as the listing does)
+ *   method AICDF_PWP : the piecewise polynomial of the table's interval
+ *                      (Horner's rule in the local variable s), sign restored
+ *                      as for PWL
  *   method AICDF_EXACT     : the library's FP32 Phi^{-1} (max rel. error < 1e-6)
  *   method AICDF_EXACT_LIB : CUDA's normcdfinvf, for comparison
  * Uniforms: if u_dev != NULL, u_i = u_dev[i] (FP32, any value; u outside
@@ -113,14 +120,31 @@ aicdf_status aicdf_sample(aicdf_table table, int method, const float *u_dev, uin
 
 /* Same samples as aicdf_sample with u_dev == NULL, delivered to HOST memory:
  * the library generates chunks into the caller's device staging buffer
- * (staging_bytes >= 2 MiB, split in two halves) and overlaps generation of
- * one chunk with the device-to-host copy of the previous one.  host_out
- * should be pinned for full speed.  Synchronous: returns when host_out is
- * complete. */
+ * (staging_bytes >= 2 MiB, 256-byte aligned; split in four parts when it
+ * holds at least 4 MiB, else two) and overlaps the generation of one chunk
+ * with the device-to-host copies of the previous ones (two copy streams).
+ * host_out should be pinned for full speed.  Synchronous: returns when
+ * host_out is complete. */
 aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint64_t seed,
                                   uint64_t offset, size_t n, void *host_out, int out_dtype,
                                   void *staging_dev, size_t staging_bytes,
                                   aicdf_stream_t stream);
+
+/* Truncated-bit sampling (Section 1 and Section 2.2: uniforms carried to a
+ * fixed number of bits and offset to the cell midpoint).  Each Philox call j
+ * (counter (j mod 2^32, j>>32, 0, 0), key as in aicdf_sample) yields four
+ * 32-bit words of F = 32/bits fields each; sample s of the stream
+ * (s = offset + i) is field h of word t of call j, s = 4F j + 4h + t, and
+ * its uniform is u = (m + 1/2) 2^-bits for the field value m.  The sample is
+ * the method's value at that u, as in aicdf_sample: PWC reads cell
+ * floor(n_table u); EXACT gives the midpoint piecewise constant approximation
+ * on 2^bits equal intervals.  bits: 8 or 16 (others AICDF_ERR_UNSUPPORTED).
+ * Fewer Philox calls per sample than aicdf_sample (1/8 or 1/16 of a call).
+ * out_dev must be aligned to its element size; with 32-byte alignment and
+ * offset a multiple of 4F the vectorised path runs.  Asynchronous on stream. */
+aicdf_status aicdf_sample_bits(aicdf_table table, int method, int bits, uint64_t seed,
+                               uint64_t offset, size_t n, void *out_dev, int out_dtype,
+                               aicdf_stream_t stream);
 
 /* ===================================================================== */
 /* Multilevel Monte Carlo levels (Section 4, Section 4.1)                 */

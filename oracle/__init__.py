@@ -73,6 +73,7 @@ def lib():
                 "or_gammp": (d, [d, d]),
                 "or_ncx2_cdf": (d, [d, d, d]), "or_ncx2_pdf": (d, [d, d, d]),
                 "or_ncx2_ppf": (d, [d, d, d]), "or_ncx2_P": (d, [d, d, d]),
+                "or_ncx2_sf": (d, [d, d, d]), "or_ncx2_isf": (d, [d, d, d]),
                 "or_mlp_forward": (None, [i, P, P, P, P, P, P, P, i64, P]),
                 "or_mlp_grad": (d, [i, P, P, P, P, P, P, P, P, i64, P, P, P, P, P, P]),
             }
@@ -245,8 +246,64 @@ def ncx2_ppf(u, nu, lam):
     return lib().or_ncx2_ppf(float(u), float(nu), float(lam))
 
 
+def ncx2_sf(x, nu, lam):
+    return lib().or_ncx2_sf(float(x), float(nu), float(lam))
+
+
+def ncx2_isf(v, nu, lam):
+    return lib().or_ncx2_isf(float(v), float(nu), float(lam))
+
+
 def ncx2_P(u, x, y):
     return lib().or_ncx2_P(float(u), float(x), float(y))
+
+
+def _ncx2_poly_sig(L):
+    if not getattr(L, "_ncx2_poly_sig", False):
+        L.or_ncx2_poly_table.restype = C.c_int
+        L.or_ncx2_poly_table.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.or_ncx2_poly_P.restype = C.c_double
+        L.or_ncx2_poly_P.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double]
+        L.or_ncx2_poly_ppf.restype = C.c_double
+        L.or_ncx2_poly_ppf.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double]
+        L.or_ncx2_poly_rmse.restype = C.c_double
+        L.or_ncx2_poly_rmse.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_double]
+        L._ncx2_poly_sig = True
+    return L
+
+
+def ncx2_poly_table(nu, K=8, n_knots=16, deg=1):
+    """Section 5.1 table: array (n_knots, 2 halves, K+1 rows, 4 coefficients)."""
+    L = _ncx2_poly_sig(lib())
+    c = np.zeros(n_knots * 2 * (K + 1) * 4, dtype=np.float64)
+    if L.or_ncx2_poly_table(float(nu), K, n_knots, deg, _p(c)) != 0:
+        raise ValueError("bad NCX2 table arguments")
+    return c.reshape(n_knots, 2, K + 1, 4)
+
+
+def _flat(coef):
+    return np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+
+
+def ncx2_poly_P(coef, u, y):
+    L = _ncx2_poly_sig(lib())
+    c = _flat(coef)
+    n_knots, _, K1, _ = coef.shape
+    return L.or_ncx2_poly_P(_p(c), K1 - 1, n_knots, float(u), float(y))
+
+
+def ncx2_poly_ppf(coef, nu, u, lam):
+    L = _ncx2_poly_sig(lib())
+    c = _flat(coef)
+    n_knots, _, K1, _ = coef.shape
+    return L.or_ncx2_poly_ppf(_p(c), float(nu), K1 - 1, n_knots, float(u), float(lam))
+
+
+def ncx2_poly_rmse(coef, nu, lam):
+    L = _ncx2_poly_sig(lib())
+    c = _flat(coef)
+    n_knots, _, K1, _ = coef.shape
+    return L.or_ncx2_poly_rmse(_p(c), float(nu), K1 - 1, n_knots, float(lam))
 
 
 # ---------------------------------------------------------------- MLP

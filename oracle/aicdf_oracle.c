@@ -598,8 +598,33 @@ static double pois_logw(int64_t j, double m) { /* log of e^{-m} m^j / j! */
   return -m + (double)j * log(m) - lgamma((double)j + 1.0);
 }
 
+/* regularised upper incomplete gamma Q(a, x) = 1 - P(a, x), computed
+ * directly from the continued fraction for x >= a + 1 (no cancellation in
+ * the upper tail) */
+static double gammq(double a, double x) {
+  if (x <= 0.0) return 1.0;
+  if (isinf(x)) return 0.0;
+  if (x < a + 1.0) return 1.0 - or_gammp(a, x);
+  const double lpre = -x + a * log(x) - lgamma(a), tiny = 1e-300;
+  double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 100000; ++i) {
+    double an = -i * (i - a);
+    b += 2.0;
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-17) break;
+  }
+  return exp(lpre) * h;
+}
+
 /* sum over j of Pois(j; lam/2) * f(j), outward from the mode until the weight
- * falls below 1e-17 on both sides */
+ * falls below 1e-17 on both sides; f = CDF (0), density (1) or upper tail (2)
+ * of the central chi^2 with nu + 2j degrees of freedom */
 static double ncx2_mix(double x, double nu, double lam, int pdf) {
   double m = 0.5 * lam;
   int64_t j0 = (int64_t)floor(m);
@@ -609,9 +634,11 @@ static double ncx2_mix(double x, double nu, double lam, int pdf) {
       double w = exp(pois_logw(j, m));
       double f;
       double a = 0.5 * nu + (double)j;
-      if (pdf) {
+      if (pdf == 1) {
         /* central chi^2_{nu+2j} density at x */
         f = (x <= 0.0) ? 0.0 : exp((a - 1.0) * log(0.5 * x) - 0.5 * x - lgamma(a)) * 0.5;
+      } else if (pdf == 2) {
+        f = gammq(a, 0.5 * x);
       } else {
         f = or_gammp(a, 0.5 * x);
       }
@@ -641,7 +668,7 @@ double or_ncx2_ppf(double u, double nu, double lam) {
   if (u == 1.0) return INFINITY;
   double mean = nu + lam, sd = sqrt(2.0 * (nu + 2.0 * lam));
   double lo = 0.0, hi = mean + 10.0 * sd;
-  while (or_ncx2_cdf(hi, nu, lam) < u) { lo = hi; hi *= 2.0; }
+  while (or_ncx2_cdf(hi, nu, lam) < u && hi < 1e300) { lo = hi; hi *= 2.0; }
   double x = 0.5 * (lo + hi);
   for (int it = 0; it < 500; ++it) {
     double F = or_ncx2_cdf(x, nu, lam) - u;
@@ -656,11 +683,193 @@ double or_ncx2_ppf(double u, double nu, double lam) {
   return x;
 }
 
+double or_ncx2_sf(double x, double nu, double lam) {
+  if (x <= 0.0) return 1.0;
+  return ncx2_mix(x, nu, lam, 2);
+}
+
+/* upper-tail quantile: the x with 1 - F(x) = v, solved on the upper tail
+ * itself so that v down to the smallest doubles keeps full relative accuracy */
+double or_ncx2_isf(double v, double nu, double lam) {
+  if (isnan(v) || v < 0.0 || v > 1.0) return NAN;
+  if (v == 0.0) return INFINITY;
+  if (v == 1.0) return 0.0;
+  double mean = nu + lam, sd = sqrt(2.0 * (nu + 2.0 * lam));
+  double lo = 0.0, hi = mean + 10.0 * sd;
+  while (or_ncx2_sf(hi, nu, lam) > v && hi < 1e300) { lo = hi; hi *= 2.0; }
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 500; ++it) {
+    double G = or_ncx2_sf(x, nu, lam) - v;   /* decreasing in x */
+    if (G < 0.0) hi = x; else lo = x;
+    double f = or_ncx2_pdf(x, nu, lam);
+    double xn = (f > 0.0) ? x + G / f : 0.5 * (lo + hi);
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    double dx = fabs(xn - x);
+    x = xn;
+    if (dx <= 1e-14 * fabs(x) || hi - lo <= 1e-15 * fabs(x)) break;
+  }
+  return x;
+}
+
 /* P_x(U; y) = sqrt(x / 4y) ( (y/x) C^{-1}_x(U; (1-y)x/y) - 1 )  (Section 5.1) */
 double or_ncx2_P(double u, double x, double y) {
   double lam = (1.0 - y) * x / y;
   double c = or_ncx2_ppf(u, x, lam);
   return sqrt(x / (4.0 * y)) * ((y / x) * c - 1.0);
+}
+
+/* ========================================================================== */
+/* Section 5.1: piecewise polynomial approximation of P_nu(.; y).  Knots y_i  */
+/* with sqrt(y_i) = i/(n-1) equally spaced (y_0 = 0: the Gaussian limit       */
+/* Phi^{-1}; y_{n-1} = 1: the central chi^2 limit), separate fits on the two   */
+/* halves u <= 1/2 and u > 1/2 (the law is not antisymmetric), K dyadic       */
+/* intervals per half in v = min(u, 1-u), the L2-optimal polynomial of degree */
+/* deg in the local variable s on each; linear interpolation between knots   */
+/* in sqrt(y).  Row 0 of each half holds the value at u = 1/2.               */
+/* ========================================================================== */
+/* P_nu(u; y) at u = v (lower half) or u = 1 - v (upper half) */
+static double ncx2_half_P(double v, int upper, double nu, double y) {
+  if (y <= 0.0) return upper ? -or_phiinv(v) : or_phiinv(v);
+  if (!upper) return or_ncx2_P(v, nu, y);
+  const double c = or_ncx2_isf(v, nu, (1.0 - y) * nu / y);
+  return sqrt(nu / (4.0 * y)) * ((y / nu) * c - 1.0);
+}
+
+/* int_{I_k} s^j g(v) dv, j = 0..3, for g = P on one half.  Regular intervals:
+ * 24-point Gauss-Legendre; the singular interval (0, 2^-K): 40 geometric
+ * panels [b 2^-(p+1), b 2^-p] of 8 points (the rest, below b 2^-40, is
+ * dropped: |P| grows at most logarithmically there). */
+#define NCX2_GL 24
+#define NCX2_GLS 8
+#define NCX2_PANELS 40
+static void ncx2_moments(int k, int K, int upper, double nu, double y, double *M) {
+  double x[NCX2_GL], w[NCX2_GL], xs[NCX2_GLS], ws[NCX2_GLS];
+  gauss_legendre(NCX2_GL, x, w);
+  gauss_legendre(NCX2_GLS, xs, ws);
+  for (int j = 0; j < 4; ++j) M[j] = 0.0;
+  const double b = ldexp(1.0, -k);
+  const int np = (k < K) ? 1 : NCX2_PANELS, nq = (k < K) ? NCX2_GL : NCX2_GLS;
+  for (int p = 0; p < np; ++p) {
+    const double hi = (k < K) ? b : ldexp(b, -p), lo = 0.5 * hi, h = hi - lo;
+    for (int i = 0; i < nq; ++i) {
+      const double xi = (k < K) ? x[i] : xs[i], wi = 0.5 * ((k < K) ? w[i] : ws[i]) * h;
+      const double v = lo + 0.5 * (xi + 1.0) * h;
+      const double s = (k < K) ? (v - lo) / h : v / b;
+      const double f = ncx2_half_P(v, upper, nu, y);
+      double sp = 1.0;
+      for (int j = 0; j < 4; ++j) {
+        M[j] += wi * sp * f;
+        sp *= s;
+      }
+    }
+  }
+}
+
+/* L2 fit of degree deg on interval k from the moments (Gram h/(i+j+1)) */
+static void poly_fit(int k, int K, int deg, const double *M, double *c) {
+  const double b = ldexp(1.0, -k), h = (k < K) ? 0.5 * b : b;
+  const int n = deg + 1;
+  double G[4][5];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) G[i][j] = h / (i + j + 1.0);
+    G[i][n] = M[i];
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
+    for (int j = 0; j <= n; ++j) {
+      double t = G[col][j];
+      G[col][j] = G[piv][j];
+      G[piv][j] = t;
+    }
+    for (int r = col + 1; r < n; ++r) {
+      double f = G[r][col] / G[col][col];
+      for (int j = col; j <= n; ++j) G[r][j] -= f * G[col][j];
+    }
+  }
+  for (int j = 0; j < 4; ++j) c[j] = 0.0;
+  for (int r = n - 1; r >= 0; --r) {
+    double acc = G[r][n];
+    for (int j = r + 1; j < n; ++j) acc -= G[r][j] * c[j];
+    c[r] = acc / G[r][r];
+  }
+}
+
+int or_ncx2_poly_table(double nu, int K, int n_knots, int deg, double *coef) {
+  if (!(nu > 0.0) || K < 1 || K > 31 || n_knots < 2 || deg < 1 || deg > 3) return -1;
+  /* every (knot, half, interval) fit is independent */
+  const int nfit = n_knots * 2 * (K + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int f = 0; f < nfit; ++f) {
+    const int k = f % (K + 1), half = (f / (K + 1)) % 2, i = f / (2 * (K + 1));
+    const double r = (double)i / (n_knots - 1), y = r * r;
+    double *c = coef + (size_t)f * 4;
+    if (k == 0) {
+      c[0] = ncx2_half_P(0.5, 0, nu, y);
+      c[1] = c[2] = c[3] = 0.0;
+    } else {
+      double M[4];
+      ncx2_moments(k, K, half, nu, y, M);
+      poly_fit(k, K, deg, M, c);
+    }
+  }
+  return 0;
+}
+
+/* P~_nu(u; y) from a table (coef as laid out by or_ncx2_poly_table) */
+double or_ncx2_poly_P(const double *coef, int K, int n_knots, double u, double y) {
+  const int upper = u > 0.5;
+  const double v = upper ? 1.0 - u : u;
+  const int k = or_pwl_index(v, K, 0.5);
+  double s = 0.0;
+  if (k > 0) {
+    const double b = ldexp(1.0, -k);
+    s = (k < K) ? (v - 0.5 * b) / (0.5 * b) : v / b;
+  }
+  double t = sqrt(y) * (n_knots - 1);
+  int i = (int)floor(t);
+  if (i > n_knots - 2) i = n_knots - 2;
+  if (i < 0) i = 0;
+  const double f = t - i;
+  double p[2];
+  for (int q = 0; q < 2; ++q) {
+    const double *c = coef + (size_t)(((i + q) * 2 + upper) * (K + 1) + k) * 4;
+    p[q] = ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+  }
+  return (1.0 - f) * p[0] + f * p[1];
+}
+
+/* C~^{-1}_nu(u; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~_nu(u; nu/(lambda + nu)) */
+double or_ncx2_poly_ppf(const double *coef, double nu, int K, int n_knots, double u, double lam) {
+  const double h = lam + nu;
+  return h + 2.0 * sqrt(h) * or_ncx2_poly_P(coef, K, n_knots, u, nu / h);
+}
+
+/* RMSE sqrt(int_0^1 (C~^{-1} - C^{-1})^2 du) by the same quadrature as the fit
+ * (each half, each dyadic interval, the singular ones on geometric panels). */
+double or_ncx2_poly_rmse(const double *coef, double nu, int K, int n_knots, double lam) {
+  double x[NCX2_GL], w[NCX2_GL], xs[NCX2_GLS], ws[NCX2_GLS];
+  gauss_legendre(NCX2_GL, x, w);
+  gauss_legendre(NCX2_GLS, xs, ws);
+  double acc = 0.0;
+  const int nseg = 2 * (K - 1 + NCX2_PANELS);  /* per half: K-1 regular intervals + panels */
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : acc)
+  for (int g = 0; g < nseg; ++g) {
+    const int half = g / (nseg / 2), r = g % (nseg / 2);
+    const int k = (r < K - 1) ? r + 1 : K, p = (r < K - 1) ? 0 : r - (K - 1);
+    const double b = ldexp(1.0, -k);
+    const double hi = (k < K) ? b : ldexp(b, -p), lo = 0.5 * hi, h = hi - lo;
+    const int nq = (k < K) ? NCX2_GL : NCX2_GLS;
+    for (int i = 0; i < nq; ++i) {
+      const double xi = (k < K) ? x[i] : xs[i], wi = 0.5 * ((k < K) ? w[i] : ws[i]) * h;
+      const double v = lo + 0.5 * (xi + 1.0) * h, u = half ? 1.0 - v : v;
+      const double ex = half ? or_ncx2_isf(v, nu, lam) : or_ncx2_ppf(v, nu, lam);
+      const double d = or_ncx2_poly_ppf(coef, nu, K, n_knots, u, lam) - ex;
+      acc += wi * d * d;
+    }
+  }
+  return sqrt(acc);
 }
 
 /* ========================================================================== */

@@ -106,8 +106,19 @@ double or_gammp(double a, double x);                     /* regularised lower ga
 double or_ncx2_cdf(double x, double nu, double lam);
 double or_ncx2_pdf(double x, double nu, double lam);
 double or_ncx2_ppf(double u, double nu, double lam);     /* root finding on the CDF */
+double or_ncx2_sf(double x, double nu, double lam);      /* 1 - CDF, summed directly */
+double or_ncx2_isf(double v, double nu, double lam);     /* x with 1 - CDF(x) = v */
 /* P_x(U; y) of Section 5.1 and its inverse map C^{-1}_nu(U; lambda) */
 double or_ncx2_P(double u, double x, double y);
+/* Section 5.1 piecewise polynomial approximation of P_nu(.; y): n_knots knots
+ * with sqrt(y) equally spaced on [0, 1], two halves, K dyadic intervals per
+ * half (v = min(u, 1-u)), L2 polynomial of degree deg in the local variable s.
+ * coef[(((i*2 + half)*(K+1)) + k)*4 + j] multiplies s^j (half 1: u > 1/2);
+ * row 0 of each half = [P(1/2; y_i), 0, 0, 0]. */
+int    or_ncx2_poly_table(double nu, int K, int n_knots, int deg, double *coef);
+double or_ncx2_poly_P(const double *coef, int K, int n_knots, double u, double y);
+double or_ncx2_poly_ppf(const double *coef, double nu, int K, int n_knots, double u, double lam);
+double or_ncx2_poly_rmse(const double *coef, double nu, int K, int n_knots, double lam);
 
 /* ---- MLP surrogate 2 -> H -> H -> 1, tanh (FP64 reference) ----------------- */
 /* weights: W1[H][2], b1[H], W2[H][H], b2[H], w3[H], b3[1] (row-major, out x in) */

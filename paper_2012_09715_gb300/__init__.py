@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libaicdf.so")
 # enums (include/aicdf.h)
 OK, ERR_ARG, ERR_CUDA, ERR_NOCONVERGE, ERR_DOMAIN, ERR_STATE, ERR_NOMEM, ERR_UNSUPPORTED = range(8)
 PWC, PWL, EXACT, EXACT_LIB, PWP = 0, 1, 2, 3, 4
-Z_E, Z_C, Z_I = 0, 1, 2
+Z_E, Z_C, Z_I, Z_V = 0, 1, 2, 3
 F32, F16 = 0, 1
 MODEL_GBM, MODEL_CIR = 0, 1
 SCHEME_EM, SCHEME_MILSTEIN = 0, 1
@@ -100,6 +100,7 @@ SIGNATURES = {
     "aicdf_table_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "aicdf_sample": (_I, [_P, _I, _P, _U64, _U64, _SZ, _P, _I, _P]),
     "aicdf_sample_to_host": (_I, [_P, _I, _U64, _U64, _SZ, _P, _I, _P, _SZ, _P]),
+    "aicdf_sample_bits": (_I, [_P, _I, _I, _U64, _U64, _SZ, _P, _I, _P]),
     "aicdf_mlmc_level_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P]),
     "aicdf_mlmc_allocate": (_I, [_I, _P, _P, _D, _P, _P]),
@@ -224,6 +225,19 @@ def sample(table, method: int, out, u=None, seed: int = 0, offset: int = 0, n: i
         out_dtype = F16 if out.dtype == torch.float16 else F32
     _check(lib().aicdf_sample(_th(table), method, _ptr(u), seed, offset, n, _ptr(out), out_dtype,
                               _stream(stream)), "sample")
+    return out
+
+
+def sample_bits(table, method: int, bits: int, out, seed: int = 0, offset: int = 0, n: int | None = None,
+                out_dtype: int | None = None, stream=None):
+    """aicdf_sample_bits: the method evaluated at B-bit truncated Philox uniforms."""
+    if n is None:
+        n = out.numel()
+    if out_dtype is None:
+        import torch
+        out_dtype = F16 if out.dtype == torch.float16 else F32
+    _check(lib().aicdf_sample_bits(_th(table), method, bits, seed, offset, n, _ptr(out), out_dtype,
+                                   _stream(stream)), "sample_bits")
     return out
 
 

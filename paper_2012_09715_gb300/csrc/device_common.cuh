@@ -54,10 +54,37 @@ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &k) {
   return c;
 }
 
+// NC independent Philox calls advanced round by round together, so that the
+// multiplies of different calls overlap (one call alone is a serial chain of
+// 10 dependent rounds).
+template <int NC>
+__device__ __forceinline__ void philox_n(uint4 (&c)[NC], const PhiloxKeys &k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const uint32_t lo0 = PHILOX_M0 * c[q].x, hi0 = __umulhi(PHILOX_M0, c[q].x);
+      const uint32_t lo1 = PHILOX_M1 * c[q].z, hi1 = __umulhi(PHILOX_M1, c[q].z);
+      c[q] = make_uint4(hi1 ^ c[q].y ^ k.k0[r], lo1, hi0 ^ c[q].w ^ k.k1[r], lo0);
+    }
+  }
+}
+
 // (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = low 23 bits of x: both
 // steps exact (one logic op and one add).
 __device__ __forceinline__ float u01(uint32_t x) {
   return __uint_as_float(0x3F800000u | (x & 0x7FFFFFu)) - 0x1.fffffep-1f;
+}
+
+// Truncated-bit uniform: cell m of 2^B, u = (m + 1/2) 2^-B = (1 + m 2^-B) -
+// (1 - 2^-(B+1)); the significand holds m exactly and the subtraction is exact
+// (its result needs at most B + 1 bits).  Such u lie on the 2^-24 grid, so the
+// grid forms below apply to them as they stand.
+template <int B>
+__device__ __forceinline__ float ubits(uint32_t m) {
+  static_assert(B >= 1 && B <= 23, "field width");
+  constexpr float c = 1.0f - 1.0f / (float)(2u << B);
+  return __uint_as_float(0x3F800000u | (m << (23 - B))) - c;
 }
 
 // ---------------------------------------------------------------------------

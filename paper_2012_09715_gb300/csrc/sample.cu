@@ -94,17 +94,55 @@ aicdf_status launch_sample(const SampleArgs &a, int method, int out_dtype, int s
                            cudaStream_t stream) {
   KernelFn k = select_kernel(method, out_dtype, src, vec);
   const int E = vec ? (out_dtype == AICDF_F32 ? 4 : 8) : 1;
+  int waves = 1;
   if (src == SRC_PHILOX && vec) {
     // 32-bit index variant when counters and element indices stay below 2^32
+    // (a warp chunk spans at most 128 vectors)
     const uint64_t nvec = (a.n + E - 1) / E;
     const uint64_t lim = 1ull << 32;
-    if ((nvec + 64) * (uint64_t)E < lim && (a.offset >> 2) + (nvec + 64) * (uint64_t)(E / 4) < lim)
+    if ((nvec + 128) * (uint64_t)E < lim && (a.offset >> 2) + (nvec + 128) * (uint64_t)(E / 4) < lim) {
       k = out_dtype == AICDF_F32 ? select_philox32<AICDF_F32>(method) : select_philox32<AICDF_F16>(method);
+      waves = 4;  // several resident-block waves even out the end of the grid-stride loop
+    }
   }
   const uint64_t units = (a.n + E - 1) / E;
   const int threads = 256;
-  // one full wave: SMs x resident blocks of this kernel (grid-stride inside)
-  const uint64_t cap = (uint64_t)sm_count() * resident_blocks((const void *)k, threads);
+  // SMs x resident blocks of this kernel x waves (grid-stride inside)
+  const uint64_t cap = (uint64_t)sm_count() * resident_blocks((const void *)k, threads) * waves;
+  uint64_t blocks = (units + threads - 1) / threads;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k<<<(unsigned)blocks, threads, 0, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error((int)e);
+    return AICDF_ERR_CUDA;
+  }
+  return AICDF_OK;
+}
+
+template <int OUT, int B>
+static KernelFn pick_bits(int method, bool vec) {
+  switch (method) {
+    case AICDF_PWC: return vec ? k_sample_bits<AICDF_PWC, OUT, B> : k_sample_bits_scalar<AICDF_PWC, OUT, B>;
+    case AICDF_PWL: return vec ? k_sample_bits<AICDF_PWL, OUT, B> : k_sample_bits_scalar<AICDF_PWL, OUT, B>;
+    case AICDF_PWP: return vec ? k_sample_bits<AICDF_PWP, OUT, B> : k_sample_bits_scalar<AICDF_PWP, OUT, B>;
+    case AICDF_EXACT:
+      return vec ? k_sample_bits<AICDF_EXACT, OUT, B> : k_sample_bits_scalar<AICDF_EXACT, OUT, B>;
+    default:
+      return vec ? k_sample_bits<AICDF_EXACT_LIB, OUT, B> : k_sample_bits_scalar<AICDF_EXACT_LIB, OUT, B>;
+  }
+}
+
+aicdf_status launch_sample_bits(const SampleArgs &a, int method, int bits, int out_dtype, bool vec,
+                                cudaStream_t stream) {
+  KernelFn k;
+  if (bits == 8) k = out_dtype == AICDF_F32 ? pick_bits<AICDF_F32, 8>(method, vec) : pick_bits<AICDF_F16, 8>(method, vec);
+  else k = out_dtype == AICDF_F32 ? pick_bits<AICDF_F32, 16>(method, vec) : pick_bits<AICDF_F16, 16>(method, vec);
+  const uint64_t S = 4 * (32 / bits);
+  const uint64_t units = vec ? (a.n + S - 1) / S : a.n;  // calls (vector) or samples per thread
+  const int threads = 256;
+  const uint64_t cap = (uint64_t)sm_count() * resident_blocks((const void *)k, threads) * 4;
   uint64_t blocks = (units + threads - 1) / threads;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
@@ -224,4 +262,28 @@ extern "C" aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint
     if (copied[i]) cudaEventDestroy(copied[i]);
   }
   return rc;
+}
+
+extern "C" aicdf_status aicdf_sample_bits(aicdf_table table, int method, int bits, uint64_t seed,
+                                          uint64_t offset, size_t n, void *out_dev, int out_dtype,
+                                          aicdf_stream_t stream) {
+  if (out_dtype != AICDF_F32 && out_dtype != AICDF_F16) return AICDF_ERR_ARG;
+  if (bits < 1 || bits > 23) return AICDF_ERR_ARG;
+  if (bits != 8 && bits != 16) return AICDF_ERR_UNSUPPORTED;
+  static thread_local SampleArgs a;
+  aicdf_status s = prepare_sample_args(table, method, &a);
+  if (s != AICDF_OK) return s;
+  if (n == 0) return AICDF_OK;
+  if (!out_dev) return AICDF_ERR_ARG;
+  const size_t esz = out_dtype == AICDF_F32 ? 4 : 2;
+  if ((uintptr_t)out_dev % esz) return AICDF_ERR_ARG;
+  a.u = nullptr;
+  a.out = out_dev;
+  a.n = n;
+  a.offset = offset;
+  a.keys = make_keys(seed);
+  const uint64_t S = 4 * (32 / bits);
+  const uintptr_t align = (out_dtype == AICDF_F16 && S == 8) ? 16 : 32;
+  const bool vec = ((uintptr_t)out_dev % align) == 0 && (offset % S) == 0;
+  return launch_sample_bits(a, method, bits, out_dtype, vec, (cudaStream_t)stream);
 }

@@ -40,6 +40,7 @@ struct Approx<AICDF_PWC, SRC> {
   float nf;
   int nmax;
   uint32_t shift;
+  int q;  // n_table = 2^q
   __device__ Approx(const SampleArgs &a, float *smem) {
     for (int i = threadIdx.x; i < a.ntab; i += blockDim.x) smem[i] = a.tab[i];
     __syncthreads();
@@ -47,9 +48,15 @@ struct Approx<AICDF_PWC, SRC> {
     nf = a.nf;
     nmax = a.ntab - 1;
     shift = a.pwc_shift;
+    q = 23 - (int)a.pwc_shift;
   }
   __device__ __forceinline__ float word(uint32_t x) const { return s[pwc_index_from_word(x, shift)]; }
   __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
+  // cell m of a B-bit uniform: floor(2^q (m + 1/2) 2^-B)
+  template <int B>
+  __device__ __forceinline__ float cell(uint32_t m) const {
+    return s[q <= B ? (m >> (B - q)) : ((2u * m + 1u) << (q - B - 1))];
+  }
 };
 
 template <int SRC>
@@ -64,6 +71,8 @@ struct Approx<AICDF_PWL, SRC> {
   }
   __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_grid(u01(x), rows); }
   __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
+  template <int B>
+  __device__ __forceinline__ float cell(uint32_t m) const { return pwl_eval_grid(ubits<B>(m), rows); }
 };
 
 template <int SRC>
@@ -80,6 +89,10 @@ struct Approx<AICDF_PWP, SRC> {
   }
   __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_grid(u01(x), rows, e_sing, scale_k); }
   __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K, scale_k); }
+  template <int B>
+  __device__ __forceinline__ float cell(uint32_t m) const {
+    return pwp_eval_grid(ubits<B>(m), rows, e_sing, scale_k);
+  }
 };
 
 template <int SRC>
@@ -87,6 +100,8 @@ struct Approx<AICDF_EXACT, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
   __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }
   __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
+  template <int B>
+  __device__ __forceinline__ float cell(uint32_t m) const { return phiinv_f32(ubits<B>(m)); }
 };
 
 template <int SRC>
@@ -94,6 +109,8 @@ struct Approx<AICDF_EXACT_LIB, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
   __device__ __forceinline__ float word(uint32_t x) const { return normcdfinvf(u01(x)); }
   __device__ __forceinline__ float operator()(float u) const { return normcdfinvf(u); }
+  template <int B>
+  __device__ __forceinline__ float cell(uint32_t m) const { return normcdfinvf(ubits<B>(m)); }
 };
 
 template <int OUT>
@@ -195,19 +212,21 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
 }
 
 // The vectorised Philox kernel when every index fits in 32 bits (the host
-// checks j0 + (nvec + 64) E/4 < 2^32 and (nvec + 64) E < 2^32): 32-bit index
+// checks j0 + (nvec + 128) E/4 < 2^32 and (nvec + 128) E < 2^32): 32-bit index
 // arithmetic, the counter's high words are the constant 0 (so the compiler
 // folds part of the first round), and chunks that lie wholly inside the
-// output are stored without per-vector bounds checks.
+// output are stored without per-vector bounds checks.  Each lane runs the
+// Philox calls of its four 16-byte vectors interleaved round by round.
 template <int METHOD, int OUT>
-__global__ void __launch_bounds__(256) k_sample_philox32(const __grid_constant__ SampleArgs a) {
+__global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constant__ SampleArgs a) {
   __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
   constexpr int E = OutVec<OUT>::kElems;
-  constexpr int VECS = 2;
-  constexpr uint32_t CH = 32 * VECS;  // 16-byte vectors per warp chunk
+  constexpr int VECS = OUT == AICDF_F32 ? 4 : 2;  // 16-byte vectors per lane per chunk
+  constexpr int NC = VECS * (E / 4);              // Philox calls per lane per chunk (4)
+  constexpr uint32_t CH = 32 * VECS;              // vectors per warp chunk
   const uint32_t n = (uint32_t)a.n;
   const uint32_t nvec = (n + E - 1) / E;
   const uint32_t nchunk = (nvec + CH - 1) / CH;
@@ -216,19 +235,24 @@ __global__ void __launch_bounds__(256) k_sample_philox32(const __grid_constant__
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t j0 = (uint32_t)(a.offset >> 2);
   for (uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk; chunk += warps) {
+    uint4 c[NC];
+#pragma unroll
+    for (int hv = 0; hv < VECS; ++hv)
+#pragma unroll
+      for (int h = 0; h < E / 4; ++h)
+        c[hv * (E / 4) + h] = make_uint4(j0 + (chunk * CH + 32 * hv + lane) * (E / 4) + h, 0u, 0u, 0u);
+    philox_n<NC>(c, a.keys);
     float z[VECS][E];
 #pragma unroll
-    for (int hv = 0; hv < VECS; ++hv) {
-      const uint32_t v = chunk * CH + 32 * hv + lane;
+    for (int hv = 0; hv < VECS; ++hv)
 #pragma unroll
       for (int h = 0; h < E / 4; ++h) {
-        const uint4 r = philox(make_uint4(j0 + v * (E / 4) + h, 0u, 0u, 0u), a.keys);
+        const uint4 r = c[hv * (E / 4) + h];
         z[hv][4 * h + 0] = f.word(r.x);
         z[hv][4 * h + 1] = f.word(r.y);
         z[hv][4 * h + 2] = f.word(r.z);
         z[hv][4 * h + 3] = f.word(r.w);
       }
-    }
     if (chunk < nfull) {  // warp-uniform
 #pragma unroll
       for (int hv = 0; hv < VECS; ++hv) store_vec(out, (uint64_t)(chunk * CH + 32 * hv + lane) * E, z[hv]);
@@ -245,6 +269,128 @@ __global__ void __launch_bounds__(256) k_sample_philox32(const __grid_constant__
         }
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Truncated-bit sampling: one Philox call gives S = 4F samples (F = 32/B
+// B-bit fields per word); sample 4h + t of call j is field h of word t.  A
+// thread owns one call and writes its S consecutive outputs as 32-byte
+// (or, for 8 halves, 16-byte) vectors, so each warp store covers one
+// contiguous 1 KiB / 512 B span.
+__device__ __forceinline__ void st_v8(void *p, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                      uint32_t a4, uint32_t a5, uint32_t a6, uint32_t a7) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a0), "r"(a1),
+               "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float x, float y) {
+  __half2 h = __floats2half2_rn(x, y);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// S consecutive samples at p (p aligned to 32 bytes, or 16 for 8 halves).
+template <int S>
+__device__ __forceinline__ void store_call(float *p, const float (&z)[S]) {
+#pragma unroll
+  for (int q = 0; q < S; q += 8)
+    st_v8(p + q, __float_as_uint(z[q]), __float_as_uint(z[q + 1]), __float_as_uint(z[q + 2]),
+          __float_as_uint(z[q + 3]), __float_as_uint(z[q + 4]), __float_as_uint(z[q + 5]),
+          __float_as_uint(z[q + 6]), __float_as_uint(z[q + 7]));
+}
+template <int S>
+__device__ __forceinline__ void store_call(__half *p, const float (&z)[S]) {
+  if constexpr (S == 8) {
+    *reinterpret_cast<uint4 *>(p) =
+        make_uint4(pack_h2(z[0], z[1]), pack_h2(z[2], z[3]), pack_h2(z[4], z[5]), pack_h2(z[6], z[7]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < S; q += 16)
+      st_v8(p + q, pack_h2(z[q], z[q + 1]), pack_h2(z[q + 2], z[q + 3]), pack_h2(z[q + 4], z[q + 5]),
+            pack_h2(z[q + 6], z[q + 7]), pack_h2(z[q + 8], z[q + 9]), pack_h2(z[q + 10], z[q + 11]),
+            pack_h2(z[q + 12], z[q + 13]), pack_h2(z[q + 14], z[q + 15]));
+  }
+}
+
+template <int METHOD, int B>
+__device__ __forceinline__ void call_samples(const Approx<METHOD, SRC_PHILOX> &f, const uint4 &r,
+                                             float (&z)[4 * (32 / B)]) {
+  constexpr int F = 32 / B;
+  constexpr uint32_t M = (1u << B) - 1u;
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int h = 0; h < F; ++h)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) z[4 * h + t] = f.template cell<B>((w[t] >> (h * B)) & M);
+}
+
+// Vector form.  Requires offset % S == 0 and out aligned to 32 bytes (16 for
+// FP16 with S = 8).  A warp chunk is NC x 32 calls; lane L runs calls
+// q x 32 + L (q < NC) interleaved, and each q writes one contiguous span.
+template <int METHOD, int OUT, int B>
+__global__ void __launch_bounds__(256) k_sample_bits(const __grid_constant__ SampleArgs a) {
+  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  const Approx<METHOD, SRC_PHILOX> f(a, smem);
+  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
+  T *out = reinterpret_cast<T *>(a.out);
+  constexpr int S = 4 * (32 / B);
+  constexpr int NC = B == 16 ? 4 : 2;
+  const uint64_t ncall = (a.n + S - 1) / S;
+  const uint64_t nchunk = (ncall + 32 * NC - 1) / (32 * NC);
+  const uint64_t j0 = a.offset / S;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  // warp-uniform loop: every lane runs every iteration (shuffles need all 32)
+  for (uint64_t chunk = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk;
+       chunk += warps) {
+    uint4 r[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const uint64_t j = j0 + chunk * (32 * NC) + 32 * q + lane;
+      r[q] = make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u);
+    }
+    philox_n<NC>(r, a.keys);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const uint64_t c = chunk * (32 * NC) + 32 * q + lane;  // call index relative to j0
+      float z[S];
+      call_samples<METHOD, B>(f, r[q], z);
+      const uint64_t e0 = c * S;
+      if (e0 + S <= a.n) {
+        store_call<S>(out + e0, z);
+      } else if (e0 < a.n) {
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+          if (e0 + t < a.n) store_one(out, e0 + t, z[t]);
+      }
+    }
+  }
+}
+
+// Any offset / alignment: one output element per lane (the lane recomputes
+// its call; only for ragged or unaligned requests).
+template <int METHOD, int OUT, int B>
+__global__ void __launch_bounds__(256) k_sample_bits_scalar(const __grid_constant__ SampleArgs a) {
+  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  const Approx<METHOD, SRC_PHILOX> f(a, smem);
+  using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
+  T *out = reinterpret_cast<T *>(a.out);
+  constexpr int F = 32 / B;
+  constexpr int S = 4 * F;
+  constexpr uint32_t M = (1u << B) - 1u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n;
+       base += stride) {
+    const uint64_t e = base + lane;
+    const uint64_t s = a.offset + e;
+    const uint64_t j = s / S;
+    const uint32_t r = (uint32_t)(s % S), h = r >> 2, t = r & 3;
+    const uint4 q = philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), 0u, 0u), a.keys);
+    const uint32_t w = t == 0 ? q.x : t == 1 ? q.y : t == 2 ? q.z : q.w;
+    const float y = f.template cell<B>((w >> (h * B)) & M);
+    if (e < a.n) store_one(out, e, y);
   }
 }
 

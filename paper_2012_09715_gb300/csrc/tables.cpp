@@ -63,7 +63,7 @@ static aicdf_status build_pwc(aicdf_table_s *t, int n, int cons) {
   for (int k = 0; k < n; ++k) {
     const double lo = (double)k / n, hi = (double)(k + 1) / n;
     double q;
-    if (cons == AICDF_Z_E) {
+    if (cons == AICDF_Z_E || cons == AICDF_Z_V) {
       // n * (phi(z_k) - phi(z_{k+1})), written as
       // -n phi(z_k) expm1(-(z_{k+1} - z_k)(z_{k+1} + z_k)/2) to keep digits near 1/2.
       if (k == 0) q = -n * npdf(z[1]);
@@ -75,6 +75,12 @@ static aicdf_status build_pwc(aicdf_table_s *t, int n, int cons) {
       q = (lo >= 0.5) ? z[k] : (hi < 0.5 ? z[k + 1] : 0.0);
     }
     t->c0[k] = q;
+  }
+  if (cons == AICDF_Z_V) {  // unit mean square (n = 2: the Rademacher values +-1)
+    double m2 = 0.0;
+    for (int k = 0; k < n; ++k) m2 += t->c0[k] * t->c0[k];
+    const double sc = 1.0 / std::sqrt(m2 / n);
+    for (int k = 0; k < n; ++k) t->c0[k] *= sc;
   }
   t->c1.clear();
   return AICDF_OK;
@@ -187,7 +193,7 @@ extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, a
   *out = nullptr;
   if (method == AICDF_PWC) {
     if (n < 2 || n > 4096 || (n & (n - 1))) return AICDF_ERR_ARG;
-    if (construction < AICDF_Z_E || construction > AICDF_Z_I) return AICDF_ERR_ARG;
+    if (construction < AICDF_Z_E || construction > AICDF_Z_V) return AICDF_ERR_ARG;
   } else if (method == AICDF_PWL) {
     if (n < 1 || n > 31) return AICDF_ERR_ARG;
   } else if (method == AICDF_PWP) {

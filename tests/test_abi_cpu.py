@@ -61,7 +61,7 @@ def test_table_build_matches_oracle(P, orc):
         assert np.allclose(b, ob, rtol=5e-12, atol=1e-14)
         assert t.info() == (P.PWL, K)
     for n in (2, 8, 1024, 4096):
-        for cons in (P.Z_E, P.Z_C, P.Z_I):
+        for cons in (P.Z_E, P.Z_C, P.Z_I, P.Z_V):
             q = P.table_build(P.PWC, n, cons).coefficients()[0]
             oq = orc.pwc_table(n, cons)
             # the oracle's plain form n (phi(z_k) - phi(z_{k+1})) cancels near
@@ -82,7 +82,7 @@ def test_table_build_matches_oracle(P, orc):
 def test_table_build_rejects_bad_arguments(P):
     L = P.lib()
     h = C.c_void_p()
-    for m, n, c in ((P.PWC, 1000, 0), (P.PWC, 1, 0), (P.PWC, 8192, 0), (P.PWC, 64, 7),
+    for m, n, c in ((P.PWC, 1000, 0), (P.PWC, 1, 0), (P.PWC, 8192, 0), (P.PWC, 64, 7), (P.PWC, 64, 4),
                     (P.PWL, 0, 0), (P.PWL, 32, 0), (9, 15, 0)):
         assert L.aicdf_table_build(m, n, c, C.byref(h)) == P.ERR_ARG
     assert L.aicdf_table_build(P.PWL, 15, 0, None) == P.ERR_ARG
@@ -122,6 +122,14 @@ def test_sample_argument_validation_without_gpu(P):
     # tables too large for the kernels are refused, not truncated
     big = P.table_build(P.PWL, 20)
     assert L.aicdf_sample(big.handle, P.PWL, None, 0, 0, 16, fake, P.F32, None) == P.ERR_UNSUPPORTED
+    # truncated-bit sampling: unsupported widths, bad dtype, misaligned output
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 12, 0, 0, 16, fake, P.F32, None) == P.ERR_UNSUPPORTED
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 0, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 24, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 16, 0, 0, 16, fake, 3, None) == P.ERR_ARG
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 16, 0, 0, 16, fake + 2, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample_bits(tc.handle, P.PWL, 16, 0, 0, 16, fake, P.F32, None) == P.ERR_ARG
+    assert L.aicdf_sample_bits(t.handle, P.PWL, 16, 0, 0, 0, None, P.F32, None) == P.OK
     # host pipeline: staging too small
     assert L.aicdf_sample_to_host(t.handle, P.PWL, 0, 0, 16, fake, P.F32, fake, 1024, None) == P.ERR_ARG
 
