@@ -622,29 +622,35 @@ static double gammq(double a, double x) {
   return exp(lpre) * h;
 }
 
-/* sum over j of Pois(j; lam/2) * f(j), outward from the mode until the weight
- * falls below 1e-17 on both sides; f = CDF (0), density (1) or upper tail (2)
- * of the central chi^2 with nu + 2j degrees of freedom */
+/* sum over j of Pois(j; lam/2) * f(j), outward from the mode; f = CDF (0),
+ * density (1) or upper tail (2) of the central chi^2 with nu + 2j degrees of
+ * freedom.  f <= 1 for the CDF and the tail, and the density is <= 1/2 for
+ * nu + 2j >= 2, so a side is cut once its Poisson weight is below 1e-17 of
+ * the running sum (the neglected terms then sum to about 1e-17 relative,
+ * however small the sum itself is); for nu < 2 the j = 0 density, unbounded
+ * near x = 0, is always added. */
+static double ncx2_f(double x, double a, int pdf) {
+  if (pdf == 1) return (x <= 0.0) ? 0.0 : exp((a - 1.0) * log(0.5 * x) - 0.5 * x - lgamma(a)) * 0.5;
+  if (pdf == 2) return gammq(a, 0.5 * x);
+  return or_gammp(a, 0.5 * x);
+}
+
 static double ncx2_mix(double x, double nu, double lam, int pdf) {
   double m = 0.5 * lam;
   int64_t j0 = (int64_t)floor(m);
   double total = 0.0;
-  for (int dir = 0; dir < 2; ++dir) {
-    for (int64_t j = (dir == 0 ? j0 : j0 - 1); j >= 0; j += (dir == 0 ? 1 : -1)) {
-      double w = exp(pois_logw(j, m));
-      double f;
-      double a = 0.5 * nu + (double)j;
-      if (pdf == 1) {
-        /* central chi^2_{nu+2j} density at x */
-        f = (x <= 0.0) ? 0.0 : exp((a - 1.0) * log(0.5 * x) - 0.5 * x - lgamma(a)) * 0.5;
-      } else if (pdf == 2) {
-        f = gammq(a, 0.5 * x);
-      } else {
-        f = or_gammp(a, 0.5 * x);
-      }
-      total += w * f;
-      if (w < 1e-17 && (dir == 1 || (double)j > m)) break;
-      if (j > j0 + 100000000) break;
+  for (int64_t j = j0;; ++j) {           /* upward from the mode */
+    double w = exp(pois_logw(j, m));
+    total += w * ncx2_f(x, 0.5 * nu + (double)j, pdf);
+    if (w == 0.0 || w < 1e-17 * total) break;
+    if (j > j0 + 100000000) break;
+  }
+  for (int64_t j = j0 - 1; j >= 0; --j) { /* downward to 0 */
+    double w = exp(pois_logw(j, m));
+    total += w * ncx2_f(x, 0.5 * nu + (double)j, pdf);
+    if ((w == 0.0 || w < 1e-17 * total) && j > 0) {
+      if (pdf == 1 && nu < 2.0) total += exp(pois_logw(0, m)) * ncx2_f(x, 0.5 * nu, pdf);
+      break;
     }
   }
   return total;

@@ -688,6 +688,64 @@ def test_ncx2_P_limits(orc):
         assert y1 == pytest.approx(chi2.ppf(u, 3.0) / (2 * math.sqrt(3.0)) - math.sqrt(3.0) / 2, abs=1e-6)
 
 
+def test_ncx2_upper_tail_against_scipy(orc):
+    """The directly summed upper tail and its quantile match scipy's ncx2.sf /
+    ncx2.isf, down to tail probabilities far below the FP64 spacing at 1."""
+    from scipy.stats import ncx2
+    for nu, lam in ((1.0, 1.0), (2.0, 30.0), (10.0, 224.0)):
+        for v in (0.3, 1e-3, 1e-9, 1e-15, 1e-25):
+            x = orc.ncx2_isf(v, nu, lam)
+            assert orc.ncx2_sf(x, nu, lam) == pytest.approx(v, rel=1e-10)
+            assert x == pytest.approx(ncx2.isf(v, nu, lam), rel=2e-7)
+        for u in (0.2, 0.6):
+            x = orc.ncx2_ppf(u, nu, lam)
+            assert orc.ncx2_sf(x, nu, lam) == pytest.approx(1 - u, rel=1e-12)
+
+
+def _ncx2_tables():
+    out = {}
+    for row in _read_golden("ncx2_rmse_table5.txt"):
+        out[(int(row[0]), int(row[1]), int(row[2]))] = float(row[3])
+    return out
+
+
+def test_ncx2_tables_reproduce_table5(orc):
+    """Section 5.1 approximation (two halves, 16 dyadic intervals per half, 16
+    knots equally spaced in sqrt(y), linear interpolation in sqrt(y), L2 fits):
+    its RMSE against the exact inverse reproduces the values printed in Table 5
+    (a: linear, b: cubic) to their three decimals."""
+    want = _ncx2_tables()
+    cases = {(1, 1): (1, 10, 200), (1, 10): (5, 100), (3, 1): (1, 50, 200), (3, 10): (10, 100)}
+    for (deg, nu), lams in cases.items():
+        c = orc.ncx2_poly_table(nu, 16, 16, deg)
+        for lam in lams:
+            r = orc.ncx2_poly_rmse(c, nu, lam)
+            assert abs(r - want[(deg, nu, lam)]) <= 0.0006, (deg, nu, lam, r)
+
+
+def test_ncx2_table_limits(orc):
+    """Knot y = 0 is the Gaussian limit: the lower half equals the L2 polynomial
+    tables of Phi^{-1} on the same intervals and the upper half its negation;
+    knot y = 1 is the central chi^2 limit, and the tables reproduce scipy's
+    chi2 quantile there to their fit error."""
+    from scipy.stats import chi2
+    K, nu = 16, 4.0
+    c = orc.ncx2_poly_table(nu, K, 16, 3)
+    g, _ = orc.pwp_table(K, 3)
+    assert np.allclose(c[0, 0, 1:], g[1:], rtol=1e-7, atol=1e-9)
+    assert np.allclose(c[0, 1, 1:], -g[1:], rtol=1e-7, atol=1e-9)
+    assert c[0, 0, 0, 0] == pytest.approx(0.0, abs=1e-12)
+    for u in (0.01, 0.2, 0.5, 0.8, 0.99):
+        want = chi2.ppf(u, nu)
+        assert orc.ncx2_poly_ppf(c, nu, u, 0.0) == pytest.approx(want, abs=2e-3 * (1 + want))
+    # between knots the interpolation is linear in sqrt(y)
+    y0, y1 = (3 / 15) ** 2, (4 / 15) ** 2
+    ym = ((3.5 / 15)) ** 2
+    for u in (0.1, 0.7):
+        p0, p1, pm = (orc.ncx2_poly_P(c, u, y) for y in (y0, y1, ym))
+        assert pm == pytest.approx(0.5 * (p0 + p1), abs=1e-13)
+
+
 # ---------------------------------------------------------------- MLP
 def test_mlp_gradient_finite_differences(orc):
     rng = np.random.default_rng(4)
