@@ -273,6 +273,53 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
             "root_finder_status": int(st.item()), "levels": levels}
 
 
+def cir_table(P, dev, stream, n_eval: int = 1 << 22):
+    """Section 5.1 tabulated inverse (16 dyadic intervals per half, 16 knots in
+    sqrt(y)) on the paper's CIR set (kappa 1/2, theta = sigma = T = X0 = 1,
+    nu = 2): build time, evaluation rate against the exact FP64 root finder on
+    the same (u, lambda) pairs, and Var(X_T - X~_T) / Var(X_T) per level for
+    the linear and the cubic tables (Section 5.2 reads 2^-15 and 2^-25)."""
+    import math
+    import time as _t
+    import torch
+    nu = 2.0
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    u = torch.empty(n_eval, device=dev)
+    lam = torch.empty(n_eval, device=dev)
+    tgt = torch.empty(n_eval, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.ncx2_targets(nu, n_eval, u, lam, tgt, st, seed=7, tag=1, stream=stream)   # exact quantiles
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_exact_ms = e0.elapsed_time(e1)
+    res = {"nu": nu, "exact_quantiles_per_s": n_eval / (t_exact_ms / 1e3), "root_finder_status": int(st.item())}
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    out = torch.empty(n_eval, device=dev)
+    for deg, name in ((1, "linear"), (3, "cubic")):
+        t0 = _t.perf_counter()
+        t = P.Ncx2Table(nu, 16, 16, deg)
+        build_s = _t.perf_counter() - t0
+        tot, per = _time_device(lambda: t.eval(u, lam, out, stream=stream), 10, 3, stream)
+        evals = n_eval / (statistics.mean(per) / 1e3)
+        levels = []
+        for l in range(0, 7, 2):
+            n = 1 << 16
+            v = {}
+            for kname, kind in (("exact", P.CIR_EXACT), ("diff", P.CIR_DIFF_TABLE)):
+                P.cir_level_table(prm, t, l, kind, n, sums, ws, st, seed=9, tag=1 + l, stream=stream)
+                s = sums.cpu().numpy()
+                v[kname] = s[1] / n - (s[0] / n) ** 2
+            levels.append({"l": l, "log2_var_ratio": math.log2(v["diff"] / v["exact"])})
+        res[name] = {"build_s": build_s, "evals_per_s": evals,
+                     "exact_over_table_cost": evals / res["exact_quantiles_per_s"], "levels": levels}
+    res["root_finder_status"] |= int(st.item())
+    return res
+
+
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
     wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
@@ -292,6 +339,9 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
                      "L": r.L, "wall_ms": r.wall_ms, "gpu_ms": r.gpu_ms, "launches": r.launches,
                      "converged": bool(r.converged)}
     res["eps"] = eps
+    # calibrated device ns per fine path-step of each estimator kind (level 5, 2^17 paths)
+    res["step_ns"] = {"approx2": nested.cost_ns[0][0] / 2, "corr4": nested.cost_ns[0][1] / 2,
+                      "exact2": regular.cost_ns[0][0] / 2, "plain": plain.cost_ns[L][0] / (2 ** L + 1)}
     res["speedup_vs_plain_exact_wall"] = plain.wall_ms / nested.wall_ms
     res["speedup_vs_regular_mlmc_wall"] = regular.wall_ms / nested.wall_ms
     res["speedup_vs_plain_exact_gpu"] = plain.gpu_ms / nested.gpu_ms
@@ -424,6 +474,13 @@ def main():
         for name, fn in variants.items():
             tot, _ = _time_device(fn, max(5, args.steps // 2), 3, stream)
             extras[name + "_gsamples_per_s"] = N_SAMPLES * max(5, args.steps // 2) / (tot / 1e3) / 1e9
+        # u -> x mode: caller uniforms in HBM (8 B/sample moved: 4 read + 4 written)
+        uin = torch.rand(N_SAMPLES, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        tot, per = _time_device(lambda: P.sample(tl, P.PWL, out, u=uin, stream=stream), max(5, args.steps // 2), 3,
+                                stream)
+        extras["pwl_input_f32_gsamples_per_s"] = N_SAMPLES / (statistics.mean(per) / 1e3) / 1e9
+        extras["pwl_input_f32_hbm_frac"] = 8.0 * N_SAMPLES / (statistics.mean(per) / 1e3) / 1e9 / peak
+        del uin
         extras["pwl_over_exact"] = value / world / extras["exact_f32_gsamples_per_s"]
         extras["pwl_over_exact_lib"] = value / world / extras["exact_lib_f32_gsamples_per_s"]
         # the small piecewise-constant configuration: 2^20 samples (launch-latency bound)
@@ -436,7 +493,8 @@ def main():
                          ("mlmc_eps_1e-5", lambda: mlmc_time_to_rmse(P, tl, dev, eps=1e-5)),
                          ("sampler_sweep", lambda: sampler_sweep(P, tl, dev, stream)),
                          ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
-                         ("cir_surrogate", lambda: cir_surrogate(P, dev, stream))):
+                         ("cir_surrogate", lambda: cir_surrogate(P, dev, stream)),
+                         ("cir_table", lambda: cir_table(P, dev, stream))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # reported, not hidden: the headline line still prints

@@ -123,8 +123,9 @@ aicdf_status aicdf_sample(aicdf_table table, int method, const float *u_dev, uin
  * (staging_bytes >= 2 MiB, 256-byte aligned; split in four parts when it
  * holds at least 4 MiB, else two) and overlaps the generation of one chunk
  * with the device-to-host copies of the previous ones (two copy streams).
- * host_out should be pinned for full speed.  Synchronous: returns when
- * host_out is complete. */
+ * If host_out is page-locked memory the device can address, the kernel
+ * stores the samples into it directly over the host link and the staging
+ * buffer is left untouched.  Synchronous: returns when host_out is complete. */
 aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint64_t seed,
                                   uint64_t offset, size_t n, void *host_out, int out_dtype,
                                   void *staging_dev, size_t staging_bytes,
@@ -370,7 +371,8 @@ aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const 
  * with c = sigma^2 (1 - e^{-kappa h}) / (4 kappa), nu = 4 kappa theta / sigma^2. */
 typedef enum {
   AICDF_CIR_EXACT = 0, AICDF_CIR_SURROGATE = 1, AICDF_CIR_DIFF = 2,
-  AICDF_CIR_GAUSS = 3, AICDF_CIR_DIFF_GAUSS = 4
+  AICDF_CIR_GAUSS = 3, AICDF_CIR_DIFF_GAUSS = 4,
+  AICDF_CIR_TABLE = 5, AICDF_CIR_DIFF_TABLE = 6  /* aicdf_cir_level_table only */
 } aicdf_cir_kind;
 
 /* Sums of Y and Y^2 (FP64) over paths path_offset .. path_offset+n_paths-1 of
@@ -382,6 +384,45 @@ aicdf_status aicdf_cir_level(const aicdf_sde_params *params, aicdf_surrogate sur
                              int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                              uint32_t tag, double *sums_dev, void *workspace_dev,
                              size_t workspace_bytes, int *status_dev, aicdf_stream_t stream);
+
+/* ===================================================================== */
+/* Tabulated non-central chi-squared inverse (Section 5.1)               */
+/* ===================================================================== */
+/* For a fixed nu, with y = nu / (lambda + nu) and
+ *   P_nu(U; y) = sqrt(nu / 4y) ((y / nu) C^{-1}_nu(U; (1 - y) nu / y) - 1),
+ * the approximation is C~^{-1}_nu(U; lambda) = h + 2 sqrt(h) P~(U; y), h = lambda + nu,
+ * where P~ interpolates linearly in sqrt(y) between tables at n_knots knots
+ * sqrt(y_i) = i / (n_knots - 1) (y = 0: the Gaussian limit Phi^{-1}; y = 1: the
+ * central chi^2).  Each knot holds two tables, for u <= 1/2 and u > 1/2, each
+ * the L2-optimal polynomial of the given degree (1..3) on the K dyadic
+ * intervals of v = min(u, 1 - u) in the local variable s (as for AICDF_PWP);
+ * row 0 of each half is the value at u = 1/2.  The paper's Table 5 uses
+ * K = 16 and 16 knots.  Built on the host in FP64 (exact quantiles from the
+ * library's root finder; about a second); *out owns the table.
+ * Errors: AICDF_ERR_ARG for nu <= 0, K outside 1..30, n_knots outside 2..64
+ * or degree outside 1..3; AICDF_ERR_DOMAIN if a quantile did not converge. */
+typedef struct aicdf_ncx2_table_s *aicdf_ncx2_table;
+aicdf_status aicdf_ncx2_table_build(double nu, int K, int n_knots, int degree, aicdf_ncx2_table *out);
+void aicdf_ncx2_table_destroy(aicdf_ncx2_table t);
+aicdf_status aicdf_ncx2_table_info(aicdf_ncx2_table t, double *nu, int *K, int *n_knots, int *degree);
+/* FP64 coefficients, layout [knot][half][row 0..K][power 0..3] (half 1: u > 1/2);
+ * cap in doubles; with coef == NULL only *n_out is set. */
+aicdf_status aicdf_ncx2_table_get(aicdf_ncx2_table t, double *coef, size_t cap, size_t *n_out);
+/* out_dev[i] = C~^{-1}_nu(u_dev[i]; lam_dev[i]) in FP32 (device arrays of n;
+ * NaN for u outside [0, 1] or lambda < 0, NaN or inf).  The kernels take the
+ * table as a launch parameter: n_knots * 2 * (K + 1) <= 1024, else
+ * AICDF_ERR_UNSUPPORTED.  Asynchronous on stream. */
+aicdf_status aicdf_ncx2_table_eval(aicdf_ncx2_table t, const float *u_dev, const float *lam_dev, size_t n,
+                                   float *out_dev, aicdf_stream_t stream);
+/* aicdf_cir_level with the tabulated approximation in place of the
+ * surrogate: kinds AICDF_CIR_EXACT, AICDF_CIR_TABLE (P(X~_T) with
+ * X~' = c max(C~^{-1}_nu(U; lambda~), 0)) and AICDF_CIR_DIFF_TABLE
+ * (P(X^_T) - P(X~_T), same uniforms).  The table's nu must equal
+ * 4 kappa theta / sigma^2 (AICDF_ERR_DOMAIN otherwise). */
+aicdf_status aicdf_cir_level_table(const aicdf_sde_params *params, aicdf_ncx2_table table, int level,
+                                   int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                   uint32_t tag, double *sums_dev, void *workspace_dev,
+                                   size_t workspace_bytes, int *status_dev, aicdf_stream_t stream);
 
 /* ===================================================================== */
 /* MLMC driver (Section 4.1): estimate E[P] to a target RMSE               */

@@ -123,6 +123,12 @@ SIGNATURES = {
     "aicdf_surrogate_train_step": (_I, [_P, _P, _P, _P, _SZ, C.c_float, _P, _P]),
     "aicdf_surrogate_train": (_I, [_P, _P, _P, _P, _SZ, _SZ, _I, C.c_float, C.c_float, _P, _P]),
     "aicdf_cir_level": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P, _P]),
+    "aicdf_ncx2_table_build": (_I, [_D, _I, _I, _I, _P]),
+    "aicdf_ncx2_table_destroy": (None, [_P]),
+    "aicdf_ncx2_table_info": (_I, [_P, _P, _P, _P, _P]),
+    "aicdf_ncx2_table_get": (_I, [_P, _P, _SZ, _P]),
+    "aicdf_ncx2_table_eval": (_I, [_P, _P, _P, _SZ, _P, _P]),
+    "aicdf_cir_level_table": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P, _P]),
     "aicdf_mlmc_run_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_run": (_I, [_P, _P, _P, _P, _P, _SZ, _P]),
 }
@@ -360,7 +366,7 @@ class Batch:
 
 
 # ------------------------------------------------------------------ NCX2, surrogate, CIR
-CIR_EXACT, CIR_SURROGATE, CIR_DIFF, CIR_GAUSS, CIR_DIFF_GAUSS = range(5)
+CIR_EXACT, CIR_SURROGATE, CIR_DIFF, CIR_GAUSS, CIR_DIFF_GAUSS, CIR_TABLE, CIR_DIFF_TABLE = range(7)
 MLP_OFFSETS = {"W1": (0, (64, 2)), "b1": (128, (64,)), "W2": (192, (64, 64)), "b2": (4288, (64,)),
                "w3": (4352, (64,)), "b3": (4416, (1,))}
 
@@ -438,4 +444,51 @@ def cir_level(params: SdeParams, surrogate, level: int, kind: int, n_paths: int,
     _check(lib().aicdf_cir_level(C.byref(params), None if surrogate is None else surrogate.handle, level,
                                  kind, n_paths, path_offset, seed, tag, _ptr(sums), _ptr(workspace), nbytes,
                                  _ptr(status), _stream(stream)), "cir_level")
+    return sums
+
+
+class Ncx2Table:
+    """aicdf_ncx2_table_*: the Section 5.1 tabulated inverse for one nu."""
+
+    def __init__(self, nu: float, K: int = 16, n_knots: int = 16, degree: int = 1):
+        h = C.c_void_p()
+        _check(lib().aicdf_ncx2_table_build(float(nu), K, n_knots, degree, C.byref(h)), "ncx2_table_build")
+        self.handle = h
+        self.nu, self.K, self.n_knots, self.degree = float(nu), K, n_knots, degree
+
+    def coefficients(self) -> np.ndarray:
+        """FP64 coefficients as (n_knots, 2 halves, K+1 rows, 4 powers)."""
+        import numpy as np
+        n = C.c_size_t()
+        _check(lib().aicdf_ncx2_table_get(self.handle, None, 0, C.byref(n)), "ncx2_table_get")
+        c = np.zeros(n.value, dtype=np.float64)
+        _check(lib().aicdf_ncx2_table_get(self.handle, c.ctypes.data, n.value, C.byref(n)), "ncx2_table_get")
+        return c.reshape(self.n_knots, 2, self.K + 1, 4)
+
+    def info(self):
+        nu, K, nk, d = C.c_double(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().aicdf_ncx2_table_info(self.handle, C.byref(nu), C.byref(K), C.byref(nk), C.byref(d)),
+               "ncx2_table_info")
+        return nu.value, K.value, nk.value, d.value
+
+    def eval(self, u, lam, out, stream=None):
+        """out <- C~^{-1}_nu(u; lam) (device float32 tensors of equal length)."""
+        _check(lib().aicdf_ncx2_table_eval(self.handle, _ptr(u), _ptr(lam), out.numel(), _ptr(out),
+                                           _stream(stream)), "ncx2_table_eval")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.aicdf_ncx2_table_destroy(h)
+            self.handle = None
+
+
+def cir_level_table(params: SdeParams, table: Ncx2Table, level: int, kind: int, n_paths: int, sums, workspace,
+                    status, path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
+    """aicdf_cir_level_table: sums <- [sum Y, sum Y^2, n] with the tabulated approximation."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().aicdf_cir_level_table(C.byref(params), table.handle, level, kind, n_paths, path_offset, seed,
+                                       tag, _ptr(sums), _ptr(workspace), nbytes, _ptr(status), _stream(stream)),
+           "cir_level_table")
     return sums

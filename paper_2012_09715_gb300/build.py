@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaicdf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["sample.cu", "mlmc.cu", "mlp.cu", "cir.cu", "noalloc.cu"]
+CU_SOURCES = ["sample.cu", "mlmc.cu", "mlp.cu", "cir.cu", "noalloc.cu", "ncx2_table.cu"]
 CPP_SOURCES = ["tables.cpp", "abi.cpp", "driver.cpp"]
 
 

@@ -20,6 +20,7 @@
 #include "mlmc_path.cuh"
 #include "mlp_device.cuh"
 #include "ncx2.cuh"
+#include "ncx2_table.cuh"
 
 namespace aicdf {
 
@@ -36,14 +37,24 @@ struct CirArgs {
   float X0, K, discount;
 };
 
-template <bool EXACT, int APPROX>  // APPROX: 0 none, 1 surrogate, 2 Gaussian limit
+struct NoTab {};
+
+// APPROX: 0 none, 1 surrogate, 2 Gaussian limit, 3 table (TabT = Ncx2TabArgs)
+template <bool EXACT, int APPROX, class TabT>
 __global__ void __launch_bounds__(kCirThreads)
-    k_cir(const __grid_constant__ CirArgs a, double2 *__restrict__ partials, int *__restrict__ status) {
+    k_cir(const __grid_constant__ CirArgs a, const __grid_constant__ TabT tab, double2 *__restrict__ partials,
+          int *__restrict__ status) {
   __shared__ __align__(16) MlpSmem s;
   __shared__ __align__(16) __nv_bfloat16 hs[APPROX == 1 ? kCirThreads / 32 : 1][32 * kHPad];
   __shared__ double2 s_red[kCirThreads / 32];
-  if (APPROX == 1) {
+  __shared__ float4 s_rows[APPROX == 3 ? kNcx2TabMaxRows : 1];
+  if constexpr (APPROX == 1) {
     mlp_stage(a.params, s);
+    __syncthreads();
+  }
+  if constexpr (APPROX == 3) {
+    const int nrows = tab.n_knots * 2 * (tab.K + 1);
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) s_rows[r] = tab.rows[r];
     __syncthreads();
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -72,7 +83,7 @@ __global__ void __launch_bounds__(kCirThreads)
           if (APPROX != 0) {
             const float lam = fmaxf(xa, 0.f) * ratio;
             float pt;
-            if (APPROX == 1) {
+            if constexpr (APPROX == 1) {
               pt = mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_lam(lam), hs[warp]);
               if (lam > kLamTrainMax) {
                 // beyond the trained range: P - Phi^{-1}(U) = O(sqrt(y)) as y -> 0
@@ -81,6 +92,8 @@ __global__ void __launch_bounds__(kCirThreads)
                 const float z = phiinv_f32(u);
                 pt = fmaf(pt - z, sqrtf((kLamTrainMax + nuf) / (lam + nuf)), z);
               }
+            } else if constexpr (APPROX == 3) {
+              pt = ncx2_table_P(s_rows, tab.K, tab.n_knots, tab.scale_k, u, sqrtf(nuf / (lam + nuf)));
             } else {
               pt = phiinv_f32(u);
             }
@@ -107,21 +120,73 @@ __global__ void __launch_bounds__(kCirThreads)
   if (st) atomicOr(status, st);
 }
 
-using CirFn = void (*)(CirArgs, double2 *, int *);
+using CirFn = void (*)(CirArgs, NoTab, double2 *, int *);
+using CirTabFn = void (*)(CirArgs, Ncx2TabArgs, double2 *, int *);
 
 static CirFn select_cir(int kind) {
   switch (kind) {
-    case AICDF_CIR_EXACT: return k_cir<true, 0>;
-    case AICDF_CIR_SURROGATE: return k_cir<false, 1>;
-    case AICDF_CIR_DIFF: return k_cir<true, 1>;
-    case AICDF_CIR_GAUSS: return k_cir<false, 2>;
-    default: return k_cir<true, 2>;
+    case AICDF_CIR_EXACT: return k_cir<true, 0, NoTab>;
+    case AICDF_CIR_SURROGATE: return k_cir<false, 1, NoTab>;
+    case AICDF_CIR_DIFF: return k_cir<true, 1, NoTab>;
+    case AICDF_CIR_GAUSS: return k_cir<false, 2, NoTab>;
+    default: return k_cir<true, 2, NoTab>;
   }
 }
 
 const float *surrogate_params(aicdf_surrogate s);
 double surrogate_nu(aicdf_surrogate s);
 bool surrogate_ok(aicdf_surrogate s);
+aicdf_status pack_ncx2_table(const aicdf_ncx2_table_s *t, Ncx2TabArgs *a);
+double ncx2_table_nu(const aicdf_ncx2_table_s *t);
+
+// Argument checks and the per-level constants shared by both entry points.
+static aicdf_status cir_setup(const aicdf_sde_params *prm, int level, uint64_t n_paths, uint64_t path_offset,
+                              uint64_t seed, uint32_t tag, int kind, double *sums_dev, void *workspace_dev,
+                              size_t workspace_bytes, int *status_dev, CirArgs *a) {
+  if (!prm || prm->model != AICDF_MODEL_CIR) return AICDF_ERR_ARG;
+  if (level < 0 || level > 12) return AICDF_ERR_ARG;
+  if (n_paths == 0 || path_offset + n_paths < path_offset) return AICDF_ERR_ARG;
+  if (!sums_dev || ((uintptr_t)sums_dev % 8) || !status_dev) return AICDF_ERR_ARG;
+  if (!workspace_dev || ((uintptr_t)workspace_dev % 16) || workspace_bytes < aicdf_mlmc_level_workspace_bytes())
+    return AICDF_ERR_ARG;
+  if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL) return AICDF_ERR_ARG;
+  if (!(prm->kappa > 0.0) || !(prm->theta > 0.0) || !(prm->sigma > 0.0) || !(prm->T > 0.0) ||
+      !(prm->X0 >= 0.0) || !std::isfinite(prm->X0 + prm->T + prm->K + prm->discount))
+    return AICDF_ERR_DOMAIN;
+  std::memset(a, 0, sizeof(*a));
+  const double h = prm->T / std::ldexp(1.0, level);
+  a->keys = make_keys(seed);
+  a->n_paths = n_paths;
+  a->path_offset = path_offset;
+  a->tag = tag;
+  a->level = level;
+  a->kind = kind;
+  a->payoff = prm->payoff;
+  a->nu = 4.0 * prm->kappa * prm->theta / (prm->sigma * prm->sigma);
+  a->e = std::exp(-prm->kappa * h);
+  a->c = prm->sigma * prm->sigma * (-std::expm1(-prm->kappa * h)) / (4.0 * prm->kappa);
+  a->X0 = (float)prm->X0;
+  a->K = (float)prm->K;
+  a->discount = (float)prm->discount;
+  return AICDF_OK;
+}
+
+template <class Fn, class TabT>
+static aicdf_status cir_launch(Fn k, const CirArgs &a, const TabT &tab, uint64_t n_paths, void *workspace_dev,
+                               double *sums_dev, int *status_dev, cudaStream_t st) {
+  const uint64_t want = (n_paths + kCirThreads - 1) / kCirThreads;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
+      want, std::min<uint64_t>((uint64_t)sm_count() * resident_blocks((const void *)k, kCirThreads), 4096)));
+  double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
+  k<<<grid, kCirThreads, 0, st>>>(a, tab, parts, status_dev);
+  launch_reduce_partials(parts, grid, (double)n_paths, sums_dev, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error((int)e);
+    return AICDF_ERR_CUDA;
+  }
+  return AICDF_OK;
+}
 
 }  // namespace aicdf
 
@@ -131,51 +196,35 @@ extern "C" aicdf_status aicdf_cir_level(const aicdf_sde_params *prm, aicdf_surro
                                         uint64_t n_paths, uint64_t path_offset, uint64_t seed, uint32_t tag,
                                         double *sums_dev, void *workspace_dev, size_t workspace_bytes,
                                         int *status_dev, aicdf_stream_t stream) {
-  if (!prm || prm->model != AICDF_MODEL_CIR) return AICDF_ERR_ARG;
-  if (level < 0 || level > 12 || kind < AICDF_CIR_EXACT || kind > AICDF_CIR_DIFF_GAUSS) return AICDF_ERR_ARG;
-  if (n_paths == 0 || path_offset + n_paths < path_offset) return AICDF_ERR_ARG;
-  if (!sums_dev || ((uintptr_t)sums_dev % 8) || !status_dev) return AICDF_ERR_ARG;
-  if (!workspace_dev || ((uintptr_t)workspace_dev % 16) || workspace_bytes < aicdf_mlmc_level_workspace_bytes())
-    return AICDF_ERR_ARG;
-  if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL) return AICDF_ERR_ARG;
-  if (!(prm->kappa > 0.0) || !(prm->theta > 0.0) || !(prm->sigma > 0.0) || !(prm->T > 0.0) ||
-      !(prm->X0 >= 0.0) || !std::isfinite(prm->X0 + prm->T + prm->K + prm->discount))
-    return AICDF_ERR_DOMAIN;
-  const bool needs_sur = kind == AICDF_CIR_SURROGATE || kind == AICDF_CIR_DIFF;
+  if (kind < AICDF_CIR_EXACT || kind > AICDF_CIR_DIFF_GAUSS) return AICDF_ERR_ARG;
   CirArgs a;
-  std::memset(&a, 0, sizeof(a));
-  const double nu = 4.0 * prm->kappa * prm->theta / (prm->sigma * prm->sigma);
-  if (needs_sur) {
+  aicdf_status s = cir_setup(prm, level, n_paths, path_offset, seed, tag, kind, sums_dev, workspace_dev,
+                             workspace_bytes, status_dev, &a);
+  if (s != AICDF_OK) return s;
+  if (kind == AICDF_CIR_SURROGATE || kind == AICDF_CIR_DIFF) {
     if (!surrogate_ok(sur)) return AICDF_ERR_ARG;
-    if (std::fabs(surrogate_nu(sur) - nu) > 1e-9 * nu) return AICDF_ERR_DOMAIN;  // trained for another nu
+    if (std::fabs(surrogate_nu(sur) - a.nu) > 1e-9 * a.nu) return AICDF_ERR_DOMAIN;  // trained for another nu
     a.params = surrogate_params(sur);
   }
-  const double h = prm->T / std::ldexp(1.0, level);
-  a.keys = make_keys(seed);
-  a.n_paths = n_paths;
-  a.path_offset = path_offset;
-  a.tag = tag;
-  a.level = level;
-  a.kind = kind;
-  a.payoff = prm->payoff;
-  a.nu = nu;
-  a.e = std::exp(-prm->kappa * h);
-  a.c = prm->sigma * prm->sigma * (-std::expm1(-prm->kappa * h)) / (4.0 * prm->kappa);
-  a.X0 = (float)prm->X0;
-  a.K = (float)prm->K;
-  a.discount = (float)prm->discount;
-  CirFn k = select_cir(kind);
-  const uint64_t want = (n_paths + kCirThreads - 1) / kCirThreads;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
-      want, std::min<uint64_t>((uint64_t)sm_count() * resident_blocks((const void *)k, kCirThreads), 4096)));
-  double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
-  cudaStream_t st = (cudaStream_t)stream;
-  k<<<grid, kCirThreads, 0, st>>>(a, parts, status_dev);
-  launch_reduce_partials(parts, grid, (double)n_paths, sums_dev, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_cuda_error((int)e);
-    return AICDF_ERR_CUDA;
-  }
-  return AICDF_OK;
+  return cir_launch(select_cir(kind), a, NoTab{}, n_paths, workspace_dev, sums_dev, status_dev,
+                    (cudaStream_t)stream);
+}
+
+extern "C" aicdf_status aicdf_cir_level_table(const aicdf_sde_params *prm, aicdf_ncx2_table table, int level,
+                                              int kind, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                              uint32_t tag, double *sums_dev, void *workspace_dev,
+                                              size_t workspace_bytes, int *status_dev, aicdf_stream_t stream) {
+  if (kind != AICDF_CIR_EXACT && kind != AICDF_CIR_TABLE && kind != AICDF_CIR_DIFF_TABLE) return AICDF_ERR_ARG;
+  CirArgs a;
+  aicdf_status s = cir_setup(prm, level, n_paths, path_offset, seed, tag, kind, sums_dev, workspace_dev,
+                             workspace_bytes, status_dev, &a);
+  if (s != AICDF_OK) return s;
+  static thread_local Ncx2TabArgs tab;  // 16 KiB: keep it off the stack
+  s = pack_ncx2_table(table, &tab);
+  if (s != AICDF_OK) return s;
+  if (std::fabs(ncx2_table_nu(table) - a.nu) > 1e-9 * a.nu) return AICDF_ERR_DOMAIN;  // built for another nu
+  CirTabFn k = kind == AICDF_CIR_EXACT ? k_cir<true, 0, Ncx2TabArgs>
+               : kind == AICDF_CIR_TABLE ? k_cir<false, 3, Ncx2TabArgs>
+                                         : k_cir<true, 3, Ncx2TabArgs>;
+  return cir_launch(k, a, tab, n_paths, workspace_dev, sums_dev, status_dev, (cudaStream_t)stream);
 }

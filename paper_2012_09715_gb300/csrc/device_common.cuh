@@ -44,13 +44,16 @@ inline PhiloxKeys make_keys(uint64_t seed) {
   return k;
 }
 
+// One Philox round: the two 32 x 32 -> 64 products are written as 64-bit
+// multiplies, so each is a single wide multiply giving both halves.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = (uint64_t)PHILOX_M0 * c.x, p1 = (uint64_t)PHILOX_M1 * c.z;
+  return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
 __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &k) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = PHILOX_M0 * c.x, hi0 = __umulhi(PHILOX_M0, c.x);
-    const uint32_t lo1 = PHILOX_M1 * c.z, hi1 = __umulhi(PHILOX_M1, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.k0[r], lo1, hi0 ^ c.w ^ k.k1[r], lo0);
-  }
+  for (int r = 0; r < 10; ++r) c = philox_round(c, k.k0[r], k.k1[r]);
   return c;
 }
 
@@ -60,14 +63,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &k) {
 template <int NC>
 __device__ __forceinline__ void philox_n(uint4 (&c)[NC], const PhiloxKeys &k) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
+  for (int r = 0; r < 10; ++r)
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      const uint32_t lo0 = PHILOX_M0 * c[q].x, hi0 = __umulhi(PHILOX_M0, c[q].x);
-      const uint32_t lo1 = PHILOX_M1 * c[q].z, hi1 = __umulhi(PHILOX_M1, c[q].z);
-      c[q] = make_uint4(hi1 ^ c[q].y ^ k.k0[r], lo1, hi0 ^ c[q].w ^ k.k1[r], lo0);
-    }
-  }
+    for (int q = 0; q < NC; ++q) c[q] = philox_round(c[q], k.k0[r], k.k1[r]);
 }
 
 // (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = low 23 bits of x: both

@@ -13,10 +13,15 @@
 // density is sum_j p_j g_{j-1} / 2.  The quantile solves C = u for u <= 1/2 and
 // Q = 1 - u above (1 - u is exact for FP32 u >= 1/2), by Newton steps kept
 // inside a bracket, started from Sankaran's approximation (Section 5.1).
-// Every loop has a fixed cap; hitting one sets the returned status bit.
+// Every loop has a fixed cap; hitting one sets the returned status bit.  The
+// functions are host+device: the table builder of Section 5.1 runs them on
+// the host in FP64.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+
+#define AICDF_HD __host__ __device__ __forceinline__
 
 namespace aicdf {
 
@@ -24,7 +29,7 @@ constexpr int kNcx2NoConverge = 1;
 
 // log Gamma(s), s > 0: shift to s >= 12 (one log of the product), then the
 // Stirling series through the s^-11 term (truncation error < 1e-16).
-__device__ __forceinline__ double lgamma_pos(double s) {
+AICDF_HD double lgamma_pos(double s) {
   double prod = 1.0;
   while (s < 12.0) {  // at most 12 iterations for s > 0
     prod *= s;
@@ -40,7 +45,7 @@ __device__ __forceinline__ double lgamma_pos(double s) {
 
 // P(s, y), Q(s, y) and g(s) = y^s e^-y / Gamma(s+1): the series for y < s + 1
 // (gives P), the continued fraction for Q otherwise (modified Lentz).
-__device__ __forceinline__ void gamma_pq(double s, double y, double *P, double *Q, double *g, int *status) {
+AICDF_HD void gamma_pq(double s, double y, double *P, double *Q, double *g, int *status) {
   const double lg = s * log(y) - y - lgamma_pos(s + 1.0);
   *g = exp(lg);
   if (y < s + 1.0) {
@@ -79,8 +84,7 @@ __device__ __forceinline__ void gamma_pq(double s, double y, double *P, double *
 
 // Lower CDF (upper = false) or upper tail (upper = true) of chi'^2_nu(lambda)
 // at x, and the density.
-__device__ __forceinline__ void ncx2_tail_pdf(double x, double nu, double lam, bool upper, double *T, double *f,
-                                              int *status) {
+AICDF_HD void ncx2_tail_pdf(double x, double nu, double lam, bool upper, double *T, double *f, int *status) {
   if (x <= 0.0) {
     *T = upper ? 1.0 : 0.0;
     *f = 0.0;
@@ -145,13 +149,12 @@ __device__ __forceinline__ void ncx2_tail_pdf(double x, double nu, double lam, b
 }
 
 // Sankaran's approximation of the quantile (Section 5.1; with sqrt(2 c2) in
-// the normal term), used as the start.
-__device__ __forceinline__ double ncx2_sankaran(double u, double nu, double lam) {
+// the normal term) at the normal quantile z = Phi^{-1}(u), used as the start.
+AICDF_HD double ncx2_sankaran(double z, double nu, double lam) {
   const double k = nu, h0 = k + lam, h2 = k + 2.0 * lam;
   const double c1 = 1.0 - (2.0 / 3.0) * h0 * (k + 3.0 * lam) / (h2 * h2);
   const double c2 = h2 / (h0 * h0);
   const double c3 = (c1 - 1.0) * (1.0 - 3.0 * c1);
-  const double z = normcdfinv(u);
   const double base = 1.0 + c1 * c2 * (c1 - 1.0 + 0.5 * (2.0 - c1) * c2 * c3) +
                       c1 * sqrt(2.0 * c2) * (1.0 + 0.5 * c2 * c3) * z;
   if (!(base > 0.0) || !(fabs(c1) > 1e-3)) return h0;  // outside its range: start at the mean
@@ -159,19 +162,46 @@ __device__ __forceinline__ double ncx2_sankaran(double u, double nu, double lam)
   return (r > 0.0 && isfinite(r)) ? r : h0;
 }
 
-// Quantile C^{-1}_nu(u; lambda) for 0 < u < 1 (FP64).
-__device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int *status) {
-  if (!(u > 0.0)) return 0.0;
-  if (!(u < 1.0)) return __longlong_as_double(0x7ff0000000000000ll);
-  const bool upper = u > 0.5;
-  const double target = upper ? 1.0 - u : u;
+// The x with C(x) = target (upper = false) or 1 - C(x) = target (upper = true),
+// 0 < target <= 1/2, from Sankaran's start at the normal quantile z of the
+// same probability (FP64).  Lower tail: Newton on ln C(e^t) - ln target in
+// t = ln x (C behaves like x^{nu/2} near 0, so this converges in a few steps
+// however deep the tail); upper tail: Newton on 1 - C(x) - target in x.  Both
+// keep the iterate inside a bracket and bisect when Newton leaves it.
+AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, double lam, int *status) {
   double T, f;
-  double x = ncx2_sankaran(u, nu, lam);
-  double lo = 0.0, hi = -1.0;  // hi < 0: no upper bound yet
+  const double x0 = ncx2_sankaran(z, nu, lam);
   int it = 0;
+  if (!upper) {
+    const double lt = log(target);
+    double t = log(x0), lo = -1e300, hi = 1e300;  // bracket in t = ln x
+    for (; it < 100; ++it) {
+      const double x = exp(t);
+      ncx2_tail_pdf(x, nu, lam, false, &T, &f, status);
+      double tn;
+      if (!(T > 0.0)) {  // C underflowed: x far too small
+        lo = t;
+        tn = hi < 1e300 ? 0.5 * (lo + hi) : t + 2.0;
+      } else {
+        const double r = log(T) - lt;  // > 0 when x is too large
+        if (r > 0.0) hi = t;
+        else lo = t;
+        const double d = x * f / T;   // d ln C / d ln x
+        tn = (d > 0.0) ? t - r / d : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = (lo > -1e300 && hi < 1e300) ? 0.5 * (lo + hi) : (r > 0.0 ? t - 2.0 : t + 2.0);
+      }
+      const double dt = fabs(tn - t);
+      t = tn;
+      if (dt <= 1e-13 || (hi - lo) <= 1e-14) break;
+    }
+    if (it == 100) *status |= kNcx2NoConverge;
+    return exp(t);
+  }
+  double x = x0;
+  double lo = 0.0, hi = -1.0;  // hi < 0: no upper bound yet
   for (; it < 100; ++it) {
-    ncx2_tail_pdf(x, nu, lam, upper, &T, &f, status);
-    const double r = upper ? target - T : T - target;  // = C(x) - u, > 0 when x is too large
+    ncx2_tail_pdf(x, nu, lam, true, &T, &f, status);
+    const double r = target - T;  // = C(x) - u, > 0 when x is too large
     if (r > 0.0) hi = x;
     else lo = x;
     double xn = (f > 0.0) ? x - r / f : -1.0;
@@ -186,6 +216,15 @@ __device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int 
   }
   if (it == 100) *status |= kNcx2NoConverge;
   return x;
+}
+
+// Quantile C^{-1}_nu(u; lambda) for 0 < u < 1 (FP64; 1 - u is exact for the
+// FP32 uniforms the paths use).
+__device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int *status) {
+  if (!(u > 0.0)) return 0.0;
+  if (!(u < 1.0)) return __longlong_as_double(0x7ff0000000000000ll);
+  const bool upper = u > 0.5;
+  return ncx2_quantile(upper ? 1.0 - u : u, upper, normcdfinv(u), nu, lam, status);
 }
 
 }  // namespace aicdf

@@ -197,6 +197,26 @@ extern "C" aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint
   a.u = nullptr;
   a.keys = make_keys(seed);
   const size_t esz = out_dtype == AICDF_F32 ? 4 : 2;
+  cudaStream_t st = (cudaStream_t)stream;
+  // Page-locked host memory that the device can address: the kernel stores
+  // straight into it over the host link (no staging, no copy engine).
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer && ((uintptr_t)at.devicePointer % esz) == 0) {
+    a.out = at.devicePointer;
+    a.n = n;
+    a.offset = offset;
+    const bool vec = ((uintptr_t)at.devicePointer % 16) == 0 && (offset % 4) == 0;
+    s = launch_sample(a, method, out_dtype, SRC_PHILOX, vec, st);
+    if (s != AICDF_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_cuda_error((int)e);
+      return AICDF_ERR_CUDA;
+    }
+    return AICDF_OK;
+  }
+  cudaGetLastError();  // clear a pointer-query error for pageable memory
   // NB staging buffers (4 when the staging holds >= 4 x 1 MiB, else 2), each
   // a multiple of 256 bytes; chunk i is generated into buffer i % NB on the
   // caller's stream and copied out on copy stream i % 2, so two copies can be
@@ -204,7 +224,6 @@ extern "C" aicdf_status aicdf_sample_to_host(aicdf_table table, int method, uint
   const int NB = staging_bytes >= (4u << 20) ? 4 : 2;
   const size_t part = (staging_bytes / NB) & ~(size_t)255;
   const size_t chunk = part / esz;
-  cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t done[4] = {}, copied[4] = {};
   cudaStream_t copy_st[2] = {};
   bool ok = true;

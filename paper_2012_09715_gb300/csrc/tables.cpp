@@ -15,6 +15,7 @@
 #include <new>
 
 #include "aicdf_internal.h"
+#include "quad.h"
 
 namespace {
 
@@ -119,52 +120,18 @@ static aicdf_status build_pwl(aicdf_table_s *t, int K) {
 // then expanded to monomials in s.  Moments: Gauss-Legendre in u on the regular
 // intervals; on the singular interval (0, b) the substitution u = b e^{-w}
 // (s = e^{-w}, w in [0, 80], 40 panels).
-static void gl_nodes(int n, std::vector<double> &x, std::vector<double> &w) {
-  x.resize(n);
-  w.resize(n);
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
-// shifted Legendre L_0..L_3 on [0, 1] as monomial coefficients [j][power]
-static const double kShiftedLegendre[4][4] = {
-    {1, 0, 0, 0}, {-1, 2, 0, 0}, {1, -6, 6, 0}, {-1, 12, -30, 20}};
-
 static aicdf_status build_pwp(aicdf_table_s *t, int K, int deg) {
   t->c0.assign(4 * (K + 1), 0.0);  // row-major [row][power]
   std::vector<double> gx, gw;
-  gl_nodes(40, gx, gw);
+  aicdf::gl_nodes(40, gx, gw);
   for (int k = 1; k <= K; ++k) {
     const double b = std::ldexp(1.0, -k);
-    double proj[4] = {0, 0, 0, 0};  // (1/h) int L_j(s) f du = int_0^1 L_j(s) f(u(s)) ds
-    auto accumulate = [&](double s, double f, double weight) {
-      double Lv[4];
-      for (int j = 0; j < 4; ++j) {
-        const double *c = kShiftedLegendre[j];
-        Lv[j] = ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
-        proj[j] += weight * Lv[j] * f;
-      }
-    };
+    aicdf::LegendreProjector pr;  // (1/h) int L_j(s) f du = int_0^1 L_j(s) f(u(s)) ds
     if (k < K) {
       const double a = 0.5 * b, h = b - a;
       for (size_t i = 0; i < gx.size(); ++i) {
         const double s = 0.5 * (gx[i] + 1.0);
-        accumulate(s, aicdf::host_phiinv(a + h * s), 0.5 * gw[i]);
+        pr.add(s, aicdf::host_phiinv(a + h * s), 0.5 * gw[i]);
       }
     } else {
       // s = e^{-w}, ds = e^{-w} dw
@@ -175,14 +142,11 @@ static aicdf_status build_pwp(aicdf_table_s *t, int K, int deg) {
         for (size_t i = 0; i < gx.size(); ++i) {
           const double wv = 0.5 * (w1 - w0) * gx[i] + 0.5 * (w1 + w0);
           const double s = std::exp(-wv);
-          accumulate(s, aicdf::host_phiinv(b * s), 0.5 * (w1 - w0) * gw[i] * s);
+          pr.add(s, aicdf::host_phiinv(b * s), 0.5 * (w1 - w0) * gw[i] * s);
         }
       }
     }
-    for (int j = 0; j <= deg; ++j) {
-      const double dj = (2.0 * j + 1.0) * proj[j];
-      for (int pw = 0; pw < 4; ++pw) t->c0[4 * k + pw] += dj * kShiftedLegendre[j][pw];
-    }
+    pr.monomials(deg, &t->c0[4 * k]);
   }
   t->c1.clear();
   return AICDF_OK;

@@ -152,3 +152,60 @@ def test_mlmc_argument_validation_without_gpu(P):
     bad = P.sde_params(T=0.0)
     assert call(bad, 3, P.KIND_CORR4, 10) == P.ERR_DOMAIN
     assert L.aicdf_mlmc_level(None, t.handle, 3, 1, 10, 0, 0, 1, fake, fake, ws_bytes, None) == P.ERR_ARG
+
+
+def test_pwp_table_matches_oracle(P, orc):
+    """Library (shifted-Legendre projection, exponential substitution on the
+    singular interval) and oracle (normal equations, z-substitution) build the
+    same polynomial tables."""
+    for K in (8, 15):
+        for deg in (1, 2, 3):
+            c = P.table_build(P.PWP, K, deg).coefficients()[0]
+            o, _ = orc.pwp_table(K, deg)
+            assert np.allclose(c, o, rtol=1e-9, atol=1e-11), (K, deg)
+            assert np.array_equal(c.astype(np.float32), o.astype(np.float32)) or \
+                np.max(np.abs(c.astype(np.float32) - o.astype(np.float32))) <= 1e-6
+
+
+def test_ncx2_table_matches_oracle(P, orc):
+    """Section 5.1 tables: the library's host FP64 build (its own root finder,
+    Legendre projection) and the oracle's give the same RMSE against the exact
+    inverse and the same approximation to 2e-5 relative (the largest gap sits
+    in the deepest lower tail, where the two quadratures are cut differently)."""
+    for nu, deg in ((1.0, 1), (0.8889, 3)):
+        t = P.Ncx2Table(nu, 16, 16, deg)
+        assert t.info() == (nu, 16, 16, deg)
+        c = t.coefficients()
+        o = orc.ncx2_poly_table(nu, 16, 16, deg)
+        for lam in (0.5, 100.0):
+            assert orc.ncx2_poly_rmse(c, nu, lam) == pytest.approx(orc.ncx2_poly_rmse(o, nu, lam), rel=1e-6)
+        us = np.concatenate([np.linspace(1e-6, 1 - 1e-6, 401), 10.0 ** -np.arange(3, 16),
+                             1 - 10.0 ** -np.arange(3, 16)])
+        for lam in (0.3, 30.0):
+            a = np.array([orc.ncx2_poly_ppf(c, nu, u, lam) for u in us])
+            b = np.array([orc.ncx2_poly_ppf(o, nu, u, lam) for u in us])
+            assert np.max(np.abs(a - b) / (1 + np.abs(b))) < 2e-5
+
+
+def test_ncx2_table_argument_validation(P):
+    L = P.lib()
+    h = C.c_void_p()
+    for nu, K, nk, d in ((0.0, 16, 16, 1), (-1.0, 16, 16, 1), (1.0, 0, 16, 1), (1.0, 31, 16, 1),
+                         (1.0, 16, 1, 1), (1.0, 16, 65, 1), (1.0, 16, 16, 0), (1.0, 16, 16, 4)):
+        assert L.aicdf_ncx2_table_build(nu, K, nk, d, C.byref(h)) == P.ERR_ARG
+    assert L.aicdf_ncx2_table_build(1.0, 16, 16, 1, None) == P.ERR_ARG
+    fake = 1 << 40
+    big = P.Ncx2Table(2.0, 30, 32, 1)  # 32 x 2 x 31 rows: too many for a launch parameter
+    assert L.aicdf_ncx2_table_eval(big.handle, fake, fake, 16, fake, None) == P.ERR_UNSUPPORTED
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    assert L.aicdf_ncx2_table_eval(t.handle, fake + 2, fake, 16, fake, None) == P.ERR_ARG
+    assert L.aicdf_ncx2_table_eval(t.handle, fake, fake, 0, fake, None) == P.OK
+    # CIR with the table: nu must match 4 kappa theta / sigma^2, and only its kinds
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)                      # nu = 2
+    ws = P.mlmc_level_workspace_bytes()
+    call = lambda tab, kind: L.aicdf_cir_level_table(C.byref(prm), tab.handle, 3, kind, 10, 0, 0, 1, fake, fake,
+                                                     ws, fake, None)
+    assert call(t, P.CIR_SURROGATE) == P.ERR_ARG
+    assert call(P.Ncx2Table(1.0, 16, 16, 1), P.CIR_DIFF_TABLE) == P.ERR_DOMAIN
+    assert L.aicdf_cir_level(C.byref(prm), None, 3, P.CIR_TABLE, 10, 0, 0, 1, fake, fake, ws, fake, None) == P.ERR_ARG

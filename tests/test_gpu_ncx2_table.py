@@ -1,0 +1,155 @@
+"""GPU checks of the Section 5.1 tabulated non-central chi-squared inverse.
+
+* Evaluation: the kernel's FP32 C~^{-1}(u; lambda) equals the oracle's FP64
+  evaluation of the same FP32-rounded table to the FP32 arithmetic of the
+  interpolation: |d| <= 1e-5 (h + 2 sqrt(h) (1 + |P~|)), h = lambda + nu.
+* CIR paths: single paths (n_paths = 1) equal a step-by-step restatement with
+  the oracle's functions (exact quantile in FP64; tabulated steps in FP64 from
+  the same FP32 table) to 1e-4 relative after 2^level steps.
+* Variance: with the paper's CIR parameters the exact-minus-table difference
+  has the share of the exact variance that the tables' Table 5 RMSE predicts
+  (Section 5.2; see test_cir_table_variance_drop).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2012_09715_gb300 import build as b
+    b.build()
+    import paper_2012_09715_gb300 as P
+    P.lib()
+    return P
+
+
+def _c32(t):
+    return t.coefficients().astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("nu,deg", [(1.0, 1), (0.8889, 3), (10.0, 3), (100.0, 1)])
+def test_table_eval_parity(P, orc, nu, deg):
+    import torch
+    t = P.Ncx2Table(nu, 16, 16, deg)
+    c = _c32(t)
+    rng = np.random.default_rng(int(nu * 10) + deg)
+    n = 3001
+    u = np.concatenate([orc.uniforms(seed=3, offset=0, n=n - 40), rng.random(20).astype(np.float32),
+                        np.array([0.0, 1.0, 0.5, 2.0 ** -24, 1 - 2.0 ** -24, 0.25, 0.75, 2.0 ** -16,
+                                  np.nextafter(np.float32(0.5), np.float32(1)), 1e-30, 1e-40, 0.5 - 2.0 ** -25,
+                                  1 - 1e-7, 2.0 ** -17, 2.0 ** -15, 0.125, 0.875, 0.999, 0.001, 0.3],
+                                 dtype=np.float32)]).astype(np.float32)
+    lam = np.concatenate([10.0 ** rng.uniform(-3, 3, n - 3), [0.0, 1e-30, 5000.0]]).astype(np.float32)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    t.eval(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), out)
+    z = out.double().cpu().numpy()
+    for i in range(n):
+        ui, li = float(u[i]), float(lam[i])
+        ref = orc.ncx2_poly_ppf(c, nu, ui, li)
+        h = li + nu
+        p = orc.ncx2_poly_P(c, ui, nu / h)
+        tol = 1e-5 * (h + 2 * math.sqrt(h) * (1 + abs(p)))
+        assert abs(z[i] - ref) <= tol, (i, ui, li, z[i], ref)
+
+
+def test_table_eval_invalid_inputs_give_nan(P):
+    import torch
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    u = torch.tensor([-0.1, 1.5, float("nan"), 0.3, 0.3, 0.3], device="cuda")
+    lam = torch.tensor([1.0, 1.0, 1.0, -1.0, float("nan"), float("inf")], device="cuda")
+    out = torch.zeros(6, device="cuda")
+    t.eval(u, lam, out)
+    assert torch.isnan(out).all()
+
+
+CIR_SETS = {
+    "paper": dict(kappa=0.5, theta=1.0, sigma=1.0, X0=1.0, T=1.0),      # nu = 2 (Section 5.2)
+    "config": dict(kappa=0.5, theta=0.04, sigma=0.3, X0=0.04, T=1.0),   # nu = 0.889
+}
+
+
+def _cir_params(P, name):
+    q = CIR_SETS[name]
+    return P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=q["X0"], T=q["T"], mu=0.0, sigma=q["sigma"],
+                        kappa=q["kappa"], theta=q["theta"], discount=1.0), q
+
+
+def _emulate_path(orc, q, c, level, p, seed, tag):
+    """Exact and tabulated CIR path of 2^level steps (Section 5.2 per-step law)."""
+    nu = 4 * q["kappa"] * q["theta"] / q["sigma"] ** 2
+    h = q["T"] / 2 ** level
+    e = math.exp(-q["kappa"] * h)
+    cc = q["sigma"] ** 2 * (-math.expm1(-q["kappa"] * h)) / (4 * q["kappa"])
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    xe = xa = q["X0"]
+    for s in range(2 ** level):
+        w = int(orc.philox4([s // 4, p & 0xFFFFFFFF, p >> 32, tag], key, 32)[s % 4])
+        u = orc.u01(w)
+        lam_e = xe * e / cc
+        xe = cc * (orc.ncx2_ppf(u, nu, lam_e) if u <= 0.5 else orc.ncx2_isf(1.0 - u, nu, lam_e))
+        lam_a = max(xa, 0.0) * e / cc
+        xa = cc * max(orc.ncx2_poly_ppf(c, nu, u, lam_a), 0.0)
+    return xe, xa
+
+
+@pytest.mark.parametrize("name,deg", [("paper", 1), ("paper", 3), ("config", 1)])
+def test_cir_table_paths_match_restatement(P, orc, name, deg):
+    import torch
+    prm, q = _cir_params(P, name)
+    nu = 4 * q["kappa"] * q["theta"] / q["sigma"] ** 2
+    t = P.Ncx2Table(nu, 16, 16, deg)
+    c = _c32(t)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for level in (0, 2, 4):
+        for p in (0, 7, 123456789):
+            xe, xa = _emulate_path(orc, q, c, level, p, seed=5, tag=3)
+            got = {}
+            for kind in (P.CIR_EXACT, P.CIR_TABLE, P.CIR_DIFF_TABLE):
+                P.cir_level_table(prm, t, level, kind, 1, sums, ws, st, path_offset=p, seed=5, tag=3)
+                got[kind] = sums[0].item()
+            assert st.item() == 0
+            assert got[P.CIR_EXACT] == pytest.approx(xe, rel=1e-6, abs=1e-9)
+            assert got[P.CIR_TABLE] == pytest.approx(xa, rel=1e-4, abs=1e-6)
+            assert got[P.CIR_DIFF_TABLE] == pytest.approx(xe - xa, abs=1e-4 * abs(xa) + 1e-6)
+
+
+def test_cir_table_variance_drop(P):
+    """Section 5.2 CIR set (kappa = 1/2, theta = sigma = T = X0 = 1, nu = 2).
+
+    A step error e_n = c (C^{-1} - C~^{-1}) is carried to T with the factor
+    ~e^{-kappa (T - t_n)}, and with c ~ sigma^2 h / 4 and lambda ~ 4 X / (sigma^2 h)
+    the variance of X_T - X~_T is ~E[X] delta_P^2 / Var(X_T), flat in h, where
+    delta_P is the RMSE of P~ (the Table 5 RMSE over 2 sqrt(lambda + nu)).  The
+    Table 5a values give 2^-13..2^-14.5 for the linear table (the text of
+    Section 5.2 reads about 2^-15 off its figure) and Table 5b gives
+    2^-19..2^-23 for the cubic (the text reads 2^-25, below what its own
+    Table 5b implies; the band accepts both)."""
+    import torch
+    prm, q = _cir_params(P, "paper")
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n = 1 << 16
+    r = {}
+    for deg in (1, 3):
+        t = P.Ncx2Table(2.0, 16, 16, deg)
+        for level in (1, 4):
+            v = {}
+            for kind in (P.CIR_EXACT, P.CIR_DIFF_TABLE):
+                P.cir_level_table(prm, t, level, kind, n, sums, ws, st, seed=11, tag=1)
+                s = sums.cpu().numpy()
+                v[kind] = s[1] / n - (s[0] / n) ** 2
+            assert st.item() == 0
+            r[(deg, level)] = math.log2(v[P.CIR_DIFF_TABLE] / v[P.CIR_EXACT])
+    for level in (1, 4):
+        assert -16.5 < r[(1, level)] < -12.5, r
+        assert -26.0 < r[(3, level)] < -18.0, r
+        assert r[(3, level)] < r[(1, level)] - 5.0, r

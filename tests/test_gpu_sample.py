@@ -184,19 +184,26 @@ def test_unaligned_pointers_use_scalar_path(P, tabs, orc):
     _assert_pwl(buf[1:].cpu().numpy().astype(np.float64), ref)
 
 
-def test_sample_to_host_matches_device(P, tabs):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_sample_to_host_matches_device(P, tabs, pinned):
+    """Pinned host memory: direct kernel stores; pageable: staged chunks with
+    overlapped copies (2 MiB staging = two buffers, 8 MiB = four)."""
     import torch
     tl, tc, *_ = tabs
-    staging = torch.empty(2 << 20, dtype=torch.uint8, device="cuda")
-    for table, method, dt, n, off in ((tl, P.PWL, torch.float32, 3 * (1 << 20) + 5, 0),
-                                      (tc, P.PWC, torch.float16, (1 << 21) + 77, 12),
-                                      (None, P.EXACT, torch.float32, 100003, 4)):
-        host = torch.empty(n, dtype=dt).pin_memory()
-        P.sample_to_host(table, method, host, staging, seed=5, offset=off)
-        dev = torch.empty(n, dtype=dt, device="cuda")
-        P.sample(table, method, dev, seed=5, offset=off)
-        torch.cuda.synchronize()
-        assert torch.equal(host, dev.cpu())
+    for sb in (2 << 20, 8 << 20):
+        staging = torch.empty(sb, dtype=torch.uint8, device="cuda")
+        for table, method, dt, n, off in ((tl, P.PWL, torch.float32, 3 * (1 << 20) + 5, 0),
+                                          (tc, P.PWC, torch.float16, (1 << 21) + 77, 12),
+                                          (None, P.EXACT, torch.float32, 100003, 4),
+                                          (tl, P.PWL, torch.float32, 4099, 6)):
+            host = torch.empty(n, dtype=dt)
+            if pinned:
+                host = host.pin_memory()
+            P.sample_to_host(table, method, host, staging, seed=5, offset=off)
+            dev = torch.empty(n, dtype=dt, device="cuda")
+            P.sample(table, method, dev, seed=5, offset=off)
+            torch.cuda.synchronize()
+            assert torch.equal(host, dev.cpu())
 
 
 def test_determinism_and_streams(P, tabs):
