@@ -320,6 +320,72 @@ def cir_table(P, dev, stream, n_eval: int = 1 << 22):
     return res
 
 
+def cir_time_to_rmse(P, dev, stream, eps: float = 1e-3, level: int = 3, deg: int = 1):
+    """Section 5.2 savings on the GPU: E[X_T] of the paper's CIR set (kappa 1/2,
+    theta = sigma = T = X0 = 1, nu = 2; 2^level exact per-step transitions, so no
+    time bias) to RMSE eps, by (a) exact transitions only and (b) the nested
+    estimator E[P~] + E[P^ - P~] with the Section 5.1 table, paths split by the
+    optimal allocation (Section 4.1) from pilot variances and timed pilot costs.
+    Wall times include the pilots."""
+    import math
+    import time as _t
+    import torch
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    table = P.Ncx2Table(2.0, 16, 16, deg)
+
+    def run(kind, n, off, tag):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.cir_level_table(prm, table, level, kind, n, sums, ws, st, path_offset=off, seed=21, tag=tag,
+                          stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v = sums.cpu().numpy().copy()
+        return v, e0.elapsed_time(e1)
+
+    run(P.CIR_EXACT, 1 << 12, 0, 99)  # warm-up
+    run(P.CIR_TABLE, 1 << 12, 0, 99)
+    res = {"eps": eps, "level": level, "degree": deg}
+    # (a) exact only
+    w0 = _t.perf_counter()
+    n0 = 1 << 12  # pilot paths per term
+    pv, pms = run(P.CIR_EXACT, n0, 0, 1)
+    var = pv[1] / n0 - (pv[0] / n0) ** 2
+    n = max(n0, int(math.ceil(var / eps ** 2)))
+    v, ms = run(P.CIR_EXACT, n - n0, n0, 1)
+    tot = pv + v
+    res["exact"] = {"estimate": tot[0] / n, "paths": n, "gpu_ms": pms + ms, "wall_ms": 1e3 * (_t.perf_counter() - w0),
+                    "var": var, "ns_per_path": 1e6 * pms / n0}
+    # (b) nested: table paths + exact-minus-table correction
+    w0 = _t.perf_counter()
+    pa, ta = run(P.CIR_TABLE, n0, 0, 2)
+    pc, tc = run(P.CIR_DIFF_TABLE, n0, 0, 3)
+    va = pa[1] / n0 - (pa[0] / n0) ** 2
+    vc = max(pc[1] / n0 - (pc[0] / n0) ** 2, 1e-300)
+    ca, cc = ta / n0, tc / n0
+    k = (math.sqrt(va * ca) + math.sqrt(vc * cc)) / eps ** 2
+    na = max(n0, int(math.ceil(k * math.sqrt(va / ca))))
+    nc = max(n0, int(math.ceil(k * math.sqrt(vc / cc))))
+    a2, ma = run(P.CIR_TABLE, na - n0, n0, 2) if na > n0 else (pa * 0, 0.0)
+    c2, mc = run(P.CIR_DIFF_TABLE, nc - n0, n0, 3) if nc > n0 else (pc * 0, 0.0)
+    sa, sc = pa + a2, pc + c2
+    est = sa[0] / na + sc[0] / nc
+    rmse = math.sqrt(va / na + vc / nc)
+    res["nested"] = {"estimate": est, "rmse_est": rmse, "paths_table": na, "paths_correction": nc,
+                     "gpu_ms": ta + tc + ma + mc, "wall_ms": 1e3 * (_t.perf_counter() - w0),
+                     "log2_var_ratio": math.log2(vc / va), "cost_ratio_exact_over_table": cc / ca}
+    res["speedup_gpu"] = res["exact"]["gpu_ms"] / res["nested"]["gpu_ms"]
+    res["speedup_wall"] = res["exact"]["wall_ms"] / res["nested"]["wall_ms"]
+    # E[X_T] = theta + (X0 - theta) e^{-kappa T} = 1 for this set
+    res["exact_expectation"] = 1.0
+    res["root_finder_status"] = int(st.item())
+    return res
+
+
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
     wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
@@ -335,9 +401,12 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     L = nested.L
     plain = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=L, seed=3)
     for name, r in (("nested", nested), ("regular", regular), ("plain_exact", plain)):
+        # fine path-steps per term slot (slot 0: APPROX2 / EXACT2 / PLAIN, slot 1: CORR4)
+        steps = [sum(r.paths[l][k] * ((1 << l) + 1 if l > 0 else 1) for l in range(r.L + 1)) for k in range(2)]
         res[name] = {"estimate": r.estimate, "rmse_est": (r.variance + r.bias ** 2) ** 0.5,
                      "L": r.L, "wall_ms": r.wall_ms, "gpu_ms": r.gpu_ms, "launches": r.launches,
-                     "converged": bool(r.converged)}
+                     "converged": bool(r.converged), "path_steps": steps,
+                     "paths": [[int(r.paths[l][0]), int(r.paths[l][1])] for l in range(r.L + 1)]}
     res["eps"] = eps
     # calibrated device ns per fine path-step of each estimator kind (level 5, 2^17 paths)
     res["step_ns"] = {"approx2": nested.cost_ns[0][0] / 2, "corr4": nested.cost_ns[0][1] / 2,
@@ -382,6 +451,24 @@ def run_reference(args):
     return 0
 
 
+def profile_mlmc_kinds():
+    """One level launch per estimator kind (GBM call, Euler-Maruyama, level 6,
+    2^20 paths): APPROX2, EXACT2, CORR4 in that order."""
+    import torch
+    import paper_2012_09715_gb300 as P
+    from paper_2012_09715_gb300 import build as B
+    B.build()
+    P.lib()
+    tl = P.table_build(P.PWL, 15)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    prm = P.sde_params()
+    for kind in (P.KIND_APPROX2, P.KIND_EXACT2, P.KIND_CORR4):
+        P.mlmc_level(prm, tl, 6, kind, 1 << 20, sums, ws, seed=1, tag=3)
+    torch.cuda.synchronize()
+    print(sums.cpu().numpy())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +478,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n-log2", type=int, default=28, help="workload size (profiling runs only)")
+    ap.add_argument("--profile-case", choices=["mlmc_kinds"], default=None,
+                    help="run one fixed launch sequence for an ncu capture and exit (no timing line)")
     args = ap.parse_args()
+    if args.profile_case == "mlmc_kinds":
+        return profile_mlmc_kinds()
     global N_SAMPLES
     N_SAMPLES = 1 << args.n_log2
     if args.warmup < 3:
@@ -494,7 +585,9 @@ def main():
                          ("sampler_sweep", lambda: sampler_sweep(P, tl, dev, stream)),
                          ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
                          ("cir_surrogate", lambda: cir_surrogate(P, dev, stream)),
-                         ("cir_table", lambda: cir_table(P, dev, stream))):
+                         ("cir_table", lambda: cir_table(P, dev, stream)),
+                         ("cir_time_to_rmse", lambda: cir_time_to_rmse(P, dev, stream)),
+                         ("cir_time_to_rmse_cubic", lambda: cir_time_to_rmse(P, dev, stream, deg=3))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # reported, not hidden: the headline line still prints

@@ -171,14 +171,23 @@ static aicdf_status cir_setup(const aicdf_sde_params *prm, int level, uint64_t n
   return AICDF_OK;
 }
 
+// Block size: 256 threads when there are paths to fill every SM with full
+// blocks; fewer paths are spread over all SMs in smaller blocks (whole warps),
+// since an exact step is FP64 work whose per-SM rate bounds a small term.
 template <class Fn, class TabT>
 static aicdf_status cir_launch(Fn k, const CirArgs &a, const TabT &tab, uint64_t n_paths, void *workspace_dev,
                                double *sums_dev, int *status_dev, cudaStream_t st) {
-  const uint64_t want = (n_paths + kCirThreads - 1) / kCirThreads;
+  const uint64_t sms = (uint64_t)sm_count();
+  int threads = kCirThreads;
+  if (n_paths < sms * kCirThreads) {
+    const uint64_t per_sm = (n_paths + sms - 1) / sms;
+    threads = (int)std::min<uint64_t>(kCirThreads, std::max<uint64_t>(32, (per_sm + 31) / 32 * 32));
+  }
+  const uint64_t want = (n_paths + threads - 1) / threads;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
-      want, std::min<uint64_t>((uint64_t)sm_count() * resident_blocks((const void *)k, kCirThreads), 4096)));
+      want, std::min<uint64_t>(sms * resident_blocks((const void *)k, threads), 4096)));
   double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
-  k<<<grid, kCirThreads, 0, st>>>(a, tab, parts, status_dev);
+  k<<<grid, threads, 0, st>>>(a, tab, parts, status_dev);
   launch_reduce_partials(parts, grid, (double)n_paths, sums_dev, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -36,8 +36,11 @@ struct Term {
 };
 
 constexpr size_t kSumsBytes = 256 + 4096;
+// Calibration launch: level 5 with 2^21 paths (33 fine steps each) fills
+// every SM for several waves, so the measured time is the throughput cost
+// per path-step rather than launch latency and the tail of a partial wave.
 constexpr int kCalLevel = 5;
-constexpr uint64_t kCalPaths = 1u << 17;
+constexpr uint64_t kCalPaths = 1u << 21;
 
 std::mutex g_cal_mu;
 std::map<std::tuple<int, int, int, int, int>, double> g_step_ns;  // (dev, model, scheme, approx, kind)

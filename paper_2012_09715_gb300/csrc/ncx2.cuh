@@ -82,30 +82,30 @@ AICDF_HD void gamma_pq(double s, double y, double *P, double *Q, double *g, int 
   *P = 1.0 - *Q;
 }
 
-// Lower CDF (upper = false) or upper tail (upper = true) of chi'^2_nu(lambda)
-// at x, and the density.
-AICDF_HD void ncx2_tail_pdf(double x, double nu, double lam, bool upper, double *T, double *f, int *status) {
-  if (x <= 0.0) {
-    *T = upper ? 1.0 : 0.0;
-    *f = 0.0;
-    return;
-  }
-  const double y = 0.5 * x, a = 0.5 * nu, m = 0.5 * lam;
-  // Poisson range [jlo, jhi] holding all but ~1e-20 of the mass, walked from the mode
-  int jlo = 0, jhi = 0;
-  double plo = 1.0, phi = 1.0;
+// Poisson range [jlo, jhi] of the mixture weights Pois(j; lambda/2) holding
+// all but ~1e-20 of the mass, walked from the mode, with the weights at both
+// ends.  It depends on lambda only, so a quantile computes it once.
+struct Ncx2Range {
+  int jlo, jhi;
+  double plo, phi;
+};
+
+AICDF_HD Ncx2Range ncx2_range(double lam, int *status) {
+  Ncx2Range r{0, 0, 1.0, 1.0};
+  const double m = 0.5 * lam;
   if (m > 0.0) {
     const int j0 = (int)floor(m);
     const double p0 = exp(-m + j0 * log(m) - lgamma_pos(j0 + 1.0));
+    const double rm = 1.0 / m;
     double p = p0;
     int j = j0, it = 0;
     for (; j > 0 && p > 1e-20 && it < 100000; ++it) {
-      p *= (double)j / m;
+      p *= (double)j * rm;
       --j;
     }
     if (it == 100000) *status |= kNcx2NoConverge;
-    jlo = j;
-    plo = p;
+    r.jlo = j;
+    r.plo = p;
     p = p0;
     j = j0;
     for (it = 0; p > 1e-20 && it < 100000; ++it) {
@@ -113,35 +113,52 @@ AICDF_HD void ncx2_tail_pdf(double x, double nu, double lam, bool upper, double 
       ++j;
     }
     if (it == 100000) *status |= kNcx2NoConverge;
-    jhi = j;
-    phi = p;
+    r.jhi = j;
+    r.phi = p;
   }
+  return r;
+}
+
+// Lower CDF (upper = false) or upper tail (upper = true) of chi'^2_nu(lambda)
+// at x, and the density, over the Poisson range rg of lambda.
+AICDF_HD void ncx2_tail_pdf(double x, double nu, double lam, const Ncx2Range &rg, bool upper, double *T,
+                            double *f, int *status) {
+  if (x <= 0.0) {
+    *T = upper ? 1.0 : 0.0;
+    *f = 0.0;
+    return;
+  }
+  const double y = 0.5 * x, a = 0.5 * nu, m = 0.5 * lam;
+  const double ry = 1.0 / y, h2y = 0.5 * ry;  // loop-invariant reciprocals
+  const int jlo = rg.jlo, jhi = rg.jhi;
+  const double plo = rg.plo, phi = rg.phi;
   double acc = 0.0, dens = 0.0;
   if (!upper) {
+    const double rm = 1.0 / m;  // only used when jhi > jlo, i.e. m > 0
     double P, Q, g;
     gamma_pq(a + jhi, y, &P, &Q, &g, status);
     double p = phi;
     acc = p * P;
-    dens = p * g * (a + jhi) / (2.0 * y);
+    dens = p * g * (a + jhi) * h2y;
     for (int j = jhi; j > jlo; --j) {
-      g = g * (a + j) / y;  // g_{j-1}
-      P += g;               // P(s_{j-1})
-      p *= (double)j / m;   // p_{j-1}
+      g = g * (a + j) * ry;  // g_{j-1}
+      P += g;                // P(s_{j-1})
+      p *= (double)j * rm;   // p_{j-1}
       acc += p * P;
-      dens += p * g * (a + j - 1) / (2.0 * y);
+      dens += p * g * (a + j - 1) * h2y;
     }
   } else {
     double P, Q, g;
     gamma_pq(a + jlo, y, &P, &Q, &g, status);
     double p = plo;
     acc = p * Q;
-    dens = p * g * (a + jlo) / (2.0 * y);
+    dens = p * g * (a + jlo) * h2y;
     for (int j = jlo; j < jhi; ++j) {
       Q += g;                    // Q(s_{j+1})
       g = g * y / (a + j + 1);   // g_{j+1}
       p *= m / (double)(j + 1);  // p_{j+1}
       acc += p * Q;
-      dens += p * g * (a + j + 1) / (2.0 * y);
+      dens += p * g * (a + j + 1) * h2y;
     }
   }
   *T = fmin(acc, 1.0);
@@ -171,13 +188,14 @@ AICDF_HD double ncx2_sankaran(double z, double nu, double lam) {
 AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, double lam, int *status) {
   double T, f;
   const double x0 = ncx2_sankaran(z, nu, lam);
+  const Ncx2Range rg = ncx2_range(lam, status);
   int it = 0;
   if (!upper) {
     const double lt = log(target);
     double t = log(x0), lo = -1e300, hi = 1e300;  // bracket in t = ln x
     for (; it < 100; ++it) {
       const double x = exp(t);
-      ncx2_tail_pdf(x, nu, lam, false, &T, &f, status);
+      ncx2_tail_pdf(x, nu, lam, rg, false, &T, &f, status);
       double tn;
       if (!(T > 0.0)) {  // C underflowed: x far too small
         lo = t;
@@ -200,7 +218,7 @@ AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, do
   double x = x0;
   double lo = 0.0, hi = -1.0;  // hi < 0: no upper bound yet
   for (; it < 100; ++it) {
-    ncx2_tail_pdf(x, nu, lam, true, &T, &f, status);
+    ncx2_tail_pdf(x, nu, lam, rg, true, &T, &f, status);
     const double r = target - T;  // = C(x) - u, > 0 when x is too large
     if (r > 0.0) hi = x;
     else lo = x;

@@ -1,7 +1,8 @@
 // Test helper: raw Philox4x32-10 words from cuRAND's documented device API,
 // an implementation independent of this repository, for pinning the oracle.
-// curand_init(seed, subsequence, offset) keys the generator with the 64-bit
-// seed and starts the 128-bit counter at (offset / 4) + subsequence * 2^64;
+// curand_init(seed, subsequence, 0) keys the generator with the 64-bit seed
+// and starts the 128-bit counter at subsequence * 2^64; skipahead(4 a) moves
+// it on by a (in steps below 2^60, since the offset counts 32-bit outputs);
 // curand4() returns the four words of the current counter.
 #include <cstdint>
 #include <curand_kernel.h>
@@ -10,7 +11,13 @@ __global__ void k_words(uint64_t seed, const uint64_t *lo64, const uint64_t *hi6
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   curandStatePhilox4_32_10_t st;
-  curand_init(seed, hi64[i], 4 * lo64[i], &st);  // counter = lo64 + hi64 * 2^64
+  curand_init(seed, hi64[i], 0ull, &st);  // counter = hi64 * 2^64
+  unsigned long long left = lo64[i];
+  while (left > 0) {  // at most 16 steps
+    const unsigned long long a = left < (1ull << 60) ? left : (1ull << 60);
+    skipahead(4ull * a, &st);
+    left -= a;
+  }
   out[i] = curand4(&st);
 }
 

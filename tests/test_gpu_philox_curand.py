@@ -28,8 +28,8 @@ def curand_words():
     L.curand_philox_words.argtypes = [C.c_uint64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 
     def words(seed, lo64, hi64):
-        lo = np.ascontiguousarray(lo64, dtype=np.uint64)
-        hi = np.ascontiguousarray(hi64, dtype=np.uint64)
+        lo = np.array([int(x) for x in lo64], dtype=np.uint64)
+        hi = np.array([int(x) for x in hi64], dtype=np.uint64)
         out = np.zeros((lo.size, 4), dtype=np.uint32)
         assert L.curand_philox_words(seed, lo.ctypes.data, hi.ctypes.data, lo.size, out.ctypes.data) == 0
         return out
@@ -39,9 +39,10 @@ def curand_words():
 def test_standalone_stream_counters(curand_words, orc):
     seeds = [0, 7, 0x1234_5678_9ABC, 2 ** 64 - 1]
     rng = np.random.default_rng(0)
-    js = np.concatenate([np.arange(8), rng.integers(0, 2 ** 40, 40), [2 ** 32 - 1, 2 ** 32, 2 ** 63 + 5]])
+    js = [int(x) for x in range(8)] + [int(x) for x in rng.integers(0, 2 ** 40, 40)]
+    js += [2 ** 32 - 1, 2 ** 32, 2 ** 62 + 3, 2 ** 63 + 5, 2 ** 64 - 1]
     for seed in seeds:
-        got = curand_words(seed, js, np.zeros_like(js))
+        got = curand_words(seed, js, [0] * len(js))
         key = [seed & 0xFFFFFFFF, seed >> 32]
         for j, w in zip(js, got):
             j = int(j)
