@@ -183,9 +183,12 @@ typedef struct {
  * level estimator `kind` at `level` (2^level fine steps of size T/2^level;
  * the coarse path takes 2^(level-1) steps with the pairwise sums of the fine
  * Brownian increments, Section 4.1).  Fine step s of path p draws its uniform
- * from Philox4x32-10 with counter (s/4, p mod 2^32, p>>32, tag), word s%4,
- * key from seed; the exact and approximate variates of a step use that same
- * uniform (Section 4.1).  approx: a PWL (K <= 15) or PWC (n <= 1024) table.
+ * from Philox4x32-10 keyed by seed: for level >= 2 with counter
+ * (s/4, p mod 2^32, p>>32, tag), word s%4; for levels 0 and 1, where a path
+ * has fewer than four steps, G = 4/2^level paths share one call: counter
+ * (0, q mod 2^32, q>>32, tag) with q = p/G, word (p mod G) 2^level + s.  The
+ * exact and approximate variates of a step use that same uniform (Section
+ * 4.1).  approx: a PWL or PWP (K <= 15) or PWC (n <= 1024) table.
  * Models: GBM dX = mu X dt + sigma X dW; CIR dX = kappa(theta-X)dt +
  * sigma sqrt(X) dW with sqrt(|X|) (truncated scheme).  Schemes: Euler-
  * Maruyama (Section 4) or Milstein.
@@ -251,10 +254,12 @@ typedef struct {
   uint64_t path_offset;
 } aicdf_batch_term;
 
-/* Launch schedule: terms are cut into tiles of tile_paths paths (a multiple
- * of 32, >= block_threads); each CTA of block_threads threads (64/128/256)
- * takes tiles from a shared counter, largest first; blocks_per_sm = 0 uses
- * the occupancy maximum.  var16 = 1 rounds every approximate variate to FP16
+/* Launch schedule: terms are cut into tiles of equal work: tile_paths (a
+ * multiple of 32, >= block_threads) paths of a level-0 two-way term, and
+ * proportionally fewer paths (by 2^level + 4 path-steps, x1.8 for the
+ * four-way kind; at least block_threads) for costlier terms.  Each CTA of
+ * block_threads threads (64/128/256) takes tiles from a shared counter,
+ * largest first; blocks_per_sm = 0 uses the occupancy maximum.  var16 = 1 rounds every approximate variate to FP16
  * before it drives a path (FP16 approximate variates); exact variates stay FP32. */
 typedef struct {
   int tile_paths;

@@ -490,10 +490,20 @@ static double path_value(const or_sde_params *prm, const float *alpha, const flo
   double xf_e = prm->X0, xc_e = prm->X0, xf_a = prm->X0, xc_a = prm->X0;
   double zc_e = 0.0, zc_a = 0.0; /* running pair sums of fine variates */
   for (int64_t s = 0; s < nf; ++s) {
-    uint64_t ctr[4] = {(uint64_t)(s / 4), p & 0xffffffffull, p >> 32, tag};
+    /* levels 0 and 1 use fewer than four words per path: G = 4 / 2^level
+     * paths share the call of group q = p / G, path p taking words
+     * (p mod G) 2^level + s; from level 2 on, path p owns its calls */
+    uint64_t q = p, c = (uint64_t)(s / 4), word = (uint64_t)(s % 4);
+    if (level < 2) {
+      const uint64_t G = 4u >> level;
+      q = p / G;
+      c = 0;
+      word = (p % G) * (uint64_t)nf + (uint64_t)s;
+    }
+    uint64_t ctr[4] = {c, q & 0xffffffffull, q >> 32, tag};
     uint64_t out[4];
     or_philox4(32, 10, ctr, key, out);
-    float u = (float)or_u01((uint32_t)out[s % 4]);
+    float u = (float)or_u01((uint32_t)out[word]);
     double ze = or_phiinv((double)u);
     double za = approx_variate(prm, alpha, beta, K, u);
     xf_e = sde_step(prm, xf_e, dtf, sdt * ze);

@@ -85,8 +85,10 @@ typedef struct {
 
 /* Sums over paths p = path_offset .. path_offset+n_paths-1 of Y and Y^2
  * for the level estimator of the given kind.  sums = {sum Y, sum Y^2, n}.
- * Uniform for fine step s of path p: Philox4x32-10 with
- * ctr = (s/4, p mod 2^32, p>>32, tag), key = (seed mod 2^32, seed>>32), word s%4.
+ * Uniform for fine step s of path p: Philox4x32-10 with key = (seed mod 2^32,
+ * seed>>32); for level >= 2, ctr = (s/4, p mod 2^32, p>>32, tag) and word s%4;
+ * for levels 0 and 1 (2^level < 4 fine steps) G = 4/2^level paths share one
+ * call: ctr = (0, q mod 2^32, q>>32, tag) with q = p/G, word (p mod G) 2^level + s.
  * approx tables: PWL (alpha, beta, K), PWC (alpha = table, K = n_table) or
  * PWP (alpha = (K+1) x 4 polynomial coefficients, K). */
 void or_mlmc_level(const or_sde_params *prm, const float *alpha, const float *beta, int K,

@@ -54,26 +54,34 @@ __global__ void __launch_bounds__(kLevelThreads)
   const PathConsts pc = make_path_consts(a.ps);
   const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  float f1 = 0.f, f2 = 0.f;
+  const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
   double d1 = 0.0, d2 = 0.0;
-  int chunk = 0;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n_paths;
-       base += stride) {
-    const uint64_t i = base + lane;
-    const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
-    if (i < a.n_paths) {
-      f1 += y;
-      f2 = fmaf(y, y, f2);
+  if (a.ps.level < 2) {  // warp-uniform: groups of paths share a Philox call
+    sum_groups<kFlushEvery>(a.path_offset, a.n_paths, a.ps.level, first, stride,
+                            [&](uint64_t q, float (&y)[4]) {
+                              group_y_level<NE, NA, AP, MODEL, false>(a.ps, pc, ap, a.keys, q, y);
+                            },
+                            d1, d2);
+  } else {
+    float f1 = 0.f, f2 = 0.f;
+    int chunk = 0;
+    for (uint64_t base = first; base < a.n_paths; base += stride) {
+      const uint64_t i = base + lane;
+      const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
+      if (i < a.n_paths) {
+        f1 += y;
+        f2 = fmaf(y, y, f2);
+      }
+      if (++chunk == kFlushEvery) {
+        d1 += (double)f1;
+        d2 += (double)f2;
+        f1 = f2 = 0.f;
+        chunk = 0;
+      }
     }
-    if (++chunk == kFlushEvery) {
-      d1 += (double)f1;
-      d2 += (double)f2;
-      f1 = f2 = 0.f;
-      chunk = 0;
-    }
+    d1 += (double)f1;
+    d2 += (double)f2;
   }
-  d1 += (double)f1;
-  d2 += (double)f2;
   const double2 t = block_reduce2(d1, d2, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
@@ -254,25 +262,31 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
     const BatchItem item = a.items[it];
     const PathSpec ps = a.specs[item.term];
     const PathConsts pc = make_path_consts(ps);
-    float f1 = 0.f, f2 = 0.f;
     double d1 = 0.0, d2 = 0.0;
-    int chunk = 0;
-    for (uint32_t base = threadIdx.x & ~31u; base < item.count; base += blockDim.x) {
-      const uint32_t i = base + lane;
-      const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
-      if (i < item.count) {
-        f1 += y;
-        f2 = fmaf(y, y, f2);
+    if (ps.level < 2) {  // block-uniform: groups of paths share a Philox call
+      sum_groups<kFlushEvery>(item.begin, item.count, ps.level, threadIdx.x & ~31u, blockDim.x,
+                              [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); },
+                              d1, d2);
+    } else {
+      float f1 = 0.f, f2 = 0.f;
+      int chunk = 0;
+      for (uint32_t base = threadIdx.x & ~31u; base < item.count; base += blockDim.x) {
+        const uint32_t i = base + lane;
+        const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
+        if (i < item.count) {
+          f1 += y;
+          f2 = fmaf(y, y, f2);
+        }
+        if (++chunk == kFlushEvery) {
+          d1 += (double)f1;
+          d2 += (double)f2;
+          f1 = f2 = 0.f;
+          chunk = 0;
+        }
       }
-      if (++chunk == kFlushEvery) {
-        d1 += (double)f1;
-        d2 += (double)f2;
-        f1 = f2 = 0.f;
-        chunk = 0;
-      }
+      d1 += (double)f1;
+      d2 += (double)f2;
     }
-    d1 += (double)f1;
-    d2 += (double)f2;
     const double2 t = block_reduce2(d1, d2, s_red);
     if (threadIdx.x == 0) a.partials[item.slot] = t;
   }
@@ -360,6 +374,15 @@ static aicdf_status check_schedule(const aicdf_schedule *s) {
   return AICDF_OK;
 }
 
+// Relative work of one path: 2^level fine steps (plus the coarse ones, about
+// one more step in all), a fixed per-path part (one Philox call at the lowest
+// levels, the payoff, the accumulation) worth about four steps, and the
+// four-way kind's two extra states and exact variate.
+double path_work(int level, int kind) {
+  const double steps = (double)(1u << level) + 4.0;
+  return kind == AICDF_KIND_CORR4 ? 1.8 * steps : steps;
+}
+
 static Plan *get_plan(aicdf_batch_s *b, const aicdf_schedule &s) {
   for (Plan *p : b->plans)
     if (same_sched(p->sched, s)) return p;
@@ -374,18 +397,24 @@ static Plan *get_plan(aicdf_batch_s *b, const aicdf_schedule &s) {
   std::vector<Tile> tiles;
   p->slot_begin.assign(nt + 1, 0);
   uint32_t slot = 0;
+  const double w0 = path_work(0, AICDF_KIND_APPROX2);
   for (int t = 0; t < nt; ++t) {
     p->slot_begin[t] = (int)slot;
     const aicdf_batch_term &tm = b->terms[t];
-    const double step_cost = (double)(1u << tm.level) * (tm.kind == AICDF_KIND_CORR4 ? 2.0 : 1.0);
-    for (uint64_t off = 0; off < tm.n_paths; off += (uint64_t)s.tile_paths) {
+    // equal work per tile: tile_paths paths of the cheapest term, proportionally
+    // fewer (a multiple of 32, at least one warp per thread) for costlier ones
+    const double w = path_work(tm.level, tm.kind);
+    uint64_t tp = (uint64_t)((double)s.tile_paths * w0 / w) & ~(uint64_t)31;
+    tp = std::max<uint64_t>(tp, (uint64_t)s.block_threads);
+    tp = std::min<uint64_t>(tp, (uint64_t)s.tile_paths);
+    for (uint64_t off = 0; off < tm.n_paths; off += tp) {
       BatchItem it;
       it.term = (uint32_t)t;
       it.slot = slot++;
       it.begin = tm.path_offset + off;
-      it.count = (uint32_t)std::min<uint64_t>((uint64_t)s.tile_paths, tm.n_paths - off);
+      it.count = (uint32_t)std::min<uint64_t>(tp, tm.n_paths - off);
       it.pad = 0;
-      tiles.push_back({step_cost * (double)it.count, it});
+      tiles.push_back({w * (double)it.count, it});
     }
   }
   p->slot_begin[nt] = (int)slot;
@@ -600,11 +629,14 @@ aicdf_status batch_run_once(const aicdf_sde_params *sets, int n_sets, const aicd
   aicdf_batch b = nullptr;
   aicdf_status s = aicdf_batch_create(sets, n_sets, terms, n_terms, approx, seed, &b);
   if (s != AICDF_OK) return s;
-  uint64_t total = 0;
-  for (int t = 0; t < n_terms; ++t) total += terms[t].n_paths;
-  uint64_t tile = std::max<uint64_t>(4096, ((total / 65536) + 255) & ~(uint64_t)255);
-  tile = std::min<uint64_t>(tile, 1u << 24);
-  const aicdf_schedule sc = {(int)tile, 256, 0, 0};
+  // about 16 tiles per resident block (balance) and at least 64 level-0 paths
+  // per thread in a tile (the per-tile reduction stays small)
+  double work = 0.0;
+  for (int t = 0; t < n_terms; ++t) work += (double)terms[t].n_paths * path_work(terms[t].level, terms[t].kind);
+  const double blocks = (double)sm_count() * 4.0;
+  double tile = work / (blocks * 16.0) / path_work(0, AICDF_KIND_APPROX2);
+  tile = std::min(std::max(tile, 16384.0), (double)(1u << 24));
+  const aicdf_schedule sc = {(int)tile & ~255, 256, 0, 0};
   Plan *p = get_plan(b, sc);
   if (!p) s = AICDF_ERR_NOMEM;
   else if (p->bytes > ws_bytes) s = AICDF_ERR_ARG;

@@ -99,21 +99,25 @@ struct PathConsts {
   float kdt, theta, sig_sdt, mq;
 };
 
+// (all products and differences rounded separately, _rn intrinsics: the
+// constants must not depend on how a kernel's compilation contracts them)
 __device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   PathConsts p;
   const float dt = a.dt, sdt = sqrtf(dt);
   const bool mil = a.scheme == AICDF_SCHEME_MILSTEIN;
-  const float hs2 = 0.5f * a.sigma * a.sigma * dt;
-  p.g0 = a.mu * dt - (mil ? hs2 : 0.f);
-  p.g1 = a.sigma * sdt;
+  const float s2 = __fmul_rn(a.sigma, a.sigma);
+  const float hs2 = __fmul_rn(__fmul_rn(0.5f, s2), dt);
+  const float mdt = __fmul_rn(a.mu, dt);
+  p.g0 = __fsub_rn(mdt, mil ? hs2 : 0.f);
+  p.g1 = __fmul_rn(a.sigma, sdt);
   p.g2 = mil ? hs2 : 0.f;
-  p.c0 = 2.0f * a.mu * dt - (mil ? 2.0f * hs2 : 0.f);
-  p.c1 = a.sigma * sdt;
+  p.c0 = __fsub_rn(__fmul_rn(2.0f, mdt), mil ? __fmul_rn(2.0f, hs2) : 0.f);
+  p.c1 = p.g1;
   p.c2 = mil ? hs2 : 0.f;
-  p.kdt = a.kappa * dt;
+  p.kdt = __fmul_rn(a.kappa, dt);
   p.theta = a.theta;
-  p.sig_sdt = a.sigma * sdt;
-  p.mq = mil ? 0.25f * a.sigma * a.sigma * dt : 0.f;
+  p.sig_sdt = p.g1;
+  p.mq = mil ? __fmul_rn(__fmul_rn(0.25f, s2), dt) : 0.f;
   return p;
 }
 
@@ -133,19 +137,40 @@ __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts 
   return x + inc;
 }
 
+// Payoffs and the differences of Y use the _rn intrinsics, which the compiler
+// never contracts into FMAs, so that Y of a path is the same bits in every
+// kernel that inlines this code (the four-way Y is a small difference of
+// nearly equal payoffs, where one contraction changes it visibly).
 __device__ __forceinline__ float payoff(const PathSpec &a, float x) {
-  return a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf(x - a.K, 0.0f) : a.discount * x;
+  return a.payoff == AICDF_PAYOFF_CALL ? __fmul_rn(a.discount, fmaxf(__fsub_rn(x, a.K), 0.0f))
+                                       : __fmul_rn(a.discount, x);
 }
 
-// Y of one path.  All 32 lanes of a warp must call it together (the PWL
-// approximation shuffles across the warp).  V16: the approximate variate is
-// rounded to FP16 before use (FP16 approximate variates).
+// Y of a path from its final fine / coarse states (exact e, approximate a).
+template <bool NE, bool NA>
+__device__ __forceinline__ float path_result(const PathSpec &a, bool coarse, float xfe, float xce, float xfa,
+                                             float xca) {
+  const float pfe = NE ? payoff(a, xfe) : 0.f, pfa = NA ? payoff(a, xfa) : 0.f;
+  const float pce = (NE && coarse) ? payoff(a, xce) : 0.f;
+  const float pca = (NA && coarse) ? payoff(a, xca) : 0.f;
+  switch (a.kind) {
+    case AICDF_KIND_APPROX2: return __fsub_rn(pfa, pca);
+    case AICDF_KIND_CORR4: return __fsub_rn(__fsub_rn(pfe, pfa), __fsub_rn(pce, pca));
+    case AICDF_KIND_EXACT2: return __fsub_rn(pfe, pce);
+    case AICDF_KIND_PLAIN: return pfe;
+    default: return pfa;
+  }
+}
+
+// Y of one path at level >= 2 (path p owns the Philox calls (s/4, p, tag)).
+// All 32 lanes of a warp must call it together (the PWL approximation
+// shuffles across the warp).  V16: the approximate variate is rounded to FP16
+// before use (FP16 approximate variates).
 template <bool NE, bool NA, int AP, int MODEL, bool V16 = false>
 __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
                                         const ApproxTable<AP> &ap, const PhiloxKeys &keys,
                                         uint64_t p) {
   const int nfine = 1 << a.level;
-  const bool coarse = a.level > 0;
   float xfe = a.X0, xce = a.X0, xfa = a.X0, xca = a.X0;
   float se = 0.f, sa = 0.f;  // pair sums of fine variates
   const uint32_t plo = (uint32_t)p, phi = (uint32_t)(p >> 32);
@@ -154,38 +179,72 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      if (t < nfine) {  // only levels 0 and 1 use part of a Philox block
-        const float u = u01(w[t]);
-        if (NE) {
-          const float ze = phiinv_f32(u);
-          xfe = step_fine<MODEL>(xfe, ze, pc);
-          se += ze;
-        }
-        if (NA) {
-          float za = ap(w[t], u);
-          if (V16) za = __half2float(__float2half_rn(za));
-          xfa = step_fine<MODEL>(xfa, za, pc);
-          sa += za;
-        }
-        if ((t & 1) && coarse) {
-          if (NE) xce = step_coarse<MODEL>(xce, se, pc);
-          if (NA) xca = step_coarse<MODEL>(xca, sa, pc);
-          se = 0.f;
-          sa = 0.f;
-        }
+      const float u = u01(w[t]);
+      if (NE) {
+        const float ze = phiinv_f32(u);
+        xfe = step_fine<MODEL>(xfe, ze, pc);
+        se += ze;
+      }
+      if (NA) {
+        float za = ap(w[t], u);
+        if (V16) za = __half2float(__float2half_rn(za));
+        xfa = step_fine<MODEL>(xfa, za, pc);
+        sa += za;
+      }
+      if (t & 1) {
+        if (NE) xce = step_coarse<MODEL>(xce, se, pc);
+        if (NA) xca = step_coarse<MODEL>(xca, sa, pc);
+        se = 0.f;
+        sa = 0.f;
       }
     }
   }
-  const float pfe = NE ? payoff(a, xfe) : 0.f, pfa = NA ? payoff(a, xfa) : 0.f;
-  const float pce = (NE && coarse) ? payoff(a, xce) : 0.f;
-  const float pca = (NA && coarse) ? payoff(a, xca) : 0.f;
-  switch (a.kind) {
-    case AICDF_KIND_APPROX2: return pfa - pca;
-    case AICDF_KIND_CORR4: return (pfe - pfa) - (pce - pca);
-    case AICDF_KIND_EXACT2: return pfe - pce;
-    case AICDF_KIND_PLAIN: return pfe;
-    default: return pfa;
+  return path_result<NE, NA>(a, true, xfe, xce, xfa, xca);
+}
+
+// Levels 0 and 1 have 1 or 2 fine steps per path, so one Philox call serves
+// G = 4 >> LEVEL paths: group q (paths q G .. q G + G - 1) uses the call
+// (0, q, tag), path q G + g taking words g 2^LEVEL .. g 2^LEVEL + 2^LEVEL - 1.
+// y[g] = Y of path q G + g.  All 32 lanes must call it together.
+template <bool NE, bool NA, int AP, int MODEL, bool V16, int LEVEL>
+__device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                        const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  constexpr int NF = 1 << LEVEL, G = 4 >> LEVEL;
+  const uint4 r = philox(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), a.tag), keys);
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    float xfe = a.X0, xce = a.X0, xfa = a.X0, xca = a.X0;
+    float se = 0.f, sa = 0.f;
+#pragma unroll
+    for (int s = 0; s < NF; ++s) {
+      const uint32_t x = w[g * NF + s];
+      const float u = u01(x);
+      if (NE) {
+        const float ze = phiinv_f32(u);
+        xfe = step_fine<MODEL>(xfe, ze, pc);
+        se += ze;
+      }
+      if (NA) {
+        float za = ap(x, u);
+        if (V16) za = __half2float(__float2half_rn(za));
+        xfa = step_fine<MODEL>(xfa, za, pc);
+        sa += za;
+      }
+    }
+    if (LEVEL == 1) {
+      if (NE) xce = step_coarse<MODEL>(xce, se, pc);
+      if (NA) xca = step_coarse<MODEL>(xca, sa, pc);
+    }
+    y[g] = path_result<NE, NA>(a, LEVEL == 1, xfe, xce, xfa, xca);
   }
+}
+
+template <bool NE, bool NA, int AP, int MODEL, bool V16>
+__device__ __forceinline__ void group_y_level(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                              const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  if (a.level == 0) group_y<NE, NA, AP, MODEL, V16, 0>(a, pc, ap, keys, q, y);
+  else group_y<NE, NA, AP, MODEL, V16, 1>(a, pc, ap, keys, q, y);
 }
 
 // Runtime dispatch on (kind, model) for kernels that mix terms; the branch is
@@ -207,6 +266,62 @@ __device__ __forceinline__ float path_y_any(const PathSpec &a, const PathConsts 
       return gbm ? path_y<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
                  : path_y<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
   }
+}
+
+template <int AP, bool V16>
+__device__ __forceinline__ void group_y_any(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                            const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  const bool gbm = a.model == AICDF_MODEL_GBM;
+  switch (a.kind) {
+    case AICDF_KIND_CORR4:
+      if (gbm) group_y_level<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_level<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+      break;
+    case AICDF_KIND_EXACT2:
+    case AICDF_KIND_PLAIN:
+      if (gbm) group_y_level<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_level<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+      break;
+    default:
+      if (gbm) group_y_level<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_level<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+  }
+}
+
+// Sums over the paths [p0, p0 + n) of a term at level 0 or 1 by groups of
+// G = 4 >> level: group-stride loop over the groups that meet the range,
+// starting at group index `first` with stride `stride` (warp-aligned), FP32
+// chunks of at most kFlushEvery paths flushed to FP64.  GROUP(q, y) fills y.
+template <int kFlushEvery, class GroupFn>
+__device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, uint64_t first, uint64_t stride,
+                                           GroupFn group, double &d1, double &d2) {
+  const int sh = 2 - level, G = 4 >> level;
+  const uint64_t q0 = p0 >> sh, ng = ((p0 + n - 1) >> sh) - q0 + 1;
+  const int lane = threadIdx.x & 31;
+  float f1 = 0.f, f2 = 0.f;
+  int chunk = 0;
+  for (uint64_t base = first; base < ng; base += stride) {
+    const uint64_t qi = base + lane, q = q0 + qi;
+    float y[4];
+    group(q, y);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const uint64_t p = (q << sh) + (uint64_t)g;
+      if (g < G && qi < ng && p >= p0 && p < p0 + n) {
+        f1 += y[g];
+        f2 = fmaf(y[g], y[g], f2);
+      }
+    }
+    chunk += G;
+    if (chunk >= kFlushEvery) {
+      d1 += (double)f1;
+      d2 += (double)f2;
+      f1 = f2 = 0.f;
+      chunk = 0;
+    }
+  }
+  d1 += (double)f1;
+  d2 += (double)f2;
 }
 
 // FP64 block reduction of two values; result valid in thread 0.  Ends with a
