@@ -471,9 +471,10 @@ typedef struct {
  * Philox stream (tag = 1 + 64*estimator + 2*l + t), extending the stream with
  * path_offset as more paths are added, so the result is reproducible from the
  * seed.  Path counts follow the optimal allocation of Section 4.1 from the
- * measured variances and per-path device times.  Levels are added while the
- * bias estimate exceeds eps/sqrt(2) (up to L_max; converged = 0 if it is
- * reached).  workspace_dev: at least aicdf_mlmc_run_workspace_bytes().
+ * measured variances and per-path device times.  While the bias estimate
+ * exceeds eps/sqrt(2), levels are added (up to L_max; converged = 0 if it is
+ * reached): as many at once as the weak order predicts are needed,
+ * ceil(log2(bias / (eps/sqrt(2))) / weak_order), at least one.  workspace_dev: at least aicdf_mlmc_run_workspace_bytes().
  * Synchronous on stream. */
 size_t aicdf_mlmc_run_workspace_bytes(void);
 aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_table approx,

@@ -247,8 +247,14 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
       break;
     }
     if (L >= o->L_max) break;
-    ++L;
-    s = add_levels(L, L);
+    // the weak error decays like 2^(-alpha l): add at once the levels that
+    // bring the estimated bias under eps / sqrt(2) (at least one), so that
+    // the counts are re-allocated once per jump rather than once per level
+    const double gap = std::log2(bias / (eps / std::sqrt(2.0))) / alpha;
+    const int jump = std::max(1, (int)std::ceil(gap));
+    const int L_new = std::min(o->L_max, L + jump);
+    s = add_levels(L + 1, L_new);
+    L = L_new;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
