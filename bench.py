@@ -386,6 +386,40 @@ def cir_time_to_rmse(P, dev, stream, eps: float = 1e-3, level: int = 3, deg: int
     return res
 
 
+def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: int = 128):
+    """C5 to a target RMSE: the 4096 CIR sets of the sweep (truncated
+    Euler-Maruyama, X0 = theta) priced as calls with K = theta (a payoff with a
+    time bias), every set to RMSE eps through aicdf_mlmc_run_sets (levels <= 12)
+    -- nested (PWL + exact correction) and regular MLMC over all sets; plain
+    Monte Carlo with exact variates at the finest level nested MLMC needed, run
+    on the first n_plain sets and scaled to all sets by the set count."""
+    import torch
+    from paper_2012_09715_gb300 import inputs
+    sw = inputs.sweep_sets(n_sets, seed=0)
+    sets = [P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_CALL, X0=float(sw["X0"][i]), T=1.0,
+                         K=float(sw["theta"][i]), mu=0.0, sigma=float(sw["sigma"][i]), kappa=float(sw["kappa"][i]),
+                         theta=float(sw["theta"][i]), discount=1.0) for i in range(n_sets)]
+    tl = P.table_build(P.PWL, 15)
+    ws = torch.empty(P.mlmc_run_sets_workspace_bytes(n_sets), dtype=torch.uint8, device=dev)
+    P.mlmc_run_sets(sets[:64], tl, 1e-3, ws, estimator=P.EST_NESTED, seed=99, L_max=12)  # warm-up
+    res = {"eps": eps, "sets": n_sets}
+    nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=12)
+    regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=12)
+    Lp = max(r.L for r in nested[:n_plain])
+    plain = P.mlmc_run_sets(sets[:n_plain], tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=Lp, seed=3)
+    for name, rr in (("nested", nested), ("regular", regular), ("plain_exact_subset", plain)):
+        res[name] = {"sets": len(rr), "gpu_ms": rr[0].gpu_ms, "wall_ms": rr[0].wall_ms,
+                     "launches": rr[0].launches, "converged": sum(int(r.converged) for r in rr),
+                     "max_rmse_est": max((r.variance + r.bias ** 2) ** 0.5 for r in rr),
+                     "L_hist": {str(l): sum(1 for r in rr if r.L == l) for l in sorted({r.L for r in rr})}}
+    res["plain_exact_fixed_L"] = Lp
+    plain_all_ms = plain[0].gpu_ms * n_sets / n_plain
+    res["plain_exact_gpu_ms_scaled"] = plain_all_ms
+    res["speedup_vs_plain_exact_gpu"] = plain_all_ms / nested[0].gpu_ms
+    res["speedup_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / nested[0].gpu_ms
+    return res
+
+
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
     wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
@@ -544,7 +578,8 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": world * N_SAMPLES * e2e_steps / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": 4 * N_SAMPLES, "steps": e2e_steps,
-               "call": "aicdf_sample_to_host (pinned host buffer, 64 MiB device staging)"}
+               "call": "aicdf_sample_to_host into a pinned host buffer (the kernel stores into it over the host link; "
+                       "pageable buffers would go through the 64 MiB device staging)"}
         del host, staging
         # other methods / dtypes on the same GPU, same workload size
         out16 = torch.empty(N_SAMPLES, dtype=torch.float16, device=dev)

@@ -481,6 +481,19 @@ aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_table approx,
                             const aicdf_mlmc_opts *opts, aicdf_mlmc_result *result,
                             void *workspace_dev, size_t workspace_bytes, aicdf_stream_t stream);
 
+/* aicdf_mlmc_run for n_sets independent parameter sets at once.  Each set
+ * follows the same procedure with its own variances, costs and bias test;
+ * every round is one batched launch holding the new paths of all sets (a
+ * small set costs no launch of its own).  Set s draws from its own streams
+ * (tag = 256 s + 1 + 64*estimator + 2*l + t).  results[s] as for
+ * aicdf_mlmc_run, except that gpu_ms, wall_ms and launches are those of the
+ * whole run.  workspace_dev: at least aicdf_mlmc_run_sets_workspace_bytes(n_sets).
+ * Synchronous on stream. */
+size_t aicdf_mlmc_run_sets_workspace_bytes(int n_sets);
+aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_sets, aicdf_table approx,
+                                 const aicdf_mlmc_opts *opts, aicdf_mlmc_result *results,
+                                 void *workspace_dev, size_t workspace_bytes, aicdf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -131,6 +131,8 @@ SIGNATURES = {
     "aicdf_cir_level_table": (_I, [_P, _P, _I, _I, _U64, _U64, _U64, _U32, _P, _P, _SZ, _P, _P]),
     "aicdf_mlmc_run_workspace_bytes": (_SZ, []),
     "aicdf_mlmc_run": (_I, [_P, _P, _P, _P, _P, _SZ, _P]),
+    "aicdf_mlmc_run_sets_workspace_bytes": (_SZ, [_I]),
+    "aicdf_mlmc_run_sets": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 
 
@@ -320,6 +322,24 @@ def mlmc_run(params: SdeParams, table: Table, eps: float, workspace, estimator: 
     _check(lib().aicdf_mlmc_run(C.byref(params), table.handle, C.byref(o), C.byref(r), _ptr(workspace),
                                 nbytes, _stream(stream)), "mlmc_run")
     return r
+
+
+def mlmc_run_sets_workspace_bytes(n_sets: int) -> int:
+    return lib().aicdf_mlmc_run_sets_workspace_bytes(n_sets)
+
+
+def mlmc_run_sets(sets, table: Table, eps: float, workspace, estimator: int = EST_NESTED, L_min: int = 2,
+                  L_max: int = 20, fixed_L: int = -1, n_pilot: int = 10000, seed: int = 0,
+                  weak_order: float = 1.0, stream=None):
+    """aicdf_mlmc_run_sets: one estimate per parameter set, all sets' paths in
+    shared batched launches (synchronous).  Returns a list of MlmcResult."""
+    o = MlmcOpts(eps, estimator, L_min, L_max, fixed_L, n_pilot, seed, weak_order)
+    arr = (SdeParams * len(sets))(*sets)
+    res = (MlmcResult * len(sets))()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().aicdf_mlmc_run_sets(arr, len(sets), table.handle, C.byref(o), res, _ptr(workspace), nbytes,
+                                     _stream(stream)), "mlmc_run_sets")
+    return list(res)
 
 
 class Batch:

@@ -30,7 +30,8 @@ int sm_count();
 int resident_blocks(const void *kernel, int threads);
 // Host FP64 inverse Gaussian CDF used for the table build.
 double host_phiinv(double p);
-// One-off batched launch of MLMC terms (no graph); see mlmc.cu.
+// One-off batched launch of MLMC terms (no graph); see mlmc.cu.  Returns
+// AICDF_ERR_NOMEM when the launch plan does not fit the workspace.
 aicdf_status batch_run_once(const aicdf_sde_params *sets, int n_sets, const aicdf_batch_term *terms,
                             int n_terms, aicdf_table approx, uint64_t seed, double *sums_dev, void *ws,
                             size_t ws_bytes, cudaStream_t st);

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -277,5 +278,255 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
   r->launches = launches;
   r->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+  return AICDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Many independent parameter sets at once (Section 4.1 per set): every round
+// is one batched launch holding the new paths of all sets' terms, so a small
+// set costs no launch of its own.  Per set: pilot paths on levels 0..L_min,
+// the optimal allocation from its own variances and the calibrated per-step
+// costs of its model, the bias test, and the predicted level jump.
+namespace {
+constexpr size_t kSetSumsBytes = 256 * 5;  // per set: 3 sums x 2 kinds x 24 levels (1152 B), 256-B multiple
+constexpr size_t kSetBatchBytes = 2 * AICDF_MAX_LEVELS * 128;                // per set: tiles, specs, slots
+constexpr size_t kBatchSlack = 16u << 20;                                    // load-balancing tiles
+}  // namespace
+
+extern "C" size_t aicdf_mlmc_run_sets_workspace_bytes(int n_sets) {
+  if (n_sets <= 0) return 0;
+  return aicdf_mlmc_level_workspace_bytes() + 256 + (size_t)n_sets * (kSetSumsBytes + kSetBatchBytes) +
+         kBatchSlack;
+}
+
+extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_sets, aicdf_table approx,
+                                            const aicdf_mlmc_opts *o, aicdf_mlmc_result *results,
+                                            void *workspace_dev, size_t workspace_bytes,
+                                            aicdf_stream_t stream) {
+  if (!sets || n_sets <= 0 || n_sets > (1 << 20) || !o || !results || !workspace_dev) return AICDF_ERR_ARG;
+  if (!aicdf::table_ok(approx)) return AICDF_ERR_ARG;
+  if (!(o->eps > 0.0) || o->L_min < 0 || o->L_max < o->L_min || o->L_max >= AICDF_MAX_LEVELS ||
+      o->L_max > 20 || o->fixed_L >= AICDF_MAX_LEVELS || o->fixed_L > 20)
+    return AICDF_ERR_ARG;
+  if (o->estimator < AICDF_EST_NESTED || o->estimator > AICDF_EST_PLAIN) return AICDF_ERR_ARG;
+  if (o->estimator == AICDF_EST_PLAIN && o->fixed_L < 0) return AICDF_ERR_ARG;
+  if (workspace_bytes < aicdf_mlmc_run_sets_workspace_bytes(n_sets) || ((uintptr_t)workspace_dev % 256))
+    return AICDF_ERR_ARG;
+  const auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)workspace_dev;
+  const size_t lvl_ws = aicdf_mlmc_level_workspace_bytes();
+  double *cal_sums = reinterpret_cast<double *>(w + lvl_ws);
+  double *term_sums = reinterpret_cast<double *>(w + lvl_ws + 256);
+  char *batch_ws = w + lvl_ws + 256 + (size_t)n_sets * kSetSumsBytes;
+  const size_t batch_wsb = workspace_bytes - (size_t)(batch_ws - w);
+
+  const int est = o->estimator;
+  std::vector<int> kinds;
+  if (est == AICDF_EST_NESTED) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
+  else if (est == AICDF_EST_REGULAR) kinds = {AICDF_KIND_EXACT2};
+  else kinds = {AICDF_KIND_PLAIN};
+  // calibrated per-step costs, per (model, scheme) of the sets (cached per process)
+  std::map<std::pair<int, int>, std::vector<double>> kind_ns;
+  for (int s = 0; s < n_sets; ++s) {
+    const auto key = std::make_pair(sets[s].model, sets[s].scheme);
+    if (kind_ns.count(key)) continue;
+    std::vector<double> ns(5, 0.0);
+    for (int k : kinds) {
+      aicdf_status rc = step_cost_ns(&sets[s], approx, k, w, lvl_ws, cal_sums, st, &ns[k]);
+      if (rc != AICDF_OK) return rc;
+    }
+    kind_ns[key] = ns;
+  }
+  struct SetState {
+    std::vector<Term> terms;
+    int L = 0;
+    bool active = true, converged = false;
+    double bias = 0.0;
+  };
+  std::vector<SetState> S(n_sets);
+  auto cost = [&](int s, const Term &t) {
+    return kind_ns[std::make_pair(sets[s].model, sets[s].scheme)][t.kind] * (double)((1u << t.level) + 1);
+  };
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double gpu_ms = 0.0;
+  int launches = 0;
+  // one batched launch adding add[s][i] paths to S[s].terms[i]
+  auto run_round = [&](const std::vector<std::vector<uint64_t>> &add) -> aicdf_status {
+    std::vector<aicdf_batch_term> bt;
+    std::vector<std::pair<int, int>> idx;
+    for (int s = 0; s < n_sets; ++s)
+      for (size_t i = 0; i < add[s].size(); ++i)
+        if (add[s][i] > 0) {
+          const Term &t = S[s].terms[i];
+          aicdf_batch_term x;
+          x.set = (uint32_t)s;
+          x.level = t.level;
+          x.kind = t.kind;
+          x.tag = t.tag;
+          x.n_paths = add[s][i];
+          x.path_offset = t.n;
+          bt.push_back(x);
+          idx.emplace_back(s, (int)i);
+        }
+    if (bt.empty()) return AICDF_OK;
+    cudaEventRecord(e0, st);
+    // one launch; a round whose tile plan does not fit the workspace is split
+    // in halves (each half one launch), recursively
+    std::function<aicdf_status(size_t, size_t)> launch = [&](size_t lo, size_t hi) -> aicdf_status {
+      aicdf_status q = aicdf::batch_run_once(sets, n_sets, bt.data() + lo, (int)(hi - lo), approx, o->seed,
+                                             term_sums + 3 * lo, batch_ws, batch_wsb, st);
+      if (q == AICDF_OK) ++launches;
+      if (q == AICDF_ERR_NOMEM && hi - lo > 1) {
+        const size_t mid = lo + (hi - lo) / 2;
+        q = launch(lo, mid);
+        if (q == AICDF_OK) q = launch(mid, hi);
+      }
+      return q;
+    };
+    aicdf_status rc = launch(0, bt.size());
+    if (rc != AICDF_OK) return rc;
+    cudaEventRecord(e1, st);
+    std::vector<double> h(3 * bt.size());
+    if (cudaMemcpyAsync(h.data(), term_sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      aicdf::set_cuda_error((int)cudaGetLastError());
+      return AICDF_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    gpu_ms += ms;
+    for (size_t j = 0; j < idx.size(); ++j) {
+      Term &t = S[idx[j].first].terms[idx[j].second];
+      t.s1 += h[3 * j];
+      t.s2 += h[3 * j + 1];
+      t.n += bt[j].n_paths;
+    }
+    return AICDF_OK;
+  };
+  const uint64_t pilot = o->n_pilot ? o->n_pilot : 10000;
+  // new terms for levels l0..l1 of set s, with their pilot counts in add
+  auto new_levels = [&](int s, int l0, int l1, std::vector<std::vector<uint64_t>> &add) {
+    for (int l = l0; l <= l1; ++l)
+      for (size_t i = 0; i < kinds.size(); ++i) {
+        Term t;
+        t.level = l;
+        t.kind = kinds[i];
+        t.slot = (int)i;
+        // distinct streams per set, estimator, level and kind
+        t.tag = ((uint32_t)s << 8) + 1u + 64u * (uint32_t)est + 2u * (uint32_t)l + (uint32_t)i;
+        S[s].terms.push_back(t);
+        add[s].push_back(pilot);
+      }
+  };
+  std::vector<std::vector<uint64_t>> add(n_sets);
+  for (int s = 0; s < n_sets; ++s) {
+    if (est == AICDF_EST_PLAIN) {
+      S[s].L = o->fixed_L;
+      new_levels(s, S[s].L, S[s].L, add);
+    } else {
+      S[s].L = o->fixed_L >= 0 ? o->fixed_L : o->L_min;
+      new_levels(s, 0, S[s].L, add);
+    }
+  }
+  aicdf_status rc = run_round(add);
+  const double eps = o->eps;
+  const double alpha = o->weak_order > 0.0 ? o->weak_order : 1.0;
+  const double a2 = std::pow(2.0, alpha);
+  while (rc == AICDF_OK) {
+    // allocation round over the active sets
+    bool any = false;
+    for (int s = 0; s < n_sets; ++s) {
+      add[s].assign(S[s].terms.size(), 0);
+      if (!S[s].active) continue;
+      any = true;
+      std::vector<double> v, c, m(S[s].terms.size());
+      for (auto &t : S[s].terms) {
+        v.push_back(t.var());
+        c.push_back(cost(s, t));
+      }
+      double total = 0.0;
+      rc = aicdf_mlmc_allocate((int)S[s].terms.size(), v.data(), c.data(), eps, m.data(), &total);
+      if (rc != AICDF_OK) break;
+      for (size_t i = 0; i < S[s].terms.size(); ++i) {
+        const double want = std::ceil(m[i]);
+        if (!(want < 1e15)) {
+          rc = AICDF_ERR_NOCONVERGE;
+          break;
+        }
+        if ((uint64_t)want > S[s].terms[i].n) add[s][i] = (uint64_t)want - S[s].terms[i].n;
+      }
+      if (rc != AICDF_OK) break;
+    }
+    if (rc != AICDF_OK || !any) break;
+    rc = run_round(add);
+    if (rc != AICDF_OK) break;
+    // bias test per set; sets that need more levels get them, piloted in one launch
+    bool grow = false;
+    for (int s = 0; s < n_sets; ++s) {
+      add[s].assign(S[s].terms.size(), 0);
+      SetState &q = S[s];
+      if (!q.active) continue;
+      if (est == AICDF_EST_PLAIN || o->fixed_L >= 0) {
+        q.active = false;
+        q.converged = true;
+        continue;
+      }
+      auto level_mean = [&](int l) {
+        double mm = 0.0;
+        for (auto &t : q.terms)
+          if (t.level == l) mm += t.mean();
+        return mm;
+      };
+      double bias = std::fabs(level_mean(q.L)) / (a2 - 1.0);
+      if (q.L > 0) bias = std::max(bias, std::fabs(level_mean(q.L - 1)) / a2 / (a2 - 1.0));
+      q.bias = bias;
+      if (bias <= eps / std::sqrt(2.0)) {
+        q.active = false;
+        q.converged = true;
+        continue;
+      }
+      if (q.L >= o->L_max) {
+        q.active = false;
+        continue;
+      }
+      const int jump = std::max(1, (int)std::ceil(std::log2(bias / (eps / std::sqrt(2.0))) / alpha));
+      const int L_new = std::min(o->L_max, q.L + jump);
+      new_levels(s, q.L + 1, L_new, add);
+      q.L = L_new;
+      grow = true;
+    }
+    if (grow) rc = run_round(add);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != AICDF_OK) return rc;
+  const double wall_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+  for (int s = 0; s < n_sets; ++s) {
+    aicdf_mlmc_result *r = &results[s];
+    std::memset(r, 0, sizeof(*r));
+    double estv = 0.0, var = 0.0;
+    for (auto &t : S[s].terms) {
+      estv += t.mean();
+      var += t.n ? t.var() / (double)t.n : 0.0;
+      r->paths[t.level][t.slot] = t.n;
+      r->mean[t.level][t.slot] = t.mean();
+      r->var[t.level][t.slot] = t.var();
+      r->cost_ns[t.level][t.slot] = cost(s, t);
+    }
+    r->estimate = estv;
+    r->variance = var;
+    r->bias = S[s].bias;
+    r->L = S[s].L;
+    r->converged = S[s].converged ? 1 : 0;
+    r->n_terms = est == AICDF_EST_NESTED ? 2 : 1;
+    r->gpu_ms = gpu_ms;
+    r->wall_ms = wall_ms;
+    r->launches = launches;
+  }
   return AICDF_OK;
 }

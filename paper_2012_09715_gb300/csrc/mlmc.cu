@@ -638,8 +638,7 @@ aicdf_status batch_run_once(const aicdf_sde_params *sets, int n_sets, const aicd
   tile = std::min(std::max(tile, 16384.0), (double)(1u << 24));
   const aicdf_schedule sc = {(int)tile & ~255, 256, 0, 0};
   Plan *p = get_plan(b, sc);
-  if (!p) s = AICDF_ERR_NOMEM;
-  else if (p->bytes > ws_bytes) s = AICDF_ERR_ARG;
+  if (!p || p->bytes > ws_bytes) s = AICDF_ERR_NOMEM;  // the caller may split the terms
   if (s == AICDF_OK) {
     char *w = (char *)ws;
     std::lock_guard<std::mutex> lock(g_resident_mu);

@@ -61,3 +61,43 @@ def test_driver_plain_and_reproducible(P):
     assert abs(r1.estimate - _bs()) <= 4 * math.sqrt(r1.variance) + 0.1045 * 2.0 ** -5 * 2
     with pytest.raises(P.AicdfError):
         P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_PLAIN)   # plain needs fixed_L
+
+
+def test_driver_sets_single_set_equals_run(P):
+    """One set through the multi-set driver takes exactly the rounds of
+    aicdf_mlmc_run (same tags, same allocations): bit-identical results."""
+    import torch
+    tl = P.table_build(P.PWL, 15)
+    prm = P.sde_params()
+    ws = torch.empty(max(P.mlmc_run_workspace_bytes(), P.mlmc_run_sets_workspace_bytes(1)), dtype=torch.uint8,
+                     device="cuda")
+    for est in (P.EST_NESTED, P.EST_REGULAR):
+        r = P.mlmc_run(prm, tl, 5e-4, ws, estimator=est, seed=4)
+        (q,) = P.mlmc_run_sets([prm], tl, 5e-4, ws, estimator=est, seed=4)
+        assert q.estimate == r.estimate and q.variance == r.variance and q.L == r.L
+        assert [list(q.paths[l]) for l in range(r.L + 1)] == [list(r.paths[l]) for l in range(r.L + 1)]
+
+
+def test_driver_sets_many_cir_sets(P):
+    """64 CIR sets (truncated Euler-Maruyama, X0 = theta): E[X_T] = theta at every
+    level, so each set's estimate is within 4 of its own standard deviations of
+    theta; every set converges, and sets of one run use their own streams."""
+    import torch
+    from paper_2012_09715_gb300 import inputs
+    sw = inputs.sweep_sets(64, seed=3)
+    sets = [P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=float(sw["X0"][i]), T=1.0, K=0.0, mu=0.0,
+                         sigma=float(sw["sigma"][i]), kappa=float(sw["kappa"][i]), theta=float(sw["theta"][i]),
+                         discount=1.0) for i in range(64)]
+    tl = P.table_build(P.PWL, 15)
+    ws = torch.empty(P.mlmc_run_sets_workspace_bytes(len(sets)), dtype=torch.uint8, device="cuda")
+    eps = 1e-3
+    res = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=7)
+    assert len(res) == 64
+    ests = []
+    for prm, r in zip(sets, res):
+        assert r.converged
+        assert r.variance <= eps * eps / 2 * 1.05
+        assert abs(r.estimate - prm.theta) <= 4 * math.sqrt(r.variance) + 1e-12, (prm.theta, r.estimate)
+        ests.append(r.estimate - prm.theta)
+    assert len(set(ests)) == len(ests)  # no two sets share a stream
+    assert res[0].launches == res[-1].launches >= 2
