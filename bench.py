@@ -403,8 +403,10 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     ws = torch.empty(P.mlmc_run_sets_workspace_bytes(n_sets), dtype=torch.uint8, device=dev)
     P.mlmc_run_sets(sets[:64], tl, 1e-3, ws, estimator=P.EST_NESTED, seed=99, L_max=12)  # warm-up
     res = {"eps": eps, "sets": n_sets}
-    nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=12)
-    regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=12)
+    # pilots of 2000 paths per new term: 4096 sets x ~9 levels of pilots at the
+    # default 10^4 would cost more than most sets' final four-way terms
+    nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=12, n_pilot=2000)
+    regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=12, n_pilot=2000)
     Lp = max(r.L for r in nested[:n_plain])
     plain = P.mlmc_run_sets(sets[:n_plain], tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=Lp, seed=3)
     for name, rr in (("nested", nested), ("regular", regular), ("plain_exact_subset", plain)):
@@ -619,6 +621,7 @@ def main():
                          ("mlmc_eps_1e-5", lambda: mlmc_time_to_rmse(P, tl, dev, eps=1e-5)),
                          ("sampler_sweep", lambda: sampler_sweep(P, tl, dev, stream)),
                          ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
+                         ("sweep_time_to_rmse", lambda: sweep_time_to_rmse(P, dev)),
                          ("cir_surrogate", lambda: cir_surrogate(P, dev, stream)),
                          ("cir_table", lambda: cir_table(P, dev, stream)),
                          ("cir_time_to_rmse", lambda: cir_time_to_rmse(P, dev, stream)),

@@ -3,7 +3,7 @@
 //  * Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed on
 //    the host: the key schedule is the same for every thread of a launch, so
 //    the xor with the round key reads a kernel-parameter (constant bank) word.
-//  * u01: the 32-bit word -> (2*(x>>9)+1) 2^-24 map, exact in FP32.
+//  * u01: the 32-bit word -> (2*(x mod 2^23)+1) 2^-24 map, exact in FP32.
 //  * pwl_eval: Algorithm 1 (Section 3.3) with the 2 x 16 coefficients held in
 //    registers across the warp and fetched by __shfl_sync -- the GPU form of
 //    keeping the table in one 512-bit vector register (Section 3.3).
