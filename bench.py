@@ -505,6 +505,62 @@ def profile_mlmc_kinds():
     print(sums.cpu().numpy())
 
 
+def profile_kernels():
+    """One representative launch of each kernel family besides the headline
+    sampler, in this order: truncated 16-bit PWL sampling (2^26 FP32), exact
+    FP32 inverse sampling (2^26), the batched MLMC sweep (4096 CIR sets, fixed
+    work), exact CIR paths and Section 5.1 table paths (nu = 2, level 4, 2^16
+    paths), the table evaluation (2^22), one surrogate training epoch (2^20
+    samples) and the surrogate evaluation (2^22)."""
+    import torch
+    import paper_2012_09715_gb300 as P
+    from paper_2012_09715_gb300 import build as B
+    from paper_2012_09715_gb300 import inputs
+    B.build()
+    P.lib()
+    dev = "cuda"
+    tl = P.table_build(P.PWL, 15)
+    out = torch.empty(1 << 26, dtype=torch.float32, device=dev)
+    P.sample_bits(tl, P.PWL, 16, out, seed=1)
+    P.sample(None, P.EXACT, out, seed=1)
+    del out
+    sw = inputs.sweep_sets(4096, seed=0)
+    sets = [P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=float(sw["X0"][i]), T=1.0, K=0.0, mu=0.0,
+                         sigma=float(sw["sigma"][i]), kappa=float(sw["kappa"][i]), theta=float(sw["theta"][i]),
+                         discount=1.0) for i in range(4096)]
+    n2, n4 = inputs.sweep_counts(sw["n_base"])
+    terms = []
+    for s_ in range(4096):
+        for l in range(n2.shape[1]):
+            terms.append(P.BatchTerm(s_, l, P.KIND_APPROX2, (s_ << 8) + 2 * l + 1, int(n2[s_, l]), 0))
+            terms.append(P.BatchTerm(s_, l, P.KIND_CORR4, (s_ << 8) + 2 * l + 2, int(n4[s_, l]), 0))
+    b = P.Batch(sets, terms, tl, seed=0)
+    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    sc = P.Schedule(16384, 128, 0, 1)
+    ws = torch.empty(b.workspace_bytes(sc), dtype=torch.uint8, device=dev)
+    b.run(sc, sums, ws)
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    P.cir_level_table(prm, t, 4, P.CIR_EXACT, 1 << 16, s3, lws, st, seed=1)
+    P.cir_level_table(prm, t, 4, P.CIR_TABLE, 1 << 16, s3, lws, st, seed=1)
+    n = 1 << 22
+    u, lam, tgt = (torch.empty(n, device=dev) for _ in range(3))
+    P.ncx2_targets(2.0, n, u, lam, tgt, st, seed=3, tag=1)
+    o = torch.empty(n, device=dev)
+    t.eval(u, lam, o)
+    sur = P.Surrogate(2.0, seed=1)
+    loss = torch.zeros(1, device=dev)
+    m = 1 << 20
+    sur.train(u[:m], lam[:m], tgt[:m], batch=8192, epochs=1, lr=3e-3, lr_final=3e-3, loss=loss)
+    sur.eval(u, lam, o)
+    torch.cuda.synchronize()
+    print(float(s3[0].item()), float(loss.item()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,11 +570,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n-log2", type=int, default=28, help="workload size (profiling runs only)")
-    ap.add_argument("--profile-case", choices=["mlmc_kinds"], default=None,
+    ap.add_argument("--profile-case", choices=["mlmc_kinds", "kernels"], default=None,
                     help="run one fixed launch sequence for an ncu capture and exit (no timing line)")
     args = ap.parse_args()
     if args.profile_case == "mlmc_kinds":
         return profile_mlmc_kinds()
+    if args.profile_case == "kernels":
+        return profile_kernels()
     global N_SAMPLES
     N_SAMPLES = 1 << args.n_log2
     if args.warmup < 3:
