@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kCirThreads)
   const float cf = (float)a.c, nuf = (float)a.nu, ratio = (float)(a.e / a.c);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   int st = 0;
-  double d1 = 0.0, d2 = 0.0;
+  PathSums acc;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n_paths;
        base += stride) {
     const uint64_t i = base + lane;
@@ -110,12 +110,10 @@ __global__ void __launch_bounds__(kCirThreads)
     if (EXACT && APPROX != 0) y = pe - pa;
     else if (EXACT) y = pe;
     else y = pa;
-    if (i < a.n_paths) {
-      d1 += (double)y;
-      d2 += (double)y * (double)y;
-    }
+    if (i < a.n_paths) acc.add(y);
   }
-  const double2 tot = block_reduce2(d1, d2, s_red);
+  acc.finish();
+  const double2 tot = block_reduce2(acc.d1, acc.d2, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   if (st) atomicOr(status, st);
 }

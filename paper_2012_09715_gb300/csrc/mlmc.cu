@@ -42,7 +42,6 @@ namespace aicdf {
 
 constexpr int kLevelThreads = 256;
 constexpr int kMaxLevelBlocks = 4096;
-constexpr int kFlushEvery = 16;  // paths per FP32 chunk before the FP64 flush
 
 // ============================================================== level kernel
 template <bool NE, bool NA, int AP, int MODEL>
@@ -55,34 +54,22 @@ __global__ void __launch_bounds__(kLevelThreads)
   const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-  double d1 = 0.0, d2 = 0.0;
+  PathSums acc;
   if (a.ps.level < 2) {  // warp-uniform: groups of paths share a Philox call
-    sum_groups<kFlushEvery>(a.path_offset, a.n_paths, a.ps.level, first, stride,
-                            [&](uint64_t q, float (&y)[4]) {
-                              group_y_level<NE, NA, AP, MODEL, false>(a.ps, pc, ap, a.keys, q, y);
-                            },
-                            d1, d2);
+    sum_groups(a.path_offset, a.n_paths, a.ps.level, first, stride,
+               [&](uint64_t q, float (&y)[4]) {
+                 group_y_level<NE, NA, AP, MODEL, false>(a.ps, pc, ap, a.keys, q, y);
+               },
+               acc);
   } else {
-    float f1 = 0.f, f2 = 0.f;
-    int chunk = 0;
     for (uint64_t base = first; base < a.n_paths; base += stride) {
       const uint64_t i = base + lane;
       const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
-      if (i < a.n_paths) {
-        f1 += y;
-        f2 = fmaf(y, y, f2);
-      }
-      if (++chunk == kFlushEvery) {
-        d1 += (double)f1;
-        d2 += (double)f2;
-        f1 = f2 = 0.f;
-        chunk = 0;
-      }
+      if (i < a.n_paths) acc.add(y);
     }
-    d1 += (double)f1;
-    d2 += (double)f2;
   }
-  const double2 t = block_reduce2(d1, d2, s_red);
+  acc.finish();
+  const double2 t = block_reduce2(acc.d1, acc.d2, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
@@ -262,31 +249,19 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
     const BatchItem item = a.items[it];
     const PathSpec ps = a.specs[item.term];
     const PathConsts pc = make_path_consts(ps);
-    double d1 = 0.0, d2 = 0.0;
+    PathSums acc;
     if (ps.level < 2) {  // block-uniform: groups of paths share a Philox call
-      sum_groups<kFlushEvery>(item.begin, item.count, ps.level, threadIdx.x & ~31u, blockDim.x,
-                              [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); },
-                              d1, d2);
+      sum_groups(item.begin, item.count, ps.level, threadIdx.x & ~31u, blockDim.x,
+                 [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); }, acc);
     } else {
-      float f1 = 0.f, f2 = 0.f;
-      int chunk = 0;
       for (uint32_t base = threadIdx.x & ~31u; base < item.count; base += blockDim.x) {
         const uint32_t i = base + lane;
         const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
-        if (i < item.count) {
-          f1 += y;
-          f2 = fmaf(y, y, f2);
-        }
-        if (++chunk == kFlushEvery) {
-          d1 += (double)f1;
-          d2 += (double)f2;
-          f1 = f2 = 0.f;
-          chunk = 0;
-        }
+        if (i < item.count) acc.add(y);
       }
-      d1 += (double)f1;
-      d2 += (double)f2;
     }
+    acc.finish();
+    const double d1 = acc.d1, d2 = acc.d2;
     const double2 t = block_reduce2(d1, d2, s_red);
     if (threadIdx.x == 0) a.partials[item.slot] = t;
   }

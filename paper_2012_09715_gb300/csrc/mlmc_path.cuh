@@ -137,6 +137,29 @@ __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts 
   return x + inc;
 }
 
+// Per-thread sums of Y and Y^2: FP32 over chunks of 16 paths, each chunk
+// added to FP64 accumulators (FP64 runs at 1/64 of the FP32 rate on this GPU,
+// so a path pays one FP32 add and one FMA, and a chunk two FP64 adds), in a
+// fixed order per thread.
+struct PathSums {
+  float f1 = 0.f, f2 = 0.f;  // current chunk
+  double d1 = 0.0, d2 = 0.0;
+  int n = 0;
+  __device__ __forceinline__ void close_chunk() {
+    d1 += (double)f1;
+    d2 += (double)f2;
+    f1 = f2 = 0.f;
+    n = 0;
+  }
+  __device__ __forceinline__ void add(float y) {
+    f1 = __fadd_rn(f1, y);
+    f2 = fmaf(y, y, f2);
+    if (++n == 16) close_chunk();
+  }
+  // totals so far (closes the open chunk); call once at the end
+  __device__ __forceinline__ void finish() { close_chunk(); }
+};
+
 // Payoffs and the differences of Y use the _rn intrinsics, which the compiler
 // never contracts into FMAs, so that Y of a path is the same bits in every
 // kernel that inlines this code (the four-way Y is a small difference of
@@ -290,16 +313,14 @@ __device__ __forceinline__ void group_y_any(const PathSpec &a, const PathConsts 
 
 // Sums over the paths [p0, p0 + n) of a term at level 0 or 1 by groups of
 // G = 4 >> level: group-stride loop over the groups that meet the range,
-// starting at group index `first` with stride `stride` (warp-aligned), FP32
-// chunks of at most kFlushEvery paths flushed to FP64.  GROUP(q, y) fills y.
-template <int kFlushEvery, class GroupFn>
+// starting at group index `first` with stride `stride` (warp-aligned), into
+// acc.  GROUP(q, y) fills y.
+template <class GroupFn>
 __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, uint64_t first, uint64_t stride,
-                                           GroupFn group, double &d1, double &d2) {
+                                           GroupFn group, PathSums &acc) {
   const int sh = 2 - level, G = 4 >> level;
   const uint64_t q0 = p0 >> sh, ng = ((p0 + n - 1) >> sh) - q0 + 1;
   const int lane = threadIdx.x & 31;
-  float f1 = 0.f, f2 = 0.f;
-  int chunk = 0;
   for (uint64_t base = first; base < ng; base += stride) {
     const uint64_t qi = base + lane, q = q0 + qi;
     float y[4];
@@ -307,21 +328,9 @@ __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, u
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const uint64_t p = (q << sh) + (uint64_t)g;
-      if (g < G && qi < ng && p >= p0 && p < p0 + n) {
-        f1 += y[g];
-        f2 = fmaf(y[g], y[g], f2);
-      }
-    }
-    chunk += G;
-    if (chunk >= kFlushEvery) {
-      d1 += (double)f1;
-      d2 += (double)f2;
-      f1 = f2 = 0.f;
-      chunk = 0;
+      if (g < G && qi < ng && p >= p0 && p < p0 + n) acc.add(y[g]);
     }
   }
-  d1 += (double)f1;
-  d2 += (double)f2;
 }
 
 // FP64 block reduction of two values; result valid in thread 0.  Ends with a
