@@ -46,6 +46,27 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def _replica_seed(rank: int) -> int:
+    """Replicas (one process per GPU) key their Philox streams with their rank:
+    disjoint streams, no data-path collective."""
+    return rank
+
+
+def _max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (the job's time): all-reduce MAX, or x alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _whole_job_gsamples(world: int, n_samples: int, steps: int, total_ms: float) -> float:
+    """Samples of all ranks over the slowest rank's time, in Gsamples/s."""
+    return world * n_samples * steps / (total_ms / 1e3) / 1e9
+
+
 def _kernel_sha() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -599,7 +620,7 @@ def main():
     stream = torch.cuda.current_stream()
     tl = P.table_build(P.PWL, 15)
     out = torch.empty(N_SAMPLES, dtype=torch.float32, device=dev)
-    seed = rank  # replicas draw disjoint streams
+    seed = _replica_seed(rank)
 
     def step():
         P.sample(tl, P.PWL, out, seed=seed, stream=stream)
@@ -609,12 +630,9 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         total_ms, per = _time_device(step, args.steps, args.warmup, stream)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(total_ms, dist, dev)
     ms = total_ms / args.steps
-    value = world * N_SAMPLES * args.steps / (total_ms / 1e3) / 1e9
+    value = _whole_job_gsamples(world, N_SAMPLES, args.steps, total_ms)
     kernel_ms = statistics.mean(per)
     bytes_per_launch = 4.0 * N_SAMPLES
     peak, peak_kind = _peaks()
