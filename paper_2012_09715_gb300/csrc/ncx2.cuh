@@ -27,80 +27,101 @@ namespace aicdf {
 
 constexpr int kNcx2NoConverge = 1;
 
+// Stopping thresholds of the series, the continued fraction and the modified
+// Lentz guard, per arithmetic (the FP32 form serves as the first phase of the
+// device quantile, which an FP64 step then polishes).
+template <class T>
+struct Ncx2Eps;
+template <>
+struct Ncx2Eps<double> {
+  static constexpr double series = 1e-17, cf = 1e-16, tiny = 1e-300, lg_min = -700.0;
+};
+template <>
+struct Ncx2Eps<float> {
+  static constexpr float series = 3e-8f, cf = 1e-7f, tiny = 1e-30f, lg_min = -80.0f;
+};
+
 // log Gamma(s), s > 0: shift to s >= 12 (one log of the product), then the
 // Stirling series through the s^-11 term (truncation error < 1e-16).
-AICDF_HD double lgamma_pos(double s) {
-  double prod = 1.0;
-  while (s < 12.0) {  // at most 12 iterations for s > 0
+template <class T>
+AICDF_HD T lgamma_pos(T s) {
+  T prod = T(1);
+  while (s < T(12)) {  // at most 12 iterations for s > 0
     prod *= s;
-    s += 1.0;
+    s += T(1);
   }
-  const double r = 1.0 / s, r2 = r * r;
-  const double series =
-      r * (1.0 / 12.0 -
-           r2 * (1.0 / 360.0 -
-                 r2 * (1.0 / 1260.0 - r2 * (1.0 / 1680.0 - r2 * (1.0 / 1188.0 - r2 * (691.0 / 360360.0))))));
-  return (s - 0.5) * log(s) - s + 0.91893853320467274178 + series - log(prod);
+  const T r = T(1) / s, r2 = r * r;
+  const T series =
+      r * (T(1.0 / 12.0) -
+           r2 * (T(1.0 / 360.0) -
+                 r2 * (T(1.0 / 1260.0) -
+                       r2 * (T(1.0 / 1680.0) - r2 * (T(1.0 / 1188.0) - r2 * T(691.0 / 360360.0))))));
+  return (s - T(0.5)) * log(s) - s + T(0.91893853320467274178) + series - log(prod);
 }
 
 // P(s, y), Q(s, y) and g(s) = y^s e^-y / Gamma(s+1): the series for y < s + 1
 // (gives P), the continued fraction for Q otherwise (modified Lentz).
-AICDF_HD void gamma_pq(double s, double y, double *P, double *Q, double *g, int *status) {
-  const double lg = s * log(y) - y - lgamma_pos(s + 1.0);
+template <class T>
+AICDF_HD void gamma_pq(T s, T y, T *P, T *Q, T *g, int *status) {
+  const T lg = s * log(y) - y - lgamma_pos<T>(s + T(1));
   *g = exp(lg);
-  if (y < s + 1.0) {
-    double term = 1.0, sum = 1.0, d = s;
+  if (y < s + T(1)) {
+    T term = T(1), sum = T(1), d = s;
     int it = 0;
     for (; it < 2000; ++it) {
-      d += 1.0;
+      d += T(1);
       term *= y / d;
       sum += term;
-      if (term < sum * 1e-17) break;
+      if (term < sum * Ncx2Eps<T>::series) break;
     }
     if (it == 2000) *status |= kNcx2NoConverge;
-    *P = fmin(*g * sum, 1.0);
-    *Q = 1.0 - *P;
+    *P = fmin(*g * sum, T(1));
+    *Q = T(1) - *P;
     return;
   }
-  const double tiny = 1e-300;
-  double b = y + 1.0 - s, c = 1.0 / tiny, dd = 1.0 / b, h = dd;
+  const T tiny = Ncx2Eps<T>::tiny;
+  T b = y + T(1) - s, c = T(1) / tiny, dd = T(1) / b, h = dd;
   int i = 1;
   for (; i < 2000; ++i) {
-    const double an = -i * (i - s);
-    b += 2.0;
+    const T an = -T(i) * (T(i) - s);
+    b += T(2);
     dd = an * dd + b;
     if (fabs(dd) < tiny) dd = tiny;
     c = b + an / c;
     if (fabs(c) < tiny) c = tiny;
-    dd = 1.0 / dd;
-    const double del = dd * c;
+    dd = T(1) / dd;
+    const T del = dd * c;
     h *= del;
-    if (fabs(del - 1.0) < 1e-16) break;
+    if (fabs(del - T(1)) < Ncx2Eps<T>::cf) break;
   }
   if (i == 2000) *status |= kNcx2NoConverge;
-  *Q = fmin((*g) * s * h, 1.0);  // e^-y y^s / Gamma(s) = g s
-  *P = 1.0 - *Q;
+  *Q = fmin((*g) * s * h, T(1));  // e^-y y^s / Gamma(s) = g s
+  *P = T(1) - *Q;
 }
 
-// Poisson range [jlo, jhi] of the mixture weights Pois(j; lambda/2) holding
-// all but ~1e-20 of the mass, walked from the mode, with the weights at both
-// ends.  It depends on lambda only, so a quantile computes it once.
+// Poisson range [jlo, jhi] of the mixture weights Pois(j; lambda/2) down to
+// the weight `cut`, walked from the mode, with the weights at both ends.  Every
+// term of the CDF or its tail is at most its weight, so a cut of 1e-8 times
+// the probability sought keeps 1e-8 of it (and 1e-20 is used at least).  A
+// quantile computes it once.
+template <class T>
 struct Ncx2Range {
   int jlo, jhi;
-  double plo, phi;
+  T plo, phi;
 };
 
-AICDF_HD Ncx2Range ncx2_range(double lam, int *status) {
-  Ncx2Range r{0, 0, 1.0, 1.0};
-  const double m = 0.5 * lam;
-  if (m > 0.0) {
+template <class T>
+AICDF_HD Ncx2Range<T> ncx2_range(T lam, T cut, int *status) {
+  Ncx2Range<T> r{0, 0, T(1), T(1)};
+  const T m = T(0.5) * lam;
+  if (m > T(0)) {
     const int j0 = (int)floor(m);
-    const double p0 = exp(-m + j0 * log(m) - lgamma_pos(j0 + 1.0));
-    const double rm = 1.0 / m;
-    double p = p0;
+    const T p0 = exp(-m + T(j0) * log(m) - lgamma_pos<T>(T(j0) + T(1)));
+    const T rm = T(1) / m;
+    T p = p0;
     int j = j0, it = 0;
-    for (; j > 0 && p > 1e-20 && it < 100000; ++it) {
-      p *= (double)j * rm;
+    for (; j > 0 && p > cut && it < 100000; ++it) {
+      p *= T(j) * rm;
       --j;
     }
     if (it == 100000) *status |= kNcx2NoConverge;
@@ -108,8 +129,8 @@ AICDF_HD Ncx2Range ncx2_range(double lam, int *status) {
     r.plo = p;
     p = p0;
     j = j0;
-    for (it = 0; p > 1e-20 && it < 100000; ++it) {
-      p *= m / (double)(j + 1);
+    for (it = 0; p > cut && it < 100000; ++it) {
+      p *= m / T(j + 1);
       ++j;
     }
     if (it == 100000) *status |= kNcx2NoConverge;
@@ -121,47 +142,65 @@ AICDF_HD Ncx2Range ncx2_range(double lam, int *status) {
 
 // Lower CDF (upper = false) or upper tail (upper = true) of chi'^2_nu(lambda)
 // at x, and the density, over the Poisson range rg of lambda.
-AICDF_HD void ncx2_tail_pdf(double x, double nu, double lam, const Ncx2Range &rg, bool upper, double *T,
-                            double *f, int *status) {
-  if (x <= 0.0) {
-    *T = upper ? 1.0 : 0.0;
-    *f = 0.0;
+template <class T>
+AICDF_HD void ncx2_tail_pdf(T x, T nu, T lam, const Ncx2Range<T> &rg, bool upper, T *Tout, T *f, int *status) {
+  if (x <= T(0)) {
+    *Tout = upper ? T(1) : T(0);
+    *f = T(0);
     return;
   }
-  const double y = 0.5 * x, a = 0.5 * nu, m = 0.5 * lam;
-  const double ry = 1.0 / y, h2y = 0.5 * ry;  // loop-invariant reciprocals
+  const T y = T(0.5) * x, a = T(0.5) * nu, m = T(0.5) * lam;
+  const T ry = T(1) / y, h2y = T(0.5) * ry;  // loop-invariant reciprocals
+  const T ly = log(y);
   const int jlo = rg.jlo, jhi = rg.jhi;
-  const double plo = rg.plo, phi = rg.phi;
-  double acc = 0.0, dens = 0.0;
+  T acc = T(0), dens = T(0);
+  // The recurrences multiply g_j = y^{s_j} e^{-y} / Gamma(s_j + 1) step by step,
+  // so a start whose g underflows would leave every term 0.  The start is moved
+  // (in log space) to the first j where g is representable; the skipped terms
+  // have P (lower) or Q (upper) below that underflow level and drop out.
   if (!upper) {
-    const double rm = 1.0 / m;  // only used when jhi > jlo, i.e. m > 0
-    double P, Q, g;
-    gamma_pq(a + jhi, y, &P, &Q, &g, status);
-    double p = phi;
+    const T rm = T(1) / m;  // only used when jhi > jlo, i.e. m > 0
+    int js = jhi;
+    T p = rg.phi;
+    T lg = (a + T(js)) * ly - y - lgamma_pos<T>(a + T(js) + T(1));
+    while (lg < Ncx2Eps<T>::lg_min && js > jlo) {
+      lg += log((a + T(js)) * ry);  // g_{j-1} = g_j (a + j) / y
+      p *= T(js) * rm;
+      --js;
+    }
+    T P, Q, g;
+    gamma_pq<T>(a + T(js), y, &P, &Q, &g, status);
     acc = p * P;
-    dens = p * g * (a + jhi) * h2y;
-    for (int j = jhi; j > jlo; --j) {
-      g = g * (a + j) * ry;  // g_{j-1}
-      P += g;                // P(s_{j-1})
-      p *= (double)j * rm;   // p_{j-1}
+    dens = p * g * (a + T(js)) * h2y;
+    for (int j = js; j > jlo; --j) {
+      g = g * (a + T(j)) * ry;  // g_{j-1}
+      P += g;                   // P(s_{j-1})
+      p *= T(j) * rm;           // p_{j-1}
       acc += p * P;
-      dens += p * g * (a + j - 1) * h2y;
+      dens += p * g * (a + T(j - 1)) * h2y;
     }
   } else {
-    double P, Q, g;
-    gamma_pq(a + jlo, y, &P, &Q, &g, status);
-    double p = plo;
+    int js = jlo;
+    T p = rg.plo;
+    T lg = (a + T(js)) * ly - y - lgamma_pos<T>(a + T(js) + T(1));
+    while (lg < Ncx2Eps<T>::lg_min && js < jhi) {
+      lg += ly - log(a + T(js + 1));  // g_{j+1} = g_j y / (a + j + 1)
+      p *= m / T(js + 1);
+      ++js;
+    }
+    T P, Q, g;
+    gamma_pq<T>(a + T(js), y, &P, &Q, &g, status);
     acc = p * Q;
-    dens = p * g * (a + jlo) * h2y;
-    for (int j = jlo; j < jhi; ++j) {
-      Q += g;                    // Q(s_{j+1})
-      g = g * y / (a + j + 1);   // g_{j+1}
-      p *= m / (double)(j + 1);  // p_{j+1}
+    dens = p * g * (a + T(js)) * h2y;
+    for (int j = js; j < jhi; ++j) {
+      Q += g;                      // Q(s_{j+1})
+      g = g * y / (a + T(j + 1));  // g_{j+1}
+      p *= m / T(j + 1);           // p_{j+1}
       acc += p * Q;
-      dens += p * g * (a + j + 1) * h2y;
+      dens += p * g * (a + T(j + 1)) * h2y;
     }
   }
-  *T = fmin(acc, 1.0);
+  *Tout = fmin(acc, T(1));
   *f = dens;
 }
 
@@ -180,69 +219,113 @@ AICDF_HD double ncx2_sankaran(double z, double nu, double lam) {
 }
 
 // The x with C(x) = target (upper = false) or 1 - C(x) = target (upper = true),
-// 0 < target <= 1/2, from Sankaran's start at the normal quantile z of the
-// same probability (FP64).  Lower tail: Newton on ln C(e^t) - ln target in
-// t = ln x (C behaves like x^{nu/2} near 0, so this converges in a few steps
-// however deep the tail); upper tail: Newton on 1 - C(x) - target in x.  Both
-// keep the iterate inside a bracket and bisect when Newton leaves it.
-AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, double lam, int *status) {
-  double T, f;
-  const double x0 = ncx2_sankaran(z, nu, lam);
-  const Ncx2Range rg = ncx2_range(lam, status);
+// 0 < target <= 1/2, from the start x0 (Sankaran's approximation), in the
+// arithmetic T with relative tolerance tol.  Lower tail: Newton on
+// ln C(e^t) - ln target in t = ln x (C behaves like x^{nu/2} near 0, so this
+// converges in a few steps however deep the tail); upper tail: Newton on
+// 1 - C(x) - target in x.  Both keep the iterate inside a bracket and bisect
+// when Newton leaves it.
+template <class T>
+AICDF_HD T ncx2_solve(T target, bool upper, T x0, T nu, T lam, T tol, int *status) {
+  T Tv, f;
+  const T cut = fmin(T(1e-20), T(1e-8) * target);
+  const Ncx2Range<T> rg = ncx2_range<T>(lam, cut, status);
+  const T big = T(1e30);
   int it = 0;
   if (!upper) {
-    const double lt = log(target);
-    double t = log(x0), lo = -1e300, hi = 1e300;  // bracket in t = ln x
+    const T lt = log(target);
+    T t = log(x0), lo = -big, hi = big;  // bracket in t = ln x
     for (; it < 100; ++it) {
-      const double x = exp(t);
-      ncx2_tail_pdf(x, nu, lam, rg, false, &T, &f, status);
-      double tn;
-      if (!(T > 0.0)) {  // C underflowed: x far too small
+      const T x = exp(t);
+      ncx2_tail_pdf<T>(x, nu, lam, rg, false, &Tv, &f, status);
+      T tn;
+      if (!(Tv > T(0))) {  // C underflowed: x far too small
         lo = t;
-        tn = hi < 1e300 ? 0.5 * (lo + hi) : t + 2.0;
+        tn = hi < big ? T(0.5) * (lo + hi) : t + T(2);
       } else {
-        const double r = log(T) - lt;  // > 0 when x is too large
-        if (r > 0.0) hi = t;
+        const T r = log(Tv) - lt;  // > 0 when x is too large
+        if (r > T(0)) hi = t;
         else lo = t;
-        const double d = x * f / T;   // d ln C / d ln x
-        tn = (d > 0.0) ? t - r / d : 0.5 * (lo + hi);
-        if (!(tn > lo && tn < hi)) tn = (lo > -1e300 && hi < 1e300) ? 0.5 * (lo + hi) : (r > 0.0 ? t - 2.0 : t + 2.0);
+        const T d = x * f / Tv;   // d ln C / d ln x
+        // converged: take the last Newton step as it is (a step that rounds to
+        // nothing must not meet the bracket test below, which would jump away)
+        if (d > T(0) && fabs(r / d) <= tol) {
+          t -= r / d;
+          break;
+        }
+        tn = (d > T(0)) ? t - r / d : T(0.5) * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = (lo > -big && hi < big) ? T(0.5) * (lo + hi) : (r > T(0) ? t - T(2) : t + T(2));
       }
-      const double dt = fabs(tn - t);
+      const T dt = fabs(tn - t);
       t = tn;
-      if (dt <= 1e-13 || (hi - lo) <= 1e-14) break;
+      if (dt <= tol || (hi - lo) <= T(0.1) * tol) break;
     }
     if (it == 100) *status |= kNcx2NoConverge;
     return exp(t);
   }
-  double x = x0;
-  double lo = 0.0, hi = -1.0;  // hi < 0: no upper bound yet
+  T x = x0;
+  T lo = T(0), hi = T(-1);  // hi < 0: no upper bound yet
   for (; it < 100; ++it) {
-    ncx2_tail_pdf(x, nu, lam, rg, true, &T, &f, status);
-    const double r = target - T;  // = C(x) - u, > 0 when x is too large
-    if (r > 0.0) hi = x;
+    ncx2_tail_pdf<T>(x, nu, lam, rg, true, &Tv, &f, status);
+    const T r = target - Tv;  // = C(x) - u, > 0 when x is too large
+    if (r > T(0)) hi = x;
     else lo = x;
-    double xn = (f > 0.0) ? x - r / f : -1.0;
-    if (hi < 0.0) {
-      if (!(xn > lo)) xn = 2.0 * x + 1.0;
-    } else if (!(xn > lo && xn < hi)) {
-      xn = 0.5 * (lo + hi);
+    if (f > T(0) && fabs(r / f) <= tol * x) {  // converged (see the lower tail)
+      x -= r / f;
+      break;
     }
-    const double dx = fabs(xn - x);
+    T xn = (f > T(0)) ? x - r / f : T(-1);
+    if (hi < T(0)) {
+      if (!(xn > lo)) xn = T(2) * x + T(1);
+    } else if (!(xn > lo && xn < hi)) {
+      xn = T(0.5) * (lo + hi);
+    }
+    const T dx = fabs(xn - x);
     x = xn;
-    if (dx <= 1e-13 * x || (hi > 0.0 && hi - lo <= 1e-14 * hi)) break;
+    if (dx <= tol * x || (hi > T(0) && hi - lo <= T(0.1) * tol * hi)) break;
   }
   if (it == 100) *status |= kNcx2NoConverge;
   return x;
 }
 
-// Quantile C^{-1}_nu(u; lambda) for 0 < u < 1 (FP64; 1 - u is exact for the
-// FP32 uniforms the paths use).
+// FP64 quantile from Sankaran's start at the normal quantile z of the same
+// probability (the host table build and the device fallback).
+AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, double lam, int *status) {
+  return ncx2_solve<double>(target, upper, ncx2_sankaran(z, nu, lam), nu, lam, 1e-13, status);
+}
+
+// Quantile C^{-1}_nu(u; lambda) for 0 < u < 1 (FP64 result; 1 - u is exact
+// for the FP32 uniforms the paths use).  FP64 runs at 1/64 of the FP32 rate on
+// this GPU, so the root is first found in FP32 to ~1e-6, then polished by FP64
+// Newton steps (each one FP64 evaluation of the tail and the density; two
+// reach 1e-12 from there, and the result agrees with the full FP64 solve to
+// ~3e-13).  Should the FP32 phase fail (a range limit, no convergence; about
+// 0.1% of calls) or the polish not settle, the full FP64 solve runs.
 __device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int *status) {
   if (!(u > 0.0)) return 0.0;
   if (!(u < 1.0)) return __longlong_as_double(0x7ff0000000000000ll);
   const bool upper = u > 0.5;
-  return ncx2_quantile(upper ? 1.0 - u : u, upper, normcdfinv(u), nu, lam, status);
+  const double target = upper ? 1.0 - u : u;
+  const double z = normcdfinv(u);
+  const double x0 = ncx2_sankaran(z, nu, lam);
+  int st32 = 0;
+  const float x32 = ncx2_solve<float>((float)target, upper, fmaxf((float)x0, 1e-30f), (float)nu, (float)lam,
+                                      1e-6f, &st32);
+  if (st32 == 0 && x32 > 1e-30f && x32 < 1e30f) {
+    const Ncx2Range<double> rg = ncx2_range<double>(lam, fmin(1e-20, 1e-8 * target), status);
+    double x = (double)x32;
+    for (int k = 0; k < 3; ++k) {
+      double Tv, f;
+      ncx2_tail_pdf<double>(x, nu, lam, rg, upper, &Tv, &f, status);
+      if (!(f > 0.0)) break;
+      const double r = upper ? target - Tv : Tv - target;  // C(x) - u
+      const double dx = r / f;
+      if (!(fabs(dx) <= 1e-3 * x)) break;  // not in Newton's range: fall back
+      x -= dx;
+      if (fabs(dx) <= 1e-12 * x) return x;  // the FP64 evaluation's noise floor is ~3e-14
+    }
+  }
+  return ncx2_solve<double>(target, upper, x0, nu, lam, 1e-13, status);
 }
 
 }  // namespace aicdf

@@ -209,3 +209,14 @@ def test_ncx2_table_argument_validation(P):
     assert call(t, P.CIR_SURROGATE) == P.ERR_ARG
     assert call(P.Ncx2Table(1.0, 16, 16, 1), P.CIR_DIFF_TABLE) == P.ERR_DOMAIN
     assert L.aicdf_cir_level(C.byref(prm), None, 3, P.CIR_TABLE, 10, 0, 0, 1, fake, fake, ws, fake, None) == P.ERR_ARG
+
+
+def test_ncx2_tables_build_across_nu(P, orc):
+    """The host build converges at every quadrature node for nu from 0.3 to 100
+    (knots down to y = 1/225, i.e. lambda up to 224 nu, and tails down to
+    1e-20), and the nu = 100 linear table has Table 5a's RMSE at lambda = 100."""
+    for nu, deg in ((0.3, 1), (5.0, 3), (10.0, 3), (50.0, 1), (100.0, 1)):
+        t = P.Ncx2Table(nu, 16, 16, deg)
+        assert t.info()[0] == nu
+    c = P.Ncx2Table(100.0, 16, 16, 1).coefficients()
+    assert abs(orc.ncx2_poly_rmse(c, 100.0, 100.0) - 0.161) <= 0.0006
