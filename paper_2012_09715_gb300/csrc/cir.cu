@@ -32,6 +32,7 @@ struct CirArgs {
   const float *params;  // surrogate weights (may be null for kinds without it)
   uint64_t n_paths, path_offset;
   uint32_t tag;
+  uint32_t lanes;       // active lanes per warp (1..32)
   int level, kind, payoff;
   double nu, c, e;      // chi^2 scale, degrees of freedom, e^{-kappa h}
   float X0, K, discount;
@@ -60,16 +61,20 @@ __global__ void __launch_bounds__(kCirThreads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nsteps = 1 << a.level;
   const float cf = (float)a.c, nuf = (float)a.nu, ratio = (float)(a.e / a.c);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // a warp takes a.lanes consecutive paths per iteration (32 unless the term
+  // is small; the surrogate's warp-wide MLP always runs all 32 lanes)
+  const uint64_t L = APPROX == 1 ? 32u : a.lanes;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * L;
   int st = 0;
   PathSums acc;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < a.n_paths;
-       base += stride) {
+  chunked_loop(gw * L, a.n_paths, stride, kChunkPaths, acc, [&](uint64_t base) {  // warp-uniform
     const uint64_t i = base + lane;
+    const bool active = (uint64_t)lane < L && i < a.n_paths;
     const uint64_t p = a.path_offset + i;
     double xe = a.X0;
     float xa = a.X0;
-    for (int s4 = 0; s4 < nsteps; s4 += 4) {
+    for (int s4 = 0; s4 < nsteps && (active || APPROX == 1); s4 += 4) {
       const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), (uint32_t)p, (uint32_t)(p >> 32), a.tag), a.keys);
       const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -110,9 +115,8 @@ __global__ void __launch_bounds__(kCirThreads)
     if (EXACT && APPROX != 0) y = pe - pa;
     else if (EXACT) y = pe;
     else y = pa;
-    if (i < a.n_paths) acc.add(y);
-  }
-  acc.finish();
+    acc.add(y, active);
+  });
   const double2 tot = block_reduce2(acc.d1, acc.d2, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   if (st) atomicOr(status, st);
@@ -169,19 +173,33 @@ static aicdf_status cir_setup(const aicdf_sde_params *prm, int level, uint64_t n
   return AICDF_OK;
 }
 
-// Block size: 256 threads when there are paths to fill every SM with full
-// blocks; fewer paths are spread over all SMs in smaller blocks (whole warps),
-// since an exact step is FP64 work whose per-SM rate bounds a small term.
+// Launch shape.  With paths to fill every SM with full blocks: 256 threads,
+// 32 paths per warp.  A smaller term is spread over all SMs, and -- for the
+// kinds without the warp-wide MLP -- over all four SM sub-partitions too: one
+// warp of 128-thread blocks per sub-partition, each warp taking
+// ceil(n / (4 SMs)) paths on that many lanes.  An exact step is a serial chain
+// of FP64 operations, and each sub-partition has its own share of the SM's
+// FP64 rate, so a small exact term finishes up to 4x sooner that way.
 template <class Fn, class TabT>
-static aicdf_status cir_launch(Fn k, const CirArgs &a, const TabT &tab, uint64_t n_paths, void *workspace_dev,
-                               double *sums_dev, int *status_dev, cudaStream_t st) {
+static aicdf_status cir_launch(Fn k, CirArgs a, const TabT &tab, bool warp_mlp, uint64_t n_paths,
+                               void *workspace_dev, double *sums_dev, int *status_dev, cudaStream_t st) {
   const uint64_t sms = (uint64_t)sm_count();
+  constexpr uint64_t kSubPartitions = 4;
   int threads = kCirThreads;
-  if (n_paths < sms * kCirThreads) {
-    const uint64_t per_sm = (n_paths + sms - 1) / sms;
-    threads = (int)std::min<uint64_t>(kCirThreads, std::max<uint64_t>(32, (per_sm + 31) / 32 * 32));
+  a.lanes = 32;
+  uint64_t want;
+  if (!warp_mlp && n_paths < sms * kSubPartitions * 32) {
+    a.lanes = (uint32_t)((n_paths + sms * kSubPartitions - 1) / (sms * kSubPartitions));  // 1..32
+    threads = 128;
+    const uint64_t warps = (n_paths + a.lanes - 1) / a.lanes;
+    want = (warps + 3) / 4;
+  } else {
+    if (n_paths < sms * kCirThreads) {
+      const uint64_t per_sm = (n_paths + sms - 1) / sms;
+      threads = (int)std::min<uint64_t>(kCirThreads, std::max<uint64_t>(32, (per_sm + 31) / 32 * 32));
+    }
+    want = (n_paths + threads - 1) / threads;
   }
-  const uint64_t want = (n_paths + threads - 1) / threads;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
       want, std::min<uint64_t>(sms * resident_blocks((const void *)k, threads), 4096)));
   double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
@@ -213,7 +231,8 @@ extern "C" aicdf_status aicdf_cir_level(const aicdf_sde_params *prm, aicdf_surro
     if (std::fabs(surrogate_nu(sur) - a.nu) > 1e-9 * a.nu) return AICDF_ERR_DOMAIN;  // trained for another nu
     a.params = surrogate_params(sur);
   }
-  return cir_launch(select_cir(kind), a, NoTab{}, n_paths, workspace_dev, sums_dev, status_dev,
+  const bool mlp = kind == AICDF_CIR_SURROGATE || kind == AICDF_CIR_DIFF;
+  return cir_launch(select_cir(kind), a, NoTab{}, mlp, n_paths, workspace_dev, sums_dev, status_dev,
                     (cudaStream_t)stream);
 }
 
@@ -233,5 +252,5 @@ extern "C" aicdf_status aicdf_cir_level_table(const aicdf_sde_params *prm, aicdf
   CirTabFn k = kind == AICDF_CIR_EXACT ? k_cir<true, 0, Ncx2TabArgs>
                : kind == AICDF_CIR_TABLE ? k_cir<false, 3, Ncx2TabArgs>
                                          : k_cir<true, 3, Ncx2TabArgs>;
-  return cir_launch(k, a, tab, n_paths, workspace_dev, sums_dev, status_dev, (cudaStream_t)stream);
+  return cir_launch(k, a, tab, false, n_paths, workspace_dev, sums_dev, status_dev, (cudaStream_t)stream);
 }

@@ -62,13 +62,12 @@ __global__ void __launch_bounds__(kLevelThreads)
                },
                acc);
   } else {
-    for (uint64_t base = first; base < a.n_paths; base += stride) {
+    chunked_loop(first, a.n_paths, stride, kChunkPaths, acc, [&](uint64_t base) {
       const uint64_t i = base + lane;
       const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
-      if (i < a.n_paths) acc.add(y);
-    }
+      acc.add(y, i < a.n_paths);
+    });
   }
-  acc.finish();
   const double2 t = block_reduce2(acc.d1, acc.d2, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
@@ -254,13 +253,12 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
       sum_groups(item.begin, item.count, ps.level, threadIdx.x & ~31u, blockDim.x,
                  [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); }, acc);
     } else {
-      for (uint32_t base = threadIdx.x & ~31u; base < item.count; base += blockDim.x) {
-        const uint32_t i = base + lane;
+      chunked_loop(threadIdx.x & ~31u, item.count, blockDim.x, kChunkPaths, acc, [&](uint64_t base) {
+        const uint32_t i = (uint32_t)base + lane;
         const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
-        if (i < item.count) acc.add(y);
-      }
+        acc.add(y, i < item.count);
+      });
     }
-    acc.finish();
     const double d1 = acc.d1, d2 = acc.d2;
     const double2 t = block_reduce2(d1, d2, s_red);
     if (threadIdx.x == 0) a.partials[item.slot] = t;

@@ -137,28 +137,45 @@ __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts 
   return x + inc;
 }
 
-// Per-thread sums of Y and Y^2: FP32 over chunks of 16 paths, each chunk
-// added to FP64 accumulators (FP64 runs at 1/64 of the FP32 rate on this GPU,
-// so a path pays one FP32 add and one FMA, and a chunk two FP64 adds), in a
-// fixed order per thread.
+// Per-thread sums of Y and Y^2: FP32 over chunks of about 16 paths, each
+// chunk added to FP64 accumulators (FP64 runs at 1/64 of the FP32 rate on this
+// GPU: a warp's FP64 add holds its sub-partition's FP64 unit for ~64 cycles),
+// in a fixed order per thread.  add() is FP32 only; flush() is called by the
+// loops below once per chunk, outside the per-path body, so that the FP64 adds
+// are never if-converted into predicated instructions issued for every path
+// (predicated-off FP64 instructions still occupy the FP64 unit).  Lanes past
+// the end of their range add zero (valid = false), which keeps every lane's
+// chunking and the control flow warp-uniform.
 struct PathSums {
   float f1 = 0.f, f2 = 0.f;  // current chunk
   double d1 = 0.0, d2 = 0.0;
-  int n = 0;
-  __device__ __forceinline__ void close_chunk() {
+  __device__ __forceinline__ void add(float y, bool valid) {
+    y = valid ? y : 0.0f;
+    f1 = __fadd_rn(f1, y);
+    f2 = fmaf(y, y, f2);
+  }
+  __device__ __forceinline__ void flush() {
     d1 += (double)f1;
     d2 += (double)f2;
     f1 = f2 = 0.f;
-    n = 0;
   }
-  __device__ __forceinline__ void add(float y) {
-    f1 = __fadd_rn(f1, y);
-    f2 = fmaf(y, y, f2);
-    if (++n == 16) close_chunk();
-  }
-  // totals so far (closes the open chunk); call once at the end
-  __device__ __forceinline__ void finish() { close_chunk(); }
 };
+
+constexpr int kChunkPaths = 16;  // paths per thread between FP64 flushes
+
+// for (b = first; b < end; b += stride) body(b), in chunks of `per_chunk`
+// iterations with acc.flush() after each chunk.  first, end and stride are
+// warp-uniform, so both loops are.
+template <class Body>
+__device__ __forceinline__ void chunked_loop(uint64_t first, uint64_t end, uint64_t stride, int per_chunk,
+                                             PathSums &acc, Body body) {
+  const uint64_t span = stride * (uint64_t)per_chunk;
+  for (uint64_t b0 = first; b0 < end; b0 += span) {
+    const uint64_t lim = end - b0 < span ? end : b0 + span;
+    for (uint64_t b = b0; b < lim; b += stride) body(b);
+    acc.flush();
+  }
+}
 
 // Payoffs and the differences of Y use the _rn intrinsics, which the compiler
 // never contracts into FMAs, so that Y of a path is the same bits in every
@@ -321,16 +338,16 @@ __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, u
   const int sh = 2 - level, G = 4 >> level;
   const uint64_t q0 = p0 >> sh, ng = ((p0 + n - 1) >> sh) - q0 + 1;
   const int lane = threadIdx.x & 31;
-  for (uint64_t base = first; base < ng; base += stride) {
+  chunked_loop(first, ng, stride, kChunkPaths / G, acc, [&](uint64_t base) {
     const uint64_t qi = base + lane, q = q0 + qi;
     float y[4];
     group(q, y);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const uint64_t p = (q << sh) + (uint64_t)g;
-      if (g < G && qi < ng && p >= p0 && p < p0 + n) acc.add(y[g]);
+      if (g < G) acc.add(y[g], qi < ng && p >= p0 && p < p0 + n);  // G is uniform
     }
-  }
+  });
 }
 
 // FP64 block reduction of two values; result valid in thread 0.  Ends with a

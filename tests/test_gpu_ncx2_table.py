@@ -153,3 +153,31 @@ def test_cir_table_variance_drop(P):
         assert -16.5 < r[(1, level)] < -12.5, r
         assert -26.0 < r[(3, level)] < -18.0, r
         assert r[(3, level)] < r[(1, level)] - 5.0, r
+
+
+@pytest.mark.parametrize("kind", ["CIR_TABLE", "CIR_EXACT", "CIR_DIFF_TABLE"])
+def test_cir_small_terms_cover_each_path_once(P, kind):
+    """Terms below 4 x 32 paths per SM run with fewer active lanes per warp
+    (a warp per SM sub-partition).  Splitting 2^15 paths (full-warp mapping)
+    into terms of 4096, 1000, 37 and 1 paths (few-lane mappings) must give
+    the same sums of Y and Y^2 up to the order of the FP64 additions."""
+    import torch
+    prm, q = _cir_params(P, "paper")
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    k = getattr(P, kind)
+    n = 1 << 15
+    P.cir_level_table(prm, t, 2, k, n, sums, ws, st, seed=4, tag=9)
+    whole = sums[:2].cpu().numpy().copy()
+    parts = np.zeros(2)
+    off = 0
+    for m in [4096] * 6 + [1000] * 4 + [37] * 3 + [1] * 5:  # 28692 paths; the rest (4076) last
+        P.cir_level_table(prm, t, 2, k, m, sums, ws, st, path_offset=off, seed=4, tag=9)
+        parts += sums[:2].cpu().numpy()
+        off += m
+    P.cir_level_table(prm, t, 2, k, n - off, sums, ws, st, path_offset=off, seed=4, tag=9)
+    parts += sums[:2].cpu().numpy()
+    assert st.item() == 0
+    assert np.allclose(parts, whole, rtol=1e-9, atol=1e-12), (parts, whole)
