@@ -475,6 +475,67 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     return res
 
 
+def oracle_host(P, tl, dev, budget_s: float = 2.0):
+    """The oracle on the host cores beside the GPU for the path workloads
+    (reported baselines, not targets): fine path-steps/s of the GBM level
+    estimator at level 5 for each kind (the oracle's OpenMP path loop over all
+    host cores; the GPU's aicdf_mlmc_level on 2^21 paths), and exact
+    non-central chi^2 quantiles/s (the oracle's FP64 root finder in one
+    thread; the GPU's aicdf_ncx2_ppf on 2^20), nu = 0.889, log lambda ~
+    U(-4, 4).  Each oracle leg runs a bounded number of paths or quantiles
+    (about budget_s seconds), stated in the result."""
+    import os
+    import numpy as np
+    import torch
+    import oracle
+    oracle.build()
+    res = {"cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "level": 5}
+    a, b = oracle.pwl_table(15, 0.5)
+    a32, b32 = a.astype(np.float32), b.astype(np.float32)
+    oprm = oracle.sde_params()
+    prm = P.sde_params()
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    lvl = 5
+    steps = 1 << lvl
+    for name, ok, gk in (("approx2", oracle.KIND_APPROX2, P.KIND_APPROX2), ("corr4", oracle.KIND_CORR4, P.KIND_CORR4),
+                         ("exact2", oracle.KIND_EXACT2, P.KIND_EXACT2)):
+        n, dt = 1024, 0.0
+        while True:  # grow the sample until it takes about budget_s
+            t0 = time.perf_counter()
+            oracle.mlmc_level(oprm, (a32, b32), lvl, ok, n, seed=7, tag=1)
+            dt = time.perf_counter() - t0
+            if dt > 0.25 * budget_s or n >= 1 << 22:
+                break
+            n *= 4
+        m = 1 << 21
+        P.mlmc_level(prm, tl, lvl, gk, m, sums, ws, seed=7, tag=1)
+        tot, per = _time_device(lambda: P.mlmc_level(prm, tl, lvl, gk, m, sums, ws, seed=7, tag=1), 5, 2,
+                                torch.cuda.current_stream())
+        host = n * steps / dt
+        gpu = m * steps / (statistics.mean(per) / 1e3)
+        res[name] = {"host_fine_steps_per_s": host, "host_paths": n, "gpu_fine_steps_per_s": gpu,
+                     "gpu_over_host": gpu / host}
+    nu = 8.0 / 9.0
+    rng = np.random.default_rng(3)
+    u = oracle.uniforms(5, 0, 1 << 20).astype(np.float32)
+    lam = np.exp(rng.uniform(-4.0, 4.0, u.size))
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < u.size:
+        oracle.ncx2_ppf(float(u[k]), nu, float(lam[k]))
+        k += 1
+    host = k / (time.perf_counter() - t0)
+    ud = torch.from_numpy(u).to(dev)
+    ld = torch.from_numpy(lam).to(dev)
+    out = torch.empty(u.size, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    tot, per = _time_device(lambda: P.ncx2_ppf(ud, ld, nu, out, st), 3, 1, torch.cuda.current_stream())
+    gpu = u.size / (statistics.mean(per) / 1e3)
+    res["ncx2_quantiles"] = {"host_per_s_1_thread": host, "host_quantiles": k, "gpu_per_s": gpu,
+                             "gpu_over_host_thread": gpu / host, "status": int(st.item())}
+    return res
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -582,6 +643,32 @@ def profile_kernels():
     print(float(s3[0].item()), float(loss.item()))
 
 
+def profile_cir_small():
+    """The exact CIR correction term of the Section 5.2 time-to-RMSE case as
+    the nested estimator's pilot runs it: 4096 paths of the paper's CIR set
+    (nu = 2) at level 3, exact-minus-table kind, launched three times."""
+    import torch
+    import paper_2012_09715_gb300 as P
+    from paper_2012_09715_gb300 import build as B
+    B.build()
+    P.lib()
+    dev = "cuda"
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for n in (4096, 4096, 4096, 608, 1 << 14, 1 << 16):
+        e0.record()
+        P.cir_level_table(prm, t, 3, P.CIR_DIFF_TABLE, n, s3, ws, st, seed=21, tag=3)
+        e1.record()
+        torch.cuda.synchronize()
+        print("paths %6d: %.3f ms" % (n, e0.elapsed_time(e1)))
+    print("status", int(st.item()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,13 +678,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n-log2", type=int, default=28, help="workload size (profiling runs only)")
-    ap.add_argument("--profile-case", choices=["mlmc_kinds", "kernels"], default=None,
+    ap.add_argument("--profile-case", choices=["mlmc_kinds", "kernels", "cir_small"], default=None,
                     help="run one fixed launch sequence for an ncu capture and exit (no timing line)")
     args = ap.parse_args()
     if args.profile_case == "mlmc_kinds":
         return profile_mlmc_kinds()
     if args.profile_case == "kernels":
         return profile_kernels()
+    if args.profile_case == "cir_small":
+        return profile_cir_small()
     global N_SAMPLES
     N_SAMPLES = 1 << args.n_log2
     if args.warmup < 3:
@@ -715,6 +804,11 @@ def main():
             "e2e": e2e, "variants": extras}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_extras:
+            try:
+                line["oracle_host"] = oracle_host(P, tl, dev)
+            except Exception as exc:  # reported, not hidden
+                line["oracle_host"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

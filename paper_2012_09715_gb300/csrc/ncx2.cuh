@@ -201,9 +201,12 @@ AICDF_HD void ncx2_tail_pdf(T x, T nu, T lam, const Ncx2Range<T> &rg, bool upper
     dens = p * g * (a + T(js)) * h2y;
     if (D1) dm = dens * (a + T(js) - T(1));
     for (int j = js; j < jhi; ++j) {
-      Q += g;                      // Q(s_{j+1})
-      g = g * y / (a + T(j + 1));  // g_{j+1}
-      p *= m / T(j + 1);           // p_{j+1}
+      // g_{j+1} = g_j y / (a + j + 1) and p_{j+1} = p_j m / (j + 1), with one
+      // division: d = 1 / ((j + 1)(a + j + 1))
+      const T d = T(1) / (T(j + 1) * (a + T(j + 1)));
+      Q += g;                          // Q(s_{j+1})
+      g = g * (y * T(j + 1)) * d;      // g_{j+1}
+      p = p * (m * (a + T(j + 1))) * d;  // p_{j+1}
       acc += p * Q;
       const T term = p * g * (a + T(j + 1)) * h2y;
       dens += term;
@@ -237,10 +240,8 @@ AICDF_HD double ncx2_sankaran(double z, double nu, double lam) {
 // 1 - C(x) - target in x.  Both keep the iterate inside a bracket and bisect
 // when Newton leaves it.
 template <class T>
-AICDF_HD T ncx2_solve(T target, bool upper, T x0, T nu, T lam, T tol, int *status) {
+AICDF_HD T ncx2_solve(T target, bool upper, T x0, T nu, T lam, T tol, const Ncx2Range<T> &rg, int *status) {
   T Tv, f;
-  const T cut = fmin(T(1e-20), T(1e-8) * target);
-  const Ncx2Range<T> rg = ncx2_range<T>(lam, cut, status);
   const T big = T(1e30);
   int it = 0;
   if (!upper) {
@@ -299,6 +300,18 @@ AICDF_HD T ncx2_solve(T target, bool upper, T x0, T nu, T lam, T tol, int *statu
   return x;
 }
 
+// The Poisson range of a quantile at `target`: weights down to
+// min(1e-20, 1e-8 target) of the probability sought.
+template <class T>
+AICDF_HD Ncx2Range<T> ncx2_quantile_range(T lam, T target, int *status) {
+  return ncx2_range<T>(lam, fmin(T(1e-20), T(1e-8) * target), status);
+}
+
+template <class T>
+AICDF_HD T ncx2_solve(T target, bool upper, T x0, T nu, T lam, T tol, int *status) {
+  return ncx2_solve<T>(target, upper, x0, nu, lam, tol, ncx2_quantile_range<T>(lam, target, status), status);
+}
+
 // FP64 quantile from Sankaran's start at the normal quantile z of the same
 // probability (the host table build and the device fallback).
 AICDF_HD double ncx2_quantile(double target, bool upper, double z, double nu, double lam, int *status) {
@@ -326,10 +339,19 @@ __device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int 
   const double z = normcdfinv(u);
   const double x0 = ncx2_sankaran(z, nu, lam);
   int st32 = 0;
+  const Ncx2Range<float> rg32 = ncx2_quantile_range<float>((float)lam, (float)target, &st32);
   const float x32 = ncx2_solve<float>((float)target, upper, fmaxf((float)x0, 1e-30f), (float)nu, (float)lam,
-                                      1e-6f, &st32);
+                                      1e-6f, rg32, &st32);
   if (st32 == 0 && x32 > 1e-30f && x32 < 1e30f) {
-    const Ncx2Range<double> rg = ncx2_range<double>(lam, fmin(1e-20, 1e-8 * target), status);
+    // the polish sums over the FP32 phase's Poisson range (an FP32 rounding
+    // at its ends moves weights of ~1e-20 of the probability), with the end
+    // weights Pois(j; lambda/2) recomputed in FP64
+    Ncx2Range<double> rg{rg32.jlo, rg32.jhi, 1.0, 1.0};
+    if (lam > 0.0) {
+      const double m = 0.5 * lam, lm = log(m);
+      rg.plo = exp(-m + rg.jlo * lm - lgamma_pos<double>(rg.jlo + 1.0));
+      rg.phi = exp(-m + rg.jhi * lm - lgamma_pos<double>(rg.jhi + 1.0));
+    }
     double x = (double)x32;
     for (int k = 0; k < 3; ++k) {
       double Tv, f, fp;
