@@ -233,6 +233,57 @@ def batch_sweep(P, dev, stream):
             "autotune_best_ms": tune_ms, "fp16_variates": True}
 
 
+def gbm_levels_batch(P, dev, stream):
+    """The GBM nested-MLMC levels in fixed-work form: levels 0..8 (2^l steps),
+    N_l = round(10^(7 - 3l/8)) paths (10^7 down to 10^4) for each of the
+    two-way approximate term and the four-way correction, FP32 paths and
+    variates, FP64 sums -- all 18 terms in one persistent graph-captured launch
+    (autotuned schedule), against the same terms as 18 separate level launches.
+    The estimate (sum of the level means) is reported with its standard error
+    beside the Black-Scholes value of the Euler limit."""
+    import math
+    import torch
+    prm = P.sde_params()
+    tl = P.table_build(P.PWL, 15)
+    terms, steps, counts = [], 0, []
+    for l in range(9):
+        n = int(round(10 ** (7 - 3 * l / 8)))
+        counts.append(n)
+        for kind in (P.KIND_APPROX2, P.KIND_CORR4):
+            terms.append(P.BatchTerm(0, l, kind, 2 * l + 1 + (kind == P.KIND_CORR4), n, 0))
+            steps += n << l
+    b = P.Batch([prm], terms, tl, seed=0)
+    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    big = max(b.workspace_bytes(P.Schedule(t * m, t, 0, 0)) for t in (128, 256) for m in (2, 8, 32, 128))
+    ws = torch.empty(big, dtype=torch.uint8, device=dev)
+    best, tune_ms = b.autotune(sums, ws, var16=0, stream=stream)
+    tot, per = _time_device(lambda: b.run(best, sums, ws, stream=stream), 5, 2, stream)
+    ms = statistics.mean(per)
+    sm = sums.view(-1, 3).cpu().numpy()
+    est = float(sum(r[0] / r[2] for r in sm))
+    var = float(sum((r[1] / r[2] - (r[0] / r[2]) ** 2) / r[2] for r in sm))
+    # the same terms as separate level launches
+    lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+
+    def separate():
+        for t in terms:
+            P.mlmc_level(prm, tl, t.level, t.kind, t.n_paths, s3, lws, seed=0, tag=t.tag, stream=stream)
+
+    tot2, _ = _time_device(separate, 5, 2, stream)
+    sep_ms = tot2 / 5
+    n_items, grid = b.info(best)
+    # Black-Scholes call, S0 = K = 1, r = 0.05, sigma = 0.2, T = 1
+    d1 = (0.05 + 0.02) / 0.2
+    d2 = d1 - 0.2
+    ncdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
+    bs = ncdf(d1) - math.exp(-0.05) * ncdf(d2)
+    return {"levels": 9, "paths_per_level": counts, "fine_path_steps": steps, "ms": ms,
+            "path_steps_per_s": steps / (ms / 1e3), "separate_launches_ms": sep_ms,
+            "schedule": best.as_dict(), "tiles": n_items, "grid": grid, "autotune_best_ms": tune_ms,
+            "estimate": est, "std_err": math.sqrt(var), "black_scholes": bs}
+
+
 def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     """CIR (kappa 0.5, theta 0.04, sigma 0.3, X0 0.04, T 1; nu = 0.889): train the
     surrogate on exact quantiles, then report its error, the exact/surrogate
@@ -785,6 +836,7 @@ def main():
         for name, fn in (("mlmc", lambda: mlmc_time_to_rmse(P, tl, dev)),
                          ("mlmc_eps_1e-5", lambda: mlmc_time_to_rmse(P, tl, dev, eps=1e-5)),
                          ("sampler_sweep", lambda: sampler_sweep(P, tl, dev, stream)),
+                         ("gbm_levels_batch", lambda: gbm_levels_batch(P, dev, stream)),
                          ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
                          ("sweep_time_to_rmse", lambda: sweep_time_to_rmse(P, dev)),
                          ("cir_surrogate", lambda: cir_surrogate(P, dev, stream)),

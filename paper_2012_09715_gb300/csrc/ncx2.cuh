@@ -66,12 +66,16 @@ AICDF_HD void gamma_pq(T s, T y, T *P, T *Q, T *g, int *status) {
   const T lg = s * log(y) - y - lgamma_pos<T>(s + T(1));
   *g = exp(lg);
   if (y < s + T(1)) {
+    // terms y^k / ((s+1)...(s+k)), two per division
     T term = T(1), sum = T(1), d = s;
     int it = 0;
-    for (; it < 2000; ++it) {
-      d += T(1);
-      term *= y / d;
-      sum += term;
+    for (; it < 2000; it += 2) {
+      const T d1 = d + T(1), d2 = d + T(2);
+      const T inv = T(1) / (d1 * d2);
+      const T t1 = term * y * d2 * inv;  // term y / d1
+      term = t1 * y * d1 * inv;          // t1 y / d2
+      sum += t1 + term;
+      d = d2;
       if (term < sum * Ncx2Eps<T>::series) break;
     }
     if (it == 2000) *status |= kNcx2NoConverge;
@@ -173,18 +177,21 @@ AICDF_HD void ncx2_tail_pdf(T x, T nu, T lam, const Ncx2Range<T> &rg, bool upper
       --js;
     }
     T P, Q, g;
-    gamma_pq<T>(a + T(js), y, &P, &Q, &g, status);
+    T sj = a + T(js), jd = T(js);  // s_j and j, stepped by exact unit decrements
+    gamma_pq<T>(sj, y, &P, &Q, &g, status);
     acc = p * P;
-    dens = p * g * (a + T(js)) * h2y;
-    if (D1) dm = dens * (a + T(js) - T(1));
+    dens = p * g * sj;  // sum p_j g_j s_j; times 1/(2y) at the end
+    if (D1) dm = dens * (sj - T(1));
     for (int j = js; j > jlo; --j) {
-      g = g * (a + T(j)) * ry;  // g_{j-1}
-      P += g;                   // P(s_{j-1})
-      p *= T(j) * rm;           // p_{j-1}
-      acc += p * P;
-      const T term = p * g * (a + T(j - 1)) * h2y;
-      dens += term;
-      if (D1) dm += term * (a + T(j - 2));
+      g *= sj * ry;  // g_{j-1} = g_j s_j / y
+      P += g;        // P(s_{j-1})
+      p *= jd * rm;  // p_{j-1} = p_j j / m
+      sj -= T(1);
+      jd -= T(1);
+      acc = fma(p, P, acc);
+      const T t = p * g * sj;
+      dens += t;
+      if (D1) dm = fma(t, sj - T(1), dm);
     }
   } else {
     int js = jlo;
@@ -196,40 +203,45 @@ AICDF_HD void ncx2_tail_pdf(T x, T nu, T lam, const Ncx2Range<T> &rg, bool upper
       ++js;
     }
     T P, Q, g;
-    gamma_pq<T>(a + T(js), y, &P, &Q, &g, status);
+    T sj = a + T(js), jd = T(js);
+    gamma_pq<T>(sj, y, &P, &Q, &g, status);
     acc = p * Q;
-    dens = p * g * (a + T(js)) * h2y;
-    if (D1) dm = dens * (a + T(js) - T(1));
+    dens = p * g * sj;
+    if (D1) dm = dens * (sj - T(1));
     for (int j = js; j < jhi; ++j) {
-      // g_{j+1} = g_j y / (a + j + 1) and p_{j+1} = p_j m / (j + 1), with one
-      // division: d = 1 / ((j + 1)(a + j + 1))
-      const T d = T(1) / (T(j + 1) * (a + T(j + 1)));
-      Q += g;                          // Q(s_{j+1})
-      g = g * (y * T(j + 1)) * d;      // g_{j+1}
-      p = p * (m * (a + T(j + 1))) * d;  // p_{j+1}
-      acc += p * Q;
-      const T term = p * g * (a + T(j + 1)) * h2y;
-      dens += term;
-      if (D1) dm += term * (a + T(j));
+      jd += T(1);  // j + 1
+      sj += T(1);  // s_{j+1}
+      // g_{j+1} = g_j y / s_{j+1} and p_{j+1} = p_j m / (j + 1), with one
+      // division: d = 1 / ((j + 1) s_{j+1})
+      const T d = T(1) / (jd * sj);
+      Q += g;  // Q(s_{j+1})
+      g *= y * jd * d;
+      p *= m * sj * d;
+      acc = fma(p, Q, acc);
+      const T t = p * g * sj;
+      dens += t;
+      if (D1) dm = fma(t, sj - T(1), dm);
     }
   }
+  dens *= h2y;
   *Tout = fmin(acc, T(1));
   *f = dens;
-  if (D1) *fprime = dm * h2y - T(0.5) * dens;
+  if (D1) *fprime = dm * h2y * h2y - T(0.5) * dens;
 }
 
 // Sankaran's approximation of the quantile (Section 5.1; with sqrt(2 c2) in
 // the normal term) at the normal quantile z = Phi^{-1}(u), used as the start.
-AICDF_HD double ncx2_sankaran(double z, double nu, double lam) {
-  const double k = nu, h0 = k + lam, h2 = k + 2.0 * lam;
-  const double c1 = 1.0 - (2.0 / 3.0) * h0 * (k + 3.0 * lam) / (h2 * h2);
-  const double c2 = h2 / (h0 * h0);
-  const double c3 = (c1 - 1.0) * (1.0 - 3.0 * c1);
-  const double base = 1.0 + c1 * c2 * (c1 - 1.0 + 0.5 * (2.0 - c1) * c2 * c3) +
-                      c1 * sqrt(2.0 * c2) * (1.0 + 0.5 * c2 * c3) * z;
-  if (!(base > 0.0) || !(fabs(c1) > 1e-3)) return h0;  // outside its range: start at the mean
-  const double r = h0 * pow(base, 1.0 / c1);
-  return (r > 0.0 && isfinite(r)) ? r : h0;
+template <class T = double>
+AICDF_HD T ncx2_sankaran(T z, T nu, T lam) {
+  const T k = nu, h0 = k + lam, h2 = k + T(2) * lam;
+  const T c1 = T(1) - T(2.0 / 3.0) * h0 * (k + T(3) * lam) / (h2 * h2);
+  const T c2 = h2 / (h0 * h0);
+  const T c3 = (c1 - T(1)) * (T(1) - T(3) * c1);
+  const T base = T(1) + c1 * c2 * (c1 - T(1) + T(0.5) * (T(2) - c1) * c2 * c3) +
+                 c1 * sqrt(T(2) * c2) * (T(1) + T(0.5) * c2 * c3) * z;
+  if (!(base > T(0)) || !(fabs(c1) > T(1e-3))) return h0;  // outside its range: start at the mean
+  const T r = h0 * pow(base, T(1) / c1);
+  return (r > T(0) && isfinite(r)) ? r : h0;
 }
 
 // The x with C(x) = target (upper = false) or 1 - C(x) = target (upper = true),
@@ -336,21 +348,22 @@ __device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int 
   if (!(u < 1.0)) return __longlong_as_double(0x7ff0000000000000ll);
   const bool upper = u > 0.5;
   const double target = upper ? 1.0 - u : u;
-  const double z = normcdfinv(u);
-  const double x0 = ncx2_sankaran(z, nu, lam);
+  // the start only needs to be near the root: FP32
+  const float x0 = ncx2_sankaran<float>(normcdfinvf((float)u), (float)nu, (float)lam);
   int st32 = 0;
   const Ncx2Range<float> rg32 = ncx2_quantile_range<float>((float)lam, (float)target, &st32);
-  const float x32 = ncx2_solve<float>((float)target, upper, fmaxf((float)x0, 1e-30f), (float)nu, (float)lam,
-                                      1e-6f, rg32, &st32);
+  const float x32 = ncx2_solve<float>((float)target, upper, fmaxf(x0, 1e-30f), (float)nu, (float)lam, 1e-6f,
+                                      rg32, &st32);
   if (st32 == 0 && x32 > 1e-30f && x32 < 1e30f) {
     // the polish sums over the FP32 phase's Poisson range (an FP32 rounding
     // at its ends moves weights of ~1e-20 of the probability), with the end
     // weights Pois(j; lambda/2) recomputed in FP64
     Ncx2Range<double> rg{rg32.jlo, rg32.jhi, 1.0, 1.0};
-    if (lam > 0.0) {
-      const double m = 0.5 * lam, lm = log(m);
-      rg.plo = exp(-m + rg.jlo * lm - lgamma_pos<double>(rg.jlo + 1.0));
-      rg.phi = exp(-m + rg.jhi * lm - lgamma_pos<double>(rg.jhi + 1.0));
+    if (lam > 0.0) {  // the lower tail starts from the top weight, the upper from the bottom one
+      const double m = 0.5 * lam;
+      const int j = upper ? rg.jlo : rg.jhi;
+      const double w = exp(-m + j * log(m) - lgamma_pos<double>(j + 1.0));
+      (upper ? rg.plo : rg.phi) = w;
     }
     double x = (double)x32;
     for (int k = 0; k < 3; ++k) {
@@ -365,7 +378,7 @@ __device__ __forceinline__ double ncx2_ppf(double u, double nu, double lam, int 
       if (fabs(d) <= 1e-5 * x && fabs(c) <= 1e-3) return x;
     }
   }
-  return ncx2_solve<double>(target, upper, x0, nu, lam, 1e-13, status);
+  return ncx2_solve<double>(target, upper, (double)x0, nu, lam, 1e-13, status);
 }
 
 }  // namespace aicdf
