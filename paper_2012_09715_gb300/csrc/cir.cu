@@ -94,13 +94,13 @@ __global__ void __launch_bounds__(kCirThreads)
                 // beyond the trained range: P - Phi^{-1}(U) = O(sqrt(y)) as y -> 0
                 // (Section 5.1), so carry the learned correction at the edge
                 // of the range over with the factor sqrt(y / y_max)
-                const float z = phiinv_f32(u);
+                const float z = phiinv_f32_grid(u);
                 pt = fmaf(pt - z, sqrtf((kLamTrainMax + nuf) / (lam + nuf)), z);
               }
             } else if constexpr (APPROX == 3) {
               pt = ncx2_table_P(s_rows, tab.K, tab.n_knots, tab.scale_k, u, sqrtf(nuf / (lam + nuf)));
             } else {
-              pt = phiinv_f32(u);
+              pt = phiinv_f32_grid(u);
             }
             const float h = lam + nuf;
             xa = cf * fmaxf(fmaf(2.0f * sqrtf(h), pt, h), 0.f);

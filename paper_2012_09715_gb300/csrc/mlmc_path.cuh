@@ -221,7 +221,7 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
     for (int t = 0; t < 4; ++t) {
       const float u = u01(w[t]);
       if (NE) {
-        const float ze = phiinv_f32(u);
+        const float ze = phiinv_f32_grid(u);
         xfe = step_fine<MODEL>(xfe, ze, pc);
         se += ze;
       }
@@ -261,7 +261,7 @@ __device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc,
       const uint32_t x = w[g * NF + s];
       const float u = u01(x);
       if (NE) {
-        const float ze = phiinv_f32(u);
+        const float ze = phiinv_f32_grid(u);
         xfe = step_fine<MODEL>(xfe, ze, pc);
         se += ze;
       }

@@ -98,10 +98,10 @@ struct Approx<AICDF_PWP, SRC> {
 template <int SRC>
 struct Approx<AICDF_EXACT, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
-  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32(u01(x)); }
+  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32_grid(u01(x)); }
   __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
   template <int B>
-  __device__ __forceinline__ float cell(uint32_t m) const { return phiinv_f32(ubits<B>(m)); }
+  __device__ __forceinline__ float cell(uint32_t m) const { return phiinv_f32_grid(ubits<B>(m)); }
 };
 
 template <int SRC>
