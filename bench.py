@@ -314,8 +314,12 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     uh, lh, th = (torch.empty(nh, device=dev) for _ in range(3))
     P.ncx2_targets(nu, nh, uh, lh, th, st, seed=99, tag=2, stream=stream)
     out = torch.empty(nh, device=dev)
-    tot, per = _time_device(lambda: s.eval(uh, lh, out, stream=stream), 10, 3, stream)
+    s.eval(uh, lh, out, stream=stream)
+    # evaluation rate on the 2^22 training inputs (the size the exact rate is taken at)
+    big = torch.empty(n_train, device=dev)
+    tot, per = _time_device(lambda: s.eval(u, lam, big, stream=stream), 10, 3, stream)
     t_eval_ms = statistics.mean(per)
+    del big
     torch.cuda.synchronize()
     from scipy.special import ndtri
     t_np = th.cpu().numpy().astype("float64")
@@ -340,8 +344,8 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     return {"nu": nu, "train_samples": n_train, "epochs": epochs, "train_ms": t_train_ms,
             "final_batch_mse": float(loss.item()), "heldout_rmse": rmse, "heldout_rmse_gauss_limit": rmse_g,
             "exact_quantiles_per_s": n_train / (t_exact_ms / 1e3),
-            "surrogate_evals_per_s": nh / (t_eval_ms / 1e3),
-            "exact_over_surrogate_cost": (t_exact_ms / n_train) / (t_eval_ms / nh),
+            "surrogate_evals_per_s": n_train / (t_eval_ms / 1e3),
+            "exact_over_surrogate_cost": (t_exact_ms / n_train) / (t_eval_ms / n_train),
             "root_finder_status": int(st.item()), "levels": levels}
 
 

@@ -2,11 +2,12 @@
 // P~(U; lambda) ~ P_nu(U; nu / (lambda + nu)), so that
 // C~^{-1}_nu(U; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~.
 //
-// Kernels: batched evaluation, a fused forward + backward training step (the
-// three 64 x 64 products -- layer 2, dH1 = dZ2 W2 and dW2 = dZ2^T H1 -- on
-// the tensor cores in BF16 with FP32 accumulation), a fixed-order reduction
-// of the per-block gradients with an Adam update of FP32 master weights, and
-// the generation of exact training targets with the FP64 root finder.
+// Kernels: batched evaluation (the 64 x 64 layer as tcgen05 MMAs into a TMEM
+// accumulator), a fused forward + backward training step (the three 64 x 64
+// products -- layer 2, dH1 = dZ2 W2 and dW2 = dZ2^T H1 -- as warp-level
+// mma.sync, BF16 with FP32 accumulation), a fixed-order reduction of the
+// per-block gradients with an Adam update of FP32 master weights, and the
+// generation of exact training targets with the FP64 root finder.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +21,7 @@
 #include "device_common.cuh"
 #include "mlp_device.cuh"
 #include "ncx2.cuh"
+#include "tc_device.cuh"
 
 namespace aicdf {
 
@@ -35,23 +37,140 @@ constexpr size_t kTrainOffW = kTrainOffDZ + kMlpWarps * kTileBytes;
 constexpr size_t kTrainSmem = kTrainOffW + sizeof(float) * kMlpWarps * (4 * kH + 2);
 
 // ------------------------------------------------------------------ evaluation
-__global__ void __launch_bounds__(kMlpThreads)
-    k_mlp_eval(const float *__restrict__ params, const float *__restrict__ u,
-               const float *__restrict__ lam, float *__restrict__ out, uint64_t n) {
-  __shared__ __align__(16) MlpSmem s;
-  __shared__ __align__(16) __nv_bfloat16 hs[kMlpWarps][32 * kHPad];
-  mlp_stage(params, s);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-    const uint64_t i = base + lane;
-    const bool ok = i < n;
-    const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
-    const float x1 = ok ? mlp_feature_lam(lam[i]) : 0.f;
-    const float y = mlp_forward_warp(s, x0, x1, hs[warp]);
-    if (ok) out[i] = y;
+// Batched evaluation on tcgen05: a CTA of 128 threads takes tiles of 128
+// samples (thread = sample = row).  Layer 1 (FP32, tanh) writes each row of
+// H1 in BF16 into a shared tile in the canonical K-major layout; one thread
+// issues the 128 x 64 x 64 product H1 W2^T as four depth-16 MMAs into a TMEM
+// accumulator (64 FP32 columns, lane = sample); each thread then reads its
+// row of Z2 from TMEM for tanh(Z2 + b2) . w3 + b3.  Two H1 tiles and two
+// accumulators let layer 1 of the next tile run while the current tile's MMA
+// is in flight.  Should an MMA's completion not arrive within the bounded
+// wait, the tile's outputs are NaN and the CTA stops.
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcCols = 128;  // TMEM columns per CTA: two 64-column accumulators
+
+struct MlpTcSmem {
+  __nv_bfloat16 a[2][kTcRows * kH];  // H1 tiles (2 x 16 KiB)
+  __nv_bfloat16 b[kH * kH];          // W2 [out][in] (8 KiB)
+  float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
+  unsigned long long mbar[2];
+  uint32_t tmem;
+};
+// Dynamic shared memory per CTA, padded so that at most 4 CTAs fit an SM and
+// their TMEM (4 x 128 columns) never exceeds the SM's 512 columns.
+constexpr size_t kTcSmemBytes = 52 * 1024;
+static_assert(sizeof(MlpTcSmem) + 1024 <= kTcSmemBytes, "tile layout exceeds the padded allocation");
+
+__device__ __forceinline__ void mlp_tc_layer1(const MlpTcSmem &s, __nv_bfloat16 *tile, int row, float x0, float x1) {
+  unsigned char *base = reinterpret_cast<unsigned char *>(tile);
+#pragma unroll
+  for (int j = 0; j < kH / 8; ++j) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 8 * j + 2 * q;
+      const float h0 = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
+      const float h1 = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
+      w[q] = pack_bf16(h0, h1);
+    }
+    *reinterpret_cast<uint4 *>(base + tc_canon_off64(row, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
+}
+
+__device__ __forceinline__ void mlp_tc_issue(uint32_t d_tmem, uint32_t a_base, uint32_t b_base, uint32_t mbar) {
+  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kH);
+#pragma unroll
+  for (int kk = 0; kk < kH / 16; ++kk)
+    tc_mma_bf16(d_tmem, tc_desc(a_base + 256 * kk, 128, 1024), tc_desc(b_base + 256 * kk, 128, 1024), idesc,
+                kk > 0);
+  tc_commit(mbar);
+}
+
+__global__ void __launch_bounds__(kTcRows)
+    k_mlp_eval(const float *__restrict__ params, const float *__restrict__ u, const float *__restrict__ lam,
+               float *__restrict__ out, uint64_t n) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(tc_raw + ((1024 - (tc_smem(tc_raw) & 1023)) & 1023));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // W2 (FP32, [out][in]) -> BF16 canonical tile, one 8-element row chunk
+  // (two float4 loads, one 16-byte store) per step
+  for (int c = tid; c < kH * kH / 8; c += blockDim.x) {
+    const int row = c >> 3, j = c & 7;
+    const float4 lo = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j);
+    const float4 hi = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j + 4);
+    *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(s.b) + tc_canon_off64(row, 8 * j)) =
+        make_uint4(pack_bf16(lo.x, lo.y), pack_bf16(lo.z, lo.w), pack_bf16(hi.x, hi.y), pack_bf16(hi.z, hi.w));
+  }
+  for (int i = tid; i < 2 * kH; i += blockDim.x) s.w1[i] = params[kOffW1 + i];
+  for (int i = tid; i < kH; i += blockDim.x) {
+    s.b1[i] = params[kOffB1 + i];
+    s.b2[i] = params[kOffB2 + i];
+    s.w3[i] = params[kOffW3 + i];
+  }
+  if (tid == 0) {
+    s.b3 = params[kOffB3];
+    tc_mbar_init(tc_smem(&s.mbar[0]), 1);
+    tc_mbar_init(tc_smem(&s.mbar[1]), 1);
+  }
+  if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTcCols);
+  tc_fence_smem_to_async();  // W2 for the MMAs
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = s.tmem, b_base = tc_smem(s.b);
+  const uint64_t ntiles = (n + kTcRows - 1) / kTcRows, step = gridDim.x;
+  auto features = [&](uint64_t tile, float &x0, float &x1) {
+    const uint64_t i = tile * kTcRows + tid;
+    x0 = i < n ? mlp_feature_u(u[i]) : 0.f;
+    x1 = i < n ? mlp_feature_lam(lam[i]) : 0.f;
+  };
+  if (blockIdx.x < ntiles) {  // first tile: layer 1 and its MMA
+    float x0, x1;
+    features(blockIdx.x, x0, x1);
+    mlp_tc_layer1(s, s.a[0], tid, x0, x1);
+    tc_fence_smem_to_async();
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    if (tid == 0) mlp_tc_issue(tmem, tc_smem(s.a[0]), b_base, tc_smem(&s.mbar[0]));
+  }
+  uint32_t j = 0;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += step, ++j) {
+    const uint32_t cur = j & 1, nxt = cur ^ 1;
+    if (tile + step < ntiles) {  // the next tile's layer 1 and MMA while this MMA runs
+      float x0, x1;
+      features(tile + step, x0, x1);
+      mlp_tc_layer1(s, s.a[nxt], tid, x0, x1);
+      tc_fence_smem_to_async();
+      tc_fence_before_sync();
+      __syncthreads();
+      tc_fence_after_sync();
+      if (tid == 0) mlp_tc_issue(tmem + kH * nxt, tc_smem(s.a[nxt]), b_base, tc_smem(&s.mbar[nxt]));
+    }
+    // warp-uniform, as the TMEM loads below are warp-collective
+    const bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar[cur]), (j >> 1) & 1));
+    tc_fence_after_sync();
+    float y = __int_as_float(0x7fc00000);
+    if (done) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < kH; c += 16) {
+        float v[16];
+        tc_ld16(tmem + kH * cur + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc = fmaf(s.w3[c + q], tanh_fast(v[q] + s.b2[c + q]), acc);
+      }
+      y = acc + s.b3;
+    }
+    const uint64_t i = tile * kTcRows + tid;
+    if (i < n) out[i] = y;
+    tc_fence_before_sync();
+    __syncthreads();  // this tile's H1 and accumulator are reused two tiles on
+    tc_fence_after_sync();
+    if (!__syncthreads_and(done)) break;
+  }
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, kTcCols);
 }
 
 // ------------------------------------------------------------------ training
@@ -458,9 +577,13 @@ extern "C" aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_d
   if (!sur_ok(s)) return AICDF_ERR_ARG;
   if (n == 0) return AICDF_OK;
   if (!u_dev || !lam_dev || !p_out_dev) return AICDF_ERR_ARG;
-  const int cap = sm_count() * resident_blocks((const void *)k_mlp_eval, kMlpThreads);
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + kMlpThreads - 1) / kMlpThreads, cap));
-  k_mlp_eval<<<grid, kMlpThreads, 0, (cudaStream_t)stream>>>(s->params, u_dev, lam_dev, p_out_dev, n);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+  if (attr != cudaSuccess) return cuda_fail();
+  // persistent: at most 4 CTAs per SM (the padded shared memory sees to it)
+  const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sm_count() * 4));
+  k_mlp_eval<<<grid, kTcRows, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, u_dev, lam_dev, p_out_dev, n);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 

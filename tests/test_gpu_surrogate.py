@@ -216,3 +216,58 @@ def test_cir_exact_mean_and_surrogate_gain(P, trained):
     assert res[P.CIR_DIFF][1] < res[P.CIR_DIFF_GAUSS][1] / 4, res
     # same uniforms: E[X^] - E[X~] from the DIFF kind equals the difference of means
     assert abs(res[P.CIR_DIFF][0] - (res[P.CIR_EXACT][0] - res[P.CIR_SURROGATE][0])) < 1e-9
+
+
+def test_eval_kernel_matches_path_kernel_surrogate(P, orc):
+    """The batched evaluation (tcgen05 MMA, TMEM accumulator, tiles of 128)
+    and the CIR path kernel's warp-level evaluation (mma.sync) compute the
+    same network: a one-step surrogate path X_1 = c max(h + 2 sqrt(h) P~, 0)
+    with h = lambda + nu equals the same formula on the evaluation kernel's P~
+    at that path's uniform, to FP32 rounding."""
+    import torch
+    rng = np.random.default_rng(5)
+    s = P.Surrogate(NU_CFG, seed=0)
+    s.set_params(_random_params(rng))
+    kappa, theta, sigma, X0 = 0.5, 0.04, 0.3, 0.04
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=X0, T=1.0, K=0.0, mu=0.0, sigma=sigma,
+                       kappa=kappa, theta=theta, discount=1.0)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    c = sigma ** 2 * (-math.expm1(-kappa)) / (4 * kappa)
+    e = math.exp(-kappa)
+    nu32 = np.float32(4 * kappa * theta / sigma ** 2)
+    lam = np.float32(max(np.float32(X0), np.float32(0)) * np.float32(e / c))
+    seed, tag, m = 3, 7, 64
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    u = np.array([orc.u01(int(orc.philox4([0, p, 0, tag], key, 32)[0])) for p in range(m)], dtype=np.float32)
+    pt = torch.zeros(m, device="cuda")
+    s.eval(torch.from_numpy(u).cuda(), torch.full((m,), float(lam), device="cuda"), pt)
+    pt = pt.cpu().numpy()
+    h = np.float32(lam + nu32)
+    want = np.float32(c) * np.maximum(np.float32(2) * np.sqrt(h) * pt + h, np.float32(0))
+    for p in range(m):
+        P.cir_level(prm, s, 0, P.CIR_SURROGATE, 1, sums, ws, st, path_offset=p, seed=seed, tag=tag)
+        got = sums[0].item()
+        assert got == pytest.approx(float(want[p]), rel=2e-6, abs=1e-9), (p, got, want[p])
+    assert st.item() == 0
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 40000])
+def test_eval_ragged_tiles(P, orc, n):
+    """Tiles of 128 samples with ragged ends, several tiles per CTA: every
+    output is written once and agrees with the oracle's network."""
+    import torch
+    rng = np.random.default_rng(n)
+    s = P.Surrogate(NU_CFG, seed=0)
+    p = _random_params(rng)
+    s.set_params(p)
+    u = orc.uniforms(11, 0, n)
+    lam = np.exp(rng.uniform(-4.0, 4.0, n)).astype(np.float32)
+    out = torch.full((n + 64,), float("inf"), device="cuda")
+    s.eval(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), out[:n])
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isinf(got[n:]))
+    idx = np.unique(np.concatenate([np.arange(min(n, 300)), rng.integers(0, n, 200), [n - 1]]))
+    ref = orc.mlp_forward(_oracle_params(p), _features(u[idx].astype(np.float64), lam[idx].astype(np.float64)))
+    assert np.all(np.abs(got[idx] - ref) <= 0.03 + 0.01 * np.abs(ref))
