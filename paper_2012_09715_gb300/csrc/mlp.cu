@@ -2,12 +2,11 @@
 // P~(U; lambda) ~ P_nu(U; nu / (lambda + nu)), so that
 // C~^{-1}_nu(U; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~.
 //
-// Kernels: batched evaluation (the 64 x 64 layer as tcgen05 MMAs into a TMEM
-// accumulator), a fused forward + backward training step (the three 64 x 64
-// products -- layer 2, dH1 = dZ2 W2 and dW2 = dZ2^T H1 -- as warp-level
-// mma.sync, BF16 with FP32 accumulation), a fixed-order reduction of the
-// per-block gradients with an Adam update of FP32 master weights, and the
-// generation of exact training targets with the FP64 root finder.
+// Kernels: batched evaluation and a fused forward + backward training step,
+// both with their 64-wide products (layer 2, dH1 = dZ2 W2, dW2 = dZ2^T H1) as
+// tcgen05 MMAs in BF16 into TMEM FP32 accumulators; a fixed-order reduction
+// of the per-block gradients with an Adam update of FP32 master weights; and
+// the generation of exact training targets with the FP64 root finder.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,16 +24,8 @@
 
 namespace aicdf {
 
-constexpr int kMlpThreads = 256;               // 8 warps = 256 samples per block
-constexpr int kMlpWarps = kMlpThreads / 32;
 constexpr int kGradSlots = kMlpParams;         // per-block partial: params + loss at kLossSlot
 constexpr int kLossSlot = kOffB3 + 1;          // 4417
-// dynamic shared-memory layout of the training kernel (16-byte aligned parts)
-constexpr size_t kTileBytes = sizeof(__nv_bfloat16) * 32 * kHPad;
-constexpr size_t kTrainOffH = (sizeof(MlpSmem) + 15) & ~(size_t)15;
-constexpr size_t kTrainOffDZ = kTrainOffH + kMlpWarps * kTileBytes;
-constexpr size_t kTrainOffW = kTrainOffDZ + kMlpWarps * kTileBytes;
-constexpr size_t kTrainSmem = kTrainOffW + sizeof(float) * kMlpWarps * (4 * kH + 2);
 
 // ------------------------------------------------------------------ evaluation
 // Batched evaluation on tcgen05: a CTA of 128 threads takes tiles of 128
@@ -174,240 +165,249 @@ __global__ void __launch_bounds__(kTcRows)
 }
 
 // ------------------------------------------------------------------ training
-// One block = 256 consecutive samples of the batch.  Writes the block's
-// gradient of sum_i (y_i - t_i)^2 * scale and its loss sum to partial[blockIdx].
-__global__ void __launch_bounds__(kMlpThreads)
+// One CTA = 128 consecutive samples of the batch (thread = sample = row),
+// the three 64-wide products on tcgen05 with TMEM accumulators:
+//   Z2  = H1 W2^T      (M 128 samples, N 64, K 64)   TMEM columns   0..63
+//   dH1 = dZ2 W2       (M 128 samples, N 64, K 64)   TMEM columns  64..127
+//   dW2 = dZ2^T H1     (M 64 outputs padded to 128 with zero rows, N 64,
+//                       K 128 samples)               TMEM columns 128..191
+// BF16 operands in the canonical K-major shared layout (H1^T and dZ2^T are
+// written column by column); everything else in FP32.  The column sums over
+// the CTA's samples (gradients of w3, b2, b1, W1) go through a transposing
+// shared buffer and are summed in sample order, so the partials are
+// deterministic.  Writes the CTA's gradient of sum_i (y_i - t_i)^2 * scale
+// and its loss sum to partial[blockIdx].
+constexpr uint32_t kTrainCols = 256;  // TMEM columns (three 64-column accumulators)
+
+struct MlpTrainSmem {
+  __nv_bfloat16 w2k[kH * kH];           // W2 [n][k]: B of Z2
+  __nv_bfloat16 w2t[kH * kH];           // W2^T [k][n]: B of dH1
+  __nv_bfloat16 h1[kTcRows * kH];       // H1 [m][k]: A of Z2
+  __nv_bfloat16 dz2[kTcRows * kH];      // dZ2 [m][n]: A of dH1
+  __nv_bfloat16 dz2t[kTcRows * kTcRows];  // dZ2^T [n][m], rows 64..127 zero: A of dW2
+  __nv_bfloat16 h1t[kH * kTcRows];      // H1^T [k][m]: B of dW2
+  float red[kTcRows][kH + 1];           // column sums (row pitch 65: no bank conflicts)
+  float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
+  float wsum[kTcRows / 32][2];          // per-warp sums of dy and err^2
+  unsigned long long mbar;
+  uint32_t tmem;
+};
+constexpr size_t kTrainSmem = sizeof(MlpTrainSmem) + 1024;
+
+// byte offset of (r, k) in a canonical K-major tile with K = 128
+__device__ __forceinline__ uint32_t canon_off128(int r, int k) {
+  return (uint32_t)((r >> 3) * 2048 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Column sums of red[0..127][c] in sample order for c < 64 (threads 0..63);
+// every thread must call (two barriers).
+__device__ __forceinline__ float train_colsum(MlpTrainSmem &s, const float (&v)[kH]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < kH; ++c) s.red[tid][c] = v[c];
+  __syncthreads();
+  float a = 0.f;
+  if (tid < kH)
+    for (int m = 0; m < kTcRows; ++m) a += s.red[m][tid];
+  __syncthreads();
+  return a;
+}
+
+__global__ void __launch_bounds__(kTcRows)
     k_mlp_train(const float *__restrict__ params, const float *__restrict__ u,
                 const float *__restrict__ lam, const float *__restrict__ target, uint64_t begin,
                 uint64_t count, float scale, float *__restrict__ partial) {
-  // dynamic shared memory (> 48 KB): MlpSmem | H1 tiles | dZ2 tiles | per-warp partials
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
-  auto hs = reinterpret_cast<__nv_bfloat16(*)[32 * kHPad]>(smem_raw + kTrainOffH);    // H1 (BF16)
-  auto dzs = reinterpret_cast<__nv_bfloat16(*)[32 * kHPad]>(smem_raw + kTrainOffDZ);  // dZ2 (BF16)
-  auto wpart = reinterpret_cast<float(*)[4 * kH + 2]>(smem_raw + kTrainOffW);          // gw3 gb2 gb1 gW1 ...
-  mlp_stage(params, s);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const uint64_t i = begin + (uint64_t)blockIdx.x * kMlpThreads + threadIdx.x;
-  const bool ok = (uint64_t)blockIdx.x * kMlpThreads + threadIdx.x < count;
+  extern __shared__ __align__(1024) unsigned char tr_raw[];
+  MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(tr_raw + ((1024 - (tc_smem(tr_raw) & 1023)) & 1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *w2k = reinterpret_cast<unsigned char *>(s.w2k), *w2t = reinterpret_cast<unsigned char *>(s.w2t);
+  unsigned char *h1 = reinterpret_cast<unsigned char *>(s.h1), *dz2 = reinterpret_cast<unsigned char *>(s.dz2);
+  unsigned char *dz2t = reinterpret_cast<unsigned char *>(s.dz2t), *h1t = reinterpret_cast<unsigned char *>(s.h1t);
+  // ---- stage W2 both ways, the zero rows of dZ2^T and the FP32 vectors
+  for (int c = tid; c < kH * kH / 8; c += blockDim.x) {
+    const int row = c >> 3, j = c & 7;
+    const float4 lo = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j);
+    const float4 hi = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j + 4);
+    *reinterpret_cast<uint4 *>(w2k + tc_canon_off64(row, 8 * j)) =
+        make_uint4(pack_bf16(lo.x, lo.y), pack_bf16(lo.z, lo.w), pack_bf16(hi.x, hi.y), pack_bf16(hi.z, hi.w));
+    const float w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<__nv_bfloat16 *>(w2t + tc_canon_off64(8 * j + q, row)) = __float2bfloat16_rn(w[q]);
+  }
+  for (int c = tid; c < (kTcRows - kH) * kTcRows / 8; c += blockDim.x)  // rows 64..127 of dZ2^T
+    *reinterpret_cast<uint4 *>(dz2t + (size_t)(kH / 8) * 2048 + 16 * (size_t)c) = make_uint4(0u, 0u, 0u, 0u);
+  for (int c = tid; c < 2 * kH; c += blockDim.x) s.w1[c] = params[kOffW1 + c];
+  for (int c = tid; c < kH; c += blockDim.x) {
+    s.b1[c] = params[kOffB1 + c];
+    s.b2[c] = params[kOffB2 + c];
+    s.w3[c] = params[kOffW3 + c];
+  }
+  if (tid == 0) {
+    s.b3 = params[kOffB3];
+    tc_mbar_init(tc_smem(&s.mbar), 1);
+  }
+  if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTrainCols);
+  // ---- layer 1: H1 (BF16) by rows and by columns
+  const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + tid;
+  const bool ok = m_idx < count;
+  const uint64_t i = begin + m_idx;
   const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
   const float x1 = ok ? mlp_feature_lam(lam[i]) : 0.f;
   const float tg = ok ? target[i] : 0.f;
-  __nv_bfloat16 *hw = hs[warp], *dw = dzs[warp];
-  // ---- forward
-  mlp_layer1(s, x0, x1, hw);
-  __syncwarp();
-  float acc[2][8][4];
-  mlp_layer2_mma(s, hw, acc);
-  float part[4];
-  mlp_layer3_partial(s, acc, part);  // acc now holds h2
-  const float y = mlp_gather_output(s, part);
-  const float err = ok ? y - tg : 0.f;
-  const float dy = 2.0f * err * scale;
-  // dy, x0, x1 of the four rows this lane holds in fragment layout
-  float dyr[4], x0r[4], x1r[4];
+  __syncthreads();  // vectors staged
 #pragma unroll
-  for (int ri = 0; ri < 4; ++ri) {
-    const int r = 16 * (ri >> 1) + g + 8 * (ri & 1);
-    dyr[ri] = __shfl_sync(0xffffffffu, dy, r);
-    x0r[ri] = __shfl_sync(0xffffffffu, x0, r);
-    x1r[ri] = __shfl_sync(0xffffffffu, x1, r);
-  }
-  // ---- layer 3 and activation 2: gw3, gb2, dZ2
-  float gw3[8][2], gb2[8][2];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) gw3[nt][j] = gb2[nt][j] = 0.f;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int ri = 2 * mt + hh;
-        const int r = 16 * mt + g + 8 * hh;
-        const int c = 8 * nt + 2 * t;
-        const float h0 = acc[mt][nt][2 * hh], h1 = acc[mt][nt][2 * hh + 1];
-        gw3[nt][0] = fmaf(dyr[ri], h0, gw3[nt][0]);
-        gw3[nt][1] = fmaf(dyr[ri], h1, gw3[nt][1]);
-        const float d0 = dyr[ri] * s.w3[c] * (1.f - h0 * h0);
-        const float d1 = dyr[ri] * s.w3[c + 1] * (1.f - h1 * h1);
-        gb2[nt][0] += d0;
-        gb2[nt][1] += d1;
-        *reinterpret_cast<uint32_t *>(dw + r * kHPad + c) = pack_bf16(d0, d1);
-      }
-    }
-  __syncwarp();
-  // ---- dH1 = dZ2 W2 (tensor cores), B fragments from W2 by transposed ldmatrix
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
-#pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    uint32_t a[2][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const __nv_bfloat16 *p = dw + (16 * mt + (lane & 15)) * kHPad + 16 * ks + (lane >> 4) * 8;
-      ldsm_x4(smem_addr(p), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-    }
-#pragma unroll
-    for (int np = 0; np < 4; ++np) {
-      const int nrow = 16 * ks + (lane & 7) + ((lane >> 3) & 1) * 8;   // W2 row = contraction index
-      const int kcol = 16 * np + (lane >> 4) * 8;                       // W2 col = output index
-      uint32_t b0, b1, b2, b3;
-      ldsm_x4_t(smem_addr(s.w2 + nrow * kHPad + kcol), b0, b1, b2, b3);
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-        mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-      }
-    }
-  }
-  // ---- activation 1: dZ1 = dH1 (1 - h1^2); gb1, gW1
-  float gb1[8][2], gw1a[8][2], gw1b[8][2];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) gb1[nt][j] = gw1a[nt][j] = gw1b[nt][j] = 0.f;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int ri = 2 * mt + hh;
-        const int r = 16 * mt + g + 8 * hh;
-        const int c = 8 * nt + 2 * t;
-        const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162 *>(hw + r * kHPad + c);
-        const float h0 = __bfloat162float(hv.x), h1 = __bfloat162float(hv.y);
-        const float d0 = acc[mt][nt][2 * hh] * (1.f - h0 * h0);
-        const float d1 = acc[mt][nt][2 * hh + 1] * (1.f - h1 * h1);
-        gb1[nt][0] += d0;
-        gb1[nt][1] += d1;
-        gw1a[nt][0] = fmaf(d0, x0r[ri], gw1a[nt][0]);
-        gw1a[nt][1] = fmaf(d1, x0r[ri], gw1a[nt][1]);
-        gw1b[nt][0] = fmaf(d0, x1r[ri], gw1b[nt][0]);
-        gw1b[nt][1] = fmaf(d1, x1r[ri], gw1b[nt][1]);
-      }
-  // reduce the per-lane column partials over the 8 groups (lanes with equal t)
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int o = 4; o < 32; o <<= 1) {
-        gw3[nt][j] += __shfl_xor_sync(0xffffffffu, gw3[nt][j], o);
-        gb2[nt][j] += __shfl_xor_sync(0xffffffffu, gb2[nt][j], o);
-        gb1[nt][j] += __shfl_xor_sync(0xffffffffu, gb1[nt][j], o);
-        gw1a[nt][j] += __shfl_xor_sync(0xffffffffu, gw1a[nt][j], o);
-        gw1b[nt][j] += __shfl_xor_sync(0xffffffffu, gw1b[nt][j], o);
-      }
-  float* wp = wpart[warp];
-  if (g == 0) {
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int c = 8 * nt + 2 * t + j;
-        wp[c] = gw3[nt][j];
-        wp[kH + c] = gb2[nt][j];
-        wp[2 * kH + c] = gb1[nt][j];
-        // gW1 stored after the block-level reduction (two values per column)
-        wp[3 * kH + c] = gw1a[nt][j];
-      }
-  }
-  // gW1[c][1] and the loss need more room: reuse the dy row slots via shuffles
-  float loss = err * err, sdy = dy;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    loss += __shfl_xor_sync(0xffffffffu, loss, o);
-    sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
-  }
-  if (lane == 0) {
-    wp[4 * kH] = sdy;
-    wp[4 * kH + 1] = loss;
-  }
-  __syncthreads();  // all warps' dZ2 and H1 tiles and partials are in shared memory
-  float *out = partial + (size_t)blockIdx.x * kGradSlots;
-  // fixed-order block sums of the small gradients
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
-    float a3 = 0.f, a2 = 0.f, a1 = 0.f, aw = 0.f;
-    for (int w = 0; w < kMlpWarps; ++w) {
-      a3 += wpart[w][c];
-      a2 += wpart[w][kH + c];
-      a1 += wpart[w][2 * kH + c];
-      aw += wpart[w][3 * kH + c];
-    }
-    out[kOffW3 + c] = a3;
-    out[kOffB2 + c] = a2;
-    out[kOffB1 + c] = a1;
-    out[kOffW1 + 2 * c] = aw;
-  }
-  if (threadIdx.x == 0) {
-    float a = 0.f, l = 0.f;
-    for (int w = 0; w < kMlpWarps; ++w) {
-      a += wpart[w][4 * kH];
-      l += wpart[w][4 * kH + 1];
-    }
-    out[kOffB3] = a;
-    out[kLossSlot] = l;
-  }
-  __syncthreads();  // wpart reused below for gW1[c][1]
-  if (g == 0) {
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) wpart[warp][8 * nt + 2 * t + j] = gw1b[nt][j];
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
-    float aw = 0.f;
-    for (int w = 0; w < kMlpWarps; ++w) aw += wpart[w][c];
-    out[kOffW1 + 2 * c + 1] = aw;
-  }
-  // ---- dW2[n][k] = sum_s dZ2[s][n] H1[s][k] over the block's 256 samples
-  // warp w: n rows 16 (w>>1) .. +15, k cols 32 (w&1) .. +31 (4 n-tiles)
-  {
-    const int mtn = warp >> 1, kb = 32 * (warp & 1);
-    float d[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) d[q][e] = 0.f;
-    for (int ks = 0; ks < kMlpThreads / 16; ++ks) {
-      const __nv_bfloat16 *dt = dzs[ks >> 1] + (ks & 1) * 16 * kHPad;   // 16 samples
-      const __nv_bfloat16 *ht = hs[ks >> 1] + (ks & 1) * 16 * kHPad;
-      uint32_t a0, a1, a2, a3;
-      {
-        const int srow = (lane & 7) + ((lane >> 4) << 3);
-        const int ncol = 16 * mtn + ((lane >> 3) & 1) * 8;
-        ldsm_x4_t(smem_addr(dt + srow * kHPad + ncol), a0, a1, a2, a3);
-      }
-#pragma unroll
-      for (int p2 = 0; p2 < 2; ++p2) {
-        const int srow = (lane & 7) + ((lane >> 3) & 1) * 8;
-        const int kcol = kb + 16 * p2 + (lane >> 4) * 8;
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(smem_addr(ht + srow * kHPad + kcol), b0, b1, b2, b3);
-        mma_bf16(d[2 * p2], a0, a1, a2, a3, b0, b1);
-        mma_bf16(d[2 * p2 + 1], a0, a1, a2, a3, b2, b3);
-      }
-    }
+  for (int j = 0; j < kH / 8; ++j) {
+    uint32_t w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int n0 = 16 * mtn + g, k0 = kb + 8 * q + 2 * t;
-      out[kOffW2 + n0 * kH + k0] = d[q][0];
-      out[kOffW2 + n0 * kH + k0 + 1] = d[q][1];
-      out[kOffW2 + (n0 + 8) * kH + k0] = d[q][2];
-      out[kOffW2 + (n0 + 8) * kH + k0 + 1] = d[q][3];
+      const int k = 8 * j + 2 * q;
+      const float a = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
+      const float b = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
+      w[q] = pack_bf16(a, b);
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k, tid)) =
+          *reinterpret_cast<const __nv_bfloat16 *>(&w[q]);
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k + 1, tid)) =
+          *(reinterpret_cast<const __nv_bfloat16 *>(&w[q]) + 1);
+    }
+    *reinterpret_cast<uint4 *>(h1 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  tc_fence_smem_to_async();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = s.tmem;
+  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kH);
+  if (tid == 0) {
+#pragma unroll
+    for (int kk = 0; kk < kH / 16; ++kk)
+      tc_mma_bf16(tmem, tc_desc(tc_smem(h1) + 256 * kk, 128, 1024), tc_desc(tc_smem(w2k) + 256 * kk, 128, 1024),
+                  idesc, kk > 0);
+    tc_commit(tc_smem(&s.mbar));
+  }
+  bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), 0));
+  tc_fence_after_sync();
+  // ---- layer 2 activation, output, dy; dZ2
+  float h2[kH], v[kH];
+  if (done) {
+#pragma unroll
+    for (int c = 0; c < kH; c += 16) {
+      float z[16];
+      tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, z);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) h2[c + q] = tanh_fast(z[q] + s.b2[c + q]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kH; ++c) h2[c] = 0.f;
+  }
+  float y = s.b3;
+#pragma unroll
+  for (int c = 0; c < kH; ++c) y = fmaf(s.w3[c], h2[c], y);
+  const float err = ok ? y - tg : 0.f;
+  const float dy = 2.0f * err * scale;
+#pragma unroll
+  for (int j = 0; j < kH / 8; ++j) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 8 * j + 2 * q;
+      const float d0 = dy * s.w3[c] * (1.f - h2[c] * h2[c]);
+      const float d1 = dy * s.w3[c + 1] * (1.f - h2[c + 1] * h2[c + 1]);
+      v[c] = d0;
+      v[c + 1] = d1;
+      w[q] = pack_bf16(d0, d1);
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c, tid)) = *reinterpret_cast<const __nv_bfloat16 *>(&w[q]);
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c + 1, tid)) =
+          *(reinterpret_cast<const __nv_bfloat16 *>(&w[q]) + 1);
+    }
+    *reinterpret_cast<uint4 *>(dz2 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  tc_fence_smem_to_async();
+  float *out = partial + (size_t)blockIdx.x * kGradSlots;
+  {
+    const float gb2 = train_colsum(s, v);  // barriers: dZ2 tiles complete after the first
+    if (tid < kH) out[kOffB2 + tid] = gb2;
+  }
+  tc_fence_after_sync();
+  if (tid == 0) {  // dH1 = dZ2 W2 and dW2 = dZ2^T H1
+#pragma unroll
+    for (int kk = 0; kk < kH / 16; ++kk)
+      tc_mma_bf16(tmem + 64, tc_desc(tc_smem(dz2) + 256 * kk, 128, 1024),
+                  tc_desc(tc_smem(w2t) + 256 * kk, 128, 1024), idesc, kk > 0);
+#pragma unroll
+    for (int kk = 0; kk < kTcRows / 16; ++kk)
+      tc_mma_bf16(tmem + 128, tc_desc(tc_smem(dz2t) + 256 * kk, 128, 2048),
+                  tc_desc(tc_smem(h1t) + 256 * kk, 128, 2048), idesc, kk > 0);
+    tc_commit(tc_smem(&s.mbar));
+  }
+  {
+#pragma unroll
+    for (int c = 0; c < kH; ++c) v[c] = dy * h2[c];
+    const float gw3 = train_colsum(s, v);
+    if (tid < kH) out[kOffW3 + tid] = gw3;
+  }
+  done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), 1)) && done;
+  tc_fence_after_sync();
+  // ---- dZ1 = dH1 (1 - h1^2), h1 as stored (BF16)
+  float dz1[kH];
+#pragma unroll
+  for (int c = 0; c < kH; c += 16) {
+    float d[16];
+    if (done) tc_ld16(tmem + 64 + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, d);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float hv = __bfloat162float(
+          *reinterpret_cast<const __nv_bfloat16 *>(h1 + tc_canon_off64(tid, c + q)));
+      dz1[c + q] = done ? d[q] * (1.f - hv * hv) : 0.f;
     }
   }
+  {
+    const float gb1 = train_colsum(s, dz1);
+    if (tid < kH) out[kOffB1 + tid] = gb1;
+#pragma unroll
+    for (int c = 0; c < kH; ++c) v[c] = dz1[c] * x0;
+    const float ga = train_colsum(s, v);
+    if (tid < kH) out[kOffW1 + 2 * tid] = ga;
+#pragma unroll
+    for (int c = 0; c < kH; ++c) v[c] = dz1[c] * x1;
+    const float gb = train_colsum(s, v);
+    if (tid < kH) out[kOffW1 + 2 * tid + 1] = gb;
+  }
+  // ---- dW2 rows n = lanes 0..63 (warps 0 and 1); every warp runs the
+  // warp-collective loads, warps 2 and 3 read the zero rows
+#pragma unroll
+  for (int c = 0; c < kH; c += 16) {
+    float d[16];
+    if (done) tc_ld16(tmem + 128 + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, d);
+    if (tid < kH) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) out[kOffW2 + tid * kH + c + q] = done ? d[q] : __int_as_float(0x7fc00000);
+    }
+  }
+  // ---- sums of dy (gradient of b3) and err^2, in a fixed order
+  float sdy = dy, loss = err * err;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
+    loss += __shfl_xor_sync(0xffffffffu, loss, o);
+  }
+  if (lane == 0) {
+    s.wsum[warp][0] = sdy;
+    s.wsum[warp][1] = loss;
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (tid == 0) {
+    float a = 0.f, l = 0.f;
+    for (int w = 0; w < kTcRows / 32; ++w) {
+      a += s.wsum[w][0];
+      l += s.wsum[w][1];
+    }
+    out[kOffB3] = done ? a : __int_as_float(0x7fc00000);
+    out[kLossSlot] = l;
+  }
+  if (warp == 0) tc_dealloc(tmem, kTrainCols);
 }
 
 // Sum per-block gradients in block order and take one Adam step.
@@ -600,7 +600,7 @@ static aicdf_status ensure_partials(aicdf_surrogate_s *s, int blocks) {
 static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, const float *lam,
                                       const float *target, uint64_t begin, uint64_t count,
                                       cudaStream_t st, int *blocks_out) {
-  const int blocks = (int)((count + kMlpThreads - 1) / kMlpThreads);
+  const int blocks = (int)((count + kTcRows - 1) / kTcRows);
   aicdf_status rc = ensure_partials(s, blocks);
   if (rc != AICDF_OK) return rc;
   static bool smem_set = false;  // opt in to > 48 KB of dynamic shared memory once
@@ -610,8 +610,8 @@ static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, cons
       return cuda_fail();
     smem_set = true;
   }
-  k_mlp_train<<<blocks, kMlpThreads, kTrainSmem, st>>>(s->params, u, lam, target, begin, count,
-                                                       1.0f / (float)count, s->partial);
+  k_mlp_train<<<blocks, kTcRows, kTrainSmem, st>>>(s->params, u, lam, target, begin, count, 1.0f / (float)count,
+                                                   s->partial);
   *blocks_out = blocks;
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
