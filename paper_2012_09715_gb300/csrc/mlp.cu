@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kTcRows)
 // BF16 operands in the canonical K-major shared layout (H1^T and dZ2^T are
 // written column by column); everything else in FP32.  The column sums over
 // the CTA's samples (gradients of w3, b2, b1, W1) go through a transposing
-// shared buffer and are summed in sample order, so the partials are
+// shared buffer and are summed in a fixed order, so the partials are
 // deterministic.  Writes the CTA's gradient of sum_i (y_i - t_i)^2 * scale
 // and its loss sum to partial[blockIdx].
 constexpr uint32_t kTrainCols = 256;  // TMEM columns (three 64-column accumulators)
@@ -186,7 +186,7 @@ struct MlpTrainSmem {
   __nv_bfloat16 dz2[kTcRows * kH];      // dZ2 [m][n]: A of dH1
   __nv_bfloat16 dz2t[kTcRows * kTcRows];  // dZ2^T [n][m], rows 64..127 zero: A of dW2
   __nv_bfloat16 h1t[kH * kTcRows];      // H1^T [k][m]: B of dW2
-  float red[kTcRows][kH + 1];           // column sums (row pitch 65: no bank conflicts)
+  float red[kTcRows][2 * kH + 1];       // column sums, two 64-wide quantities per pass (pitch 129)
   float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
   float wsum[kTcRows / 32][2];          // per-warp sums of dy and err^2
   unsigned long long mbar;
@@ -199,16 +199,21 @@ __device__ __forceinline__ uint32_t canon_off128(int r, int k) {
   return (uint32_t)((r >> 3) * 2048 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Column sums of red[0..127][c] in sample order for c < 64 (threads 0..63);
-// every thread must call (two barriers).
-__device__ __forceinline__ float train_colsum(MlpTrainSmem &s, const float (&v)[kH]) {
+// Column sums in a fixed order: thread c sums red[0..127][c] (c < 128 for two
+// 64-wide quantities at once) as eight interleaved partial sums combined
+// pairwise.  The caller has filled red and passed a
+// barrier; ends with a barrier so that red may be refilled.
+__device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
   const int tid = threadIdx.x;
-#pragma unroll
-  for (int c = 0; c < kH; ++c) s.red[tid][c] = v[c];
-  __syncthreads();
   float a = 0.f;
-  if (tid < kH)
-    for (int m = 0; m < kTcRows; ++m) a += s.red[m][tid];
+  if (tid < ncols) {
+    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // rows m = 8 r + q into p[q]: 8 independent chains
+#pragma unroll 4
+    for (int r = 0; r < kTcRows / 8; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] += s.red[8 * r + q][tid];
+    a = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+  }
   __syncthreads();
   return a;
 }
@@ -323,14 +328,17 @@ __global__ void __launch_bounds__(kTcRows)
     }
     *reinterpret_cast<uint4 *>(dz2 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  tc_fence_smem_to_async();
-  float *out = partial + (size_t)blockIdx.x * kGradSlots;
-  {
-    const float gb2 = train_colsum(s, v);  // barriers: dZ2 tiles complete after the first
-    if (tid < kH) out[kOffB2 + tid] = gb2;
+  // FP32 rows for the column sums: dZ2 (gradient of b2) and dy h2 (of w3)
+#pragma unroll
+  for (int c = 0; c < kH; ++c) {
+    s.red[tid][c] = v[c];
+    s.red[tid][kH + c] = dy * h2[c];
   }
+  tc_fence_smem_to_async();
+  tc_fence_before_sync();
+  __syncthreads();  // dZ2 tiles and red rows complete
   tc_fence_after_sync();
-  if (tid == 0) {  // dH1 = dZ2 W2 and dW2 = dZ2^T H1
+  if (tid == 0) {  // dH1 = dZ2 W2 and dW2 = dZ2^T H1, in flight during the sums below
 #pragma unroll
     for (int kk = 0; kk < kH / 16; ++kk)
       tc_mma_bf16(tmem + 64, tc_desc(tc_smem(dz2) + 256 * kk, 128, 1024),
@@ -341,11 +349,10 @@ __global__ void __launch_bounds__(kTcRows)
                   tc_desc(tc_smem(h1t) + 256 * kk, 128, 2048), idesc, kk > 0);
     tc_commit(tc_smem(&s.mbar));
   }
+  float *out = partial + (size_t)blockIdx.x * kGradSlots;
   {
-#pragma unroll
-    for (int c = 0; c < kH; ++c) v[c] = dy * h2[c];
-    const float gw3 = train_colsum(s, v);
-    if (tid < kH) out[kOffW3 + tid] = gw3;
+    const float a = train_colsum(s, 2 * kH);
+    out[(tid < kH ? kOffB2 : kOffW3 - kH) + tid] = a;
   }
   done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), 1)) && done;
   tc_fence_after_sync();
@@ -362,17 +369,22 @@ __global__ void __launch_bounds__(kTcRows)
       dz1[c + q] = done ? d[q] * (1.f - hv * hv) : 0.f;
     }
   }
+#pragma unroll
+  for (int c = 0; c < kH; ++c) {
+    s.red[tid][c] = dz1[c];
+    s.red[tid][kH + c] = dz1[c] * x0;
+  }
+  __syncthreads();
   {
-    const float gb1 = train_colsum(s, dz1);
-    if (tid < kH) out[kOffB1 + tid] = gb1;
+    const float a = train_colsum(s, 2 * kH);  // gradient of b1, then of W1[., 0]
+    out[tid < kH ? kOffB1 + tid : kOffW1 + 2 * (tid - kH)] = a;
+  }
 #pragma unroll
-    for (int c = 0; c < kH; ++c) v[c] = dz1[c] * x0;
-    const float ga = train_colsum(s, v);
-    if (tid < kH) out[kOffW1 + 2 * tid] = ga;
-#pragma unroll
-    for (int c = 0; c < kH; ++c) v[c] = dz1[c] * x1;
-    const float gb = train_colsum(s, v);
-    if (tid < kH) out[kOffW1 + 2 * tid + 1] = gb;
+  for (int c = 0; c < kH; ++c) s.red[tid][c] = dz1[c] * x1;
+  __syncthreads();
+  {
+    const float a = train_colsum(s, kH);  // gradient of W1[., 1]
+    if (tid < kH) out[kOffW1 + 2 * tid + 1] = a;
   }
   // ---- dW2 rows n = lanes 0..63 (warps 0 and 1); every warp runs the
   // warp-collective loads, warps 2 and 3 read the zero rows
