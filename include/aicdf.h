@@ -326,9 +326,10 @@ aicdf_status aicdf_ncx2_targets(double nu, float loglam_lo, float loglam_hi, uin
  * x0 = s(u)/3 with s(u) = sign(u-1/2) sqrt(-2 ln(2 min(u,1-u))) and
  * x1 = clamp(ln(lambda)/4, -1, 1); then
  * C~^{-1}_nu(u; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~(u, lambda).
- * The 64 x 64 layer runs on the tensor cores in BF16 with FP32 accumulation;
- * FP32 master weights.  The handle owns its device buffers (allocated at
- * create).  Parameter blob layout (FP32): W1[64][2] | b1[64] | W2[64 out][64 in]
+ * The 64 x 64 layer runs on the tensor cores in BF16 with FP32 accumulation
+ * (tcgen05 MMAs into tensor memory for evaluation and training; the CIR path
+ * kernel's in-loop evaluation uses warp-level MMAs); FP32 master weights.  The
+ * handle owns its device buffers (allocated at create).  Parameter blob layout (FP32): W1[64][2] | b1[64] | W2[64 out][64 in]
  * | b2[64] | w3[64] | b3, aicdf_surrogate_param_count() floats. */
 typedef struct aicdf_surrogate_s *aicdf_surrogate;
 aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_surrogate *out);
@@ -337,7 +338,9 @@ int aicdf_surrogate_param_count(void);
 aicdf_status aicdf_surrogate_get_params(aicdf_surrogate s, float *host, int cap);
 /* Replaces the weights and resets the optimiser state. */
 aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const float *host, int n);
-/* p_out_dev[i] = P~(u_dev[i], lam_dev[i]). */
+/* p_out_dev[i] = P~(u_dev[i], lam_dev[i]).  Should a tensor-core product not
+ * signal completion within the kernel's bounded wait (a fault of the device,
+ * not of the inputs), the affected outputs are NaN. */
 aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                   size_t n, float *p_out_dev, aicdf_stream_t stream);
 /* Gradient of L = mean_i (P~_i - target_i)^2 over the n samples, into

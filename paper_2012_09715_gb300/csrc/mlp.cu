@@ -269,11 +269,10 @@ __global__ void __launch_bounds__(kTcRows)
       const int k = 8 * j + 2 * q;
       const float a = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
       const float b = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
       w[q] = pack_bf16(a, b);
-      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k, tid)) =
-          *reinterpret_cast<const __nv_bfloat16 *>(&w[q]);
-      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k + 1, tid)) =
-          *(reinterpret_cast<const __nv_bfloat16 *>(&w[q]) + 1);
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k, tid)) = hb.x;
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k + 1, tid)) = hb.y;
     }
     *reinterpret_cast<uint4 *>(h1 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
@@ -321,10 +320,10 @@ __global__ void __launch_bounds__(kTcRows)
       const float d1 = dy * s.w3[c + 1] * (1.f - h2[c + 1] * h2[c + 1]);
       v[c] = d0;
       v[c + 1] = d1;
+      const __nv_bfloat162 db = __floats2bfloat162_rn(d0, d1);
       w[q] = pack_bf16(d0, d1);
-      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c, tid)) = *reinterpret_cast<const __nv_bfloat16 *>(&w[q]);
-      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c + 1, tid)) =
-          *(reinterpret_cast<const __nv_bfloat16 *>(&w[q]) + 1);
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c, tid)) = db.x;
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c + 1, tid)) = db.y;
     }
     *reinterpret_cast<uint4 *>(dz2 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
