@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -44,9 +45,13 @@ struct MlpTcSmem {
   __nv_bfloat16 a[2][kTcRows * kH];  // H1 tiles (2 x 16 KiB)
   __nv_bfloat16 b[kH * kH];          // W2 [out][in] (8 KiB)
   float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
-  unsigned long long mbar[2];
+  unsigned long long mbar[2], wbar;
   uint32_t tmem;
 };
+
+// The handle keeps W2 in BF16 in the canonical layout twice -- W2 [n][k]
+// (kW2cBytes) then W2^T [k][n] -- so that a CTA loads it with one bulk copy.
+constexpr uint32_t kW2cBytes = kH * kH * sizeof(__nv_bfloat16);
 // Dynamic shared memory per CTA, padded so that at most 4 CTAs fit an SM and
 // their TMEM (4 x 128 columns) never exceeds the SM's 512 columns.
 constexpr size_t kTcSmemBytes = 52 * 1024;
@@ -78,19 +83,14 @@ __device__ __forceinline__ void mlp_tc_issue(uint32_t d_tmem, uint32_t a_base, u
 }
 
 __global__ void __launch_bounds__(kTcRows)
-    k_mlp_eval(const float *__restrict__ params, const float *__restrict__ u, const float *__restrict__ lam,
-               float *__restrict__ out, uint64_t n) {
+    k_mlp_eval(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
+               const float *__restrict__ u, const float *__restrict__ lam, float *__restrict__ out, uint64_t n) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(tc_raw + ((1024 - (tc_smem(tc_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5;
-  // W2 (FP32, [out][in]) -> BF16 canonical tile, one 8-element row chunk
-  // (two float4 loads, one 16-byte store) per step
-  for (int c = tid; c < kH * kH / 8; c += blockDim.x) {
-    const int row = c >> 3, j = c & 7;
-    const float4 lo = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j);
-    const float4 hi = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j + 4);
-    *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(s.b) + tc_canon_off64(row, 8 * j)) =
-        make_uint4(pack_bf16(lo.x, lo.y), pack_bf16(lo.z, lo.w), pack_bf16(hi.x, hi.y), pack_bf16(hi.z, hi.w));
+  if (tid == 0) {  // W2 (BF16, canonical) by one bulk copy
+    tc_mbar_init(tc_smem(&s.wbar), 1);
+    tc_bulk_g2s(tc_smem(s.b), w2c, kW2cBytes, tc_smem(&s.wbar));
   }
   for (int i = tid; i < 2 * kH; i += blockDim.x) s.w1[i] = params[kOffW1 + i];
   for (int i = tid; i < kH; i += blockDim.x) {
@@ -104,11 +104,12 @@ __global__ void __launch_bounds__(kTcRows)
     tc_mbar_init(tc_smem(&s.mbar[1]), 1);
   }
   if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTcCols);
-  tc_fence_smem_to_async();  // W2 for the MMAs
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = s.tmem, b_base = tc_smem(s.b);
+  // the MMA issuer needs W2 in place; a copy that never lands leaves NaN outputs
+  const bool w2_ok = tid == 0 ? tc_mbar_wait(tc_smem(&s.wbar), 0) : true;
   const uint64_t ntiles = (n + kTcRows - 1) / kTcRows, step = gridDim.x;
   auto features = [&](uint64_t tile, float &x0, float &x1) {
     const uint64_t i = tile * kTcRows + tid;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kTcRows)
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    if (tid == 0) mlp_tc_issue(tmem, tc_smem(s.a[0]), b_base, tc_smem(&s.mbar[0]));
+    if (tid == 0 && w2_ok) mlp_tc_issue(tmem, tc_smem(s.a[0]), b_base, tc_smem(&s.mbar[0]));
   }
   uint32_t j = 0;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += step, ++j) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kTcRows)
       tc_fence_before_sync();
       __syncthreads();
       tc_fence_after_sync();
-      if (tid == 0) mlp_tc_issue(tmem + kH * nxt, tc_smem(s.a[nxt]), b_base, tc_smem(&s.mbar[nxt]));
+      if (tid == 0 && w2_ok) mlp_tc_issue(tmem + kH * nxt, tc_smem(s.a[nxt]), b_base, tc_smem(&s.mbar[nxt]));
     }
     // warp-uniform, as the TMEM loads below are warp-collective
     const bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar[cur]), (j >> 1) & 1));
@@ -189,9 +190,10 @@ struct MlpTrainSmem {
   float red[kTcRows][2 * kH + 1];       // column sums, two 64-wide quantities per pass (pitch 129)
   float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
   float wsum[kTcRows / 32][2];          // per-warp sums of dy and err^2
-  unsigned long long mbar;
+  unsigned long long mbar, wbar;
   uint32_t tmem;
 };
+static_assert(offsetof(MlpTrainSmem, w2t) == offsetof(MlpTrainSmem, w2k) + kW2cBytes, "W2 tiles not adjacent");
 constexpr size_t kTrainSmem = sizeof(MlpTrainSmem) + 1024;
 
 // byte offset of (r, k) in a canonical K-major tile with K = 128
@@ -219,26 +221,20 @@ __device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
 }
 
 __global__ void __launch_bounds__(kTcRows)
-    k_mlp_train(const float *__restrict__ params, const float *__restrict__ u,
-                const float *__restrict__ lam, const float *__restrict__ target, uint64_t begin,
-                uint64_t count, float scale, float *__restrict__ partial) {
+    k_mlp_train(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
+                const float *__restrict__ u, const float *__restrict__ lam, const float *__restrict__ target,
+                uint64_t begin, uint64_t count, float scale, float *__restrict__ partial) {
   extern __shared__ __align__(1024) unsigned char tr_raw[];
   MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(tr_raw + ((1024 - (tc_smem(tr_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *w2k = reinterpret_cast<unsigned char *>(s.w2k), *w2t = reinterpret_cast<unsigned char *>(s.w2t);
   unsigned char *h1 = reinterpret_cast<unsigned char *>(s.h1), *dz2 = reinterpret_cast<unsigned char *>(s.dz2);
   unsigned char *dz2t = reinterpret_cast<unsigned char *>(s.dz2t), *h1t = reinterpret_cast<unsigned char *>(s.h1t);
-  // ---- stage W2 both ways, the zero rows of dZ2^T and the FP32 vectors
-  for (int c = tid; c < kH * kH / 8; c += blockDim.x) {
-    const int row = c >> 3, j = c & 7;
-    const float4 lo = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j);
-    const float4 hi = *reinterpret_cast<const float4 *>(params + kOffW2 + row * kH + 8 * j + 4);
-    *reinterpret_cast<uint4 *>(w2k + tc_canon_off64(row, 8 * j)) =
-        make_uint4(pack_bf16(lo.x, lo.y), pack_bf16(lo.z, lo.w), pack_bf16(hi.x, hi.y), pack_bf16(hi.z, hi.w));
-    const float w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      *reinterpret_cast<__nv_bfloat16 *>(w2t + tc_canon_off64(8 * j + q, row)) = __float2bfloat16_rn(w[q]);
+  // ---- W2 and W2^T (BF16, canonical, adjacent) by one bulk copy; the zero
+  // rows of dZ2^T and the FP32 vectors by the threads
+  if (tid == 0) {
+    tc_mbar_init(tc_smem(&s.wbar), 1);
+    tc_bulk_g2s(tc_smem(w2k), w2c, 2 * kW2cBytes, tc_smem(&s.wbar));
   }
   for (int c = tid; c < (kTcRows - kH) * kTcRows / 8; c += blockDim.x)  // rows 64..127 of dZ2^T
     *reinterpret_cast<uint4 *>(dz2t + (size_t)(kH / 8) * 2048 + 16 * (size_t)c) = make_uint4(0u, 0u, 0u, 0u);
@@ -282,7 +278,9 @@ __global__ void __launch_bounds__(kTcRows)
   tc_fence_after_sync();
   const uint32_t tmem = s.tmem;
   constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kH);
-  if (tid == 0) {
+  // the MMA issuer needs W2 in place; a copy that never lands leaves NaN gradients
+  const bool w2_ok = tid == 0 ? tc_mbar_wait(tc_smem(&s.wbar), 0) : true;
+  if (tid == 0 && w2_ok) {
 #pragma unroll
     for (int kk = 0; kk < kH / 16; ++kk)
       tc_mma_bf16(tmem, tc_desc(tc_smem(h1) + 256 * kk, 128, 1024), tc_desc(tc_smem(w2k) + 256 * kk, 128, 1024),
@@ -337,7 +335,7 @@ __global__ void __launch_bounds__(kTcRows)
   tc_fence_before_sync();
   __syncthreads();  // dZ2 tiles and red rows complete
   tc_fence_after_sync();
-  if (tid == 0) {  // dH1 = dZ2 W2 and dW2 = dZ2^T H1, in flight during the sums below
+  if (tid == 0 && w2_ok) {  // dH1 = dZ2 W2 and dW2 = dZ2^T H1, in flight during the sums below
 #pragma unroll
     for (int kk = 0; kk < kH / 16; ++kk)
       tc_mma_bf16(tmem + 64, tc_desc(tc_smem(dz2) + 256 * kk, 128, 1024),
@@ -423,9 +421,9 @@ __global__ void __launch_bounds__(kTcRows)
 
 // Sum per-block gradients in block order and take one Adam step.
 __global__ void k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2,
-                           const float *__restrict__ partial, int nblocks, float lr, float b1,
-                           float b2, float eps, float bc1, float bc2, float *__restrict__ loss_out,
-                           float loss_scale) {
+                           __nv_bfloat16 *__restrict__ w2c, const float *__restrict__ partial, int nblocks,
+                           float lr, float b1, float b2, float eps, float bc1, float bc2,
+                           float *__restrict__ loss_out, float loss_scale) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p == 0 && loss_out) {
     float l = 0.f;
@@ -439,7 +437,14 @@ __global__ void k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, f
   const float v = b2 * m2[p] + (1.f - b2) * gsum * gsum;
   m1[p] = m;
   m2[p] = v;
-  params[p] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+  const float w = params[p] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+  params[p] = w;
+  if (p >= kOffW2 && p < kOffW2 + kH * kH) {  // the BF16 canonical copies of W2 and W2^T
+    const int nn = (p - kOffW2) / kH, k = (p - kOffW2) % kH;
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    w2c[tc_canon_off64(nn, k) / 2] = wb;
+    w2c[kH * kH + tc_canon_off64(k, nn) / 2] = wb;
+  }
 }
 
 // Just the gradient (summed over blocks), for the gradient check.
@@ -495,6 +500,7 @@ struct aicdf_surrogate_s {
   int device;
   double nu;
   float *params = nullptr;   // FP32 master weights [kMlpParams]
+  __nv_bfloat16 *w2c = nullptr;  // W2 in BF16, canonical tcgen05 layout: W2 [n][k] | W2^T [k][n]
   float *m1 = nullptr, *m2 = nullptr;
   float *partial = nullptr;  // per-block gradient partials
   int partial_blocks = 0;
@@ -511,6 +517,30 @@ static aicdf_status cuda_fail() {
   return AICDF_ERR_CUDA;
 }
 
+// FP32 -> BF16, round to nearest even (NaN kept quiet)
+static uint16_t host_bf16(float f) {
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  if ((b & 0x7F800000u) == 0x7F800000u && (b & 0x7FFFFFu)) return (uint16_t)((b >> 16) | 0x40u);
+  return (uint16_t)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);
+}
+
+// Upload the BF16 canonical copies of W2 from host FP32 parameters.
+static aicdf_status upload_w2c(aicdf_surrogate_s *s, const float *p) {
+  std::vector<uint16_t> c(2 * kH * kH);
+  for (int n = 0; n < kH; ++n)
+    for (int k = 0; k < kH; ++k) {
+      const uint16_t b = host_bf16(p[kOffW2 + n * kH + k]);
+      const int o1 = (n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;  // (row n, col k)
+      const int o2 = (k >> 3) * 1024 + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;  // (row k, col n)
+      c[o1 / 2] = b;
+      c[kH * kH + o2 / 2] = b;
+    }
+  if (cudaMemcpy(s->w2c, c.data(), c.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail();
+  return AICDF_OK;
+}
+
 extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_surrogate *out) {
   if (!out || !(nu > 0.0) || !std::isfinite(nu)) return AICDF_ERR_ARG;
   *out = nullptr;
@@ -522,6 +552,7 @@ extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_s
   if (cudaMalloc(&s->params, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&s->m1, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&s->m2, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMalloc(&s->w2c, 2 * (size_t)kW2cBytes) != cudaSuccess ||
       cudaMalloc(&s->status, sizeof(int)) != cudaSuccess) {
     aicdf_surrogate_destroy(s);
     return cuda_fail();
@@ -539,7 +570,7 @@ extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_s
   if (cudaMemcpy(s->params, p.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
-      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess || upload_w2c(s, p.data()) != AICDF_OK) {
     aicdf_surrogate_destroy(s);
     return cuda_fail();
   }
@@ -550,6 +581,7 @@ extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_s
 extern "C" void aicdf_surrogate_destroy(aicdf_surrogate s) {
   if (!sur_ok(s)) return;
   cudaFree(s->params);
+  cudaFree(s->w2c);
   cudaFree(s->m1);
   cudaFree(s->m2);
   cudaFree(s->partial);
@@ -571,6 +603,7 @@ extern "C" aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const floa
       cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess)
     return cuda_fail();
+  if (upload_w2c(s, host) != AICDF_OK) return AICDF_ERR_CUDA;
   s->step = 0;
   return AICDF_OK;
 }
@@ -594,7 +627,8 @@ extern "C" aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_d
   // persistent: at most 4 CTAs per SM (the padded shared memory sees to it)
   const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sm_count() * 4));
-  k_mlp_eval<<<grid, kTcRows, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, u_dev, lam_dev, p_out_dev, n);
+  k_mlp_eval<<<grid, kTcRows, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, s->w2c, u_dev, lam_dev, p_out_dev,
+                                                                     n);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
@@ -621,8 +655,8 @@ static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, cons
       return cuda_fail();
     smem_set = true;
   }
-  k_mlp_train<<<blocks, kTcRows, kTrainSmem, st>>>(s->params, u, lam, target, begin, count, 1.0f / (float)count,
-                                                   s->partial);
+  k_mlp_train<<<blocks, kTcRows, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, begin, count,
+                                                   1.0f / (float)count, s->partial);
   *blocks_out = blocks;
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
@@ -653,7 +687,7 @@ extern "C" aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const floa
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.f - (float)std::pow((double)b1, (double)s->step);
   const float bc2 = 1.f - (float)std::pow((double)b2, (double)s->step);
-  k_mlp_adam<<<(kOffB3 + 256) / 256, 256, 0, st>>>(s->params, s->m1, s->m2, s->partial, blocks, lr, b1,
+  k_mlp_adam<<<(kOffB3 + 256) / 256, 256, 0, st>>>(s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1,
                                                    b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }

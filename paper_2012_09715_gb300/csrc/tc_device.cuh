@@ -71,6 +71,18 @@ __device__ __forceinline__ bool tc_mbar_wait(uint32_t mbar, uint32_t parity, int
   return false;
 }
 
+// Bulk (TMA) copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on `mbar`:
+// the issuing thread first adds the byte count to the barrier's expected
+// transactions (and arrives), then starts the copy.
+__device__ __forceinline__ void tc_bulk_g2s(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_smem),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 // TMEM columns: allocated and freed by one whole warp.
 __device__ __forceinline__ void tc_alloc(uint32_t slot_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols));
