@@ -166,18 +166,21 @@ __global__ void __launch_bounds__(kTcRows)
 }
 
 // ------------------------------------------------------------------ training
-// One CTA = 128 consecutive samples of the batch (thread = sample = row),
-// the three 64-wide products on tcgen05 with TMEM accumulators:
+// One CTA = 128 consecutive samples of the batch, two threads per sample
+// (thread t: sample m = t mod 128, hidden units 32 (t / 128) .. +31), the
+// three 64-wide products on tcgen05 with TMEM accumulators:
 //   Z2  = H1 W2^T      (M 128 samples, N 64, K 64)   TMEM columns   0..63
 //   dH1 = dZ2 W2       (M 128 samples, N 64, K 64)   TMEM columns  64..127
 //   dW2 = dZ2^T H1     (M 64 outputs padded to 128 with zero rows, N 64,
 //                       K 128 samples)               TMEM columns 128..191
 // BF16 operands in the canonical K-major shared layout (H1^T and dZ2^T are
-// written column by column); everything else in FP32.  The column sums over
-// the CTA's samples (gradients of w3, b2, b1, W1) go through a transposing
-// shared buffer and are summed in a fixed order, so the partials are
-// deterministic.  Writes the CTA's gradient of sum_i (y_i - t_i)^2 * scale
-// and its loss sum to partial[blockIdx].
+// written column by column; W2 and W2^T arrive by one bulk copy); everything
+// else in FP32.  The column sums over the CTA's samples (gradients of w3, b2,
+// b1, W1) go through a transposing shared buffer and are added in a fixed
+// order, so the partials are deterministic.  Writes the CTA's gradient of
+// sum_i (y_i - t_i)^2 * scale and its loss sum to partial[blockIdx].
+constexpr int kTrainThreads = 2 * kTcRows;
+constexpr int kHalf = kH / 2;         // hidden units per thread
 constexpr uint32_t kTrainCols = 256;  // TMEM columns (three 64-column accumulators)
 
 struct MlpTrainSmem {
@@ -188,6 +191,8 @@ struct MlpTrainSmem {
   __nv_bfloat16 dz2t[kTcRows * kTcRows];  // dZ2^T [n][m], rows 64..127 zero: A of dW2
   __nv_bfloat16 h1t[kH * kTcRows];      // H1^T [k][m]: B of dW2
   float red[kTcRows][2 * kH + 1];       // column sums, two 64-wide quantities per pass (pitch 129)
+  float psum[2][2 * kH];                // the two row halves of a pass's column sums
+  float ypart[2][kTcRows];              // the two halves of each sample's output
   float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
   float wsum[kTcRows / 32][2];          // per-warp sums of dy and err^2
   unsigned long long mbar, wbar;
@@ -201,32 +206,34 @@ __device__ __forceinline__ uint32_t canon_off128(int r, int k) {
   return (uint32_t)((r >> 3) * 2048 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Column sums in a fixed order: thread c sums red[0..127][c] (c < 128 for two
-// 64-wide quantities at once) as eight interleaved partial sums combined
-// pairwise.  The caller has filled red and passed a
-// barrier; ends with a barrier so that red may be refilled.
+// Column sums of red[0..127][c], c < ncols (<= 128), in a fixed order: thread
+// t sums column t mod 128 over rows 64 (t / 128) .. +63 as eight interleaved
+// partial sums, and the two row halves are then added.  The caller has filled
+// red and passed a barrier; two barriers inside, so red may be refilled after.
 __device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
-  const int tid = threadIdx.x;
-  float a = 0.f;
-  if (tid < ncols) {
-    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // rows m = 8 r + q into p[q]: 8 independent chains
-#pragma unroll 4
-    for (int r = 0; r < kTcRows / 8; ++r)
+  const int tid = threadIdx.x, c = tid & (kTcRows - 1), rh = tid >> 7;
+  if (c < ncols) {
+    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < 8; ++q) p[q] += s.red[8 * r + q][tid];
-    a = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    for (int r = 0; r < kTcRows / 16; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] += s.red[64 * rh + 8 * r + q][c];
+    s.psum[rh][c] = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
   }
+  __syncthreads();
+  const float a = (rh == 0 && c < ncols) ? s.psum[0][c] + s.psum[1][c] : 0.f;
   __syncthreads();
   return a;
 }
 
-__global__ void __launch_bounds__(kTcRows)
+__global__ void __launch_bounds__(kTrainThreads)
     k_mlp_train(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
                 const float *__restrict__ u, const float *__restrict__ lam, const float *__restrict__ target,
                 uint64_t begin, uint64_t count, float scale, float *__restrict__ partial) {
   extern __shared__ __align__(1024) unsigned char tr_raw[];
   MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(tr_raw + ((1024 - (tc_smem(tr_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = tid & (kTcRows - 1), hf = tid >> 7, c0 = kHalf * hf;  // sample, half, first unit
   unsigned char *w2k = reinterpret_cast<unsigned char *>(s.w2k), *w2t = reinterpret_cast<unsigned char *>(s.w2t);
   unsigned char *h1 = reinterpret_cast<unsigned char *>(s.h1), *dz2 = reinterpret_cast<unsigned char *>(s.dz2);
   unsigned char *dz2t = reinterpret_cast<unsigned char *>(s.dz2t), *h1t = reinterpret_cast<unsigned char *>(s.h1t);
@@ -249,8 +256,8 @@ __global__ void __launch_bounds__(kTcRows)
     tc_mbar_init(tc_smem(&s.mbar), 1);
   }
   if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTrainCols);
-  // ---- layer 1: H1 (BF16) by rows and by columns
-  const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + tid;
+  // ---- layer 1: this thread's 32 units of H1 (BF16), by rows and by columns
+  const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + m;
   const bool ok = m_idx < count;
   const uint64_t i = begin + m_idx;
   const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
@@ -258,25 +265,26 @@ __global__ void __launch_bounds__(kTcRows)
   const float tg = ok ? target[i] : 0.f;
   __syncthreads();  // vectors staged
 #pragma unroll
-  for (int j = 0; j < kH / 8; ++j) {
+  for (int j = 0; j < kHalf / 8; ++j) {
     uint32_t w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int k = 8 * j + 2 * q;
+      const int k = c0 + 8 * j + 2 * q;
       const float a = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
       const float b = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
       const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
       w[q] = pack_bf16(a, b);
-      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k, tid)) = hb.x;
-      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k + 1, tid)) = hb.y;
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k, m)) = hb.x;
+      *reinterpret_cast<__nv_bfloat16 *>(h1t + canon_off128(k + 1, m)) = hb.y;
     }
-    *reinterpret_cast<uint4 *>(h1 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(h1 + tc_canon_off64(m, c0 + 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   tc_fence_smem_to_async();
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = s.tmem;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lane quarter
   constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kH);
   // the MMA issuer needs W2 in place; a copy that never lands leaves NaN gradients
   const bool w2_ok = tid == 0 ? tc_mbar_wait(tc_smem(&s.wbar), 0) : true;
@@ -289,47 +297,46 @@ __global__ void __launch_bounds__(kTcRows)
   }
   bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), 0));
   tc_fence_after_sync();
-  // ---- layer 2 activation, output, dy; dZ2
-  float h2[kH], v[kH];
-  if (done) {
+  // ---- layer 2 activation on this thread's 32 units; the output from both halves
+  float h2[kHalf], v[kHalf];
 #pragma unroll
-    for (int c = 0; c < kH; c += 16) {
-      float z[16];
-      tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, z);
+  for (int c = 0; c < kHalf; c += 16) {
+    float z[16];
+    if (done) tc_ld16(tmem + lane_base + (uint32_t)(c0 + c), z);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) h2[c + q] = tanh_fast(z[q] + s.b2[c + q]);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < kH; ++c) h2[c] = 0.f;
+    for (int q = 0; q < 16; ++q) h2[c + q] = done ? tanh_fast(z[q] + s.b2[c0 + c + q]) : 0.f;
   }
-  float y = s.b3;
+  float yp = 0.f;
 #pragma unroll
-  for (int c = 0; c < kH; ++c) y = fmaf(s.w3[c], h2[c], y);
+  for (int c = 0; c < kHalf; ++c) yp = fmaf(s.w3[c0 + c], h2[c], yp);
+  s.ypart[hf][m] = yp;
+  __syncthreads();
+  const float y = s.b3 + (s.ypart[0][m] + s.ypart[1][m]);  // the same in both threads of a sample
   const float err = ok ? y - tg : 0.f;
   const float dy = 2.0f * err * scale;
+  // ---- dZ2 on this thread's 32 units, by rows and by columns
 #pragma unroll
-  for (int j = 0; j < kH / 8; ++j) {
+  for (int j = 0; j < kHalf / 8; ++j) {
     uint32_t w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int c = 8 * j + 2 * q;
-      const float d0 = dy * s.w3[c] * (1.f - h2[c] * h2[c]);
-      const float d1 = dy * s.w3[c + 1] * (1.f - h2[c + 1] * h2[c + 1]);
+      const int c = 8 * j + 2 * q, n = c0 + c;
+      const float d0 = dy * s.w3[n] * (1.f - h2[c] * h2[c]);
+      const float d1 = dy * s.w3[n + 1] * (1.f - h2[c + 1] * h2[c + 1]);
       v[c] = d0;
       v[c + 1] = d1;
       const __nv_bfloat162 db = __floats2bfloat162_rn(d0, d1);
       w[q] = pack_bf16(d0, d1);
-      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c, tid)) = db.x;
-      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(c + 1, tid)) = db.y;
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(n, m)) = db.x;
+      *reinterpret_cast<__nv_bfloat16 *>(dz2t + canon_off128(n + 1, m)) = db.y;
     }
-    *reinterpret_cast<uint4 *>(dz2 + tc_canon_off64(tid, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(dz2 + tc_canon_off64(m, c0 + 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   // FP32 rows for the column sums: dZ2 (gradient of b2) and dy h2 (of w3)
 #pragma unroll
-  for (int c = 0; c < kH; ++c) {
-    s.red[tid][c] = v[c];
-    s.red[tid][kH + c] = dy * h2[c];
+  for (int c = 0; c < kHalf; ++c) {
+    s.red[m][c0 + c] = v[c];
+    s.red[m][kH + c0 + c] = dy * h2[c];
   }
   tc_fence_smem_to_async();
   tc_fence_before_sync();
@@ -349,61 +356,64 @@ __global__ void __launch_bounds__(kTcRows)
   float *out = partial + (size_t)blockIdx.x * kGradSlots;
   {
     const float a = train_colsum(s, 2 * kH);
-    out[(tid < kH ? kOffB2 : kOffW3 - kH) + tid] = a;
+    if (tid < kTcRows) out[(tid < kH ? kOffB2 : kOffW3 - kH) + tid] = a;
   }
   done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), 1)) && done;
   tc_fence_after_sync();
-  // ---- dZ1 = dH1 (1 - h1^2), h1 as stored (BF16)
-  float dz1[kH];
+  // ---- dZ1 = dH1 (1 - h1^2) on this thread's 32 units, h1 as stored (BF16)
+  float dz1[kHalf];
 #pragma unroll
-  for (int c = 0; c < kH; c += 16) {
+  for (int c = 0; c < kHalf; c += 16) {
     float d[16];
-    if (done) tc_ld16(tmem + 64 + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, d);
+    if (done) tc_ld16(tmem + 64 + lane_base + (uint32_t)(c0 + c), d);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const float hv = __bfloat162float(
-          *reinterpret_cast<const __nv_bfloat16 *>(h1 + tc_canon_off64(tid, c + q)));
+          *reinterpret_cast<const __nv_bfloat16 *>(h1 + tc_canon_off64(m, c0 + c + q)));
       dz1[c + q] = done ? d[q] * (1.f - hv * hv) : 0.f;
     }
   }
 #pragma unroll
-  for (int c = 0; c < kH; ++c) {
-    s.red[tid][c] = dz1[c];
-    s.red[tid][kH + c] = dz1[c] * x0;
+  for (int c = 0; c < kHalf; ++c) {
+    s.red[m][c0 + c] = dz1[c];
+    s.red[m][kH + c0 + c] = dz1[c] * x0;
   }
   __syncthreads();
   {
     const float a = train_colsum(s, 2 * kH);  // gradient of b1, then of W1[., 0]
-    out[tid < kH ? kOffB1 + tid : kOffW1 + 2 * (tid - kH)] = a;
+    if (tid < kTcRows) out[tid < kH ? kOffB1 + tid : kOffW1 + 2 * (tid - kH)] = a;
   }
 #pragma unroll
-  for (int c = 0; c < kH; ++c) s.red[tid][c] = dz1[c] * x1;
+  for (int c = 0; c < kHalf; ++c) s.red[m][c0 + c] = dz1[c] * x1;
   __syncthreads();
   {
     const float a = train_colsum(s, kH);  // gradient of W1[., 1]
     if (tid < kH) out[kOffW1 + 2 * tid + 1] = a;
   }
-  // ---- dW2 rows n = lanes 0..63 (warps 0 and 1); every warp runs the
-  // warp-collective loads, warps 2 and 3 read the zero rows
+  // ---- dW2 rows n = TMEM lanes 0..63 (warps 0, 1 and 4, 5 for the two
+  // column halves); every warp runs the warp-collective loads
 #pragma unroll
-  for (int c = 0; c < kH; c += 16) {
+  for (int c = 0; c < kHalf; c += 16) {
     float d[16];
-    if (done) tc_ld16(tmem + 128 + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, d);
-    if (tid < kH) {
+    if (done) tc_ld16(tmem + 128 + lane_base + (uint32_t)(c0 + c), d);
+    if (m < kH) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) out[kOffW2 + tid * kH + c + q] = done ? d[q] : __int_as_float(0x7fc00000);
+      for (int q = 0; q < 16; ++q) out[kOffW2 + m * kH + c0 + c + q] = done ? d[q] : __int_as_float(0x7fc00000);
     }
   }
-  // ---- sums of dy (gradient of b3) and err^2, in a fixed order
-  float sdy = dy, loss = err * err;
+  // ---- sums of dy (gradient of b3) and err^2 over the samples (first half
+  // of the threads), in a fixed order
+  if (hf == 0) {
+    float sdy = dy, loss = err * err;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
-    loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  }
-  if (lane == 0) {
-    s.wsum[warp][0] = sdy;
-    s.wsum[warp][1] = loss;
+    for (int o = 16; o > 0; o >>= 1) {
+      sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
+      loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    }
+    if (lane == 0) {
+      s.wsum[warp][0] = sdy;
+      s.wsum[warp][1] = loss;
+    }
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -419,20 +429,31 @@ __global__ void __launch_bounds__(kTcRows)
   if (warp == 0) tc_dealloc(tmem, kTrainCols);
 }
 
-// Sum per-block gradients in block order and take one Adam step.
-__global__ void k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2,
-                           __nv_bfloat16 *__restrict__ w2c, const float *__restrict__ partial, int nblocks,
-                           float lr, float b1, float b2, float eps, float bc1, float bc2,
-                           float *__restrict__ loss_out, float loss_scale) {
+// Sum of partial[b * kGradSlots + p] over the blocks b in a fixed order: eight
+// interleaved chains (b mod 8) combined pairwise, so that the loads overlap.
+__device__ __forceinline__ float sum_partials(const float *__restrict__ partial, int nblocks, int p) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int b = 0;
+  for (; b + 8 <= nblocks; b += 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] += partial[(size_t)(b + q) * kGradSlots + p];
+  for (int q = 0; b + q < nblocks; ++q) a[q] += partial[(size_t)(b + q) * kGradSlots + p];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+// Sum per-block gradients in a fixed order and take one Adam step (one thread
+// per parameter, in small blocks so that the summing spreads over many SMs).
+constexpr int kAdamThreads = 64;
+
+__global__ void __launch_bounds__(kAdamThreads)
+    k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2,
+               __nv_bfloat16 *__restrict__ w2c, const float *__restrict__ partial, int nblocks, float lr,
+               float b1, float b2, float eps, float bc1, float bc2, float *__restrict__ loss_out,
+               float loss_scale) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0 && loss_out) {
-    float l = 0.f;
-    for (int b = 0; b < nblocks; ++b) l += partial[(size_t)b * kGradSlots + kLossSlot];
-    *loss_out = l * loss_scale;
-  }
+  if (p == 0 && loss_out) *loss_out = sum_partials(partial, nblocks, kLossSlot) * loss_scale;
   if (p > kOffB3) return;
-  float gsum = 0.f;
-  for (int b = 0; b < nblocks; ++b) gsum += partial[(size_t)b * kGradSlots + p];
+  const float gsum = sum_partials(partial, nblocks, p);
   const float m = b1 * m1[p] + (1.f - b1) * gsum;
   const float v = b2 * m2[p] + (1.f - b2) * gsum * gsum;
   m1[p] = m;
@@ -451,9 +472,7 @@ __global__ void k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, f
 __global__ void k_mlp_grad_sum(const float *__restrict__ partial, int nblocks, float *__restrict__ grad) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p > kLossSlot) return;
-  float gsum = 0.f;
-  for (int b = 0; b < nblocks; ++b) gsum += partial[(size_t)b * kGradSlots + p];
-  grad[p] = gsum;
+  grad[p] = sum_partials(partial, nblocks, p);
 }
 
 // ------------------------------------------------------------------ exact targets
@@ -655,7 +674,7 @@ static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, cons
       return cuda_fail();
     smem_set = true;
   }
-  k_mlp_train<<<blocks, kTcRows, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, begin, count,
+  k_mlp_train<<<blocks, kTrainThreads, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, begin, count,
                                                    1.0f / (float)count, s->partial);
   *blocks_out = blocks;
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
@@ -669,7 +688,7 @@ extern "C" aicdf_status aicdf_surrogate_grad(aicdf_surrogate s, const float *u_d
   int blocks = 0;
   aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, (cudaStream_t)stream, &blocks);
   if (rc != AICDF_OK) return rc;
-  k_mlp_grad_sum<<<(kLossSlot + 256) / 256, 256, 0, (cudaStream_t)stream>>>(s->partial, blocks, grad_dev);
+  k_mlp_grad_sum<<<(kLossSlot + 64) / 64, 64, 0, (cudaStream_t)stream>>>(s->partial, blocks, grad_dev);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
@@ -687,8 +706,8 @@ extern "C" aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const floa
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.f - (float)std::pow((double)b1, (double)s->step);
   const float bc2 = 1.f - (float)std::pow((double)b2, (double)s->step);
-  k_mlp_adam<<<(kOffB3 + 256) / 256, 256, 0, st>>>(s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1,
-                                                   b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n);
+  k_mlp_adam<<<(kOffB3 + kAdamThreads) / kAdamThreads, kAdamThreads, 0, st>>>(
+      s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1, b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
