@@ -21,6 +21,7 @@
 #include "device_common.cuh"
 #include "mlp_device.cuh"
 #include "ncx2.cuh"
+#include "mlp_tc.cuh"
 #include "tc_device.cuh"
 
 namespace aicdf {
@@ -29,58 +30,24 @@ constexpr int kGradSlots = kMlpParams;         // per-block partial: params + lo
 constexpr int kLossSlot = kOffB3 + 1;          // 4417
 
 // ------------------------------------------------------------------ evaluation
-// Batched evaluation on tcgen05: a CTA of 128 threads takes tiles of 128
-// samples (thread = sample = row).  Layer 1 (FP32, tanh) writes each row of
-// H1 in BF16 into a shared tile in the canonical K-major layout; one thread
-// issues the 128 x 64 x 64 product H1 W2^T as four depth-16 MMAs into a TMEM
-// accumulator (64 FP32 columns, lane = sample); each thread then reads its
-// row of Z2 from TMEM for tanh(Z2 + b2) . w3 + b3.  Two H1 tiles and two
-// accumulators let layer 1 of the next tile run while the current tile's MMA
-// is in flight.  Should an MMA's completion not arrive within the bounded
-// wait, the tile's outputs are NaN and the CTA stops.
-constexpr int kTcRows = 128;
+// Batched evaluation on tcgen05 (the pieces in mlp_tc.cuh): tiles of 128
+// samples per CTA.  Two H1 tiles and two accumulators let layer 1 of the next
+// tile run while the current tile's MMA is in flight.  Should an MMA's
+// completion not arrive within the bounded wait, the tile's outputs are NaN
+// and the CTA stops.
 constexpr uint32_t kTcCols = 128;  // TMEM columns per CTA: two 64-column accumulators
 
 struct MlpTcSmem {
   __nv_bfloat16 a[2][kTcRows * kH];  // H1 tiles (2 x 16 KiB)
   __nv_bfloat16 b[kH * kH];          // W2 [out][in] (8 KiB)
-  float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
+  MlpVecs v;
   unsigned long long mbar[2], wbar;
   uint32_t tmem;
 };
-
-// The handle keeps W2 in BF16 in the canonical layout twice -- W2 [n][k]
-// (kW2cBytes) then W2^T [k][n] -- so that a CTA loads it with one bulk copy.
-constexpr uint32_t kW2cBytes = kH * kH * sizeof(__nv_bfloat16);
 // Dynamic shared memory per CTA, padded so that at most 4 CTAs fit an SM and
 // their TMEM (4 x 128 columns) never exceeds the SM's 512 columns.
 constexpr size_t kTcSmemBytes = 52 * 1024;
 static_assert(sizeof(MlpTcSmem) + 1024 <= kTcSmemBytes, "tile layout exceeds the padded allocation");
-
-__device__ __forceinline__ void mlp_tc_layer1(const MlpTcSmem &s, __nv_bfloat16 *tile, int row, float x0, float x1) {
-  unsigned char *base = reinterpret_cast<unsigned char *>(tile);
-#pragma unroll
-  for (int j = 0; j < kH / 8; ++j) {
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = 8 * j + 2 * q;
-      const float h0 = tanh_fast(fmaf(s.w1[2 * k], x0, fmaf(s.w1[2 * k + 1], x1, s.b1[k])));
-      const float h1 = tanh_fast(fmaf(s.w1[2 * k + 2], x0, fmaf(s.w1[2 * k + 3], x1, s.b1[k + 1])));
-      w[q] = pack_bf16(h0, h1);
-    }
-    *reinterpret_cast<uint4 *>(base + tc_canon_off64(row, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-__device__ __forceinline__ void mlp_tc_issue(uint32_t d_tmem, uint32_t a_base, uint32_t b_base, uint32_t mbar) {
-  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kH);
-#pragma unroll
-  for (int kk = 0; kk < kH / 16; ++kk)
-    tc_mma_bf16(d_tmem, tc_desc(a_base + 256 * kk, 128, 1024), tc_desc(b_base + 256 * kk, 128, 1024), idesc,
-                kk > 0);
-  tc_commit(mbar);
-}
 
 __global__ void __launch_bounds__(kTcRows)
     k_mlp_eval(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
@@ -92,14 +59,8 @@ __global__ void __launch_bounds__(kTcRows)
     tc_mbar_init(tc_smem(&s.wbar), 1);
     tc_bulk_g2s(tc_smem(s.b), w2c, kW2cBytes, tc_smem(&s.wbar));
   }
-  for (int i = tid; i < 2 * kH; i += blockDim.x) s.w1[i] = params[kOffW1 + i];
-  for (int i = tid; i < kH; i += blockDim.x) {
-    s.b1[i] = params[kOffB1 + i];
-    s.b2[i] = params[kOffB2 + i];
-    s.w3[i] = params[kOffW3 + i];
-  }
+  mlp_stage_vecs(params, s.v);
   if (tid == 0) {
-    s.b3 = params[kOffB3];
     tc_mbar_init(tc_smem(&s.mbar[0]), 1);
     tc_mbar_init(tc_smem(&s.mbar[1]), 1);
   }
@@ -119,7 +80,7 @@ __global__ void __launch_bounds__(kTcRows)
   if (blockIdx.x < ntiles) {  // first tile: layer 1 and its MMA
     float x0, x1;
     features(blockIdx.x, x0, x1);
-    mlp_tc_layer1(s, s.a[0], tid, x0, x1);
+    mlp_tc_layer1(s.v, s.a[0], tid, x0, x1);
     tc_fence_smem_to_async();
     tc_fence_before_sync();
     __syncthreads();
@@ -132,7 +93,7 @@ __global__ void __launch_bounds__(kTcRows)
     if (tile + step < ntiles) {  // the next tile's layer 1 and MMA while this MMA runs
       float x0, x1;
       features(tile + step, x0, x1);
-      mlp_tc_layer1(s, s.a[nxt], tid, x0, x1);
+      mlp_tc_layer1(s.v, s.a[nxt], tid, x0, x1);
       tc_fence_smem_to_async();
       tc_fence_before_sync();
       __syncthreads();
@@ -142,18 +103,8 @@ __global__ void __launch_bounds__(kTcRows)
     // warp-uniform, as the TMEM loads below are warp-collective
     const bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar[cur]), (j >> 1) & 1));
     tc_fence_after_sync();
-    float y = __int_as_float(0x7fc00000);
-    if (done) {
-      float acc = 0.f;
-#pragma unroll
-      for (int c = 0; c < kH; c += 16) {
-        float v[16];
-        tc_ld16(tmem + kH * cur + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc = fmaf(s.w3[c + q], tanh_fast(v[q] + s.b2[c + q]), acc);
-      }
-      y = acc + s.b3;
-    }
+    const float y = done ? mlp_tc_output(s.v, tmem + kH * cur + ((uint32_t)(32 * warp) << 16))
+                         : __int_as_float(0x7fc00000);
     const uint64_t i = tile * kTcRows + tid;
     if (i < n) out[i] = y;
     tc_fence_before_sync();
