@@ -448,7 +448,9 @@ typedef struct {
   int estimator;          /* aicdf_estimator                                              */
   int L_min, L_max;       /* first and last admissible finest level                      */
   int fixed_L;            /* >= 0: use exactly this finest level (no bias test)           */
-  uint64_t n_pilot;       /* pilot paths per new term                                     */
+  uint64_t n_pilot;       /* pilot paths per new term (0: 10^4); a nested estimator's
+                             four-way terms, with their far smaller variance, take
+                             max(128, n_pilot / 16) (at most n_pilot)                     */
   uint64_t seed;
   double weak_order;      /* alpha in the bias estimate |E Y_L| / (2^alpha - 1)           */
 } aicdf_mlmc_opts;
