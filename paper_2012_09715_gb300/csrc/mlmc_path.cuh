@@ -121,10 +121,20 @@ __device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   return p;
 }
 
+// sqrt|X| of the CIR step with the hardware's approximate square root: its
+// error of a few ulps of sqrt|X| enters the step scaled by sig_sdt Z, while
+// the IEEE-rounded sqrtf is a multi-instruction sequence paid once per fine
+// and coarse step.
+__device__ __forceinline__ float cir_sqrt_abs(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fabsf(x)));
+  return r;
+}
+
 template <int MODEL>
 __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.g2, z, p.g1), z, p.g0), x);
-  const float r = sqrtf(fabsf(x));
+  const float r = cir_sqrt_abs(x);
   const float inc = fmaf(p.kdt, p.theta - x, fmaf(p.sig_sdt * r, z, p.mq * fmaf(z, z, -1.0f)));
   return x + inc;
 }
@@ -132,7 +142,7 @@ __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p
 template <int MODEL>
 __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.c2, s, p.c1), s, p.c0), x);
-  const float r = sqrtf(fabsf(x));
+  const float r = cir_sqrt_abs(x);
   const float inc = fmaf(2.0f * p.kdt, p.theta - x, fmaf(p.sig_sdt * r, s, p.mq * fmaf(s, s, -2.0f)));
   return x + inc;
 }
