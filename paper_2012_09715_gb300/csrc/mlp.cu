@@ -30,18 +30,24 @@ constexpr int kGradSlots = kMlpParams;         // per-block partial: params + lo
 constexpr int kLossSlot = kOffB3 + 1;          // 4417
 
 // ------------------------------------------------------------------ evaluation
-// Batched evaluation on tcgen05 (the pieces in mlp_tc.cuh): tiles of 128
-// samples per CTA.  Two H1 tiles and two accumulators let layer 1 of the next
-// tile run while the current tile's MMA is in flight.  Should an MMA's
-// completion not arrive within the bounded wait, the tile's outputs are NaN
-// and the CTA stops.
+// Batched evaluation on tcgen05 (the pieces in mlp_tc.cuh): a CTA of 256
+// threads takes tiles of 128 samples two at a time (thread t: sample t mod 128
+// of both tiles, hidden units 32 (t / 128) .. +31; both halves of a warp group
+// read the same TMEM lane quarter), so that each FP32 weight read from shared
+// memory serves two samples.  The pair's two MMAs go to two 64-column
+// accumulators under one commit; other CTAs on the SM fill the wait.  Inputs
+// are loaded one pair ahead.  The output is b3 + (lower half + upper half),
+// the training step's forward value.  Should the MMAs' completion not arrive
+// within the bounded wait, the pair's outputs are NaN and the CTA stops.
+constexpr int kEvalThreads = 2 * kTcRows;
 constexpr uint32_t kTcCols = 128;  // TMEM columns per CTA: two 64-column accumulators
 
 struct MlpTcSmem {
   __nv_bfloat16 a[2][kTcRows * kH];  // H1 tiles (2 x 16 KiB)
   __nv_bfloat16 b[kH * kH];          // W2 [out][in] (8 KiB)
   MlpVecs v;
-  unsigned long long mbar[2], wbar;
+  float ypart[2][kTcRows];           // upper halves of the pair's outputs
+  unsigned long long mbar, wbar;
   uint32_t tmem;
 };
 // Dynamic shared memory per CTA, padded so that at most 4 CTAs fit an SM and
@@ -49,68 +55,70 @@ struct MlpTcSmem {
 constexpr size_t kTcSmemBytes = 52 * 1024;
 static_assert(sizeof(MlpTcSmem) + 1024 <= kTcSmemBytes, "tile layout exceeds the padded allocation");
 
-__global__ void __launch_bounds__(kTcRows)
+__global__ void __launch_bounds__(kEvalThreads, 4)
     k_mlp_eval(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
                const float *__restrict__ u, const float *__restrict__ lam, float *__restrict__ out, uint64_t n) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(tc_raw + ((1024 - (tc_smem(tc_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = tid & (kTcRows - 1), hf = tid >> 7, c0 = kHalf * hf;  // sample, half, first unit
   if (tid == 0) {  // W2 (BF16, canonical) by one bulk copy
     tc_mbar_init(tc_smem(&s.wbar), 1);
     tc_bulk_g2s(tc_smem(s.b), w2c, kW2cBytes, tc_smem(&s.wbar));
   }
   mlp_stage_vecs(params, s.v);
-  if (tid == 0) {
-    tc_mbar_init(tc_smem(&s.mbar[0]), 1);
-    tc_mbar_init(tc_smem(&s.mbar[1]), 1);
-  }
+  if (tid == 0) tc_mbar_init(tc_smem(&s.mbar), 1);
   if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTcCols);
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = s.tmem, b_base = tc_smem(s.b);
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lane quarter
   // the MMA issuer needs W2 in place; a copy that never lands leaves NaN outputs
   const bool w2_ok = tid == 0 ? tc_mbar_wait(tc_smem(&s.wbar), 0) : true;
-  const uint64_t ntiles = (n + kTcRows - 1) / kTcRows, step = gridDim.x;
-  auto features = [&](uint64_t tile, float &x0, float &x1) {
-    const uint64_t i = tile * kTcRows + tid;
-    x0 = i < n ? mlp_feature_u(u[i]) : 0.f;
-    x1 = i < n ? mlp_feature_lam(lam[i]) : 0.f;
+  const uint64_t ntiles = (n + kTcRows - 1) / kTcRows, step = 2 * (uint64_t)gridDim.x;
+  auto load = [&](uint64_t tile, float &ru, float &rl) {  // raw inputs of one row of a tile
+    const uint64_t i = tile * kTcRows + m;
+    ru = tile < ntiles && i < n ? u[i] : 0.5f;
+    rl = tile < ntiles && i < n ? lam[i] : 1.0f;
   };
-  if (blockIdx.x < ntiles) {  // first tile: layer 1 and its MMA
-    float x0, x1;
-    features(blockIdx.x, x0, x1);
-    mlp_tc_layer1(s.v, s.a[0], tid, x0, x1);
+  uint64_t t0 = 2 * (uint64_t)blockIdx.x;  // first tile of this CTA's pair
+  float pua, pla, pub, plb;                  // inputs of the pair at t0
+  load(t0, pua, pla);
+  load(t0 + 1, pub, plb);
+  for (uint32_t j = 0; t0 < ntiles; t0 += step, ++j) {
+    const float xa0 = mlp_feature_u(pua), xa1 = mlp_feature_lam(pla);
+    const float xb0 = mlp_feature_u(pub), xb1 = mlp_feature_lam(plb);
+    load(t0 + step, pua, pla);  // the next pair's inputs, in flight during this pair
+    load(t0 + step + 1, pub, plb);
+    mlp_tc_layer1_pair(s.v, s.a[0], s.a[1], m, c0, xa0, xa1, xb0, xb1);
     tc_fence_smem_to_async();
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    if (tid == 0 && w2_ok) mlp_tc_issue(tmem, tc_smem(s.a[0]), b_base, tc_smem(&s.mbar[0]));
-  }
-  uint32_t j = 0;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += step, ++j) {
-    const uint32_t cur = j & 1, nxt = cur ^ 1;
-    if (tile + step < ntiles) {  // the next tile's layer 1 and MMA while this MMA runs
-      float x0, x1;
-      features(tile + step, x0, x1);
-      mlp_tc_layer1(s.v, s.a[nxt], tid, x0, x1);
-      tc_fence_smem_to_async();
-      tc_fence_before_sync();
-      __syncthreads();
-      tc_fence_after_sync();
-      if (tid == 0 && w2_ok) mlp_tc_issue(tmem + kH * nxt, tc_smem(s.a[nxt]), b_base, tc_smem(&s.mbar[nxt]));
+    if (tid == 0 && w2_ok) {
+      mlp_tc_issue(tmem, tc_smem(s.a[0]), b_base);
+      mlp_tc_issue(tmem + kH, tc_smem(s.a[1]), b_base);
+      tc_commit(tc_smem(&s.mbar));
     }
     // warp-uniform, as the TMEM loads below are warp-collective
-    const bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar[cur]), (j >> 1) & 1));
+    const bool done = __all_sync(0xffffffffu, tc_mbar_wait(tc_smem(&s.mbar), j & 1));
     tc_fence_after_sync();
-    const float y = done ? mlp_tc_output(s.v, tmem + kH * cur + ((uint32_t)(32 * warp) << 16))
-                         : __int_as_float(0x7fc00000);
-    const uint64_t i = tile * kTcRows + tid;
-    if (i < n) out[i] = y;
+    float ya = __int_as_float(0x7fc00000), yb = ya;
+    if (done) mlp_tc_output_half_pair(s.v, tmem + lane_base, c0, ya, yb);
+    if (hf) {
+      s.ypart[0][m] = ya;
+      s.ypart[1][m] = yb;
+    }
     tc_fence_before_sync();
-    __syncthreads();  // this tile's H1 and accumulator are reused two tiles on
+    __syncthreads();  // ypart written; H1 tiles and accumulators free for the next pair
     tc_fence_after_sync();
-    if (!__syncthreads_and(done)) break;
+    if (!hf) {
+      const uint64_t ia = t0 * kTcRows + m, ib = ia + kTcRows;
+      if (ia < n) out[ia] = s.v.b3 + (ya + s.ypart[0][m]);
+      if (ib < n) out[ib] = s.v.b3 + (yb + s.ypart[1][m]);
+    }
+    if (!__syncthreads_and(done)) break;  // also: ypart read before the next pair writes it
   }
   __syncthreads();
   if (warp == 0) tc_dealloc(tmem, kTcCols);
@@ -131,7 +139,6 @@ __global__ void __launch_bounds__(kTcRows)
 // order, so the partials are deterministic.  Writes the CTA's gradient of
 // sum_i (y_i - t_i)^2 * scale and its loss sum to partial[blockIdx].
 constexpr int kTrainThreads = 2 * kTcRows;
-constexpr int kHalf = kH / 2;         // hidden units per thread
 constexpr uint32_t kTrainCols = 256;  // TMEM columns (three 64-column accumulators)
 
 struct MlpTrainSmem {
@@ -594,10 +601,11 @@ extern "C" aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_d
   static const cudaError_t attr =
       cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (attr != cudaSuccess) return cuda_fail();
-  // persistent: at most 4 CTAs per SM (the padded shared memory sees to it)
-  const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sm_count() * 4));
-  k_mlp_eval<<<grid, kTcRows, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, s->w2c, u_dev, lam_dev, p_out_dev,
+  // persistent: at most 4 CTAs per SM (the padded shared memory sees to it),
+  // each taking tiles two at a time
+  const uint64_t pairs = ((n + kTcRows - 1) / kTcRows + 1) / 2;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(pairs, (uint64_t)sm_count() * 4));
+  k_mlp_eval<<<grid, kEvalThreads, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, s->w2c, u_dev, lam_dev, p_out_dev,
                                                                      n);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }

@@ -227,7 +227,8 @@ def test_eval_kernel_matches_path_kernel_surrogate(P, orc):
     import torch
     rng = np.random.default_rng(5)
     s = P.Surrogate(NU_CFG, seed=0)
-    s.set_params(_random_params(rng))
+    params = _random_params(rng)
+    s.set_params(params)
     kappa, theta, sigma, X0 = 0.5, 0.04, 0.3, 0.04
     prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=X0, T=1.0, K=0.0, mu=0.0, sigma=sigma,
                        kappa=kappa, theta=theta, discount=1.0)
@@ -246,10 +247,15 @@ def test_eval_kernel_matches_path_kernel_surrogate(P, orc):
     pt = pt.cpu().numpy()
     h = np.float32(lam + nu32)
     want = np.float32(c) * np.maximum(np.float32(2) * np.sqrt(h) * pt + h, np.float32(0))
+    # the two kernels add the last layer's 64 products w3_k h_k (|h_k| <= 1) in
+    # different orders, so their P~ agree to a few ulps of sum |w3|; near
+    # X_1 = 0 the cancellation in h + 2 sqrt(h) P~ magnifies that by 2 sqrt(h) c
+    tol_p = 4 * 2.0 ** -24 * (float(np.abs(params[4352:4416]).sum()) + 1.0)
     for p in range(m):
         P.cir_level(prm, s, 0, P.CIR_SURROGATE, 1, sums, ws, st, path_offset=p, seed=seed, tag=tag)
         got = sums[0].item()
-        assert got == pytest.approx(float(want[p]), rel=2e-6, abs=1e-9), (p, got, want[p])
+        tol = 2e-6 * abs(float(want[p])) + c * 2 * math.sqrt(h) * tol_p
+        assert abs(got - float(want[p])) <= tol, (p, got, want[p], tol)
     assert st.item() == 0
 
 
