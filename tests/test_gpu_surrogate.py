@@ -259,10 +259,12 @@ def test_eval_kernel_matches_path_kernel_surrogate(P, orc):
     assert st.item() == 0
 
 
-@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 40000])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 257, 1000, 40000, 400001])
 def test_eval_ragged_tiles(P, orc, n):
-    """Tiles of 128 samples with ragged ends, several tiles per CTA: every
-    output is written once and agrees with the oracle's network."""
+    """Tiles of 128 samples taken in pairs, with ragged ends (a half-empty
+    last pair, a one-sample last tile) and, at 400001 samples, several pairs
+    per CTA: every output is written, nothing past the end, and the outputs
+    agree with the oracle's network."""
     import torch
     rng = np.random.default_rng(n)
     s = P.Surrogate(NU_CFG, seed=0)
@@ -274,6 +276,7 @@ def test_eval_ragged_tiles(P, orc, n):
     s.eval(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), out[:n])
     got = out.cpu().numpy().astype(np.float64)
     assert np.all(np.isinf(got[n:]))
+    assert np.all(np.isfinite(got[:n]))
     idx = np.unique(np.concatenate([np.arange(min(n, 300)), rng.integers(0, n, 200), [n - 1]]))
     ref = orc.mlp_forward(_oracle_params(p), _features(u[idx].astype(np.float64), lam[idx].astype(np.float64)))
     assert np.all(np.abs(got[idx] - ref) <= 0.03 + 0.01 * np.abs(ref))
