@@ -15,9 +15,11 @@
  *     cudaError_t value).
  *   - Uniforms.  Where the library draws uniforms itself it uses
  *     Philox4x32-10 (Salmon et al., SC'11) with key (seed mod 2^32, seed>>32)
- *     and maps a 32-bit word x to u = (2*(x mod 2^23)+1) * 2^-24 (its low 23
- *     bits), the midpoint of one of 2^23 equal cells: u lies in
- *     [2^-24, 1-2^-24], and u and 1-u are both exact in FP32.
+ *     and maps a 32-bit word x to the midpoint u = (2k+1) * 2^-24 of one of
+ *     2^23 equal cells: with m = x mod 2^22 (its low 22 bits), k = m when bit
+ *     31 is clear (u < 1/2) and k = 2^23 - 1 - m when it is set (u > 1/2);
+ *     bits 22..30 are unused.  u lies in [2^-24, 1-2^-24], is never 1/2, and
+ *     u and 1-u are both exact in FP32.
  */
 #ifndef AICDF_H
 #define AICDF_H

@@ -79,8 +79,12 @@ void or_philox4(int w, int rounds, const uint64_t ctr[4], const uint64_t key[2],
 }
 
 double or_u01(uint32_t x) {
-  /* midpoint of the k-th of 2^23 equal cells, k = low 23 bits of x */
-  return ((double)(x & 0x7FFFFFu) + 0.5) / 8388608.0;
+  /* midpoint of the k-th of 2^23 equal cells: the top bit of x picks the half
+   * of (0, 1) and the low 22 bits m the cell, counted from 0 in the lower half
+   * and from 1 in the upper half (k = m, or k = 2^23 - 1 - m) */
+  const uint32_t m = x & 0x3FFFFFu;
+  const uint32_t k = (x >> 31) ? 0x7FFFFFu - m : m;
+  return ((double)k + 0.5) / 8388608.0;
 }
 
 void or_uniforms(uint64_t seed, uint64_t offset, int64_t n, float *u) {

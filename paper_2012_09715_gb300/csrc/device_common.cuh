@@ -68,10 +68,19 @@ __device__ __forceinline__ void philox_n(uint4 (&c)[NC], const PhiloxKeys &k) {
     for (int q = 0; q < NC; ++q) c[q] = philox_round(c[q], k.k0[r], k.k1[r]);
 }
 
-// (1 + m 2^-23) - (1 - 2^-24) = (2m+1) 2^-24, m = low 23 bits of x: both
-// steps exact (one logic op and one add).
+// The library's uniform from a Philox word x: the sign bit picks the half of
+// (0, 1) and the low 22 bits m the cell within it.  v = (1 + m 2^-23) -
+// (1 - 2^-24) = (2m+1) 2^-24 (one logic op and one exact add) is min(u, 1-u)
+// in (0, 1/2); u = v when bit 31 is clear and 1 - v (exact) when it is set.
+// So u is the midpoint (2k+1) 2^-24 of cell k of 2^23 equal cells, k = m or
+// 2^23 - 1 - m, and never 1/2; bits 22..30 are unused.  The samplers' word
+// forms take v and the sign bit as they stand, with no compare or reflection.
+__device__ __forceinline__ float v01(uint32_t x) {
+  return __uint_as_float(0x3F800000u | (x & 0x3FFFFFu)) - 0x1.fffffep-1f;
+}
 __device__ __forceinline__ float u01(uint32_t x) {
-  return __uint_as_float(0x3F800000u | (x & 0x7FFFFFu)) - 0x1.fffffep-1f;
+  const float v = v01(x);
+  return (x & 0x80000000u) ? 1.0f - v : v;
 }
 
 // Truncated-bit uniform: cell m of 2^B, u = (m + 1/2) 2^-B = (1 + m 2^-B) -
@@ -103,6 +112,15 @@ __device__ __forceinline__ PwlRows pwl_lane_rows(const float *alpha, const float
   c.a = alpha[r];
   c.b = beta[r];
   return c;
+}
+
+// Must be called by all 32 lanes of the warp.  Equals pwl_eval_grid(u01(x)).
+__device__ __forceinline__ float pwl_eval_word(uint32_t x, const PwlRows &c) {
+  const float v = v01(x);
+  const uint32_t e = __float_as_uint(v) >> 23;  // the shuffle uses e mod 32
+  const float a = __shfl_sync(0xffffffffu, c.a, e);
+  const float b = __shfl_sync(0xffffffffu, c.b, e);
+  return __uint_as_float(__float_as_uint(fmaf(b, v, a)) ^ (x & 0x80000000u));
 }
 
 // Must be called by all 32 lanes of the warp.
@@ -151,6 +169,14 @@ __device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c, uint32
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
 }
 
+// The same for a word x: equals pwp_eval_grid(u01(x), ...).
+__device__ __forceinline__ float pwp_eval_word(uint32_t x, const PwpRows &c, uint32_t e_sing, float scale_k) {
+  const float v = v01(x);
+  const uint32_t e = __float_as_uint(v) >> 23;
+  const float z = pwp_eval_v(v, e, e <= e_sing, scale_k, c);
+  return __uint_as_float(__float_as_uint(z) ^ (x & 0x80000000u));
+}
+
 // Any FP32 u (caller uniforms): reflection by 1 - u, capped row.  The row is
 // taken in unsigned arithmetic as in pwl_eval: a set sign bit (u = -0, or the
 // NaN / out-of-range inputs whose result the caller discards) wraps 126 - e
@@ -164,11 +190,22 @@ __device__ __forceinline__ float pwp_eval(float u, const PwpRows &c, uint32_t K,
   return lower ? z : -z;
 }
 
-// Piecewise constant with n = 2^q intervals for a grid uniform from word x:
-// floor(n u) = floor((2m+1) 2^-(24-q)) = m >> (23 - q), m = low 23 bits.
-__device__ __forceinline__ uint32_t pwc_index_from_word(uint32_t x, uint32_t shift) {
-  return (x & 0x7FFFFFu) >> shift;
+// Piecewise constant with n = 2^q intervals (q >= 1) for the uniform of word
+// x: u = (2k+1) 2^-24 with k = m (bit 31 clear) or 2^23 - 1 - m (set), m = low
+// 22 bits, so floor(n u) = k >> (23 - q) is j = m >> (23 - q) below 1/2 and
+// n - 1 - j above.  The word forms index a word-order copy of the table,
+// W[j] = T[j] and W[n/2 + j] = T[n - 1 - j] (j < n/2), at slot j + (n/2) bit31:
+// the low q - 1 bits of x >> (23 - q) joined to bit q - 1 of x >> (32 - q), one
+// select.
+struct PwcWord {
+  uint32_t shift, shift_top, lo;  // 23 - q, 32 - q, n/2 - 1
+};
+__host__ __device__ inline PwcWord pwc_word(uint32_t q) { return PwcWord{23u - q, 32u - q, (1u << (q - 1)) - 1u}; }
+__device__ __forceinline__ uint32_t pwc_slot_from_word(uint32_t x, const PwcWord &p) {
+  return ((x >> p.shift) & p.lo) | ((x >> p.shift_top) & ~p.lo);
 }
+// The row of T held at slot i of the word-order copy.
+__device__ __forceinline__ int pwc_word_row(int i, int n) { return i < n / 2 ? i : n - 1 - (i - n / 2); }
 
 // ---------------------------------------------------------------------------
 // Algorithm 1.  Lane L of every warp holds the coefficients of row (L & 15);
@@ -247,14 +284,21 @@ __device__ __forceinline__ float phiinv_f32(float u) {
 // truncated-bit cells): v >= 2^-24 keeps w <= 24 ln 2 - ln 4 < W1, so the FP64
 // far-tail branch is never taken and is left out -- identical results, and no
 // call site in the callers' unrolled loops (6% more exact samples per second).
-__device__ __forceinline__ float phiinv_f32_grid(float u) {
-  const bool lower = u < 0.5f;
-  const float v = lower ? u : 1.0f - u;
+// Lower half: v in (0, 1/2] -> Phi^-1(v) <= 0.
+__device__ __forceinline__ float phiinv_f32_half(float v) {
   const float x = fmaf(2.0f, v, -1.0f);
   const float w = -__logf(4.0f * v * (1.0f - v));
-  const float z = w < AICDF_PHIINV_W0 ? x * aicdf_phiinv_poly_central(w - AICDF_PHIINV_WC)
-                                      : x * aicdf_phiinv_poly_tail(sqrtf(w) - AICDF_PHIINV_S0);
+  return w < AICDF_PHIINV_W0 ? x * aicdf_phiinv_poly_central(w - AICDF_PHIINV_WC)
+                             : x * aicdf_phiinv_poly_tail(sqrtf(w) - AICDF_PHIINV_S0);
+}
+__device__ __forceinline__ float phiinv_f32_grid(float u) {
+  const bool lower = u < 0.5f;
+  const float z = phiinv_f32_half(lower ? u : 1.0f - u);
   return lower ? z : -z;
+}
+// The same for a word x: equals phiinv_f32_grid(u01(x)) (v < 1/2, so z != 0).
+__device__ __forceinline__ float phiinv_f32_word(uint32_t x) {
+  return __uint_as_float(__float_as_uint(phiinv_f32_half(v01(x))) ^ (x & 0x80000000u));
 }
 
 __device__ __forceinline__ bool in_unit(float u) { return u >= 0.0f && u <= 1.0f; }

@@ -37,8 +37,8 @@ inline bool kind_needs_approx(int kind) {
 }
 
 // Approximation evaluator used inside path loops.  Path uniforms always come
-// from the library's Philox words, so both forms use the grid shortcuts:
-// (x, u) = (the word, its uniform u01(x)).
+// from the library's Philox words, so it takes the word x and evaluates at
+// u01(x) through the word forms (v and the sign bit straight from x).
 template <int AP>
 struct ApproxTable;
 
@@ -48,7 +48,7 @@ struct ApproxTable<AICDF_PWL> {
   __device__ ApproxTable(const float *tab, int ntab, float *) {
     rows = pwl_lane_rows(tab, tab + 16, ntab);
   }
-  __device__ __forceinline__ float operator()(uint32_t, float u) const { return pwl_eval_grid(u, rows); }
+  __device__ __forceinline__ float operator()(uint32_t x) const { return pwl_eval_word(x, rows); }
 };
 
 template <>
@@ -61,24 +61,20 @@ struct ApproxTable<AICDF_PWP> {
     e_sing = 126u - (uint32_t)ntab;
     scale_k = __int_as_float((127 + ntab) << 23);  // 2^K
   }
-  __device__ __forceinline__ float operator()(uint32_t, float u) const {
-    return pwp_eval_grid(u, rows, e_sing, scale_k);
-  }
+  __device__ __forceinline__ float operator()(uint32_t x) const { return pwp_eval_word(x, rows, e_sing, scale_k); }
 };
 
 template <>
 struct ApproxTable<AICDF_PWC> {
-  const float *s;
-  uint32_t shift;
+  const float *w;  // word-order copy of the table
+  PwcWord pw;
   __device__ ApproxTable(const float *tab, int ntab, float *smem) {
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) smem[i] = tab[i];
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) smem[i] = tab[pwc_word_row(i, ntab)];
     __syncthreads();
-    s = smem;
-    shift = 23u - (31u - __clz(ntab));  // ntab = 2^q: floor(ntab u) = m >> (23 - q)
+    w = smem;
+    pw = pwc_word(31u - __clz(ntab));  // ntab = 2^q
   }
-  __device__ __forceinline__ float operator()(uint32_t x, float) const {
-    return s[pwc_index_from_word(x, shift)];
-  }
+  __device__ __forceinline__ float operator()(uint32_t x) const { return w[pwc_slot_from_word(x, pw)]; }
 };
 
 // Steps are written as X <- X + increment so that FP32 rounding of the
@@ -229,14 +225,13 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const float u = u01(w[t]);
       if (NE) {
-        const float ze = phiinv_f32_grid(u);
+        const float ze = phiinv_f32_word(w[t]);
         xfe = step_fine<MODEL>(xfe, ze, pc);
         se += ze;
       }
       if (NA) {
-        float za = ap(w[t], u);
+        float za = ap(w[t]);
         if (V16) za = __half2float(__float2half_rn(za));
         xfa = step_fine<MODEL>(xfa, za, pc);
         sa += za;
@@ -269,14 +264,13 @@ __device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc,
 #pragma unroll
     for (int s = 0; s < NF; ++s) {
       const uint32_t x = w[g * NF + s];
-      const float u = u01(x);
       if (NE) {
-        const float ze = phiinv_f32_grid(u);
+        const float ze = phiinv_f32_word(x);
         xfe = step_fine<MODEL>(xfe, ze, pc);
         se += ze;
       }
       if (NA) {
-        float za = ap(x, u);
+        float za = ap(x);
         if (V16) za = __half2float(__float2half_rn(za));
         xfa = step_fine<MODEL>(xfa, za, pc);
         sa += za;

@@ -36,21 +36,27 @@ struct Approx;
 
 template <int SRC>
 struct Approx<AICDF_PWC, SRC> {
-  const float *s;
+  const float *s, *w;  // the table in row order; its word-order copy (Philox source)
   float nf;
   int nmax;
-  uint32_t shift;
+  PwcWord pw;
   int q;  // n_table = 2^q
-  __device__ Approx(const SampleArgs &a, float *smem) {
-    for (int i = threadIdx.x; i < a.ntab; i += blockDim.x) smem[i] = a.tab[i];
+  __device__ Approx(const SampleArgs &a, float *smem) {  // smem: 2 n floats
+    const int n = a.ntab;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = a.tab[i];
     __syncthreads();
+    if (SRC == SRC_PHILOX) {  // the word-order copy from shared memory, not the parameter space
+      for (int i = threadIdx.x; i < n; i += blockDim.x) smem[n + i] = smem[pwc_word_row(i, n)];
+      __syncthreads();
+    }
     s = smem;
+    w = smem + n;
     nf = a.nf;
-    nmax = a.ntab - 1;
-    shift = a.pwc_shift;
+    nmax = n - 1;
     q = 23 - (int)a.pwc_shift;
+    pw = pwc_word((uint32_t)q);
   }
-  __device__ __forceinline__ float word(uint32_t x) const { return s[pwc_index_from_word(x, shift)]; }
+  __device__ __forceinline__ float word(uint32_t x) const { return w[pwc_slot_from_word(x, pw)]; }
   __device__ __forceinline__ float operator()(float u) const { return pwc_eval(u, s, nf, nmax); }
   // cell m of a B-bit uniform: floor(2^q (m + 1/2) 2^-B)
   template <int B>
@@ -69,7 +75,7 @@ struct Approx<AICDF_PWL, SRC> {
     else c = pwl_lane_coefs(a.tab, a.tab + 16);
     kmax = (unsigned)a.ntab;
   }
-  __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_grid(u01(x), rows); }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_word(x, rows); }
   __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const { return pwl_eval_grid(ubits<B>(m), rows); }
@@ -87,7 +93,7 @@ struct Approx<AICDF_PWP, SRC> {
     e_sing = 126u - (uint32_t)a.ntab;
     scale_k = a.nf;  // 2^K
   }
-  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_grid(u01(x), rows, e_sing, scale_k); }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_word(x, rows, e_sing, scale_k); }
   __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K, scale_k); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const {
@@ -98,7 +104,7 @@ struct Approx<AICDF_PWP, SRC> {
 template <int SRC>
 struct Approx<AICDF_EXACT, SRC> {
   __device__ Approx(const SampleArgs &, float *) {}
-  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32_grid(u01(x)); }
+  __device__ __forceinline__ float word(uint32_t x) const { return phiinv_f32_word(x); }
   __device__ __forceinline__ float operator()(float u) const { return phiinv_f32(u); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const { return phiinv_f32_grid(ubits<B>(m)); }
@@ -146,7 +152,7 @@ __device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
 // SRC_INPUT: u 16-byte aligned.
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
   const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
 // Philox calls of its four 16-byte vectors interleaved round by round.
 template <int METHOD, int OUT>
 __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -330,7 +336,7 @@ __device__ __forceinline__ void call_samples(const Approx<METHOD, SRC_PHILOX> &f
 // q x 32 + L (q < NC) interleaved, and each q writes one contiguous span.
 template <int METHOD, int OUT, int B>
 __global__ void __launch_bounds__(256) k_sample_bits(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(256) k_sample_bits(const __grid_constant__ Sam
 // its call; only for ragged or unaligned requests).
 template <int METHOD, int OUT, int B>
 __global__ void __launch_bounds__(256) k_sample_bits_scalar(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(256) k_sample_bits_scalar(const __grid_constan
 // Scalar kernel for unaligned pointers or an offset not divisible by 4.
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 1024 : 1];
+  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
   const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);

@@ -69,15 +69,27 @@ def test_philox_stream_mapping(orc):
 
 
 def test_u01_grid(orc):
-    """Open, symmetric, FP32-exact grid from the low 23 bits: u(x) + u(~x) = 1,
-    u in [2^-24, 1-2^-24], and the top 9 bits are ignored."""
-    xs = [0, 1, 511, 512, 0x7FFFFF, 0x800000, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF, 0x12345678]
+    """Open, FP32-exact midpoint grid of 2^23 cells: the top bit picks the
+    half and the low 22 bits the cell, mirrored in the upper half, so that
+    u(x) + u(x ^ 2^31) = 1; u in [2^-24, 1-2^-24], never 1/2, and bits 22..30
+    are ignored."""
+    xs = [0, 1, 511, 512, 0x3FFFFF, 0x400000, 0x7FFFFF, 0x800000, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00,
+          0xFFFFFFFF, 0x12345678]
     for x in xs:
-        a, b = orc.u01(x), orc.u01((~x) & 0xFFFFFFFF)
-        assert a + b == 1.0
+        a, b = orc.u01(x), orc.u01(x ^ 0x80000000)
+        assert a + b == 1.0 and a != 0.5
         assert float(np.float32(a)) == a and float(np.float32(1.0 - a)) == 1.0 - a
-    assert orc.u01(0) == 2.0 ** -24 and orc.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
-    assert orc.u01(0xFF800000) == 2.0 ** -24 and orc.u01(0x0000_1235) == (2 * 0x1235 + 1) * 2.0 ** -24
+        assert orc.u01(x ^ 0x7FC00000) == a  # bits 22..30
+        assert (a < 0.5) == (x < 0x80000000)
+    assert orc.u01(0) == 2.0 ** -24 and orc.u01(0x80000000) == 1.0 - 2.0 ** -24
+    assert orc.u01(0x3FFFFF) == 0.5 - 2.0 ** -24 and orc.u01(0xBFFFFFFF) == 0.5 + 2.0 ** -24
+    assert orc.u01(0x0000_1235) == (2 * 0x1235 + 1) * 2.0 ** -24
+    assert orc.u01(0x8000_1235) == 1.0 - (2 * 0x1235 + 1) * 2.0 ** -24
+    # distinct (top bit, low 22 bits) give distinct cells
+    rng = np.random.default_rng(3)
+    ws = np.unique(rng.integers(0, 1 << 23, 4000)).tolist()
+    us = {orc.u01(((w >> 22) << 31) | (w & 0x3FFFFF)) for w in ws}
+    assert len(us) == len(ws)
 
 
 @pytest.mark.parametrize("bits", [1, 8, 10, 16])
