@@ -94,6 +94,15 @@ __device__ __forceinline__ float ubits(uint32_t m) {
   return __uint_as_float(0x3F800000u | (m << (23 - B))) - c;
 }
 
+// u - 1/2 of the same cell in one exact add: (1 + m 2^-B) - (3/2 - 2^-(B+1));
+// the constant is exact in FP32 for B <= 22 and the result needs B + 1 bits.
+template <int B>
+__device__ __forceinline__ float tbits(uint32_t m) {
+  static_assert(B >= 1 && B <= 22, "field width");
+  constexpr float c = 1.5f - 1.0f / (float)(2u << B);
+  return __uint_as_float(0x3F800000u | (m << (23 - B))) - c;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 1 for uniforms on the 2^-24 grid (the library's own uniforms).
 // On the grid, u - 1/2 and 1/2 - |u - 1/2| are exact, so v = min(u, 1-u) costs
@@ -123,9 +132,8 @@ __device__ __forceinline__ float pwl_eval_word(uint32_t x, const PwlRows &c) {
   return __uint_as_float(__float_as_uint(fmaf(b, v, a)) ^ (x & 0x80000000u));
 }
 
-// Must be called by all 32 lanes of the warp.
-__device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) {
-  const float t = u - 0.5f;
+// Must be called by all 32 lanes of the warp; t = u - 1/2 (exact).
+__device__ __forceinline__ float pwl_eval_t(float t, const PwlRows &c) {
   const float v = 0.5f - fabsf(t);
   const uint32_t e = __float_as_uint(v) >> 23;  // the shuffle uses e mod 32
   const float a = __shfl_sync(0xffffffffu, c.a, e);
@@ -133,6 +141,7 @@ __device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) {
   const float z = fmaf(b, v, a);
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
 }
+__device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) { return pwl_eval_t(u - 0.5f, c); }
 
 // ---------------------------------------------------------------------------
 // Piecewise polynomial (degree <= 3) on the dyadic intervals, Horner's rule in
@@ -161,12 +170,14 @@ __device__ __forceinline__ float pwp_eval_v(float v, uint32_t lane, bool singula
 }
 
 // Grid uniforms: lane = biased exponent e of v (mod 32), singular when e <= 126 - K.
-__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c, uint32_t e_sing, float scale_k) {
-  const float t = u - 0.5f;
+__device__ __forceinline__ float pwp_eval_t(float t, const PwpRows &c, uint32_t e_sing, float scale_k) {
   const float v = 0.5f - fabsf(t);
   const uint32_t e = __float_as_uint(v) >> 23;
   const float z = pwp_eval_v(v, e, e <= e_sing, scale_k, c);
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
+}
+__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c, uint32_t e_sing, float scale_k) {
+  return pwp_eval_t(u - 0.5f, c, e_sing, scale_k);
 }
 
 // The same for a word x: equals pwp_eval_grid(u01(x), ...).

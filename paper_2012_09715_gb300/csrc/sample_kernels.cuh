@@ -78,7 +78,7 @@ struct Approx<AICDF_PWL, SRC> {
   __device__ __forceinline__ float word(uint32_t x) const { return pwl_eval_word(x, rows); }
   __device__ __forceinline__ float operator()(float u) const { return pwl_eval(u, c, kmax); }
   template <int B>
-  __device__ __forceinline__ float cell(uint32_t m) const { return pwl_eval_grid(ubits<B>(m), rows); }
+  __device__ __forceinline__ float cell(uint32_t m) const { return pwl_eval_t(tbits<B>(m), rows); }
 };
 
 template <int SRC>
@@ -97,7 +97,7 @@ struct Approx<AICDF_PWP, SRC> {
   __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K, scale_k); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const {
-    return pwp_eval_grid(ubits<B>(m), rows, e_sing, scale_k);
+    return pwp_eval_t(tbits<B>(m), rows, e_sing, scale_k);
   }
 };
 
