@@ -206,7 +206,7 @@ def _approx_arrays(approx_table):
 def mlmc_level(prm: SdeParams, approx_table, level: int, kind: int, n_paths: int,
                path_offset: int = 0, seed: int = 0, tag: int = 1) -> np.ndarray:
     a, b, K = _approx_arrays(approx_table)
-    sums = np.zeros(3, dtype=np.float64)
+    sums = np.zeros(5, dtype=np.float64)
     lib().or_mlmc_level(C.byref(prm), _p(a), _p(b), K, level, kind, n_paths, path_offset,
                         seed, tag, _p(sums))
     return sums

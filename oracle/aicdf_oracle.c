@@ -19,7 +19,10 @@
  *                   mpmath quadrature of the normal equations, the Peano bound.
  *   samplers        brute force over the uniform grid near every interval edge.
  *   or_mlmc_level   exact Euler-Maruyama moments for P(X)=X, the Black-Scholes
- *                   price, the CIR mean.
+ *                   price, the CIR mean; Milstein: the GBM step-factor moments
+ *                   E[X_N^k], k <= 3, for exact and approximate variates, the
+ *                   strong-order-1 decay of the two-way variance (GBM and CIR),
+ *                   and the CIR mean with exact and approximate variates.
  *   or_mlmc_alloc   the speed-ups printed in Table 2 and Table 6.
  *   ncx2            lambda = 0 closed forms, moments, scipy.stats.ncx2.ppf.
  *   mlp             central finite differences.
@@ -544,17 +547,21 @@ void or_mlmc_paths(const or_sde_params *prm, const float *alpha, const float *be
 
 void or_mlmc_level(const or_sde_params *prm, const float *alpha, const float *beta, int K,
                    int level, int kind, uint64_t n_paths, uint64_t path_offset,
-                   uint64_t seed, uint32_t tag, double sums[3]) {
-  double s1 = 0.0, s2 = 0.0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : s1, s2)
+                   uint64_t seed, uint32_t tag, double sums[5]) {
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : s1, s2, s3, s4)
   for (int64_t i = 0; i < (int64_t)n_paths; ++i) {
     double y = path_value(prm, alpha, beta, K, level, kind, path_offset + (uint64_t)i, seed, tag);
     s1 += y;
     s2 += y * y;
+    s3 += y * y * y;
+    s4 += y * y * y * y;
   }
   sums[0] = s1;
   sums[1] = s2;
-  sums[2] = (double)n_paths;
+  sums[2] = s3;
+  sums[3] = s4;
+  sums[4] = (double)n_paths;
 }
 
 /* ========================================================================== */

@@ -83,8 +83,10 @@ typedef struct {
   double discount;        /* payoff multiplier, e.g. exp(-rT)             */
 } or_sde_params;
 
-/* Sums over paths p = path_offset .. path_offset+n_paths-1 of Y and Y^2
- * for the level estimator of the given kind.  sums = {sum Y, sum Y^2, n}.
+/* Power sums over paths p = path_offset .. path_offset+n_paths-1 of Y for the
+ * level estimator of the given kind (Section 4.1: sample mean and variance,
+ * plus the third and fourth power sums behind the kurtosis).
+ * sums = {sum Y, sum Y^2, sum Y^3, sum Y^4, n}.
  * Uniform for fine step s of path p: Philox4x32-10 with key = (seed mod 2^32,
  * seed>>32); for level >= 2, ctr = (s/4, p mod 2^32, p>>32, tag) and word s%4;
  * for levels 0 and 1 (2^level < 4 fine steps) G = 4/2^level paths share one
@@ -93,7 +95,7 @@ typedef struct {
  * PWP (alpha = (K+1) x 4 polynomial coefficients, K). */
 void or_mlmc_level(const or_sde_params *prm, const float *alpha, const float *beta, int K,
                    int level, int kind, uint64_t n_paths, uint64_t path_offset,
-                   uint64_t seed, uint32_t tag, double sums[3]);
+                   uint64_t seed, uint32_t tag, double sums[5]);
 /* single path values (for tests): writes Y of each path */
 void or_mlmc_paths(const or_sde_params *prm, const float *alpha, const float *beta, int K,
                    int level, int kind, uint64_t n_paths, uint64_t path_offset,

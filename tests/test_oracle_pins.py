@@ -520,6 +520,114 @@ def test_mlmc_em_exact_moments(orc):
             assert abs((y ** 2).mean() - m2) < 4.5 * se2
 
 
+def _pwl_even_moments(a, b, K=15):
+    """E[D(U)^k] for k = 0..6 of the piecewise-linear approximation on (0, 1):
+    D is odd about 1/2, so odd moments vanish and the even ones are twice the
+    integrals of (alpha_k + beta_k u)^k over the lower-half intervals."""
+    m = np.zeros(7)
+    for k in range(1, K + 1):
+        hi = 2.0 ** -k
+        lo = 0.0 if k == K else hi / 2
+        line = np.polynomial.Polynomial([a[k], b[k]])
+        for p in (2, 4, 6):
+            F = (line ** p).integ()
+            m[p] += 2 * (F(hi) - F(lo))
+    m[0] = 1.0
+    return m
+
+
+def _milstein_factor_moments(mu, sigma, h, mz):
+    """E[f^k], k = 1..3, of the GBM Milstein step factor f = A + B Z + C Z^2
+    (A = 1 + mu h - sigma^2 h / 2, B = sigma sqrt(h), C = sigma^2 h / 2), from
+    the moments mz[0..6] of Z (Section 4, Fig. 3b: X' = X f)."""
+    A, B, C = 1 + mu * h - 0.5 * sigma ** 2 * h, sigma * math.sqrt(h), 0.5 * sigma ** 2 * h
+    f = np.polynomial.Polynomial([A, B, C])
+    out = []
+    for k in (1, 2, 3):
+        coef = (f ** k).coef
+        out.append(sum(c * mz[j] for j, c in enumerate(coef)))
+    return out
+
+
+def test_mlmc_milstein_gbm_moments(orc):
+    """GBM Milstein with P(X) = X: the step factors are independent, so
+    E[X_N^k] = X0^k (E f^k)^N.  For exact variates E f = 1 + mu h and
+    E f^2 = (1 + mu h)^2 + sigma^2 h + sigma^4 h^2 / 2; for the approximate ones
+    the moments of D enter through the same polynomial.  sigma = 0.5 makes the
+    Milstein term large enough that a wrong sign or factor in it (both change
+    E f^2 or E f^3 by 10-20 standard errors here) fails the test."""
+    a, b = orc.pwl_table(15, 0.5)
+    mz_exact = np.array([1.0, 0.0, 1.0, 0.0, 3.0, 0.0, 15.0])
+    mz_pwl = _pwl_even_moments(a, b)
+    mu, sigma = 0.05, 0.5
+    # the expansion reproduces the closed forms for the exact Gaussian
+    for h in (1.0, 0.125):
+        e1, e2, _ = _milstein_factor_moments(mu, sigma, h, mz_exact)
+        assert e1 == pytest.approx(1 + mu * h, rel=1e-14)
+        assert e2 == pytest.approx((1 + mu * h) ** 2 + sigma ** 2 * h + sigma ** 4 * h * h / 2, rel=1e-14)
+    prm = orc.sde_params(model=orc.MODEL_GBM, scheme=orc.SCHEME_MILSTEIN, payoff=orc.PAYOFF_X,
+                         X0=1.0, T=1.0, mu=mu, sigma=sigma, discount=1.0)
+    n = 40000
+    for level in (0, 2):
+        N = 2 ** level
+        h = 1.0 / N
+        for kind, mz in ((orc.KIND_PLAIN, mz_exact), (orc.KIND_PLAIN_APPROX, mz_pwl)):
+            y = orc.mlmc_paths(prm, (a, b), level, kind, n, seed=13, tag=17)
+            want = _milstein_factor_moments(mu, sigma, h, mz)
+            for k in (1, 2, 3):
+                yk = y ** k
+                se = yk.std() / math.sqrt(n)
+                assert abs(yk.mean() - want[k - 1] ** N) < 4.5 * se, (level, kind, k)
+
+
+def test_mlmc_milstein_strong_order(orc):
+    """Milstein has strong order 1, so the two-way exact variance
+    V[P_l - P_(l-1)] of P(X) = X falls like h^2: slope -2 per level, against -1
+    for Euler-Maruyama (Section 4, Fig. 3a/3b).  GBM with the config's
+    parameters, and CIR with the Feller condition well satisfied (kappa = 0.5,
+    theta = X0 = 1, sigma = 0.3), where sqrt(|X|) never meets 0 and the
+    Milstein term sigma^2 (dW^2 - h) / 4 gives order 1 as well.  A wrong sign or
+    factor in either Milstein term brings the slope back to about -1.  (For
+    this CIR set Euler-Maruyama's order-1/2 term sigma^4 h / 8 per unit time
+    is small, so at levels 2..6 its slope reads about -1.5: the test asks that
+    it stay well above Milstein's.)"""
+    a, b = orc.pwl_table(15, 0.5)
+    gbm = dict(model=orc.MODEL_GBM, payoff=orc.PAYOFF_X, X0=1.0, T=1.0, mu=0.05, sigma=0.2, discount=1.0)
+    cir = dict(model=orc.MODEL_CIR, payoff=orc.PAYOFF_X, X0=1.0, T=1.0, sigma=0.3, kappa=0.5, theta=1.0,
+               discount=1.0)
+    for base in (gbm, cir):
+        slopes = {}
+        for scheme in (orc.SCHEME_EM, orc.SCHEME_MILSTEIN):
+            prm = orc.sde_params(scheme=scheme, **base)
+            v = [orc.mlmc_paths(prm, (a, b), level, orc.KIND_EXACT2, 20000, seed=4, tag=3).var()
+                 for level in (2, 4, 6)]
+            slopes[scheme] = (math.log2(v[2]) - math.log2(v[0])) / 4
+        assert -2.4 < slopes[orc.SCHEME_MILSTEIN] < -1.7, (base["model"], slopes)
+        em_lo = -1.3 if base is gbm else -1.7
+        assert em_lo < slopes[orc.SCHEME_EM] < -0.7, (base["model"], slopes)
+        assert slopes[orc.SCHEME_EM] > slopes[orc.SCHEME_MILSTEIN] + 0.4, (base["model"], slopes)
+
+
+def test_mlmc_milstein_cir_mean_exact(orc):
+    """The CIR Milstein step adds sigma^2 (dW^2 - h) / 4, whose mean is zero for
+    exact variates, so E[X_N] = theta + (X0 - theta)(1 - kappa h)^N as for
+    Euler-Maruyama; with the approximate variates E[dW~^2] = h E[D^2], which
+    moves the fixed point to theta + sigma^2 (E[D^2] - 1) / (4 kappa)."""
+    a, b = orc.pwl_table(15, 0.5)
+    m2 = _pwl_even_moments(a, b)[2]
+    kappa, theta, sigma, X0 = 0.5, 0.04, 0.3, 0.09
+    prm = orc.sde_params(model=orc.MODEL_CIR, scheme=orc.SCHEME_MILSTEIN, payoff=orc.PAYOFF_X, X0=X0,
+                         T=1.0, sigma=sigma, kappa=kappa, theta=theta, discount=1.0)
+    for level in (2, 5):
+        N = 2 ** level
+        h = 1.0 / N
+        for kind, th in ((orc.KIND_PLAIN, theta),
+                         (orc.KIND_PLAIN_APPROX, theta + sigma ** 2 * (m2 - 1) / (4 * kappa))):
+            y = orc.mlmc_paths(prm, (a, b), level, kind, 30000, seed=6, tag=10)
+            want = th + (X0 - th) * (1 - kappa * h) ** N
+            assert abs(y.mean() - want) < 4.5 * y.std() / math.sqrt(y.size), (level, kind)
+
+
 def test_mlmc_telescoping_black_scholes(orc):
     """Nested MLMC sum over levels of APPROX2 + CORR4 means matches the
     Black-Scholes call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1) within the
@@ -536,12 +644,44 @@ def test_mlmc_telescoping_black_scholes(orc):
                           (4, 20000, 2000), (5, 10000, 2000)):
         s2 = orc.mlmc_level(prm, (a, b), level, orc.KIND_APPROX2, n2, seed=3, tag=100 + level)
         s4 = orc.mlmc_level(prm, (a, b), level, orc.KIND_CORR4, n4, seed=3, tag=200 + level)
-        for (S1, S2, N) in (s2, s4):
+        for (S1, S2, _, _, N) in (s2, s4):
             m = S1 / N
             est += m
             var += (S2 / N - m * m) / N
     bias_bound = 0.1045 * 2.0 ** -5 * 2   # EM weak error is O(dt); generous constant
     assert abs(est - bs) < 4 * math.sqrt(var) + bias_bound
+
+
+def test_mlmc_level_power_sums(orc):
+    """The level sums carry sum Y^k, k = 1..4 (Section 4.1 sample moments and
+    the kurtosis).  For GBM Euler-Maruyama with P(X) = X the step factors
+    f = 1 + mu h + sigma sqrt(h) Z are independent, so E[Y^k] = X0^k (E f^k)^N
+    with E f^k from the Gaussian moments 1, 0, 1, 0, 3; each power sum / n
+    must match within 4.5 standard errors, and a dropped or mis-indexed power
+    fails.  The fourth-moment ratio of a one-step PLAIN term is the Gaussian 3
+    less a small correction, which the same sums reproduce."""
+    mz = np.array([1.0, 0.0, 1.0, 0.0, 3.0, 0.0, 15.0, 0.0, 105.0])
+    mu, sigma = 0.05, 0.2
+    prm = _gbm(orc, orc.PAYOFF_X)
+    a, b = orc.pwl_table(15, 0.5)
+    n = 60000
+    for level in (0, 2):
+        N = 2 ** level
+        h = 1.0 / N
+        f = np.polynomial.Polynomial([1 + mu * h, sigma * math.sqrt(h)])
+        want = [sum(c * mz[j] for j, c in enumerate((f ** k).coef)) ** N for k in (1, 2, 3, 4)]
+        sums = orc.mlmc_level(prm, (a, b), level, orc.KIND_PLAIN, n, seed=21, tag=5)
+        y = orc.mlmc_paths(prm, (a, b), level, orc.KIND_PLAIN, n, seed=21, tag=5)   # for the SEs
+        assert sums[4] == n
+        for k in (1, 2, 3, 4):
+            se = (y ** k).std() / math.sqrt(n)
+            assert abs(sums[k - 1] / n - want[k - 1]) < 4.5 * se, (level, k, sums[k - 1] / n, want[k - 1])
+    # level 0: Y = X0 f, kurtosis of f = 3 exactly (a Gaussian), from the sums
+    s = orc.mlmc_level(prm, (a, b), 0, orc.KIND_PLAIN, 200000, seed=22, tag=6)
+    m, e2, e3, e4 = (s[k] / s[4] for k in range(4))
+    v = e2 - m * m
+    kurt = (e4 - 4 * m * e3 + 6 * m * m * e2 - 3 * m ** 4) / v ** 2
+    assert abs(kurt - 3.0) < 0.1, kurt
 
 
 def test_mlmc_cir_mean_exact(orc):
