@@ -167,23 +167,58 @@ def _time_device(fn, steps, warmup, stream):
     return t0.elapsed_time(t1), per
 
 
-def cpu_baseline(budget_s: float = 12.0, chunk: int = 1 << 20):
-    """The oracle (plain C, single thread) on a bounded sample of the workload:
-    Philox uniforms for consecutive sample indices + the piecewise-linear map."""
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_sampler_rate(threads: int, budget_s: float, chunk: int):
+    """Gsamples/s of the oracle (Philox uniforms + the piecewise-linear map, FP64
+    arithmetic) with `threads` OpenMP threads, over consecutive chunks of the
+    2^28-sample workload for about budget_s seconds; (rate, samples, seconds)."""
     import numpy as np
     import oracle
+    oracle.set_threads(threads)
     a, b = oracle.pwl_table(15, 0.5)
     a32, b32 = a.astype(np.float32), b.astype(np.float32)
     done, t = 0, 0.0
     while t < budget_s and done < N_SAMPLES:
+        m = min(chunk, N_SAMPLES - done)
         t0 = time.perf_counter()
-        u = oracle.uniforms(0, done, chunk)
+        u = oracle.uniforms(0, done, m)
         oracle.sample_pwl(a32, b32, u)
         t += time.perf_counter() - t0
-        done += chunk
-    return {"value": done / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of the 2^28 samples (Philox + piecewise-linear map, FP64 "
-                      f"arithmetic), single thread, {t:.1f} s"}
+        done += m
+    return done / t / 1e9, done, t
+
+
+def cpu_baseline(budget_s: float = 12.0, chunk: int = 1 << 20):
+    """The oracle on the host: one thread, and OpenMP over every host core, each
+    on a bounded sample of the workload (Philox uniforms for consecutive sample
+    indices + the piecewise-linear map).  The headline value is the all-core
+    rate; the single-thread rate is reported beside it."""
+    cores = os.cpu_count() or 1
+    v1, n1, t1 = _oracle_sampler_rate(1, budget_s, chunk)
+    va, na, ta = _oracle_sampler_rate(cores, budget_s / 2, chunk * 8)
+    return {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {na} of the 2^28 samples with {cores} threads ({ta:.1f} s); first {n1} with one "
+                      f"thread ({t1:.1f} s); Philox + piecewise-linear map, FP64 arithmetic",
+            "value_1thread": v1, "cores_all": cores, "value_all": va, "cpu_model": _cpu_model()}
 
 
 def sampler_sweep(P, tl, dev, stream):
@@ -221,7 +256,7 @@ def batch_sweep(P, dev, stream):
             steps += (int(n2[s, l]) + int(n4[s, l])) << l
     tl = P.table_build(P.PWL, 15)
     b = P.Batch(sets, terms, tl, seed=0)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device=dev)
     big = max(b.workspace_bytes(P.Schedule(t * m, t, 0, 1)) for t in (128, 256) for m in (2, 8, 32, 128))
     ws = torch.empty(big, dtype=torch.uint8, device=dev)
     best, tune_ms = b.autotune(sums, ws, var16=1, stream=stream)
@@ -253,18 +288,18 @@ def gbm_levels_batch(P, dev, stream):
             terms.append(P.BatchTerm(0, l, kind, 2 * l + 1 + (kind == P.KIND_CORR4), n, 0))
             steps += n << l
     b = P.Batch([prm], terms, tl, seed=0)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device=dev)
     big = max(b.workspace_bytes(P.Schedule(t * m, t, 0, 0)) for t in (128, 256) for m in (2, 8, 32, 128))
     ws = torch.empty(big, dtype=torch.uint8, device=dev)
     best, tune_ms = b.autotune(sums, ws, var16=0, stream=stream)
     tot, per = _time_device(lambda: b.run(best, sums, ws, stream=stream), 5, 2, stream)
     ms = statistics.mean(per)
-    sm = sums.view(-1, 3).cpu().numpy()
-    est = float(sum(r[0] / r[2] for r in sm))
-    var = float(sum((r[1] / r[2] - (r[0] / r[2]) ** 2) / r[2] for r in sm))
+    sm = sums.view(-1, P.SUMS).cpu().numpy()
+    est = float(sum(r[0] / r[4] for r in sm))
+    var = float(sum((r[1] / r[4] - (r[0] / r[4]) ** 2) / r[4] for r in sm))
     # the same terms as separate level launches
     lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+    s3 = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
 
     def separate():
         for t in terms:
@@ -282,6 +317,9 @@ def gbm_levels_batch(P, dev, stream):
             "path_steps_per_s": steps / (ms / 1e3), "separate_launches_ms": sep_ms,
             "schedule": best.as_dict(), "tiles": n_items, "grid": grid, "autotune_best_ms": tune_ms,
             "estimate": est, "std_err": math.sqrt(var), "black_scholes": bs}
+
+
+_TRAINED = {}   # the surrogate trained by cir_surrogate, reused by cir_learned_vs_table
 
 
 def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
@@ -328,7 +366,7 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=0.04, T=1.0, K=0.0, mu=0.0, sigma=0.3, kappa=0.5,
                        theta=0.04, discount=1.0)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
     levels = []
     for l in range(7):
         n = 20000
@@ -341,6 +379,7 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
         row["log2_var_ratio_surrogate"] = math.log2(row["diff_var"] / row["exact_var"])
         row["log2_var_ratio_gauss"] = math.log2(row["diff_gauss_var"] / row["exact_var"])
         levels.append(row)
+    _TRAINED["surrogate"] = s
     return {"nu": nu, "train_samples": n_train, "epochs": epochs, "train_ms": t_train_ms,
             "final_batch_mse": float(loss.item()), "heldout_rmse": rmse, "heldout_rmse_gauss_limit": rmse_g,
             "exact_quantiles_per_s": n_train / (t_exact_ms / 1e3),
@@ -373,7 +412,7 @@ def cir_table(P, dev, stream, n_eval: int = 1 << 22):
     prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
                        theta=1.0, discount=1.0)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
     out = torch.empty(n_eval, device=dev)
     for deg, name in ((1, "linear"), (3, "cubic")):
         t0 = _t.perf_counter()
@@ -396,68 +435,165 @@ def cir_table(P, dev, stream, n_eval: int = 1 << 22):
     return res
 
 
-def cir_time_to_rmse(P, dev, stream, eps: float = 1e-3, level: int = 3, deg: int = 1):
-    """Section 5.2 savings on the GPU: E[X_T] of the paper's CIR set (kappa 1/2,
-    theta = sigma = T = X0 = 1, nu = 2; 2^level exact per-step transitions, so no
-    time bias) to RMSE eps, by (a) exact transitions only and (b) the nested
-    estimator E[P~] + E[P^ - P~] with the Section 5.1 table, paths split by the
-    optimal allocation (Section 4.1) from pilot variances and timed pilot costs.
-    Wall times include the pilots."""
+def _nested_vs_exact(run, eps, n0=1 << 12):
+    """E[P] to RMSE eps (a) with exact transitions only and (b) with the nested
+    estimator E[P~] + E[P^ - P~] (Section 5.2), the paths of (b) split by the
+    optimal allocation (Section 4.1) from pilot variances and timed pilot
+    costs.  run(kind, n, offset, tag) -> (sums, gpu_ms) for kind in 'exact',
+    'approx', 'diff'.  Wall times include the pilots."""
     import math
     import time as _t
-    import torch
-    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
-                       theta=1.0, discount=1.0)
-    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    sums = torch.zeros(3, dtype=torch.float64, device=dev)
-    st = torch.zeros(1, dtype=torch.int32, device=dev)
-    table = P.Ncx2Table(2.0, 16, 16, deg)
-
-    def run(kind, n, off, tag):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.cir_level_table(prm, table, level, kind, n, sums, ws, st, path_offset=off, seed=21, tag=tag,
-                          stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        v = sums.cpu().numpy().copy()
-        return v, e0.elapsed_time(e1)
-
-    run(P.CIR_EXACT, 1 << 12, 0, 99)  # warm-up
-    run(P.CIR_TABLE, 1 << 12, 0, 99)
-    res = {"eps": eps, "level": level, "degree": deg}
-    # (a) exact only
+    res = {"eps": eps, "pilot_paths": n0}
     w0 = _t.perf_counter()
-    n0 = 1 << 12  # pilot paths per term
-    pv, pms = run(P.CIR_EXACT, n0, 0, 1)
+    pv, pms = run("exact", n0, 0, 1)
     var = pv[1] / n0 - (pv[0] / n0) ** 2
     n = max(n0, int(math.ceil(var / eps ** 2)))
-    v, ms = run(P.CIR_EXACT, n - n0, n0, 1)
+    v, ms = run("exact", n - n0, n0, 1)
     tot = pv + v
     res["exact"] = {"estimate": tot[0] / n, "paths": n, "gpu_ms": pms + ms, "wall_ms": 1e3 * (_t.perf_counter() - w0),
                     "var": var, "ns_per_path": 1e6 * pms / n0}
-    # (b) nested: table paths + exact-minus-table correction
     w0 = _t.perf_counter()
-    pa, ta = run(P.CIR_TABLE, n0, 0, 2)
-    pc, tc = run(P.CIR_DIFF_TABLE, n0, 0, 3)
+    pa, ta = run("approx", n0, 0, 2)
+    pc, tc = run("diff", n0, 0, 3)
     va = pa[1] / n0 - (pa[0] / n0) ** 2
     vc = max(pc[1] / n0 - (pc[0] / n0) ** 2, 1e-300)
     ca, cc = ta / n0, tc / n0
     k = (math.sqrt(va * ca) + math.sqrt(vc * cc)) / eps ** 2
     na = max(n0, int(math.ceil(k * math.sqrt(va / ca))))
     nc = max(n0, int(math.ceil(k * math.sqrt(vc / cc))))
-    a2, ma = run(P.CIR_TABLE, na - n0, n0, 2) if na > n0 else (pa * 0, 0.0)
-    c2, mc = run(P.CIR_DIFF_TABLE, nc - n0, n0, 3) if nc > n0 else (pc * 0, 0.0)
+    a2, ma = run("approx", na - n0, n0, 2) if na > n0 else (pa * 0, 0.0)
+    c2, mc = run("diff", nc - n0, n0, 3) if nc > n0 else (pc * 0, 0.0)
     sa, sc = pa + a2, pc + c2
     est = sa[0] / na + sc[0] / nc
     rmse = math.sqrt(va / na + vc / nc)
-    res["nested"] = {"estimate": est, "rmse_est": rmse, "paths_table": na, "paths_correction": nc,
+    res["nested"] = {"estimate": est, "rmse_est": rmse, "paths_approx": na, "paths_correction": nc,
                      "gpu_ms": ta + tc + ma + mc, "wall_ms": 1e3 * (_t.perf_counter() - w0),
-                     "log2_var_ratio": math.log2(vc / va), "cost_ratio_exact_over_table": cc / ca}
+                     "log2_var_ratio": math.log2(vc / va), "cost_ratio_diff_over_approx": cc / ca}
     res["speedup_gpu"] = res["exact"]["gpu_ms"] / res["nested"]["gpu_ms"]
     res["speedup_wall"] = res["exact"]["wall_ms"] / res["nested"]["wall_ms"]
+    return res
+
+
+def _cir_runner(P, prm, level, stream, seed, table=None, sur=None):
+    """run(kind, n, offset, tag) for _nested_vs_exact: CIR paths of 2^level exact
+    transitions and either the Section 5.1 table or the learned surrogate."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    kinds = ({"exact": P.CIR_EXACT, "approx": P.CIR_TABLE, "diff": P.CIR_DIFF_TABLE} if table is not None else
+             {"exact": P.CIR_EXACT, "approx": P.CIR_SURROGATE, "diff": P.CIR_DIFF})
+
+    def run(kind, n, off, tag):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if table is not None:
+            P.cir_level_table(prm, table, level, kinds[kind], n, sums, ws, st, path_offset=off, seed=seed, tag=tag,
+                              stream=stream)
+        else:
+            P.cir_level(prm, sur, level, kinds[kind], n, sums, ws, st, path_offset=off, seed=seed, tag=tag,
+                        stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return sums.cpu().numpy().copy(), e0.elapsed_time(e1)
+
+    run("exact", 1 << 12, 0, 99)  # warm-up
+    run("approx", 1 << 12, 0, 99)
+    return run, st
+
+
+def cir_time_to_rmse(P, dev, stream, eps: float = 1e-3, level: int = 3, deg: int = 1):
+    """Section 5.2 savings on the GPU: E[X_T] of the paper's CIR set (kappa 1/2,
+    theta = sigma = T = X0 = 1, nu = 2; 2^level exact per-step transitions, so no
+    time bias) to RMSE eps, by (a) exact transitions only and (b) the nested
+    estimator with the Section 5.1 table of the given degree."""
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=1.0, T=1.0, K=0.0, mu=0.0, sigma=1.0, kappa=0.5,
+                       theta=1.0, discount=1.0)
+    table = P.Ncx2Table(2.0, 16, 16, deg)
+    run, st = _cir_runner(P, prm, level, stream, 21, table=table)
+    res = dict(_nested_vs_exact(run, eps), level=level, degree=deg)
     # E[X_T] = theta + (X0 - theta) e^{-kappa T} = 1 for this set
     res["exact_expectation"] = 1.0
+    res["root_finder_status"] = int(st.item())
+    return res
+
+
+def cir_learned_vs_table(P, dev, stream, sur, n_eval: int = 1 << 22, eps: float = 1e-4, level: int = 3):
+    """The learned surrogate against the Section 5.1 tables at the CIR
+    configuration's own nu = 4 kappa theta / sigma^2 = 0.889 (kappa 0.5, theta
+    0.04, sigma 0.3, X0 0.04, T 1): (1) RMSE of P~ against the exact P on
+    held-out (u, lambda) pairs with ln lambda ~ U(-4, 4) (the surrogate's
+    training law) and on lambda at the levels' own X = theta values; (2)
+    evaluations per second at 2^22 pairs; (3) log2 Var(X^_T - X~_T) / Var(X^_T)
+    for levels 0..6; (4) E[X_T] to RMSE eps at level `level` through the nested
+    estimator with each approximation, against exact transitions only."""
+    import math
+    import torch
+    if sur is None:
+        return {"error": "no trained surrogate (cir_surrogate did not run)"}
+    kappa, theta, sigma, X0 = 0.5, 0.04, 0.3, 0.04
+    nu = 4 * kappa * theta / sigma ** 2
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=X0, T=1.0, K=0.0, mu=0.0, sigma=sigma, kappa=kappa,
+                       theta=theta, discount=1.0)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    u, lam, tgt = (torch.empty(n_eval, device=dev) for _ in range(3))
+    P.ncx2_targets(nu, n_eval, u, lam, tgt, st, seed=123, tag=5, stream=stream)   # held out: other seed
+    tables = {"table_linear": P.Ncx2Table(nu, 16, 16, 1), "table_cubic": P.Ncx2Table(nu, 16, 16, 3)}
+    out = torch.empty(n_eval, device=dev)
+    res = {"nu": nu, "eval_pairs": n_eval, "approximations": {}}
+    t64 = tgt.double()
+    h = (lam + nu).double()
+
+    def p_rmse(p):
+        return math.sqrt(float(((p.double() - t64) ** 2).mean()))
+
+    for name, obj in [("surrogate", sur)] + list(tables.items()):
+        tot, per = _time_device(lambda: obj.eval(u, lam, out, stream=stream), 10, 3, stream)
+        torch.cuda.synchronize()
+        if name == "surrogate":
+            p = out
+        else:   # the table gives C~^{-1}; its P~ = (C~^{-1} - h) / (2 sqrt(h))
+            p = ((out.double() - h) / (2 * h.sqrt())).float()
+        res["approximations"][name] = {"evals_per_s": n_eval / (statistics.mean(per) / 1e3),
+                                       "heldout_rmse_P": p_rmse(p)}
+    from scipy.special import ndtri
+    res["approximations"]["gauss_limit"] = {
+        "heldout_rmse_P": math.sqrt(float(((torch.from_numpy(ndtri(u.cpu().numpy().astype("float64"))).to(dev)
+                                            - t64) ** 2).mean()))}
+    # per-level variance ratio of the two-way difference, same paths for all
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
+    n = 1 << 16
+    levels = []
+    for l in range(7):
+        row = {"l": l}
+        P.cir_level(prm, sur, l, P.CIR_EXACT, n, sums, ws, st, seed=31, tag=1 + l, stream=stream)
+        s = sums.cpu().numpy()
+        vx = s[1] / n - (s[0] / n) ** 2
+        P.cir_level(prm, sur, l, P.CIR_DIFF, n, sums, ws, st, seed=31, tag=1 + l, stream=stream)
+        s = sums.cpu().numpy()
+        row["surrogate"] = math.log2((s[1] / n - (s[0] / n) ** 2) / vx)
+        for name, t in tables.items():
+            P.cir_level_table(prm, t, l, P.CIR_DIFF_TABLE, n, sums, ws, st, seed=31, tag=1 + l, stream=stream)
+            s = sums.cpu().numpy()
+            row[name] = math.log2((s[1] / n - (s[0] / n) ** 2) / vx)
+        levels.append(row)
+    res["log2_var_ratio_per_level"] = levels
+    # nested time to RMSE with each approximation (same exact leg definition)
+    ttr = {}
+    for name, kw in (("surrogate", {"sur": sur}), ("table_linear", {"table": tables["table_linear"]}),
+                     ("table_cubic", {"table": tables["table_cubic"]})):
+        run, st2 = _cir_runner(P, prm, level, stream, 41, **kw)
+        r = _nested_vs_exact(run, eps)
+        ttr[name] = {"nested_gpu_ms": r["nested"]["gpu_ms"], "nested_wall_ms": r["nested"]["wall_ms"],
+                     "exact_gpu_ms": r["exact"]["gpu_ms"], "speedup_gpu": r["speedup_gpu"],
+                     "estimate": r["nested"]["estimate"], "rmse_est": r["nested"]["rmse_est"],
+                     "exact_estimate": r["exact"]["estimate"], "log2_var_ratio": r["nested"]["log2_var_ratio"],
+                     "paths_approx": r["nested"]["paths_approx"], "paths_correction": r["nested"]["paths_correction"],
+                     "status": int(st2.item())}
+    # E[X_T] = theta + (X0 - theta) e^{-kappa T} = theta here (X0 = theta)
+    res["time_to_rmse"] = dict(ttr, eps=eps, level=level, exact_expectation=theta)
     res["root_finder_status"] = int(st.item())
     return res
 
@@ -550,7 +686,7 @@ def oracle_host(P, tl, dev, budget_s: float = 2.0):
     oprm = oracle.sde_params()
     prm = P.sde_params()
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
     lvl = 5
     steps = 1 << lvl
     for name, ok, gk in (("approx2", oracle.KIND_APPROX2, P.KIND_APPROX2), ("corr4", oracle.KIND_CORR4, P.KIND_CORR4),
@@ -592,33 +728,50 @@ def oracle_host(P, tl, dev, budget_s: float = 2.0):
 
 
 def run_reference(args):
+    """The oracle timed on the host cores on the headline workload: every step
+    generates and maps the full 2^28 samples with OpenMP over all host cores
+    (a step whose first warm-up takes over 20 s is cut to a stated bounded
+    sample instead, so that the run ends within minutes)."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     import numpy as np
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     a, b = oracle.pwl_table(15, 0.5)
     a32, b32 = a.astype(np.float32), b.astype(np.float32)
-    chunk = 1 << 20   # bounded sample per step
+    sub = 1 << 22
+    per_step = N_SAMPLES
 
     def step(i):
-        u = oracle.uniforms(0, i * chunk, chunk)
-        oracle.sample_pwl(a32, b32, u)
+        base = (i * per_step) % N_SAMPLES
+        for off in range(0, per_step, sub):
+            m = min(sub, per_step - off)
+            u = oracle.uniforms(0, base + off, m)
+            oracle.sample_pwl(a32, b32, u)
 
-    for i in range(args.warmup):
+    t0 = time.perf_counter()
+    step(0)
+    first = time.perf_counter() - t0
+    if first > 20.0:   # bound the step to about 20 s of CPU work
+        per_step = max(sub, int(N_SAMPLES * 20.0 / first) // sub * sub)
+    for i in range(1, args.warmup):
         step(i)
     t0 = time.perf_counter()
     for i in range(args.steps):
         step(args.warmup + i)
     dt = time.perf_counter() - t0
-    val = args.steps * chunk / dt / 1e9
+    val = args.steps * per_step / dt / 1e9
+    sample = (f"{per_step} samples per step ({'the full 2^28 workload' if per_step == N_SAMPLES else 'of the 2^28 workload'}),"
+              f" {cores} OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, reference_sample_per_step=chunk),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{chunk} samples per step (of the 2^28 workload), single thread"},
+            "data": "synthetic", "config": dict(WORKLOAD, reference_sample_per_step=per_step),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -634,7 +787,7 @@ def profile_mlmc_kinds():
     P.lib()
     tl = P.table_build(P.PWL, 15)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     prm = P.sde_params()
     for kind in (P.KIND_APPROX2, P.KIND_EXACT2, P.KIND_CORR4):
         P.mlmc_level(prm, tl, 6, kind, 1 << 20, sums, ws, seed=1, tag=3)
@@ -672,7 +825,7 @@ def profile_kernels():
             terms.append(P.BatchTerm(s_, l, P.KIND_APPROX2, (s_ << 8) + 2 * l + 1, int(n2[s_, l]), 0))
             terms.append(P.BatchTerm(s_, l, P.KIND_CORR4, (s_ << 8) + 2 * l + 2, int(n4[s_, l]), 0))
     b = P.Batch(sets, terms, tl, seed=0)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device=dev)
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device=dev)
     sc = P.Schedule(16384, 128, 0, 1)
     ws = torch.empty(b.workspace_bytes(sc), dtype=torch.uint8, device=dev)
     b.run(sc, sums, ws)
@@ -680,7 +833,7 @@ def profile_kernels():
                        theta=1.0, discount=1.0)
     t = P.Ncx2Table(2.0, 16, 16, 1)
     lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+    s3 = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     P.cir_level_table(prm, t, 4, P.CIR_EXACT, 1 << 16, s3, lws, st, seed=1)
     P.cir_level_table(prm, t, 4, P.CIR_TABLE, 1 << 16, s3, lws, st, seed=1)
@@ -712,7 +865,7 @@ def profile_cir_small():
                        theta=1.0, discount=1.0)
     t = P.Ncx2Table(2.0, 16, 16, 1)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
-    s3 = torch.zeros(3, dtype=torch.float64, device=dev)
+    s3 = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for n in (4096, 4096, 4096, 608, 1 << 14, 1 << 16):
@@ -844,6 +997,8 @@ def main():
                          ("batch_sweep", lambda: batch_sweep(P, dev, stream)),
                          ("sweep_time_to_rmse", lambda: sweep_time_to_rmse(P, dev)),
                          ("cir_surrogate", lambda: cir_surrogate(P, dev, stream)),
+                         ("cir_learned_vs_table", lambda: cir_learned_vs_table(P, dev, stream,
+                                                                               _TRAINED.get("surrogate"))),
                          ("cir_table", lambda: cir_table(P, dev, stream)),
                          ("cir_time_to_rmse", lambda: cir_time_to_rmse(P, dev, stream)),
                          ("cir_time_to_rmse_cubic", lambda: cir_time_to_rmse(P, dev, stream, deg=3))):

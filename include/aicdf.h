@@ -101,7 +101,8 @@ typedef enum { AICDF_F32 = 0, AICDF_F16 = 1 } aicdf_dtype;
  *   method AICDF_PWC : Q(u) = table[min(floor(n_table u), n_table-1)]  (Section 3.2)
  *   method AICDF_PWL : Algorithm 1 -- reflect about 1/2, interval index from
  *                      the FP32 exponent bits, one FMA, restore the sign
- *                      (u = 1/2 gives -0, as the listing does)
+ *                      (u = 1/2 gives -0, as the piecewise linear C
+ *                      listing of Section 3.3 does)
  *   method AICDF_PWP : the piecewise polynomial of the table's interval
  *                      (Horner's rule in the local variable s), sign restored
  *                      as for PWL
@@ -181,7 +182,18 @@ typedef struct {
   double discount;  /* payoff multiplier, e.g. exp(-rT)                    */
 } aicdf_sde_params;
 
-/* Sum over paths p = path_offset .. path_offset+n_paths-1 of Y and Y^2 for the
+/* Level sums: every call below that returns the sums of one estimator term
+ * writes AICDF_SUMS_PER_TERM FP64 values, [sum Y, sum Y^2, sum Y^3, sum Y^4,
+ * n] over its paths -- the sample mean and variance of the Section 4.1
+ * estimators, plus the third and fourth power sums from which the term's
+ * kurtosis (the reliability of its variance estimate) follows.  Sums of Y and
+ * Y^2 are exact FP64 sums of per-chunk FP32 partial sums (chunks of ~16 paths
+ * per thread); those of Y^3 and Y^4 are per-chunk FP32 sums added with Kahan
+ * compensation in FP32 and reduced across threads in FP64 (relative error
+ * ~1e-6; |Y| below ~1e-9 underflows Y^4 in FP32). */
+#define AICDF_SUMS_PER_TERM 5
+
+/* Sums over paths p = path_offset .. path_offset+n_paths-1 of the powers of Y for the
  * level estimator `kind` at `level` (2^level fine steps of size T/2^level;
  * the coarse path takes 2^(level-1) steps with the pairwise sums of the fine
  * Brownian increments, Section 4.1).  Fine step s of path p draws its uniform
@@ -194,7 +206,7 @@ typedef struct {
  * Models: GBM dX = mu X dt + sigma X dW; CIR dX = kappa(theta-X)dt +
  * sigma sqrt(X) dW with sqrt(|X|) (truncated scheme).  Schemes: Euler-
  * Maruyama (Section 4) or Milstein.
- * Writes sums_dev[0] = sum Y, sums_dev[1] = sum Y^2, sums_dev[2] = n (FP64).
+ * Writes sums_dev[0..4] = (sum Y, sum Y^2, sum Y^3, sum Y^4, n) (FP64).
  * workspace_dev: caller-owned device scratch of at least
  * aicdf_mlmc_level_workspace_bytes() bytes (per-block partial sums), not
  * shared with a concurrent call.  Deterministic: the same arguments give
@@ -216,12 +228,15 @@ aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_table approx
  * workspace that aicdf_mlmc_level asks for.
  *
  * Same arguments and results as aicdf_mlmc_level, without the workspace: the
- * per-block partial sums go to a fixed array inside the library (2048 FP64
- * pairs, 32 KiB, held on every GPU that loads the library until the process
- * exits).  The caller still passes the output sums_dev.  The call allocates
- * nothing.  Its first call on a device looks up that array's device address
- * (cudaGetSymbolAddress), so make the first call on each device before any
- * stream capture.  A launch that would need more than 2048 thread blocks is
+ * per-block partial sums go to a fixed array inside the library (2048
+ * partials of four FP64 sums, 64 KiB, held on every GPU that loads the
+ * library until the process exits).  The caller still passes the output
+ * sums_dev (AICDF_SUMS_PER_TERM values).  The call allocates nothing.  Its
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * the first call on each device before any stream capture, and do not call
+ * it on a device after cudaDeviceReset there (the reset unloads the array and
+ * the kept address goes stale).  A launch that would need more than 2048 thread blocks is
  * refused with AICDF_ERR_UNSUPPORTED (the library sizes the grid itself; this
  * does not happen on GPUs with up to 256 SMs).  All calls share the one
  * array: two calls that can run at the same time on the GPU (different
@@ -280,7 +295,8 @@ aicdf_status aicdf_batch_create(const aicdf_sde_params *sets, int n_sets,
 void aicdf_batch_destroy(aicdf_batch b);
 /* Device workspace a schedule needs (0 for an invalid schedule). */
 size_t aicdf_batch_workspace_bytes(aicdf_batch b, const aicdf_schedule *s);
-/* Run every term: sums_dev[3t .. 3t+2] = (sum Y, sum Y^2, n) of term t (FP64).
+/* Run every term: sums_dev[5t .. 5t+4] = (sum Y, sum Y^2, sum Y^3, sum Y^4, n)
+ * of term t (FP64).
  * The tile list of the schedule is uploaded into the workspace whenever
  * another schedule or batch used that workspace since (or never), and the
  * counter reset, the persistent kernel and the per-term reduction are
@@ -385,7 +401,8 @@ typedef enum {
   AICDF_CIR_TABLE = 5, AICDF_CIR_DIFF_TABLE = 6  /* aicdf_cir_level_table only */
 } aicdf_cir_kind;
 
-/* Sums of Y and Y^2 (FP64) over paths path_offset .. path_offset+n_paths-1 of
+/* Sums of Y, Y^2, Y^3, Y^4 and n (FP64, sums_dev[0..4]) over paths
+ * path_offset .. path_offset+n_paths-1 of
  * a CIR model (params->model = AICDF_MODEL_CIR, payoff X or call; level <=
  * 12).  sur: a surrogate trained for this nu (required by SURROGATE and
  * DIFF, else may be NULL).  workspace: as for aicdf_mlmc_level.  Root-finder
@@ -471,6 +488,7 @@ typedef struct {
   uint64_t paths[AICDF_MAX_LEVELS][2];
   double mean[AICDF_MAX_LEVELS][2];
   double var[AICDF_MAX_LEVELS][2];
+  double kurt[AICDF_MAX_LEVELS][2];     /* kurtosis E(Y-EY)^4 / Var(Y)^2 of the term          */
   double cost_ns[AICDF_MAX_LEVELS][2];  /* measured device ns per path                     */
 } aicdf_mlmc_result;
 
@@ -478,7 +496,10 @@ typedef struct {
  * Philox stream (tag = 1 + 64*estimator + 2*l + t), extending the stream with
  * path_offset as more paths are added, so the result is reproducible from the
  * seed.  Path counts follow the optimal allocation of Section 4.1 from the
- * measured variances and per-path device times.  While the bias estimate
+ * measured variances and per-path device times, and every term keeps at
+ * least 16 (k - 1) paths, k its measured kurtosis, so that its variance
+ * estimate is good to about 25% (a library choice; the paper assumes the
+ * variances known).  While the bias estimate
  * exceeds eps/sqrt(2), levels are added (up to L_max; converged = 0 if it is
  * reached): as many at once as the weak order predicts are needed,
  * ceil(log2(bias / (eps/sqrt(2))) / weak_order), at least one.  workspace_dev: at least aicdf_mlmc_run_workspace_bytes().

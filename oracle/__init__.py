@@ -46,6 +46,14 @@ class SdeParams(C.Structure):
                 ("kappa", C.c_double), ("theta", C.c_double), ("discount", C.c_double)]
 
 
+def set_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops (samplers, uniforms, MLMC
+    paths): one libgomp runtime serves the process, so this sets it for
+    every later oracle call."""
+    lib()
+    C.CDLL("libgomp.so.1").omp_set_num_threads(max(1, int(n)))
+
+
 def lib():
     global _lib
     with _lock:

@@ -92,6 +92,7 @@ double or_u01(uint32_t x) {
 
 void or_uniforms(uint64_t seed, uint64_t offset, int64_t n, float *u) {
   const uint64_t key[2] = {seed & 0xffffffffull, seed >> 32};
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     uint64_t s = offset + (uint64_t)i;
     uint64_t j = s / 4;
@@ -397,6 +398,7 @@ double or_pwp_table(int K, int deg, double *coef) {
 }
 
 void or_sample_pwp(const float *coef, int K, const float *u, int64_t n, double *out) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double x = (double)u[i];
     if (!(x >= 0.0 && x <= 1.0)) {
@@ -422,6 +424,7 @@ void or_sample_pwp(const float *coef, int K, const float *u, int64_t n, double *
 /* ========================================================================== */
 void or_sample_pwc(const float *table, int n_table, const float *u, int64_t n,
                    double *out, int32_t *idx) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double x = (double)u[i];
     if (!(x >= 0.0 && x <= 1.0)) {
@@ -439,6 +442,7 @@ void or_sample_pwc(const float *table, int n_table, const float *u, int64_t n,
 
 void or_sample_pwl(const float *alpha, const float *beta, int K, const float *u, int64_t n,
                    double *out, int32_t *idx) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double x = (double)u[i];
     if (!(x >= 0.0 && x <= 1.0)) {

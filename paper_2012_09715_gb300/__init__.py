@@ -26,6 +26,7 @@ MODEL_GBM, MODEL_CIR = 0, 1
 SCHEME_EM, SCHEME_MILSTEIN = 0, 1
 PAYOFF_X, PAYOFF_CALL = 0, 1
 KIND_APPROX2, KIND_CORR4, KIND_EXACT2, KIND_PLAIN, KIND_PLAIN_APPROX = range(5)
+SUMS = 5  # AICDF_SUMS_PER_TERM: (sum Y, sum Y^2, sum Y^3, sum Y^4, n) per term
 
 _lock = threading.Lock()
 _lib = None
@@ -62,7 +63,8 @@ class MlmcResult(C.Structure):
                 ("gpu_ms", C.c_double), ("wall_ms", C.c_double), ("L", C.c_int),
                 ("converged", C.c_int), ("n_terms", C.c_int), ("launches", C.c_int),
                 ("paths", (C.c_uint64 * 2) * MAX_LEVELS), ("mean", (C.c_double * 2) * MAX_LEVELS),
-                ("var", (C.c_double * 2) * MAX_LEVELS), ("cost_ns", (C.c_double * 2) * MAX_LEVELS)]
+                ("var", (C.c_double * 2) * MAX_LEVELS), ("kurt", (C.c_double * 2) * MAX_LEVELS),
+                ("cost_ns", (C.c_double * 2) * MAX_LEVELS)]
 
     def as_dict(self):
         L, t = self.L, self.n_terms
@@ -71,7 +73,8 @@ class MlmcResult(C.Structure):
                 "gpu_ms": self.gpu_ms, "wall_ms": self.wall_ms, "L": L, "converged": bool(self.converged),
                 "launches": self.launches,
                 "levels": [{"l": l, "paths": list(self.paths[l])[:t], "mean": list(self.mean[l])[:t],
-                            "var": list(self.var[l])[:t], "cost_ns": list(self.cost_ns[l])[:t]}
+                            "var": list(self.var[l])[:t], "kurt": list(self.kurt[l])[:t],
+                            "cost_ns": list(self.cost_ns[l])[:t]}
                            for l in lv]}
 
 
@@ -156,6 +159,15 @@ def lib():
 def _check(status: int, where: str):
     if status != OK:
         raise AicdfError(status, where)
+
+
+def _sums(x, terms: int = 1):
+    """Pointer of a sums buffer after checking that it holds SUMS values per
+    term (a shorter buffer would be overrun by the device writes)."""
+    if hasattr(x, "numel") and hasattr(x, "element_size"):
+        if x.element_size() != 8 or x.numel() < SUMS * terms:
+            raise ValueError(f"sums must hold {SUMS * terms} float64 values ({SUMS} per term)")
+    return _ptr(x)
 
 
 def _ptr(x):
@@ -277,10 +289,10 @@ def mlmc_level_workspace_bytes() -> int:
 
 def mlmc_level(params: SdeParams, table: Table, level: int, kind: int, n_paths: int, sums,
                workspace, path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
-    """aicdf_mlmc_level: sums (device float64[3]) <- [sum Y, sum Y^2, n]."""
+    """aicdf_mlmc_level: sums (device float64[SUMS]) <- [sum Y, sum Y^2, sum Y^3, sum Y^4, n]."""
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().aicdf_mlmc_level(C.byref(params), table.handle, level, kind, n_paths, path_offset,
-                                  seed, tag, _ptr(sums), _ptr(workspace), nbytes, _stream(stream)),
+                                  seed, tag, _sums(sums), _ptr(workspace), nbytes, _stream(stream)),
            "mlmc_level")
     return sums
 
@@ -291,7 +303,7 @@ def mlmc_level_noalloc(params: SdeParams, table: Table, level: int, kind: int, n
     allocate device memory; the scratch lives in a fixed array inside the
     library, shared by all calls (serialise calls that could overlap)."""
     _check(lib().aicdf_mlmc_level_noalloc(C.byref(params), table.handle, level, kind, n_paths,
-                                          path_offset, seed, tag, _ptr(sums), _stream(stream)),
+                                          path_offset, seed, tag, _sums(sums), _stream(stream)),
            "mlmc_level_noalloc")
     return sums
 
@@ -360,7 +372,7 @@ class Batch:
 
     def run(self, sched: Schedule, sums, workspace, stream=None):
         nbytes = workspace.numel() * workspace.element_size()
-        _check(lib().aicdf_batch_run(self.handle, C.byref(sched), _ptr(sums), _ptr(workspace), nbytes,
+        _check(lib().aicdf_batch_run(self.handle, C.byref(sched), _sums(sums, self.n_terms), _ptr(workspace), nbytes,
                                      _stream(stream)), "batch_run")
         return sums
 
@@ -373,7 +385,7 @@ class Batch:
         best = Schedule()
         ms = C.c_double()
         nbytes = workspace.numel() * workspace.element_size()
-        _check(lib().aicdf_batch_autotune(self.handle, var16, _ptr(sums), _ptr(workspace), nbytes,
+        _check(lib().aicdf_batch_autotune(self.handle, var16, _sums(sums, self.n_terms), _ptr(workspace), nbytes,
                                           _stream(stream), cache_path.encode() if cache_path else None,
                                           C.byref(best), C.byref(ms)), "batch_autotune")
         return best, ms.value
@@ -459,10 +471,10 @@ class Surrogate:
 
 def cir_level(params: SdeParams, surrogate, level: int, kind: int, n_paths: int, sums, workspace, status,
               path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
-    """aicdf_cir_level: sums <- [sum Y, sum Y^2, n] for a CIR kind (see aicdf.h)."""
+    """aicdf_cir_level: sums <- [sum Y, sum Y^2, sum Y^3, sum Y^4, n] for a CIR kind (see aicdf.h)."""
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().aicdf_cir_level(C.byref(params), None if surrogate is None else surrogate.handle, level,
-                                 kind, n_paths, path_offset, seed, tag, _ptr(sums), _ptr(workspace), nbytes,
+                                 kind, n_paths, path_offset, seed, tag, _sums(sums), _ptr(workspace), nbytes,
                                  _ptr(status), _stream(stream)), "cir_level")
     return sums
 
@@ -506,9 +518,9 @@ class Ncx2Table:
 
 def cir_level_table(params: SdeParams, table: Ncx2Table, level: int, kind: int, n_paths: int, sums, workspace,
                     status, path_offset: int = 0, seed: int = 0, tag: int = 1, stream=None):
-    """aicdf_cir_level_table: sums <- [sum Y, sum Y^2, n] with the tabulated approximation."""
+    """aicdf_cir_level_table: sums <- [sum Y, sum Y^2, sum Y^3, sum Y^4, n] with the tabulated approximation."""
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().aicdf_cir_level_table(C.byref(params), table.handle, level, kind, n_paths, path_offset, seed,
-                                       tag, _ptr(sums), _ptr(workspace), nbytes, _ptr(status), _stream(stream)),
+                                       tag, _sums(sums), _ptr(workspace), nbytes, _ptr(status), _stream(stream)),
            "cir_level_table")
     return sums

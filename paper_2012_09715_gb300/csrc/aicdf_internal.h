@@ -20,6 +20,8 @@ struct aicdf_table_s {
 constexpr uint32_t AICDF_TABLE_MAGIC = 0x41494344u;  // "AICD"
 
 namespace aicdf {
+// Values per estimator term in every sums_dev array: sum Y, Y^2, Y^3, Y^4, n.
+constexpr int kSumsPerTerm = AICDF_SUMS_PER_TERM;
 // Set by the launch wrappers; read by aicdf_last_cuda_error().
 void set_cuda_error(int e);
 bool table_ok(const aicdf_table_s *t);

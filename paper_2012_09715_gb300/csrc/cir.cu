@@ -43,11 +43,11 @@ struct NoTab {};
 // APPROX: 0 none, 1 surrogate, 2 Gaussian limit, 3 table (TabT = Ncx2TabArgs)
 template <bool EXACT, int APPROX, class TabT>
 __global__ void __launch_bounds__(kCirThreads)
-    k_cir(const __grid_constant__ CirArgs a, const __grid_constant__ TabT tab, double2 *__restrict__ partials,
+    k_cir(const __grid_constant__ CirArgs a, const __grid_constant__ TabT tab, Moments *__restrict__ partials,
           int *__restrict__ status) {
   __shared__ __align__(16) MlpSmem s;
   __shared__ __align__(16) __nv_bfloat16 hs[APPROX == 1 ? kCirThreads / 32 : 1][32 * kHPad];
-  __shared__ double2 s_red[kCirThreads / 32];
+  __shared__ Moments s_red[kCirThreads / 32];
   __shared__ float4 s_rows[APPROX == 3 ? kNcx2TabMaxRows : 1];
   if constexpr (APPROX == 1) {
     mlp_stage(a.params, s);
@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(kCirThreads)
     else y = pa;
     acc.add(y, active);
   });
-  const double2 tot = block_reduce2(acc.d1, acc.d2, s_red);
+  const Moments tot = block_reduce_moments(acc.total(), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   if (st) atomicOr(status, st);
 }
 
-using CirFn = void (*)(CirArgs, NoTab, double2 *, int *);
-using CirTabFn = void (*)(CirArgs, Ncx2TabArgs, double2 *, int *);
+using CirFn = void (*)(CirArgs, NoTab, Moments *, int *);
+using CirTabFn = void (*)(CirArgs, Ncx2TabArgs, Moments *, int *);
 
 static CirFn select_cir(int kind) {
   switch (kind) {
@@ -202,7 +202,7 @@ static aicdf_status cir_launch(Fn k, CirArgs a, const TabT &tab, bool warp_mlp, 
   }
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(
       want, std::min<uint64_t>(sms * resident_blocks((const void *)k, threads), 4096)));
-  double2 *parts = reinterpret_cast<double2 *>(workspace_dev);
+  Moments *parts = reinterpret_cast<Moments *>(workspace_dev);
   k<<<grid, threads, 0, st>>>(a, tab, parts, status_dev);
   launch_reduce_partials(parts, grid, (double)n_paths, sums_dev, st);
   cudaError_t e = cudaGetLastError();

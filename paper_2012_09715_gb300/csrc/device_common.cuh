@@ -3,7 +3,9 @@
 //  * Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed on
 //    the host: the key schedule is the same for every thread of a launch, so
 //    the xor with the round key reads a kernel-parameter (constant bank) word.
-//  * u01: the 32-bit word -> (2*(x mod 2^23)+1) 2^-24 map, exact in FP32.
+//  * v01 / u01: the 32-bit word -> uniform map: the top bit picks the half of
+//    (0, 1) and the low 22 bits m the cell, v = min(u, 1-u) = (2m+1) 2^-24 and
+//    u = v or 1 - v, both exact in FP32.
 //  * pwl_eval: Algorithm 1 (Section 3.3) with the 2 x 16 coefficients held in
 //    registers across the warp and fetched by __shfl_sync -- the GPU form of
 //    keeping the table in one 512-bit vector register (Section 3.3).
@@ -110,7 +112,8 @@ __device__ __forceinline__ float tbits(uint32_t m) {
 // 126 - e; since the shuffle reads lane (e mod 32) = e - 96, lane L holds row
 // min(30 - L, K) and the exponent is the lane index as it stands (no bias
 // subtraction, no cap).  The sign is restored by one xor with the complement
-// of the sign of u - 1/2 (u = 1/2 gives -0, as in the listing).
+// of the sign of u - 1/2 (u = 1/2 gives -0, as the piecewise linear C listing
+// of Section 3.3 does).
 struct PwlRows {
   float a, b;
 };

@@ -27,14 +27,45 @@ struct Term {
   int level = 0, kind = 0, slot = 0;
   uint32_t tag = 0;
   uint64_t n = 0;
-  double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
   double mean() const { return n ? s1 / (double)n : 0.0; }
   double var() const {
     if (n < 2) return 0.0;
     const double m = s1 / (double)n;
     return std::max(s2 / (double)n - m * m, 0.0) * (double)n / (double)(n - 1);
   }
+  // Kurtosis E[(Y - EY)^4] / Var(Y)^2 from the four power sums (3 for a
+  // Gaussian Y; 0 when it cannot be formed).
+  double kurt() const {
+    if (n < 4) return 0.0;
+    const double N = (double)n, m = s1 / N, e2 = s2 / N, e3 = s3 / N, e4 = s4 / N;
+    const double v = e2 - m * m;
+    if (!(v > 0.0)) return 0.0;
+    const double c4 = e4 - 4.0 * m * e3 + 6.0 * m * m * e2 - 3.0 * m * m * m * m;
+    return std::max(c4, 0.0) / (v * v);
+  }
+  void add_sums(const double *h, uint64_t paths) {
+    s1 += h[0];
+    s2 += h[1];
+    s3 += h[2];
+    s4 += h[3];
+    n += paths;
+  }
 };
+
+// The sample variance of n paths of a term with kurtosis k has relative
+// standard error about sqrt((k - 1) / n).  The optimal allocation (Section
+// 4.1) trusts each term's variance estimate, so a term gets at least the
+// paths that bring that error to 1/4: n >= 16 (k - 1).  Heavy-tailed terms
+// -- the four-way corrections, whose Y is the rare large difference between
+// exact and approximate paths -- are the ones this protects; for a Gaussian
+// Y the floor is 32 paths, below every pilot.
+constexpr double kVarRelErr = 0.25;
+uint64_t kurtosis_floor(const Term &t) {
+  const double k = t.kurt();
+  if (!(k > 1.0)) return 0;
+  return (uint64_t)std::min(1e12, std::ceil((k - 1.0) / (kVarRelErr * kVarRelErr)));
+}
 
 // Pilot paths of a new four-way correction term of the nested estimator.
 // Its variance is that of the approximation error -- 2^-11 .. 2^-14 of the
@@ -44,7 +75,7 @@ struct Term {
 // least 128) still estimates the variance to ~10%.
 uint64_t corr_pilot(uint64_t pilot) { return std::min(pilot, std::max<uint64_t>(128, pilot / 16)); }
 
-constexpr size_t kSumsBytes = 256 + 4096;
+constexpr size_t kSumsBytes = 256 + 8192;
 // Calibration launch: level 5 with 2^21 paths (33 fine steps each) fills
 // every SM for several waves, so the measured time is the throughput cost
 // per path-step rather than launch latency and the tail of a partial wave.
@@ -99,7 +130,7 @@ aicdf_status step_cost_ns(const aicdf_sde_params *prm, aicdf_table tab, int kind
 
 extern "C" size_t aicdf_mlmc_run_workspace_bytes(void) {
   // level-kernel partials | calibration sums (256 B) | per-round term sums
-  // (4 KiB: 2 x 21 terms x 3 doubles) | batch tile list and partials
+  // (8 KiB: 2 x 21 terms x 5 doubles) | batch tile list and partials
   return aicdf_mlmc_level_workspace_bytes() + kSumsBytes + (8u << 20);
 }
 
@@ -122,7 +153,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
   char *w = (char *)workspace_dev;
   const size_t lvl_ws = aicdf_mlmc_level_workspace_bytes();
   double *cal_sums = reinterpret_cast<double *>(w + lvl_ws);
-  double *term_sums = reinterpret_cast<double *>(w + lvl_ws + 256);  // <= 2 x 21 terms x 3 doubles
+  double *term_sums = reinterpret_cast<double *>(w + lvl_ws + 256);  // <= 2 x 21 terms x 5 doubles
   void *batch_ws = w + lvl_ws + kSumsBytes;
   const size_t batch_wsb = workspace_bytes - lvl_ws - kSumsBytes;
 
@@ -166,7 +197,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
                                            batch_ws, batch_wsb, st);
     if (s != AICDF_OK) return s;
     cudaEventRecord(e1, st);
-    std::vector<double> h(3 * bt.size());
+    std::vector<double> h(aicdf::kSumsPerTerm * bt.size());
     if (cudaMemcpyAsync(h.data(), term_sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -177,12 +208,8 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     cudaEventElapsedTime(&ms, e0, e1);
     gpu_ms += ms;
     launches += 1;
-    for (size_t j = 0; j < idx.size(); ++j) {
-      Term &t = terms[idx[j]];
-      t.s1 += h[3 * j];
-      t.s2 += h[3 * j + 1];
-      t.n += bt[j].n_paths;
-    }
+    for (size_t j = 0; j < idx.size(); ++j)
+      terms[idx[j]].add_sums(&h[aicdf::kSumsPerTerm * j], bt[j].n_paths);
     return AICDF_OK;
   };
   const uint64_t pilot = o->n_pilot ? o->n_pilot : 10000;
@@ -227,7 +254,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     if (s != AICDF_OK) break;
     std::vector<uint64_t> add(terms.size(), 0);
     for (size_t i = 0; i < terms.size(); ++i) {
-      const double want = std::ceil(m[i]);
+      const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(terms[i]));
       if (!(want < 1e15)) {
         s = AICDF_ERR_NOCONVERGE;
         break;
@@ -276,6 +303,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     r->paths[t.level][t.slot] = t.n;
     r->mean[t.level][t.slot] = t.mean();
     r->var[t.level][t.slot] = t.var();
+    r->kurt[t.level][t.slot] = t.kurt();
     r->cost_ns[t.level][t.slot] = cost(t);
   }
   r->estimate = estv;
@@ -297,7 +325,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
 // the optimal allocation from its own variances and the calibrated per-step
 // costs of its model, the bias test, and the predicted level jump.
 namespace {
-constexpr size_t kSetSumsBytes = 256 * 5;  // per set: 3 sums x 2 kinds x 24 levels (1152 B), 256-B multiple
+constexpr size_t kSetSumsBytes = 256 * 8;  // per set: 5 sums x 2 kinds x 24 levels (1920 B), 256-B multiple
 constexpr size_t kSetBatchBytes = 2 * AICDF_MAX_LEVELS * 128;                // per set: tiles, specs, slots
 constexpr size_t kBatchSlack = 16u << 20;                                    // load-balancing tiles
 }  // namespace
@@ -386,7 +414,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     // in halves (each half one launch), recursively
     std::function<aicdf_status(size_t, size_t)> launch = [&](size_t lo, size_t hi) -> aicdf_status {
       aicdf_status q = aicdf::batch_run_once(sets, n_sets, bt.data() + lo, (int)(hi - lo), approx, o->seed,
-                                             term_sums + 3 * lo, batch_ws, batch_wsb, st);
+                                             term_sums + aicdf::kSumsPerTerm * lo, batch_ws, batch_wsb, st);
       if (q == AICDF_OK) ++launches;
       if (q == AICDF_ERR_NOMEM && hi - lo > 1) {
         const size_t mid = lo + (hi - lo) / 2;
@@ -398,7 +426,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     aicdf_status rc = launch(0, bt.size());
     if (rc != AICDF_OK) return rc;
     cudaEventRecord(e1, st);
-    std::vector<double> h(3 * bt.size());
+    std::vector<double> h(aicdf::kSumsPerTerm * bt.size());
     if (cudaMemcpyAsync(h.data(), term_sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -408,12 +436,8 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     gpu_ms += ms;
-    for (size_t j = 0; j < idx.size(); ++j) {
-      Term &t = S[idx[j].first].terms[idx[j].second];
-      t.s1 += h[3 * j];
-      t.s2 += h[3 * j + 1];
-      t.n += bt[j].n_paths;
-    }
+    for (size_t j = 0; j < idx.size(); ++j)
+      S[idx[j].first].terms[idx[j].second].add_sums(&h[aicdf::kSumsPerTerm * j], bt[j].n_paths);
     return AICDF_OK;
   };
   const uint64_t pilot = o->n_pilot ? o->n_pilot : 10000;
@@ -462,7 +486,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       rc = aicdf_mlmc_allocate((int)S[s].terms.size(), v.data(), c.data(), eps, m.data(), &total);
       if (rc != AICDF_OK) break;
       for (size_t i = 0; i < S[s].terms.size(); ++i) {
-        const double want = std::ceil(m[i]);
+        const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(S[s].terms[i]));
         if (!(want < 1e15)) {
           rc = AICDF_ERR_NOCONVERGE;
           break;
@@ -526,6 +550,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       r->paths[t.level][t.slot] = t.n;
       r->mean[t.level][t.slot] = t.mean();
       r->var[t.level][t.slot] = t.var();
+      r->kurt[t.level][t.slot] = t.kurt();
       r->cost_ns[t.level][t.slot] = cost(s, t);
     }
     r->estimate = estv;

@@ -6,8 +6,9 @@
 // (or Q(U)); the fine exact and approximate states advance with Z and Z~,
 // and every second step the coarse states advance with the pairwise sums
 // (Section 4.1: coarse Wiener increments are pairwise sums of the fine
-// ones).  The payoff difference Y of the requested estimator kind is
-// accumulated per thread in FP32 over a chunk of paths and flushed to FP64
+// ones).  The payoff difference Y of the requested estimator kind and its
+// powers Y^2, Y^3, Y^4 are accumulated per thread in FP32 over a chunk of
+// paths and flushed to FP64 (Y, Y^2) or to compensated FP32 sums (Y^3, Y^4)
 // (FP64 issues at a small fraction of the FP32 rate on this GPU); warps
 // reduce in FP64 by shuffles, blocks write one FP64 partial each, and a
 // second one-block kernel adds the partials in a fixed order, so the sums
@@ -46,9 +47,9 @@ constexpr int kMaxLevelBlocks = 4096;
 // ============================================================== level kernel
 template <bool NE, bool NA, int AP, int MODEL>
 __global__ void __launch_bounds__(kLevelThreads)
-    k_mlmc_level(const __grid_constant__ LevelArgs a, double2 *__restrict__ partials) {
+    k_mlmc_level(const __grid_constant__ LevelArgs a, Moments *__restrict__ partials) {
   __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
-  __shared__ double2 s_red[kLevelThreads / 32];
+  __shared__ Moments s_red[kLevelThreads / 32];
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
   const PathConsts pc = make_path_consts(a.ps);
   const int lane = threadIdx.x & 31;
@@ -68,34 +69,40 @@ __global__ void __launch_bounds__(kLevelThreads)
       acc.add(y, i < a.n_paths);
     });
   }
-  const double2 t = block_reduce2(acc.d1, acc.d2, s_red);
+  const Moments t = block_reduce_moments(acc.total(), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-// Fixed-order sum of the per-block partials (one block).
-__global__ void __launch_bounds__(256) k_reduce_partials(const double2 *__restrict__ partials,
+// Fixed-order sum of the per-block partials (one block):
+// sums[0..4] = (sum Y, sum Y^2, sum Y^3, sum Y^4, count).
+__global__ void __launch_bounds__(256) k_reduce_partials(const Moments *__restrict__ partials,
                                                          int nparts, double count,
                                                          double *__restrict__ sums) {
-  __shared__ double2 s_red[256 / 32];
-  double d1 = 0.0, d2 = 0.0;
+  __shared__ Moments s_red[256 / 32];
+  Moments m{0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    d1 += partials[i].x;
-    d2 += partials[i].y;
+    const Moments p = partials[i];
+    m.s1 += p.s1;
+    m.s2 += p.s2;
+    m.s3 += p.s3;
+    m.s4 += p.s4;
   }
-  const double2 t = block_reduce2(d1, d2, s_red);
+  const Moments t = block_reduce_moments(m, s_red);
   if (threadIdx.x == 0) {
-    sums[0] = t.x;
-    sums[1] = t.y;
-    sums[2] = count;
+    sums[0] = t.s1;
+    sums[1] = t.s2;
+    sums[2] = t.s3;
+    sums[3] = t.s4;
+    sums[4] = count;
   }
 }
 
-void launch_reduce_partials(const double2 *partials, int nparts, double count, double *sums,
+void launch_reduce_partials(const Moments *partials, int nparts, double count, double *sums,
                             cudaStream_t st) {
   k_reduce_partials<<<1, 256, 0, st>>>(partials, nparts, count, sums);
 }
 
-using LevelFn = void (*)(LevelArgs, double2 *);
+using LevelFn = void (*)(LevelArgs, Moments *);
 
 template <bool NE, bool NA, int AP>
 LevelFn pick_model(int model) {
@@ -202,7 +209,7 @@ int level_launch_grid(const LevelArgs &a) {
 aicdf_status launch_level(const LevelArgs &a, double *sums_dev, void *ws, cudaStream_t st) {
   LevelFn k = select_level_kernel(a.ps.kind, a.approx, a.ps.model);
   const int grid = level_grid(a.n_paths, (const void *)k);
-  double2 *parts = reinterpret_cast<double2 *>(ws);
+  Moments *parts = reinterpret_cast<Moments *>(ws);
   k<<<grid, kLevelThreads, 0, st>>>(a, parts);
   k_reduce_partials<<<1, 256, 0, st>>>(parts, grid, (double)a.n_paths, sums_dev);
   cudaError_t e = cudaGetLastError();
@@ -227,7 +234,7 @@ struct BatchArgs {
   const BatchItem *items;
   const PathSpec *specs;
   int *counter;
-  double2 *partials;
+  Moments *partials;
   int n_items, approx, ntab;
   float tab[1024];
 };
@@ -235,7 +242,7 @@ struct BatchArgs {
 template <int AP, bool V16>
 __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ BatchArgs a) {
   __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
-  __shared__ double2 s_red[256 / 32];
+  __shared__ Moments s_red[256 / 32];
   __shared__ int s_item;
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
   const int lane = threadIdx.x & 31;
@@ -259,26 +266,31 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
         acc.add(y, i < item.count);
       });
     }
-    const double d1 = acc.d1, d2 = acc.d2;
-    const double2 t = block_reduce2(d1, d2, s_red);
+    const Moments t = block_reduce_moments(acc.total(), s_red);
     if (threadIdx.x == 0) a.partials[item.slot] = t;
   }
 }
 
-// sums[3 t + {0,1,2}] = (sum Y, sum Y^2, n) of term t from its slots, in slot order.
-__global__ void k_reduce_terms(const double2 *__restrict__ partials, const int *__restrict__ slot_begin,
+// sums[5 t + {0..4}] = (sum Y, sum Y^2, sum Y^3, sum Y^4, n) of term t from
+// its slots, in slot order.
+__global__ void k_reduce_terms(const Moments *__restrict__ partials, const int *__restrict__ slot_begin,
                                const double *__restrict__ counts, int n_terms,
                                double *__restrict__ sums) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_terms) return;
-  double d1 = 0.0, d2 = 0.0;
+  Moments m{0.0, 0.0, 0.0, 0.0};
   for (int s = slot_begin[t]; s < slot_begin[t + 1]; ++s) {
-    d1 += partials[s].x;
-    d2 += partials[s].y;
+    const Moments p = partials[s];
+    m.s1 += p.s1;
+    m.s2 += p.s2;
+    m.s3 += p.s3;
+    m.s4 += p.s4;
   }
-  sums[3 * t + 0] = d1;
-  sums[3 * t + 1] = d2;
-  sums[3 * t + 2] = counts[t];
+  sums[kSumsPerTerm * t + 0] = m.s1;
+  sums[kSumsPerTerm * t + 1] = m.s2;
+  sums[kSumsPerTerm * t + 2] = m.s3;
+  sums[kSumsPerTerm * t + 3] = m.s4;
+  sums[kSumsPerTerm * t + 4] = counts[t];
 }
 
 using BatchFn = void (*)(BatchArgs);
@@ -406,7 +418,7 @@ static Plan *get_plan(aicdf_batch_s *b, const aicdf_schedule &s) {
   p->off_counts = off;
   off = align256(off + sizeof(double) * b->counts.size());
   p->off_partials = off;
-  off = align256(off + sizeof(double2) * p->items.size());
+  off = align256(off + sizeof(Moments) * p->items.size());
   p->bytes = off;
   b->plans.push_back(p);
   return p;
@@ -503,7 +515,7 @@ static aicdf_status record_batch(aicdf_batch_s *b, Plan *p, void *ws, double *su
   a.items = reinterpret_cast<const BatchItem *>(w + p->off_items);
   a.specs = reinterpret_cast<const PathSpec *>(w + p->off_specs);
   a.counter = reinterpret_cast<int *>(w + p->off_counter);
-  a.partials = reinterpret_cast<double2 *>(w + p->off_partials);
+  a.partials = reinterpret_cast<Moments *>(w + p->off_partials);
   a.n_items = (int)p->items.size();
   BatchFn k = select_batch_kernel(a.approx, p->sched.var16 != 0);
   const int threads = p->sched.block_threads;
@@ -731,7 +743,7 @@ extern "C" aicdf_status aicdf_batch_autotune(aicdf_batch b, int var16, double *s
 
 // ---------------------------------------------------------------- level ABI
 extern "C" size_t aicdf_mlmc_level_workspace_bytes(void) {
-  return sizeof(double2) * (size_t)kMaxLevelBlocks;
+  return sizeof(Moments) * (size_t)kMaxLevelBlocks;
 }
 
 extern "C" aicdf_status aicdf_mlmc_level(const aicdf_sde_params *params, aicdf_table approx,

@@ -143,27 +143,55 @@ __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts 
   return x + inc;
 }
 
-// Per-thread sums of Y and Y^2: FP32 over chunks of about 16 paths, each
-// chunk added to FP64 accumulators (FP64 runs at 1/64 of the FP32 rate on this
-// GPU: a warp's FP64 add holds its sub-partition's FP64 unit for ~64 cycles),
-// in a fixed order per thread.  add() is FP32 only; flush() is called by the
-// loops below once per chunk, outside the per-path body, so that the FP64 adds
-// are never if-converted into predicated instructions issued for every path
-// (predicated-off FP64 instructions still occupy the FP64 unit).  Lanes past
-// the end of their range add zero (valid = false), which keeps every lane's
-// chunking and the control flow warp-uniform.
+// The four power sums of Y over one term's paths (Section 4.1 estimators:
+// the sample mean and variance, plus the third and fourth moments that show
+// how far the variance estimate can be trusted).
+struct __align__(16) Moments {
+  double s1, s2, s3, s4;  // sum Y, sum Y^2, sum Y^3, sum Y^4
+};
+
+// s + x with the rounding error carried in c (Kahan's compensated sum), each
+// operation rounded on its own (_rn intrinsics are never contracted).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+// Per-thread power sums of Y: FP32 over chunks of about 16 paths.  At each
+// chunk's end the sums of Y and Y^2 are added to FP64 accumulators (FP64 runs
+// at 1/64 of the FP32 rate on this GPU: a warp's FP64 add holds its
+// sub-partition's FP64 unit for ~64 cycles), and those of Y^3 and Y^4 to
+// FP32 running sums with Kahan compensation (relative error ~2^-24 per chunk
+// sum, no FP64 work per chunk), in a fixed order per thread.  add() is FP32
+// only; flush() is called by the loops below once per chunk, outside the
+// per-path body, so that the FP64 adds are never if-converted into predicated
+// instructions issued for every path (predicated-off FP64 instructions still
+// occupy the FP64 unit).  Lanes past the end of their range add zero (valid =
+// false), which keeps every lane's chunking and the control flow warp-uniform.
 struct PathSums {
-  float f1 = 0.f, f2 = 0.f;  // current chunk
+  float f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f;  // current chunk
   double d1 = 0.0, d2 = 0.0;
+  float k3 = 0.f, c3 = 0.f, k4 = 0.f, c4 = 0.f;  // compensated running sums of Y^3, Y^4
   __device__ __forceinline__ void add(float y, bool valid) {
     y = valid ? y : 0.0f;
     f1 = __fadd_rn(f1, y);
     f2 = fmaf(y, y, f2);
+    const float y2 = __fmul_rn(y, y);
+    f3 = fmaf(y2, y, f3);
+    f4 = fmaf(y2, y2, f4);
   }
   __device__ __forceinline__ void flush() {
     d1 += (double)f1;
     d2 += (double)f2;
-    f1 = f2 = 0.f;
+    kahan_add(k3, c3, f3);
+    kahan_add(k4, c4, f4);
+    f1 = f2 = f3 = f4 = 0.f;
+  }
+  // the thread's totals (call after the last flush)
+  __device__ __forceinline__ Moments total() const {
+    return Moments{d1, d2, (double)k3 - (double)c3, (double)k4 - (double)c4};
   }
 };
 
@@ -354,24 +382,28 @@ __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, u
   });
 }
 
-// FP64 block reduction of two values; result valid in thread 0.  Ends with a
-// barrier so that s_red may be reused right away.
+// FP64 block reduction of the four sums; result valid in thread 0.  Ends with
+// a barrier so that s_red may be reused right away.
 template <int NW>
-__device__ __forceinline__ double2 block_reduce2(double d1, double d2, double2 (&s_red)[NW]) {
+__device__ __forceinline__ Moments block_reduce_moments(Moments m, Moments (&s_red)[NW]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    d1 += __shfl_down_sync(FULL_MASK, d1, o);
-    d2 += __shfl_down_sync(FULL_MASK, d2, o);
+    m.s1 += __shfl_down_sync(FULL_MASK, m.s1, o);
+    m.s2 += __shfl_down_sync(FULL_MASK, m.s2, o);
+    m.s3 += __shfl_down_sync(FULL_MASK, m.s3, o);
+    m.s4 += __shfl_down_sync(FULL_MASK, m.s4, o);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) s_red[warp] = make_double2(d1, d2);
+  if (lane == 0) s_red[warp] = m;
   __syncthreads();
-  double2 t = make_double2(0.0, 0.0);
+  Moments t{0.0, 0.0, 0.0, 0.0};
   if (threadIdx.x == 0) {
     const int nw = (int)(blockDim.x >> 5);
     for (int w = 0; w < nw; ++w) {
-      t.x += s_red[w].x;
-      t.y += s_red[w].y;
+      t.s1 += s_red[w].s1;
+      t.s2 += s_red[w].s2;
+      t.s3 += s_red[w].s3;
+      t.s4 += s_red[w].s4;
     }
   }
   __syncthreads();
@@ -389,12 +421,12 @@ aicdf_status prepare_level_args(const aicdf_sde_params *prm, aicdf_table approx,
                                 uint32_t tag, LevelArgs *a);
 // Thread blocks launch_level will use for these arguments (= partial-sum slots).
 int level_launch_grid(const LevelArgs &a);
-// Launch the level kernel (one FP64 partial per block into ws) and the
+// Launch the level kernel (one Moments partial per block into ws) and the
 // fixed-order reduction into sums_dev (host).
 aicdf_status launch_level(const LevelArgs &a, double *sums_dev, void *ws, cudaStream_t st);
 // Launch the one-block fixed-order sum of per-block partials into
-// sums[0..2] = (sum Y, sum Y^2, count) (host).
-void launch_reduce_partials(const double2 *partials, int nparts, double count, double *sums,
+// sums[0..4] = (sum Y, sum Y^2, sum Y^3, sum Y^4, count) (host).
+void launch_reduce_partials(const Moments *partials, int nparts, double count, double *sums,
                             cudaStream_t st);
 
 }  // namespace aicdf

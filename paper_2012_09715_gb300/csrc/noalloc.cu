@@ -1,7 +1,7 @@
 // aicdf_mlmc_level for callers that cannot allocate device memory (the paper
-// has no counterpart).  The level kernel's only scratch -- one FP64
-// (sum Y, sum Y^2) pair per thread block -- lives in a fixed array inside the
-// library instead of a caller workspace.
+// has no counterpart).  The level kernel's only scratch -- one partial of the
+// four FP64 power sums of Y per thread block -- lives in a fixed array inside
+// the library instead of a caller workspace.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -12,10 +12,10 @@
 namespace aicdf {
 namespace {
 
-// Every GPU that loads the library holds this array (32 KiB) until the
+// Every GPU that loads the library holds this array (64 KiB) until the
 // process exits.  All calls share it.
 constexpr int kNoAllocSlots = 2048;
-static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocSlots];
+static __device__ __align__(256) Moments g_noalloc_partials[kNoAllocSlots];
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[64] = {nullptr};

@@ -130,10 +130,11 @@ struct OutVec<AICDF_F16> {
   static constexpr int kElems = 8;
 };
 
-__device__ __forceinline__ void store_vec(float *out, uint64_t e, const float (&z)[4]) {
-  *reinterpret_cast<float4 *>(out + e) = make_float4(z[0], z[1], z[2], z[3]);
+// The bits of one 16-byte output vector: 4 FP32 or 8 FP16 (round to nearest even).
+__device__ __forceinline__ uint4 pack_vec(const float (&z)[4]) {
+  return make_uint4(__float_as_uint(z[0]), __float_as_uint(z[1]), __float_as_uint(z[2]), __float_as_uint(z[3]));
 }
-__device__ __forceinline__ void store_vec(__half *out, uint64_t e, const float (&z)[8]) {
+__device__ __forceinline__ uint4 pack_vec(const float (&z)[8]) {
   uint4 w;
   __half2 h0 = __floats2half2_rn(z[0], z[1]), h1 = __floats2half2_rn(z[2], z[3]);
   __half2 h2 = __floats2half2_rn(z[4], z[5]), h3 = __floats2half2_rn(z[6], z[7]);
@@ -141,7 +142,13 @@ __device__ __forceinline__ void store_vec(__half *out, uint64_t e, const float (
   w.y = *reinterpret_cast<uint32_t *>(&h1);
   w.z = *reinterpret_cast<uint32_t *>(&h2);
   w.w = *reinterpret_cast<uint32_t *>(&h3);
-  *reinterpret_cast<uint4 *>(out + e) = w;
+  return w;
+}
+__device__ __forceinline__ void store_vec(float *out, uint64_t e, const float (&z)[4]) {
+  *reinterpret_cast<uint4 *>(out + e) = pack_vec(z);
+}
+__device__ __forceinline__ void store_vec(__half *out, uint64_t e, const float (&z)[8]) {
+  *reinterpret_cast<uint4 *>(out + e) = pack_vec(z);
 }
 __device__ __forceinline__ void store_one(float *out, uint64_t e, float z) { out[e] = z; }
 __device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
@@ -222,7 +229,11 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
 // arithmetic, the counter's high words are the constant 0 (so the compiler
 // folds part of the first round), and chunks that lie wholly inside the
 // output are stored without per-vector bounds checks.  Each lane runs the
-// Philox calls of its four 16-byte vectors interleaved round by round.
+// Philox calls of its four 16-byte vectors interleaved round by round.  The
+// counter of the lane's first call and the address of its first vector are
+// carried from chunk to chunk (one add each per grid stride), so no vector
+// address is formed by a 64-bit multiply: the kernel is bound by its integer
+// multiply and logic pipes, and those products were ~6% of its multiply work.
 template <int METHOD, int OUT>
 __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constant__ SampleArgs a) {
   __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
@@ -231,7 +242,8 @@ __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constan
   T *out = reinterpret_cast<T *>(a.out);
   constexpr int E = OutVec<OUT>::kElems;
   constexpr int VECS = OUT == AICDF_F32 ? 4 : 2;  // 16-byte vectors per lane per chunk
-  constexpr int NC = VECS * (E / 4);              // Philox calls per lane per chunk (4)
+  constexpr int CPV = E / 4;                      // Philox calls per vector
+  constexpr int NC = VECS * CPV;                  // Philox calls per lane per chunk (4)
   constexpr uint32_t CH = 32 * VECS;              // vectors per warp chunk
   const uint32_t n = (uint32_t)a.n;
   const uint32_t nvec = (n + E - 1) / E;
@@ -239,21 +251,24 @@ __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constan
   const uint32_t nfull = (n / E) / CH;  // chunks with every vector complete
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t j0 = (uint32_t)(a.offset >> 2);
-  for (uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < nchunk; chunk += warps) {
+  uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint32_t ctr = (uint32_t)(a.offset >> 2) + (chunk * CH + lane) * CPV;  // call of vector 0, word 0
+  const uint32_t ctr_step = warps * CH * CPV;
+  uint4 *pv = reinterpret_cast<uint4 *>(a.out) + (size_t)chunk * CH + lane;  // vector 0 of the lane
+  const size_t pv_step = (size_t)warps * CH;
+  for (; chunk < nchunk; chunk += warps, ctr += ctr_step, pv += pv_step) {
     uint4 c[NC];
 #pragma unroll
     for (int hv = 0; hv < VECS; ++hv)
 #pragma unroll
-      for (int h = 0; h < E / 4; ++h)
-        c[hv * (E / 4) + h] = make_uint4(j0 + (chunk * CH + 32 * hv + lane) * (E / 4) + h, 0u, 0u, 0u);
+      for (int h = 0; h < CPV; ++h) c[hv * CPV + h] = make_uint4(ctr + 32 * CPV * hv + h, 0u, 0u, 0u);
     philox_n<NC>(c, a.keys);
     float z[VECS][E];
 #pragma unroll
     for (int hv = 0; hv < VECS; ++hv)
 #pragma unroll
-      for (int h = 0; h < E / 4; ++h) {
-        const uint4 r = c[hv * (E / 4) + h];
+      for (int h = 0; h < CPV; ++h) {
+        const uint4 r = c[hv * CPV + h];
         z[hv][4 * h + 0] = f.word(r.x);
         z[hv][4 * h + 1] = f.word(r.y);
         z[hv][4 * h + 2] = f.word(r.z);
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constan
       }
     if (chunk < nfull) {  // warp-uniform
 #pragma unroll
-      for (int hv = 0; hv < VECS; ++hv) store_vec(out, (uint64_t)(chunk * CH + 32 * hv + lane) * E, z[hv]);
+      for (int hv = 0; hv < VECS; ++hv) pv[32 * hv] = pack_vec(z[hv]);
     } else {
 #pragma unroll
       for (int hv = 0; hv < VECS; ++hv) {

@@ -54,19 +54,22 @@ def test_batch_matches_level_kernel(P, method):
     table = P.table_build(getattr(P, method), 15 if method == "PWL" else 1024)
     sets, terms = _sets(P), _terms(P)
     b = P.Batch(sets, terms, table, seed=3)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     sched = P.Schedule(2048, 128, 0, 0)
     ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
     b.run(sched, sums, ws)
-    got = sums.cpu().numpy().reshape(-1, 3)
+    got = sums.cpu().numpy().reshape(-1, P.SUMS)
     lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    ls = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ls = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     for i, t in enumerate(terms):
         ref = _level_sums(P, sets[t.set], table, t, lws, ls, 3)
-        assert got[i, 2] == t.n_paths
+        assert got[i, 4] == t.n_paths
         scale = math.sqrt(t.n_paths * ref[1]) + 1e-30
         assert abs(got[i, 0] - ref[0]) <= 2e-6 * scale, (i, got[i], ref)
         assert got[i, 1] == pytest.approx(ref[1], rel=2e-6, abs=1e-30)
+        # Y^3, Y^4: the same paths regrouped into other FP32 chunks
+        assert abs(got[i, 2] - ref[2]) <= 4e-6 * math.sqrt(ref[1] * ref[3]) + 1e-30, (i, got[i], ref)
+        assert got[i, 3] == pytest.approx(ref[3], rel=4e-6, abs=1e-30)
 
 
 def test_batch_deterministic_across_replays_and_schedules(P):
@@ -74,15 +77,15 @@ def test_batch_deterministic_across_replays_and_schedules(P):
     table = P.table_build(P.PWL, 15)
     sets, terms = _sets(P), _terms(P)
     b = P.Batch(sets, terms, table, seed=9)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     res = []
     for sched in (P.Schedule(4096, 256, 0, 0), P.Schedule(4096, 256, 0, 0), P.Schedule(256, 64, 2, 0)):
         ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
         b.run(sched, sums, ws)
         b.run(sched, sums, ws)      # graph replay
-        res.append(sums.cpu().numpy().reshape(-1, 3).copy())
+        res.append(sums.cpu().numpy().reshape(-1, P.SUMS).copy())
     assert np.array_equal(res[0], res[1])
-    scale = np.sqrt(res[0][:, 2] * res[0][:, 1]) + 1e-30
+    scale = np.sqrt(res[0][:, 4] * res[0][:, 1]) + 1e-30
     assert np.all(np.abs(res[0][:, 0] - res[2][:, 0]) <= 2e-6 * scale)
 
 
@@ -97,11 +100,11 @@ def test_batch_against_oracle(P, orc):
     terms = [P.BatchTerm(s, level, kind, 50 + s * 16 + level * 2 + (kind == 1), 4000, 123)
              for s in range(4) for level in (0, 2, 5) for kind in (0, 1)]
     b = P.Batch(sets, terms, table, seed=21)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     sched = P.Schedule(1024, 128, 0, 0)
     ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
     b.run(sched, sums, ws)
-    got = sums.cpu().numpy().reshape(-1, 3)
+    got = sums.cpu().numpy().reshape(-1, P.SUMS)
     for i, t in enumerate(terms):
         o = orc.mlmc_level(osets[t.set], (a, bb), t.level, t.kind, t.n_paths, path_offset=t.path_offset,
                            seed=21, tag=t.tag)
@@ -121,13 +124,13 @@ def test_fp16_variates_keep_the_correction_unbiased(P):
     terms = [P.BatchTerm(0, level, P.KIND_APPROX2, 1, n, 0), P.BatchTerm(0, level, P.KIND_CORR4, 2, n, 0),
              P.BatchTerm(0, level, P.KIND_EXACT2, 3, n, 0)]
     b = P.Batch(sets, terms, table, seed=5)
-    sums = torch.zeros(9, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(3 * P.SUMS, dtype=torch.float64, device="cuda")
     out = {}
     for v16 in (0, 1):
         sched = P.Schedule(8192, 256, 0, v16)
         ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
         b.run(sched, sums, ws)
-        out[v16] = sums.cpu().numpy().reshape(-1, 3).copy()
+        out[v16] = sums.cpu().numpy().reshape(-1, P.SUMS).copy()
     for v16 in (0, 1):
         s = out[v16]
         m = s[:, 0] / n
@@ -145,7 +148,7 @@ def test_autotune_and_cache(P, tmp_path):
     table = P.table_build(P.PWL, 15)
     sets, terms = _sets(P), _terms(P)
     b = P.Batch(sets, terms, table, seed=1)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     biggest = max(b.workspace_bytes(P.Schedule(t * m, t, 0, 0)) for t in (128, 256) for m in (2, 8, 32, 128))
     ws = torch.empty(biggest, dtype=torch.uint8, device="cuda")
     cache = str(tmp_path / "tune.txt")
@@ -174,14 +177,14 @@ def test_full_sweep_sampled_terms(P):
             terms.append(P.BatchTerm(s, l, P.KIND_CORR4, 2 * (8 * s + l) + 2, int(n4[s, l]), 0))
     table = P.table_build(P.PWL, 15)
     b = P.Batch(sets, terms, table, seed=0)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     sched = P.Schedule(8192, 256, 0, 0)
     ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
     b.run(sched, sums, ws)
-    got = sums.cpu().numpy().reshape(-1, 3)
-    assert np.all(np.isfinite(got)) and np.array_equal(got[:, 2], [t.n_paths for t in terms])
+    got = sums.cpu().numpy().reshape(-1, P.SUMS)
+    assert np.all(np.isfinite(got)) and np.array_equal(got[:, 4], [t.n_paths for t in terms])
     lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    ls = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ls = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     rng = np.random.default_rng(0)
     for i in rng.choice(len(terms), 24, replace=False):
         t = terms[i]
@@ -190,5 +193,5 @@ def test_full_sweep_sampled_terms(P):
         assert abs(got[i, 0] - ref[0]) <= 2e-6 * scale
     # the level-0 two-way means estimate E[X_T]: truncated EM keeps the exact
     # mean theta + (X0 - theta)(1 - kappa dt)^N, = theta here since X0 = theta
-    m0 = got[0::16, 0] / got[0::16, 2]
-    assert np.all(np.abs(m0 - sw["theta"]) < 6 * sw["sigma"] * np.sqrt(sw["theta"] / got[0::16, 2]) + 1e-6)
+    m0 = got[0::16, 0] / got[0::16, 4]
+    assert np.all(np.abs(m0 - sw["theta"]) < 6 * sw["sigma"] * np.sqrt(sw["theta"] / got[0::16, 4]) + 1e-6)

@@ -33,7 +33,7 @@ def env(P):
     tl = P.table_build(P.PWL, 15)
     tc = P.table_build(P.PWC, 1024)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     a, b = tl.coefficients()
     q = tc.coefficients()[0]
     return dict(tl=tl, tc=tc, ws=ws, sums=sums, pwl=(a, b), pwc=q)
@@ -84,7 +84,7 @@ def test_level_sums_within_3se(P, orc, env, level, kind):
     n = 20000 if level < 6 else 5000
     g = _level(P, env, gp, env["tl"], level, kind, n, off=777, seed=4, tag=9)
     o = orc.mlmc_level(op, env["pwl"], level, kind, n, path_offset=777, seed=4, tag=9)
-    assert g[2] == n
+    assert g[4] == n
     var = max(o[1] / n - (o[0] / n) ** 2, 0.0)
     se = math.sqrt(var / n)
     assert abs(g[0] / n - o[0] / n) <= 3 * se + 1e-12
@@ -96,6 +96,14 @@ def test_level_sums_within_3se(P, orc, env, level, kind):
     # terms |Y| is itself small, so this, not a fraction of sum Y^2, sets the band.
     d = math.sqrt(2 ** level + 2) * 2.0 ** -24 * 2.0
     assert abs(g[1] - o[1]) <= 1e-4 * o[1] + 8 * math.sqrt(o[1]) * d + 1e-12
+    # sum Y^3 and sum Y^4: a per-path error of at most D (the per-path parity
+    # bound) moves y^3 by <= 3 y^2 D + 3 |y| D^2 + D^3 and y^4 by <= 4 |y|^3 D +
+    # 6 y^2 D^2 + ..., with sum |y|^3 <= sqrt(sum y^2 sum y^4); the FP32 chunk
+    # sums and their compensated total add ~1e-6 of sum |y|^k
+    D = 4 * (2 ** level + 2) * 2.0 ** -23 * 2.0
+    abs3 = math.sqrt(o[1] * o[3])
+    assert abs(g[2] - o[2]) <= 1e-5 * abs3 + 3 * D * o[1] + 3 * D * D * math.sqrt(n * o[1]) + n * D ** 3 + 1e-30
+    assert abs(g[3] - o[3]) <= 1e-5 * o[3] + 4 * D * abs3 + 7 * D * D * o[1] + 1e-30
 
 
 def test_determinism_and_additivity(P, orc, env):
@@ -105,10 +113,10 @@ def test_determinism_and_additivity(P, orc, env):
     s2 = _level(P, env, gp, env["tl"], 4, 1, n, seed=8, tag=2)
     assert np.array_equal(s1, s2)                     # bit-identical reruns
     parts = [(0, 1_000_000), (1_000_000, 1_234_567), (2_234_567, 765_434)]
-    tot = np.zeros(3)
+    tot = np.zeros(P.SUMS)
     for off, m in parts:
         tot += _level(P, env, gp, env["tl"], 4, 1, m, off=off, seed=8, tag=2)
-    assert tot[2] == n
+    assert tot[4] == n
     # a different split regroups the per-thread FP32 chunks: the sums agree to
     # the chunk rounding, ~1e-6 of sum |Y| <= 1e-6 sqrt(n sum Y^2)
     scale = math.sqrt(n * s1[1])

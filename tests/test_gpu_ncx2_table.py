@@ -106,7 +106,7 @@ def test_cir_table_paths_match_restatement(P, orc, name, deg):
     t = P.Ncx2Table(nu, 16, 16, deg)
     c = _c32(t)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     for level in (0, 2, 4):
         for p in (0, 7, 123456789):
@@ -135,7 +135,7 @@ def test_cir_table_variance_drop(P):
     import torch
     prm, q = _cir_params(P, "paper")
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     n = 1 << 16
     r = {}
@@ -165,7 +165,7 @@ def test_cir_small_terms_cover_each_path_once(P, kind):
     prm, q = _cir_params(P, "paper")
     t = P.Ncx2Table(2.0, 16, 16, 1)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     k = getattr(P, kind)
     n = 1 << 15

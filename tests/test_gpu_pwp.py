@@ -143,7 +143,7 @@ def test_pwp_statistics(P, tables):
 def lvl(P):
     import torch
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     return ws, sums
 
 
@@ -184,7 +184,7 @@ def test_pwp_mlmc_level_sums_match_oracle(P, orc, tables, lvl):
         n = 20000
         g = _level(P, lvl, gp, t, level, kind, n, off=777, seed=4, tag=9)
         o = orc.mlmc_level(op, c32, level, kind, n, path_offset=777, seed=4, tag=9)
-        assert g[2] == n
+        assert g[4] == n
         assert abs(g[0] - o[0]) <= 1e-4 * (abs(o[0]) + math.sqrt(o[1] * n)) + 1e-9
         assert g[1] == pytest.approx(o[1], rel=1e-4, abs=1e-12)
 
@@ -222,18 +222,18 @@ def test_pwp_batch_matches_level_kernel(P, tables):
                 terms.append(P.BatchTerm(s, level, kind, 50 + 7 * s + 3 * level + kind,
                                          int(rng.integers(1, 30000)), int(rng.integers(0, 1 << 20))))
     b = P.Batch(sets, terms, t, seed=5)
-    sums = torch.zeros(3 * len(terms), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
     sched = P.Schedule(2048, 128, 0, 0)
     ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
     b.run(sched, sums, ws)
-    got = sums.cpu().numpy().reshape(-1, 3)
+    got = sums.cpu().numpy().reshape(-1, P.SUMS)
     lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    ls = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ls = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     for i, tm in enumerate(terms):
         P.mlmc_level(sets[tm.set], t, tm.level, tm.kind, tm.n_paths, ls, lws, path_offset=tm.path_offset,
                      seed=5, tag=tm.tag)
         ref = ls.cpu().numpy()
-        assert got[i, 2] == tm.n_paths
+        assert got[i, 4] == tm.n_paths
         scale = math.sqrt(tm.n_paths * ref[1]) + 1e-30
         assert abs(got[i, 0] - ref[0]) <= 2e-6 * scale, (i, got[i], ref)
         assert got[i, 1] == pytest.approx(ref[1], rel=2e-6, abs=1e-30)

@@ -200,7 +200,7 @@ def test_cir_exact_mean_and_surrogate_gain(P, trained):
     prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=0.08, T=1.0, K=0.0, mu=0.0, sigma=0.3,
                        kappa=0.5, theta=0.04, discount=1.0)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     n = 20000
     res = {}
@@ -233,7 +233,7 @@ def test_eval_kernel_matches_path_kernel_surrogate(P, orc):
     prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=X0, T=1.0, K=0.0, mu=0.0, sigma=sigma,
                        kappa=kappa, theta=theta, discount=1.0)
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     c = sigma ** 2 * (-math.expm1(-kappa)) / (4 * kappa)
     e = math.exp(-kappa)
