@@ -397,45 +397,66 @@ double or_pwp_table(int K, int deg, double *coef) {
   return 1.0 - 2.0 * proj;
 }
 
+/* The piecewise polynomial approximation at one uniform (NaN outside [0, 1]). */
+static double pwp_value(const float *coef, int K, float uf) {
+  double x = (double)uf;
+  if (!(x >= 0.0 && x <= 1.0)) return NAN;
+  int lower = x < 0.5;
+  double v = lower ? x : 1.0 - x;
+  int k = or_pwl_index(v, K, 0.5);
+  double s = 0.0;
+  if (k > 0) {
+    const double b = ldexp(1.0, -k);
+    s = (k < K) ? (v - 0.5 * b) / (0.5 * b) : v / b;
+  }
+  double z = 0.0;
+  for (int j = 3; j >= 0; --j) z = z * s + (double)coef[4 * k + j];
+  return lower ? z : -z;
+}
+
 void or_sample_pwp(const float *coef, int K, const float *u, int64_t n, double *out) {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < n; ++i) {
-    double x = (double)u[i];
-    if (!(x >= 0.0 && x <= 1.0)) {
-      out[i] = NAN;
-      continue;
-    }
-    int lower = x < 0.5;
-    double v = lower ? x : 1.0 - x;
-    int k = or_pwl_index(v, K, 0.5);
-    double s = 0.0;
-    if (k > 0) {
-      const double b = ldexp(1.0, -k);
-      s = (k < K) ? (v - 0.5 * b) / (0.5 * b) : v / b;
-    }
-    double z = 0.0;
-    for (int j = 3; j >= 0; --j) z = z * s + (double)coef[4 * k + j];
-    out[i] = lower ? z : -z;
-  }
+  for (int64_t i = 0; i < n; ++i) out[i] = pwp_value(coef, K, u[i]);
 }
 
 /* ========================================================================== */
 /* Samplers (Section 3.2 piecewise constant; Section 3.3 / Algorithm 1)       */
 /* ========================================================================== */
+/* One uniform: the value and the interval index (-1 and NaN outside [0, 1]). */
+static double pwc_value(const float *table, int n_table, float uf, int32_t *m_out) {
+  double x = (double)uf;
+  if (!(x >= 0.0 && x <= 1.0)) {
+    *m_out = -1;
+    return NAN;
+  }
+  /* interval [m/N, (m+1)/N) containing x; x = 1 goes to the last interval */
+  int m = (int)floor(x * n_table);
+  if (m > n_table - 1) m = n_table - 1;
+  *m_out = m;
+  return (double)table[m];
+}
+
+static double pwl_value(const float *alpha, const float *beta, int K, float uf, int32_t *k_out) {
+  double x = (double)uf;
+  if (!(x >= 0.0 && x <= 1.0)) {
+    *k_out = -1;
+    return NAN;
+  }
+  int lower = x < 0.5;                  /* predicate                       */
+  double v = lower ? x : 1.0 - x;       /* reflect about 1/2 (exact)        */
+  int k = or_pwl_index(v, K, 0.5);      /* dyadic interval of v             */
+  double z = (double)alpha[k] + (double)beta[k] * v;
+  *k_out = k;
+  return lower ? z : -z;                /* restore the sign (u=1/2 -> -0)   */
+}
+
+/* The samplers spread their independent elements over the OpenMP threads. */
 void or_sample_pwc(const float *table, int n_table, const float *u, int64_t n,
                    double *out, int32_t *idx) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
-    double x = (double)u[i];
-    if (!(x >= 0.0 && x <= 1.0)) {
-      out[i] = NAN;
-      if (idx) idx[i] = -1;
-      continue;
-    }
-    /* interval [m/N, (m+1)/N) containing x; x = 1 goes to the last interval */
-    int m = (int)floor(x * n_table);
-    if (m > n_table - 1) m = n_table - 1;
-    out[i] = (double)table[m];
+    int32_t m;
+    out[i] = pwc_value(table, n_table, u[i], &m);
     if (idx) idx[i] = m;
   }
 }
@@ -444,17 +465,8 @@ void or_sample_pwl(const float *alpha, const float *beta, int K, const float *u,
                    double *out, int32_t *idx) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
-    double x = (double)u[i];
-    if (!(x >= 0.0 && x <= 1.0)) {
-      out[i] = NAN;
-      if (idx) idx[i] = -1;
-      continue;
-    }
-    int lower = x < 0.5;                  /* predicate                       */
-    double v = lower ? x : 1.0 - x;       /* reflect about 1/2 (exact)        */
-    int k = or_pwl_index(v, K, 0.5);      /* dyadic interval of v             */
-    double z = (double)alpha[k] + (double)beta[k] * v;
-    out[i] = lower ? z : -z;              /* restore the sign (u=1/2 -> -0)   */
+    int32_t k;
+    out[i] = pwl_value(alpha, beta, K, u[i], &k);
     if (idx) idx[i] = k;
   }
 }
@@ -466,11 +478,10 @@ void or_sample_pwl(const float *alpha, const float *beta, int K, const float *u,
 /* ========================================================================== */
 static double approx_variate(const or_sde_params *prm, const float *alpha, const float *beta,
                              int K, float u) {
-  double z;
-  if (prm->approx == OR_APPROX_PWC) or_sample_pwc(alpha, K, &u, 1, &z, NULL);
-  else if (prm->approx == OR_APPROX_PWP) or_sample_pwp(alpha, K, &u, 1, &z);
-  else or_sample_pwl(alpha, beta, K, &u, 1, &z, NULL);
-  return z;
+  int32_t k;
+  if (prm->approx == OR_APPROX_PWC) return pwc_value(alpha, K, u, &k);
+  if (prm->approx == OR_APPROX_PWP) return pwp_value(alpha, K, u);
+  return pwl_value(alpha, beta, K, u, &k);
 }
 
 /* one step of the scheme with Brownian increment dW over time dt */
