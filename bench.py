@@ -324,8 +324,10 @@ _TRAINED = {}   # the surrogate trained by cir_surrogate, reused by cir_learned_
 
 def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     """CIR (kappa 0.5, theta 0.04, sigma 0.3, X0 0.04, T 1; nu = 0.889): train the
-    surrogate on exact quantiles, then report its error, the exact/surrogate
-    cost ratio, and the variance of the two-way differences per level."""
+    surrogate (P~ = Phi^{-1} + sqrt(y) N) on exact quantiles, batch 8192, 48
+    epochs (each epoch one replayed CUDA graph), then report its error, the
+    exact/surrogate cost ratio, and the variance of the two-way differences
+    per level."""
     import math
     import torch
     nu = 4 * 0.5 * 0.04 / 0.3 ** 2
@@ -335,13 +337,14 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    P.ncx2_targets(nu, n_train, u, lam, tgt, st, seed=11, tag=1, stream=stream)
+    # ln(lambda) ~ U(-6, 7): lambda up to ~1100, past the CIR levels' own range
+    P.ncx2_targets(nu, n_train, u, lam, tgt, st, seed=11, tag=1, loglam_lo=-6.0, loglam_hi=7.0, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t_exact_ms = e0.elapsed_time(e1)
     s = P.Surrogate(nu, seed=3)
     loss = torch.zeros(1, device=dev)
-    epochs = 12
+    epochs = 48
     e0.record(stream)
     s.train(u, lam, tgt, batch=8192, epochs=epochs, lr=3e-3, lr_final=3e-5, loss=loss, stream=stream)
     e1.record(stream)
@@ -380,7 +383,8 @@ def cir_surrogate(P, dev, stream, n_train: int = 1 << 22):
         row["log2_var_ratio_gauss"] = math.log2(row["diff_gauss_var"] / row["exact_var"])
         levels.append(row)
     _TRAINED["surrogate"] = s
-    return {"nu": nu, "train_samples": n_train, "epochs": epochs, "train_ms": t_train_ms,
+    return {"nu": nu, "train_samples": n_train, "train_loglam_range": [-6.0, 7.0], "batch": 8192, "epochs": epochs,
+            "train_ms": t_train_ms, "train_us_per_step": 1e3 * t_train_ms / (epochs * (n_train // 8192)),
             "final_batch_mse": float(loss.item()), "heldout_rmse": rmse, "heldout_rmse_gauss_limit": rmse_g,
             "exact_quantiles_per_s": n_train / (t_exact_ms / 1e3),
             "surrogate_evals_per_s": n_train / (t_eval_ms / 1e3),
@@ -617,18 +621,62 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     res = {"eps": eps, "sets": n_sets}
     # pilots of 2000 paths per new term: 4096 sets x ~9 levels of pilots at the
     # default 10^4 would cost more than most sets' final four-way terms
-    nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=12, n_pilot=2000)
-    regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=12, n_pilot=2000)
+    L_max = 12
+    nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=L_max, n_pilot=2000)
+    regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=L_max, n_pilot=2000)
     Lp = max(r.L for r in nested[:n_plain])
     plain = P.mlmc_run_sets(sets[:n_plain], tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=Lp, seed=3)
+    res["L_max"] = L_max
+
+    def summary(rr):
+        out = {"sets": len(rr), "gpu_ms": rr[0].gpu_ms, "wall_ms": rr[0].wall_ms,
+               "launches": rr[0].launches, "converged": sum(int(r.converged) for r in rr),
+               "max_rmse_est": max((r.variance + r.bias ** 2) ** 0.5 for r in rr),
+               "L_hist": {str(l): sum(1 for r in rr if r.L == l) for l in sorted({r.L for r in rr})}}
+        # modelled device time by term slot (calibrated ns per path x paths)
+        t = [0.0, 0.0]
+        for r in rr:
+            for l in range(r.L + 1):
+                for k in range(2):
+                    t[k] += r.paths[l][k] * r.cost_ns[l][k] * 1e-6
+        out["modelled_ms_by_slot"] = t
+        out["unconverged_max_rmse_est"] = max(((r.variance + r.bias ** 2) ** 0.5 for r in rr if not r.converged),
+                                              default=0.0)
+        return out
+
     for name, rr in (("nested", nested), ("regular", regular), ("plain_exact_subset", plain)):
-        res[name] = {"sets": len(rr), "gpu_ms": rr[0].gpu_ms, "wall_ms": rr[0].wall_ms,
-                     "launches": rr[0].launches, "converged": sum(int(r.converged) for r in rr),
-                     "max_rmse_est": max((r.variance + r.bias ** 2) ** 0.5 for r in rr),
-                     "L_hist": {str(l): sum(1 for r in rr if r.L == l) for l in sorted({r.L for r in rr})}}
+        res[name] = summary(rr)
+    # where the nested estimator's work goes: per level, the median over sets of
+    # log2 Var(four-way) / Var(two-way), and the per-step costs of the kinds
+    import math as _m
+    diag = []
+    for l in range(L_max + 1):
+        r_l = [_m.log2(r.var[l][1] / r.var[l][0]) for r in nested if r.L >= l and r.var[l][0] > 0 and r.var[l][1] > 0]
+        if r_l:
+            r_l.sort()
+            diag.append({"l": l, "sets": len(r_l), "median_log2_v4_over_v2": r_l[len(r_l) // 2],
+                         "p90_log2_v4_over_v2": r_l[int(0.9 * (len(r_l) - 1))]})
+    res["nested_levels"] = diag
+    r0 = nested[0]
+    res["step_cost_ratio"] = {"approx2_over_exact2": (r0.cost_ns[5][0] / regular[0].cost_ns[5][0]),
+                              "corr4_over_exact2": (r0.cost_ns[5][1] / regular[0].cost_ns[5][0])}
+    # the slow-decay class: the sets nested MLMC left unconverged at L_max, run
+    # again with four more levels allowed; their Feller ratio 2 kappa theta / sigma^2
+    slow = [i for i, r in enumerate(nested) if not r.converged]
+    if slow:
+        ss = [sets[i] for i in slow]
+        wss = torch.empty(P.mlmc_run_sets_workspace_bytes(len(ss)), dtype=torch.uint8, device=dev)
+        n16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_NESTED, seed=4, L_max=L_max + 4, n_pilot=2000)
+        r16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_REGULAR, seed=5, L_max=L_max + 4, n_pilot=2000)
+        feller = sorted(2 * sw["kappa"][i] * sw["theta"][i] / sw["sigma"][i] ** 2 for i in slow)
+        res["slow_class"] = {"sets": len(slow), "feller_ratio_median": feller[len(feller) // 2],
+                             "feller_ratio_max": feller[-1], "L_max": L_max + 4,
+                             "nested": summary(n16), "regular": summary(r16)}
     res["plain_exact_fixed_L"] = Lp
     plain_all_ms = plain[0].gpu_ms * n_sets / n_plain
     res["plain_exact_gpu_ms_scaled"] = plain_all_ms
+    res["plain_exact_note"] = (f"plain exact MC timed on the first {n_plain} sets at L = {Lp} (the finest level "
+                               f"nested MLMC used there) and scaled by {n_sets}/{n_plain}")
     res["speedup_vs_plain_exact_gpu"] = plain_all_ms / nested[0].gpu_ms
     res["speedup_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / nested[0].gpu_ms
     return res
@@ -777,9 +825,11 @@ def run_reference(args):
     return 0
 
 
-def profile_mlmc_kinds():
-    """One level launch per estimator kind (GBM call, Euler-Maruyama, level 6,
-    2^20 paths): APPROX2, EXACT2, CORR4 in that order."""
+def profile_mlmc_kinds(model: str = "gbm"):
+    """One level launch per estimator kind (Euler-Maruyama, level 6, 2^20
+    paths): APPROX2, EXACT2, CORR4 in that order.  GBM: the call of the GBM
+    configuration.  CIR: a set from the middle of the batched sweep's ranges
+    (kappa 1, theta 0.05, sigma 0.3, X0 = K = theta), truncated scheme."""
     import torch
     import paper_2012_09715_gb300 as P
     from paper_2012_09715_gb300 import build as B
@@ -789,6 +839,9 @@ def profile_mlmc_kinds():
     ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
     sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
     prm = P.sde_params()
+    if model == "cir":
+        prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_CALL, X0=0.05, T=1.0, K=0.05, mu=0.0, sigma=0.3,
+                           kappa=1.0, theta=0.05, discount=1.0)
     for kind in (P.KIND_APPROX2, P.KIND_EXACT2, P.KIND_CORR4):
         P.mlmc_level(prm, tl, 6, kind, 1 << 20, sums, ws, seed=1, tag=3)
     torch.cuda.synchronize()
@@ -886,11 +939,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n-log2", type=int, default=28, help="workload size (profiling runs only)")
-    ap.add_argument("--profile-case", choices=["mlmc_kinds", "kernels", "cir_small"], default=None,
+    ap.add_argument("--profile-case", choices=["mlmc_kinds", "mlmc_kinds_cir", "kernels", "cir_small"], default=None,
                     help="run one fixed launch sequence for an ncu capture and exit (no timing line)")
     args = ap.parse_args()
     if args.profile_case == "mlmc_kinds":
         return profile_mlmc_kinds()
+    if args.profile_case == "mlmc_kinds_cir":
+        return profile_mlmc_kinds("cir")
     if args.profile_case == "kernels":
         return profile_kernels()
     if args.profile_case == "cir_small":

@@ -340,14 +340,20 @@ aicdf_status aicdf_ncx2_targets(double nu, float loglam_lo, float loglam_hi, uin
 /* ===================================================================== */
 /* Learned surrogate of P_nu(U; y) (Section 5.1 rescaling)                 */
 /* ===================================================================== */
-/* A 2 -> 64 -> 64 -> 1 tanh network P~(u, lambda) for one fixed nu, inputs
- * x0 = s(u)/3 with s(u) = sign(u-1/2) sqrt(-2 ln(2 min(u,1-u))) and
- * x1 = clamp(ln(lambda)/4, -1, 1); then
- * C~^{-1}_nu(u; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~(u, lambda).
- * The 64 x 64 layer runs on the tensor cores in BF16 with FP32 accumulation
- * (tcgen05 MMAs into tensor memory for evaluation and training; the CIR path
- * kernel's in-loop evaluation uses warp-level MMAs); FP32 master weights.  The
- * handle owns its device buffers (allocated at create).  Parameter blob layout (FP32): W1[64][2] | b1[64] | W2[64 out][64 in]
+/* A learned surrogate of P_nu(U; y), y = nu / (lambda + nu) (the rescaled
+ * quantile of Section 5.1), for one fixed nu:
+ *   P~(u, lambda) = Phi^{-1}(u) + sqrt(y) N(x0, x1),
+ *   x0 = s(u)/3, s(u) = sign(u-1/2) sqrt(-2 ln(2 min(u,1-u))),  x1 = 2 sqrt(y) - 1,
+ * with N a 2 -> 64 -> 64 -> 1 tanh network; then
+ * C~^{-1}_nu(u; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~.  P tends to
+ * Phi^{-1}(u) as y -> 0 with P - Phi^{-1} = O(sqrt(y)), so N learns the bounded
+ * correction (P - Phi^{-1}) / sqrt(y) over every lambda >= 0 (x1 covers
+ * [-1, 1) as lambda runs over [0, inf)); Phi^{-1} is the library's FP32
+ * inverse.  The 64 x 64 layer runs on the tensor cores in BF16 with FP32
+ * accumulation (tcgen05 MMAs into tensor memory for evaluation and training;
+ * the CIR path kernel's in-loop evaluation uses warp-level MMAs); FP32 master
+ * weights.  The handle owns its device buffers (allocated at create).
+ * Parameter blob layout (FP32): W1[64][2] | b1[64] | W2[64 out][64 in]
  * | b2[64] | w3[64] | b3, aicdf_surrogate_param_count() floats. */
 typedef struct aicdf_surrogate_s *aicdf_surrogate;
 aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_surrogate *out);
@@ -356,25 +362,37 @@ int aicdf_surrogate_param_count(void);
 aicdf_status aicdf_surrogate_get_params(aicdf_surrogate s, float *host, int cap);
 /* Replaces the weights and resets the optimiser state. */
 aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const float *host, int n);
+/* Save the trained network (nu and the parameter blob, not the optimiser
+ * state) to a host file, and create a handle from such a file (on the
+ * current device); AICDF_ERR_ARG if the file cannot be written or read or is
+ * not a saved surrogate.  Host I/O, synchronous. */
+aicdf_status aicdf_surrogate_save(aicdf_surrogate s, const char *path);
+aicdf_status aicdf_surrogate_load(const char *path, aicdf_surrogate *out);
 /* p_out_dev[i] = P~(u_dev[i], lam_dev[i]).  Should a tensor-core product not
  * signal completion within the kernel's bounded wait (a fault of the device,
  * not of the inputs), the affected outputs are NaN. */
 aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                   size_t n, float *p_out_dev, aicdf_stream_t stream);
-/* Gradient of L = mean_i (P~_i - target_i)^2 over the n samples, into
- * grad_dev[0 .. param_count) (same layout as the parameters), with the loss
- * sum at grad_dev[param_count]; n <= 2^24. */
+/* The network is fitted to g_i = (target_i - Phi^{-1}(u_i)) / sqrt(y_i) for
+ * targets of P: gradient of L = mean_i (N_i - g_i)^2 (= mean_i (P~_i -
+ * target_i)^2 / y_i, the squared error of P~ in the units that a CIR step
+ * carries equally at every lambda) over the n samples, into
+ * grad_dev[0 .. param_count) (same layout as the parameters), with the sum of
+ * (N_i - g_i)^2 at grad_dev[param_count]; n <= 2^24. */
 aicdf_status aicdf_surrogate_grad(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                   const float *target_dev, size_t n, float *grad_dev,
                                   aicdf_stream_t stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch; writes the
- * batch's mean squared error to *loss_dev if loss_dev is not NULL. */
+ * batch's L to *loss_dev if loss_dev is not NULL. */
 aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                         const float *target_dev, size_t n, float lr,
                                         float *loss_dev, aicdf_stream_t stream);
 /* epochs passes over n samples in batches of `batch` (the tail that does not
  * fill a batch is skipped), step size decaying geometrically from lr to
- * lr_final; the last batch's loss goes to *loss_dev. */
+ * lr_final; the last batch's L goes to *loss_dev.  One epoch's launches are
+ * captured as a CUDA graph and replayed per epoch (the step sizes come from a
+ * device step counter), so the call must not itself be made during a stream
+ * capture. */
 aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                    const float *target_dev, size_t n, size_t batch, int epochs,
                                    float lr, float lr_final, float *loss_dev, aicdf_stream_t stream);
@@ -386,10 +404,7 @@ aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const 
  * draws one uniform U (Philox counter (s/4, p mod 2^32, p>>32, tag), word
  * s%4) and both sides use the same U:
  *   EXACT       P(X^_T), X^' = c C^{-1}_nu(U; X^ e^{-kappa h}/c)  (FP64 root finder)
- *   SURROGATE   P(X~_T), X~' = c max(C~^{-1}_nu(U; lambda~), 0)   (learned P~;
- *               for lambda > e^4, beyond the trained range, P~ = Phi^{-1}(U) +
- *               sqrt(y/y_max) (P~(U, e^4) - Phi^{-1}(U)), the O(sqrt(y)) decay of
- *               P - Phi^{-1} as y = nu/(lambda+nu) -> 0)
+ *   SURROGATE   P(X~_T), X~' = c max(C~^{-1}_nu(U; lambda~), 0)   (learned P~)
  *   DIFF        P(X^_T) - P(X~_T)                                  (same steps)
  *   GAUSS       as SURROGATE with P~ replaced by Phi^{-1}(U), the y -> 0
  *               limit of P (Section 5.1): the approximation without the network
@@ -467,9 +482,12 @@ typedef struct {
   int estimator;          /* aicdf_estimator                                              */
   int L_min, L_max;       /* first and last admissible finest level                      */
   int fixed_L;            /* >= 0: use exactly this finest level (no bias test)           */
-  uint64_t n_pilot;       /* pilot paths per new term (0: 10^4); a nested estimator's
-                             four-way terms, with their far smaller variance, take
-                             max(128, n_pilot / 16) (at most n_pilot)                     */
+  uint64_t n_pilot;       /* pilot paths per new term at levels <= L_min (0: 10^4),
+                             halved for each level above L_min (at least 128;
+                             plain Monte Carlo keeps n_pilot); a
+                             nested estimator's four-way terms, with their far
+                             smaller variance, start from max(128, n_pilot / 16)
+                             (at most n_pilot)                                            */
   uint64_t seed;
   double weak_order;      /* alpha in the bias estimate |E Y_L| / (2^alpha - 1)           */
 } aicdf_mlmc_opts;
@@ -496,10 +514,11 @@ typedef struct {
  * Philox stream (tag = 1 + 64*estimator + 2*l + t), extending the stream with
  * path_offset as more paths are added, so the result is reproducible from the
  * seed.  Path counts follow the optimal allocation of Section 4.1 from the
- * measured variances and per-path device times, and every term keeps at
- * least 16 (k - 1) paths, k its measured kurtosis, so that its variance
- * estimate is good to about 25% (a library choice; the paper assumes the
- * variances known).  While the bias estimate
+ * measured variances and per-path device times.  A term whose share f of
+ * the estimator's variance sum_i V_i / n_i is not small keeps at least
+ * (k - 1) (4 f)^2 paths, k its measured kurtosis, so that its variance
+ * estimate moves the estimator's by no more than about 25% of its share (a
+ * library choice; the paper takes the variances as known).  While the bias estimate
  * exceeds eps/sqrt(2), levels are added (up to L_max; converged = 0 if it is
  * reached): as many at once as the weak order predicts are needed,
  * ceil(log2(bias / (eps/sqrt(2))) / weak_order), at least one.  workspace_dev: at least aicdf_mlmc_run_workspace_bytes().

@@ -121,6 +121,8 @@ SIGNATURES = {
     "aicdf_surrogate_param_count": (_I, []),
     "aicdf_surrogate_get_params": (_I, [_P, _P, _I]),
     "aicdf_surrogate_set_params": (_I, [_P, _P, _I]),
+    "aicdf_surrogate_save": (_I, [_P, C.c_char_p]),
+    "aicdf_surrogate_load": (_I, [C.c_char_p, _P]),
     "aicdf_surrogate_eval": (_I, [_P, _P, _P, _SZ, _P, _P]),
     "aicdf_surrogate_grad": (_I, [_P, _P, _P, _P, _SZ, _P, _P]),
     "aicdf_surrogate_train_step": (_I, [_P, _P, _P, _P, _SZ, C.c_float, _P, _P]),
@@ -420,12 +422,29 @@ def ncx2_targets(nu: float, n: int, u, lam, p, status, seed: int = 0, tag: int =
 class Surrogate:
     """Owning handle of the learned P_nu(U; y) surrogate (device weights)."""
 
-    def __init__(self, nu: float, seed: int = 0):
-        h = C.c_void_p()
-        _check(lib().aicdf_surrogate_create(nu, seed, C.byref(h)), "surrogate_create")
+    def __init__(self, nu: float, seed: int = 0, _handle=None):
+        h = _handle
+        if h is None:
+            h = C.c_void_p()
+            _check(lib().aicdf_surrogate_create(nu, seed, C.byref(h)), "surrogate_create")
         self.handle = h
         self.nu = nu
         self.n_params = lib().aicdf_surrogate_param_count()
+
+    def save(self, path: str):
+        """aicdf_surrogate_save: nu and the weights to a host file."""
+        _check(lib().aicdf_surrogate_save(self.handle, os.fsencode(path)), "surrogate_save")
+
+    @classmethod
+    def load(cls, path: str, nu: float | None = None):
+        """aicdf_surrogate_load: a new handle from a file written by save()."""
+        h = C.c_void_p()
+        _check(lib().aicdf_surrogate_load(os.fsencode(path), C.byref(h)), "surrogate_load")
+        import struct
+        with open(path, "rb") as f:
+            f.read(8)
+            file_nu = struct.unpack("<d", f.read(8))[0]
+        return cls(file_nu if nu is None else nu, _handle=h)
 
     def get_params(self):
         import numpy as np

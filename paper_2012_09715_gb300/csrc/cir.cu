@@ -6,8 +6,9 @@
 // horizon-T law of Section 5.2 applied per step).  Exact: X' = c C^{-1}_nu(U; lambda)
 // by the FP64 root finder.  Approximate: X' = c max(C~^{-1}_nu(U; lambda), 0) with
 // C~^{-1} = lambda + nu + 2 sqrt(lambda + nu) P~ and P~ either the learned
-// surrogate (tensor-core MLP, one warp = 32 paths) or, for comparison, the
-// limit P -> Phi^{-1}(U) of Section 5.1.  As in the paper's CIR experiment the
+// surrogate P~ = Phi^{-1}(U) + sqrt(y) N (tensor-core MLP, one warp = 32
+// paths; y = nu / (lambda + nu)) or, for comparison, the limit P ->
+// Phi^{-1}(U) of Section 5.1.  As in the paper's CIR experiment the
 // two-way difference uses the same time step on both sides.
 #include <cuda_runtime.h>
 
@@ -25,7 +26,6 @@
 namespace aicdf {
 
 constexpr int kCirThreads = 256;
-constexpr float kLamTrainMax = 54.598150033144236f;  // e^4: top of the surrogate's trained range
 
 struct CirArgs {
   PhiloxKeys keys;
@@ -89,14 +89,8 @@ __global__ void __launch_bounds__(kCirThreads)
             const float lam = fmaxf(xa, 0.f) * ratio;
             float pt;
             if constexpr (APPROX == 1) {
-              pt = mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_lam(lam), hs[warp]);
-              if (lam > kLamTrainMax) {
-                // beyond the trained range: P - Phi^{-1}(U) = O(sqrt(y)) as y -> 0
-                // (Section 5.1), so carry the learned correction at the edge
-                // of the range over with the factor sqrt(y / y_max)
-                const float z = phiinv_f32_grid(u);
-                pt = fmaf(pt - z, sqrtf((kLamTrainMax + nuf) / (lam + nuf)), z);
-              }
+              const float sy = mlp_sqrt_y(lam, nuf);
+              pt = fmaf(sy, mlp_forward_warp(s, mlp_feature_u(u), mlp_feature_y(sy), hs[warp]), phiinv_f32_grid(u));
             } else if constexpr (APPROX == 3) {
               pt = ncx2_table_P(s_rows, tab.K, tab.n_knots, tab.scale_k, u, sqrtf(nuf / (lam + nuf)));
             } else {

@@ -55,16 +55,44 @@ struct Term {
 
 // The sample variance of n paths of a term with kurtosis k has relative
 // standard error about sqrt((k - 1) / n).  The optimal allocation (Section
-// 4.1) trusts each term's variance estimate, so a term gets at least the
-// paths that bring that error to 1/4: n >= 16 (k - 1).  Heavy-tailed terms
-// -- the four-way corrections, whose Y is the rare large difference between
-// exact and approximate paths -- are the ones this protects; for a Gaussian
-// Y the floor is 32 paths, below every pilot.
+// 4.1) trusts each term's variance; what matters is the error that a term's
+// variance estimate puts into the estimator's variance sum_i V_i / n_i, in
+// which the term has the share f = (V / n) / sum.  So a term keeps at least
+// the paths that make f sqrt((k - 1) / n) <= 1/4, n >= (k - 1) (4 f)^2: a
+// heavy-tailed term (the four-way corrections, whose Y is the rare large
+// difference between exact and approximate paths) with a real share of the
+// variance gets enough paths to be measured, and one whose share is tiny
+// costs nothing extra.
 constexpr double kVarRelErr = 0.25;
-uint64_t kurtosis_floor(const Term &t) {
+uint64_t kurtosis_floor(const Term &t, double share) {
   const double k = t.kurt();
-  if (!(k > 1.0)) return 0;
-  return (uint64_t)std::min(1e12, std::ceil((k - 1.0) / (kVarRelErr * kVarRelErr)));
+  if (!(k > 1.0) || !(share > 0.0)) return 0;
+  const double f = share / kVarRelErr;
+  return (uint64_t)std::min(1e12, std::ceil((k - 1.0) * f * f));
+}
+
+// Shares (V_i / m_i) / sum_j (V_j / m_j) of the terms in the estimator's
+// variance at the allocated counts m.
+std::vector<double> variance_shares(const std::vector<double> &v, const std::vector<double> &m) {
+  std::vector<double> f(v.size(), 0.0);
+  double tot = 0.0;
+  for (size_t i = 0; i < v.size(); ++i)
+    if (m[i] > 0.0) tot += v[i] / m[i];
+  if (tot > 0.0)
+    for (size_t i = 0; i < v.size(); ++i)
+      if (m[i] > 0.0) f[i] = v[i] / m[i] / tot;
+  return f;
+}
+
+// Pilot paths of a new multilevel term at level l: n at levels <= L_min,
+// halved for each level above (at least 128).  The optimal counts of level
+// corrections fall like 2^-l for the usual variance decay and cost growth
+// (Section 4.1), so a full pilot at a fine level would be most of that
+// level's cost.  Plain Monte Carlo (one term at its level) keeps n.
+uint64_t level_pilot(uint64_t n, int l, int L_min, int estimator) {
+  if (estimator == AICDF_EST_PLAIN) return n;
+  const int d = std::max(0, l - L_min);
+  return std::max<uint64_t>(std::min<uint64_t>(n, 128), d >= 63 ? 0 : n >> d);
 }
 
 // Pilot paths of a new four-way correction term of the nested estimator.
@@ -226,7 +254,8 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
         terms.push_back(t);
       }
     std::vector<uint64_t> add(terms.size(), 0);
-    for (size_t i = first; i < terms.size(); ++i) add[i] = terms[i].kind == AICDF_KIND_CORR4 ? pilot4 : pilot;
+    for (size_t i = first; i < terms.size(); ++i)
+      add[i] = level_pilot(terms[i].kind == AICDF_KIND_CORR4 ? pilot4 : pilot, terms[i].level, o->L_min, est);
     return run_round(add);
   };
 
@@ -253,8 +282,9 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     s = aicdf_mlmc_allocate((int)terms.size(), v.data(), c.data(), eps, m.data(), &total);
     if (s != AICDF_OK) break;
     std::vector<uint64_t> add(terms.size(), 0);
+    const std::vector<double> share = variance_shares(v, m);
     for (size_t i = 0; i < terms.size(); ++i) {
-      const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(terms[i]));
+      const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(terms[i], share[i]));
       if (!(want < 1e15)) {
         s = AICDF_ERR_NOCONVERGE;
         break;
@@ -453,7 +483,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
         // distinct streams per set, estimator, level and kind
         t.tag = ((uint32_t)s << 8) + 1u + 64u * (uint32_t)est + 2u * (uint32_t)l + (uint32_t)i;
         S[s].terms.push_back(t);
-        add[s].push_back(t.kind == AICDF_KIND_CORR4 ? pilot4 : pilot);
+        add[s].push_back(level_pilot(t.kind == AICDF_KIND_CORR4 ? pilot4 : pilot, l, o->L_min, est));
       }
   };
   std::vector<std::vector<uint64_t>> add(n_sets);
@@ -485,8 +515,9 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       double total = 0.0;
       rc = aicdf_mlmc_allocate((int)S[s].terms.size(), v.data(), c.data(), eps, m.data(), &total);
       if (rc != AICDF_OK) break;
+      const std::vector<double> share = variance_shares(v, m);
       for (size_t i = 0; i < S[s].terms.size(); ++i) {
-        const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(S[s].terms[i]));
+        const double want = std::max(std::ceil(m[i]), (double)kurtosis_floor(S[s].terms[i], share[i]));
         if (!(want < 1e15)) {
           rc = AICDF_ERR_NOCONVERGE;
           break;

@@ -1,6 +1,7 @@
 // Learned surrogate for the non-central chi-squared inverse CDF (Section 5.1):
-// P~(U; lambda) ~ P_nu(U; nu / (lambda + nu)), so that
-// C~^{-1}_nu(U; lambda) = lambda + nu + 2 sqrt(lambda + nu) P~.
+// P~(U; lambda) = Phi^{-1}(U) + sqrt(y) N(s(U)/3, 2 sqrt(y) - 1) ~ P_nu(U; y),
+// y = nu / (lambda + nu), so that C~^{-1}_nu(U; lambda) = lambda + nu +
+// 2 sqrt(lambda + nu) P~ (mlp_device.cuh explains the form).
 //
 // Kernels: batched evaluation and a fused forward + backward training step,
 // both with their 64-wide products (layer 2, dH1 = dZ2 W2, dW2 = dZ2^T H1) as
@@ -12,6 +13,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <random>
@@ -36,8 +38,9 @@ constexpr int kLossSlot = kOffB3 + 1;          // 4417
 // read the same TMEM lane quarter), so that each FP32 weight read from shared
 // memory serves two samples.  The pair's two MMAs go to two 64-column
 // accumulators under one commit; other CTAs on the SM fill the wait.  Inputs
-// are loaded one pair ahead.  The output is b3 + (lower half + upper half),
-// the training step's forward value.  Should the MMAs' completion not arrive
+// are loaded one pair ahead.  The network's output is b3 + (lower half + upper
+// half), the training step's forward value, and the sample is
+// Phi^{-1}(u) + sqrt(y) times it.  Should the MMAs' completion not arrive
 // within the bounded wait, the pair's outputs are NaN and the CTA stops.
 constexpr int kEvalThreads = 2 * kTcRows;
 constexpr uint32_t kTcCols = 128;  // TMEM columns per CTA: two 64-column accumulators
@@ -57,7 +60,8 @@ static_assert(sizeof(MlpTcSmem) + 1024 <= kTcSmemBytes, "tile layout exceeds the
 
 __global__ void __launch_bounds__(kEvalThreads, 4)
     k_mlp_eval(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
-               const float *__restrict__ u, const float *__restrict__ lam, float *__restrict__ out, uint64_t n) {
+               const float *__restrict__ u, const float *__restrict__ lam, float *__restrict__ out, uint64_t n,
+               float nu) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(tc_raw + ((1024 - (tc_smem(tc_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -87,8 +91,10 @@ __global__ void __launch_bounds__(kEvalThreads, 4)
   load(t0, pua, pla);
   load(t0 + 1, pub, plb);
   for (uint32_t j = 0; t0 < ntiles; t0 += step, ++j) {
-    const float xa0 = mlp_feature_u(pua), xa1 = mlp_feature_lam(pla);
-    const float xb0 = mlp_feature_u(pub), xb1 = mlp_feature_lam(plb);
+    const float sya = mlp_sqrt_y(pla, nu), syb = mlp_sqrt_y(plb, nu);
+    const float xa0 = mlp_feature_u(pua), xa1 = mlp_feature_y(sya);
+    const float xb0 = mlp_feature_u(pub), xb1 = mlp_feature_y(syb);
+    const float za = phiinv_f32(pua), zb = phiinv_f32(pub);
     load(t0 + step, pua, pla);  // the next pair's inputs, in flight during this pair
     load(t0 + step + 1, pub, plb);
     mlp_tc_layer1_pair(s.v, s.a[0], s.a[1], m, c0, xa0, xa1, xb0, xb1);
@@ -115,8 +121,8 @@ __global__ void __launch_bounds__(kEvalThreads, 4)
     tc_fence_after_sync();
     if (!hf) {
       const uint64_t ia = t0 * kTcRows + m, ib = ia + kTcRows;
-      if (ia < n) out[ia] = s.v.b3 + (ya + s.ypart[0][m]);
-      if (ib < n) out[ib] = s.v.b3 + (yb + s.ypart[1][m]);
+      if (ia < n) out[ia] = fmaf(sya, s.v.b3 + (ya + s.ypart[0][m]), za);
+      if (ib < n) out[ib] = fmaf(syb, s.v.b3 + (yb + s.ypart[1][m]), zb);
     }
     if (!__syncthreads_and(done)) break;  // also: ypart read before the next pair writes it
   }
@@ -136,8 +142,10 @@ __global__ void __launch_bounds__(kEvalThreads, 4)
 // written column by column; W2 and W2^T arrive by one bulk copy); everything
 // else in FP32.  The column sums over the CTA's samples (gradients of w3, b2,
 // b1, W1) go through a transposing shared buffer and are added in a fixed
-// order, so the partials are deterministic.  Writes the CTA's gradient of
-// sum_i (y_i - t_i)^2 * scale and its loss sum to partial[blockIdx].
+// order, so the partials are deterministic.  The network is fitted to
+// g_i = (t_i - Phi^{-1}(u_i)) / sqrt(y_i) for the target t_i of P (the form
+// of mlp_device.cuh).  Writes the CTA's gradient of sum_i (N_i - g_i)^2 * scale
+// and its sum of (N_i - g_i)^2 to partial[blockIdx].
 constexpr int kTrainThreads = 2 * kTcRows;
 constexpr uint32_t kTrainCols = 256;  // TMEM columns (three 64-column accumulators)
 
@@ -187,7 +195,8 @@ __device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
 __global__ void __launch_bounds__(kTrainThreads)
     k_mlp_train(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
                 const float *__restrict__ u, const float *__restrict__ lam, const float *__restrict__ target,
-                uint64_t begin, uint64_t count, float scale, float *__restrict__ partial) {
+                uint64_t begin, uint64_t count, float scale, float *__restrict__ partial, float nu,
+                long long *__restrict__ step_count) {
   extern __shared__ __align__(1024) unsigned char tr_raw[];
   MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(tr_raw + ((1024 - (tc_smem(tr_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -218,9 +227,12 @@ __global__ void __launch_bounds__(kTrainThreads)
   const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + m;
   const bool ok = m_idx < count;
   const uint64_t i = begin + m_idx;
-  const float x0 = ok ? mlp_feature_u(u[i]) : 0.f;
-  const float x1 = ok ? mlp_feature_lam(lam[i]) : 0.f;
-  const float tg = ok ? target[i] : 0.f;
+  if (step_count && blockIdx.x == 0 && tid == 0) *step_count += 1;  // the Adam kernel after this reads it
+  const float ui = ok ? u[i] : 0.5f;
+  const float sy = ok ? mlp_sqrt_y(lam[i], nu) : 1.f;
+  const float x0 = ok ? mlp_feature_u(ui) : 0.f;
+  const float x1 = ok ? mlp_feature_y(sy) : 0.f;
+  const float tg = ok ? (target[i] - phiinv_f32(ui)) / sy : 0.f;  // g: the network's own target
   __syncthreads();  // vectors staged
 #pragma unroll
   for (int j = 0; j < kHalf / 8; ++j) {
@@ -403,14 +415,32 @@ __device__ __forceinline__ float sum_partials(const float *__restrict__ partial,
 // per parameter, in small blocks so that the summing spreads over many SMs).
 constexpr int kAdamThreads = 64;
 
+// The step size and bias corrections of a scheduled Adam step come from the
+// device step counter (advanced by the gradient kernel before it): step st
+// (1-based) has lr = lr0 2^(log2_ratio (st - 1 - base)) -- the geometric decay
+// from lr0 to lr_final over the steps after `base` -- and corrections
+// 1 - b^st.  With on = 0 the kernel's explicit lr, bc1, bc2 are used.
+struct AdamSched {
+  int on;
+  float lr0, log2_ratio;
+  long long base;
+  float log2_b1, log2_b2;
+};
+
 __global__ void __launch_bounds__(kAdamThreads)
     k_mlp_adam(float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2,
                __nv_bfloat16 *__restrict__ w2c, const float *__restrict__ partial, int nblocks, float lr,
                float b1, float b2, float eps, float bc1, float bc2, float *__restrict__ loss_out,
-               float loss_scale) {
+               float loss_scale, const long long *__restrict__ step_count, AdamSched sch) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p == 0 && loss_out) *loss_out = sum_partials(partial, nblocks, kLossSlot) * loss_scale;
   if (p > kOffB3) return;
+  if (sch.on) {
+    const float st = (float)*step_count;
+    lr = sch.lr0 * exp2f(sch.log2_ratio * (st - 1.0f - (float)sch.base));
+    bc1 = 1.0f - exp2f(st * sch.log2_b1);
+    bc2 = 1.0f - exp2f(st * sch.log2_b2);
+  }
   const float gsum = sum_partials(partial, nblocks, p);
   const float m = b1 * m1[p] + (1.f - b1) * gsum;
   const float v = b2 * m2[p] + (1.f - b2) * gsum * gsum;
@@ -482,7 +512,8 @@ struct aicdf_surrogate_s {
   float *partial = nullptr;  // per-block gradient partials
   int partial_blocks = 0;
   int *status = nullptr;
-  long long step = 0;
+  long long *d_step = nullptr;  // Adam steps taken, on the device (scheduled training reads it)
+  long long step = 0;           // the same on the host
 };
 
 constexpr uint32_t kSurrogateMagic = 0x53555247u;
@@ -530,7 +561,8 @@ extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_s
       cudaMalloc(&s->m1, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&s->m2, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&s->w2c, 2 * (size_t)kW2cBytes) != cudaSuccess ||
-      cudaMalloc(&s->status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&s->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&s->d_step, sizeof(long long)) != cudaSuccess) {
     aicdf_surrogate_destroy(s);
     return cuda_fail();
   }
@@ -547,7 +579,8 @@ extern "C" aicdf_status aicdf_surrogate_create(double nu, uint64_t seed, aicdf_s
   if (cudaMemcpy(s->params, p.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
-      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess || upload_w2c(s, p.data()) != AICDF_OK) {
+      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(s->d_step, 0, sizeof(long long)) != cudaSuccess || upload_w2c(s, p.data()) != AICDF_OK) {
     aicdf_surrogate_destroy(s);
     return cuda_fail();
   }
@@ -563,6 +596,7 @@ extern "C" void aicdf_surrogate_destroy(aicdf_surrogate s) {
   cudaFree(s->m2);
   cudaFree(s->partial);
   cudaFree(s->status);
+  cudaFree(s->d_step);
   s->magic = 0;
   delete s;
 }
@@ -578,7 +612,8 @@ extern "C" aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const floa
   if (!sur_ok(s) || !host || n < kOffB3 + 1 || n > kMlpParams) return AICDF_ERR_ARG;
   if (cudaMemcpy(s->params, host, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->m1, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
-      cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess)
+      cudaMemset(s->m2, 0, sizeof(float) * kMlpParams) != cudaSuccess ||
+      cudaMemset(s->d_step, 0, sizeof(long long)) != cudaSuccess)
     return cuda_fail();
   if (upload_w2c(s, host) != AICDF_OK) return AICDF_ERR_CUDA;
   s->step = 0;
@@ -586,6 +621,50 @@ extern "C" aicdf_status aicdf_surrogate_set_params(aicdf_surrogate s, const floa
 }
 
 extern "C" int aicdf_surrogate_param_count(void) { return kOffB3 + 1; }
+
+// File format of a saved surrogate: the 8 bytes "AICDFSG1", nu (FP64), the
+// parameter count (int32), then the FP32 parameter blob; little-endian, as
+// written by the host.  The optimiser state is not saved.
+static const char kSurrogateFileMagic[8] = {'A', 'I', 'C', 'D', 'F', 'S', 'G', '1'};
+
+extern "C" aicdf_status aicdf_surrogate_save(aicdf_surrogate s, const char *path) {
+  if (!sur_ok(s) || !path) return AICDF_ERR_ARG;
+  std::vector<float> p(kMlpParams);
+  aicdf_status rc = aicdf_surrogate_get_params(s, p.data(), kMlpParams);
+  if (rc != AICDF_OK) return rc;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return AICDF_ERR_ARG;
+  const int32_t np = kOffB3 + 1;
+  const bool ok = std::fwrite(kSurrogateFileMagic, 1, 8, f) == 8 && std::fwrite(&s->nu, sizeof(double), 1, f) == 1 &&
+                  std::fwrite(&np, sizeof(np), 1, f) == 1 && std::fwrite(p.data(), sizeof(float), np, f) == (size_t)np;
+  return (std::fclose(f) == 0 && ok) ? AICDF_OK : AICDF_ERR_ARG;
+}
+
+extern "C" aicdf_status aicdf_surrogate_load(const char *path, aicdf_surrogate *out) {
+  if (!path || !out) return AICDF_ERR_ARG;
+  *out = nullptr;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return AICDF_ERR_ARG;
+  char magic[8];
+  double nu = 0.0;
+  int32_t np = 0;
+  std::vector<float> p(kMlpParams, 0.f);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSurrogateFileMagic, 8) == 0 &&
+            std::fread(&nu, sizeof(double), 1, f) == 1 && std::fread(&np, sizeof(np), 1, f) == 1 &&
+            np == kOffB3 + 1 && std::fread(p.data(), sizeof(float), np, f) == (size_t)np;
+  std::fclose(f);
+  if (!ok || !(nu > 0.0) || !std::isfinite(nu)) return AICDF_ERR_ARG;
+  aicdf_surrogate s = nullptr;
+  aicdf_status rc = aicdf_surrogate_create(nu, 0, &s);
+  if (rc != AICDF_OK) return rc;
+  rc = aicdf_surrogate_set_params(s, p.data(), np);
+  if (rc != AICDF_OK) {
+    aicdf_surrogate_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return AICDF_OK;
+}
 
 namespace aicdf {
 const float *surrogate_params(aicdf_surrogate s) { return sur_ok(s) ? s->params : nullptr; }
@@ -606,7 +685,7 @@ extern "C" aicdf_status aicdf_surrogate_eval(aicdf_surrogate s, const float *u_d
   const uint64_t pairs = ((n + kTcRows - 1) / kTcRows + 1) / 2;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(pairs, (uint64_t)sm_count() * 4));
   k_mlp_eval<<<grid, kEvalThreads, kTcSmemBytes, (cudaStream_t)stream>>>(s->params, s->w2c, u_dev, lam_dev, p_out_dev,
-                                                                     n);
+                                                                     n, (float)s->nu);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
@@ -620,21 +699,26 @@ static aicdf_status ensure_partials(aicdf_surrogate_s *s, int blocks) {
   return AICDF_OK;
 }
 
-static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, const float *lam,
-                                      const float *target, uint64_t begin, uint64_t count,
-                                      cudaStream_t st, int *blocks_out) {
-  const int blocks = (int)((count + kTcRows - 1) / kTcRows);
+// Partials for `blocks` CTAs and the kernel's shared-memory opt-in: the
+// set-up of a gradient launch, done before any launch (and any capture).
+static aicdf_status prepare_train_grad(aicdf_surrogate_s *s, int blocks) {
   aicdf_status rc = ensure_partials(s, blocks);
   if (rc != AICDF_OK) return rc;
-  static bool smem_set = false;  // opt in to > 48 KB of dynamic shared memory once
-  if (!smem_set) {
-    if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem) !=
-        cudaSuccess)
-      return cuda_fail();
-    smem_set = true;
-  }
+  static const cudaError_t attr =  // opt in to > 48 KB of dynamic shared memory once
+      cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+  return attr == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+// The gradient kernel over samples [begin, begin + count); step_count (may be
+// NULL) is advanced by one for the Adam step that follows.
+static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, const float *lam,
+                                      const float *target, uint64_t begin, uint64_t count,
+                                      cudaStream_t st, int *blocks_out, long long *step_count) {
+  const int blocks = (int)((count + kTcRows - 1) / kTcRows);
+  aicdf_status rc = prepare_train_grad(s, blocks);
+  if (rc != AICDF_OK) return rc;
   k_mlp_train<<<blocks, kTrainThreads, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, begin, count,
-                                                   1.0f / (float)count, s->partial);
+                                                   1.0f / (float)count, s->partial, (float)s->nu, step_count);
   *blocks_out = blocks;
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
@@ -645,7 +729,8 @@ extern "C" aicdf_status aicdf_surrogate_grad(aicdf_surrogate s, const float *u_d
   if (!sur_ok(s) || !u_dev || !lam_dev || !target_dev || !grad_dev || n == 0 || n > (1u << 24))
     return AICDF_ERR_ARG;
   int blocks = 0;
-  aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, (cudaStream_t)stream, &blocks);
+  aicdf_status rc =
+      launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, (cudaStream_t)stream, &blocks, nullptr);
   if (rc != AICDF_OK) return rc;
   k_mlp_grad_sum<<<(kLossSlot + 64) / 64, 64, 0, (cudaStream_t)stream>>>(s->partial, blocks, grad_dev);
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
@@ -659,14 +744,15 @@ extern "C" aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const floa
     return AICDF_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int blocks = 0;
-  aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, st, &blocks);
+  aicdf_status rc = launch_train_grad(s, u_dev, lam_dev, target_dev, 0, n, st, &blocks, s->d_step);
   if (rc != AICDF_OK) return rc;
   s->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.f - (float)std::pow((double)b1, (double)s->step);
   const float bc2 = 1.f - (float)std::pow((double)b2, (double)s->step);
   k_mlp_adam<<<(kOffB3 + kAdamThreads) / kAdamThreads, kAdamThreads, 0, st>>>(
-      s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1, b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n);
+      s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1, b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n,
+      s->d_step, AdamSched{0, 0.f, 0.f, 0, 0.f, 0.f});
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
@@ -680,18 +766,44 @@ extern "C" aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_
   const size_t steps_per_epoch = n / batch;
   if (steps_per_epoch == 0) return AICDF_ERR_ARG;
   const size_t total = steps_per_epoch * (size_t)epochs;
-  size_t k = 0;
-  for (int e = 0; e < epochs; ++e)
-    for (size_t b = 0; b < steps_per_epoch; ++b, ++k) {
-      // geometric decay of the step size from lr to lr_final
-      const float l = lr * std::pow(lr_final / lr, (float)k / (float)std::max<size_t>(total - 1, 1));
-      const bool last = (k + 1 == total);
-      aicdf_status rc = aicdf_surrogate_train_step(s, u_dev + b * batch, lam_dev + b * batch,
-                                                   target_dev + b * batch, batch, l,
-                                                   last ? loss_dev : nullptr, stream);
-      if (rc != AICDF_OK) return rc;
+  const int blocks = (int)((batch + kTcRows - 1) / kTcRows);
+  aicdf_status rc = prepare_train_grad(s, blocks);
+  if (rc != AICDF_OK) return rc;
+  // One epoch -- a gradient launch and an Adam launch per batch -- is captured
+  // as a CUDA graph and replayed once per epoch: the launches run back to back
+  // with no host in between.  The step size and bias corrections of each step
+  // follow from the device step counter (AdamSched), so every epoch replays
+  // the same graph.
+  const AdamSched sch{1, lr, (float)(std::log2((double)lr_final / (double)lr) / (double)std::max<size_t>(total - 1, 1)),
+                      s->step, (float)std::log2(0.9), (float)std::log2(0.999)};
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail();
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  rc = AICDF_OK;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    rc = AICDF_ERR_CUDA;
+  } else {
+    for (size_t b = 0; b < steps_per_epoch; ++b) {
+      k_mlp_train<<<blocks, kTrainThreads, kTrainSmem, cap>>>(s->params, s->w2c, u_dev, lam_dev, target_dev,
+                                                          b * batch, batch, 1.0f / (float)batch, s->partial,
+                                                          (float)s->nu, s->d_step);
+      k_mlp_adam<<<(kOffB3 + kAdamThreads) / kAdamThreads, kAdamThreads, 0, cap>>>(
+          s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, 0.9f, 0.999f, 1e-8f, 1.f, 1.f,
+          b + 1 == steps_per_epoch ? loss_dev : nullptr, 1.0f / (float)batch, s->d_step, sch);
     }
-  return AICDF_OK;
+    if (cudaStreamEndCapture(cap, &g) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = AICDF_ERR_CUDA;
+  }
+  if (rc == AICDF_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) rc = AICDF_ERR_CUDA;
+  for (int e = 0; e < epochs && rc == AICDF_OK; ++e)
+    if (cudaGraphLaunch(exec, (cudaStream_t)stream) != cudaSuccess) rc = AICDF_ERR_CUDA;
+  if (rc != AICDF_OK) set_cuda_error((int)cudaGetLastError());
+  // the launches are queued on the caller's stream; the graph may go once they are
+  if (exec) cudaGraphExecDestroy(exec);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (rc == AICDF_OK) s->step += (long long)total;
+  return rc;
 }
 
 extern "C" aicdf_status aicdf_ncx2_targets(double nu, float loglam_lo, float loglam_hi, uint64_t seed,

@@ -1,5 +1,14 @@
-// Small MLP surrogate y = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3  (2 -> 64 -> 64 -> 1)
-// for the rescaled non-central chi-squared quantile P_nu(U; y) of Section 5.1.
+// Small MLP N(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3  (2 -> 64 -> 64 -> 1)
+// behind the surrogate of the rescaled non-central chi-squared quantile
+// P_nu(U; y) of Section 5.1, y = nu / (lambda + nu):
+//   P~(U; y) = Phi^{-1}(U) + sqrt(y) N(s(U) / 3, 2 sqrt(y) - 1).
+// P tends to Phi^{-1}(U) as y -> 0 with P - Phi^{-1} = O(sqrt(y)) (Section 5.1,
+// where the tables' knots are equally spaced in sqrt(y)), so the network learns
+// the bounded correction (P - Phi^{-1}) / sqrt(y) over the whole range 0 < y <= 1
+// (lambda from 0 to infinity) with no clamp.  A CIR step X' = c (h + 2 sqrt(h) P~)
+// with h = lambda + nu then carries the network's error as 2 c sqrt(nu) dN, the
+// same at every lambda, so the training loss is the plain mean square of N - g,
+// g = (P - Phi^{-1}(U)) / sqrt(y).
 //
 // One warp evaluates 32 samples (lane = sample).  Layers 1 and 3 and the
 // activations run on the FP32 pipes; the 64 x 64 layer runs on the tensor
@@ -39,16 +48,15 @@ __device__ __forceinline__ float tanh_fast(float x) {
 }
 
 // Input features: x0 = s(u)/3 with the tail stretch s(u) = sign(u - 1/2)
-// sqrt(-2 ln(2 min(u, 1-u))) (smooth, monotone, s(1/2) = 0), x1 = ln(lambda)/4
-// clamped to the trained range [-1, 1].
+// sqrt(-2 ln(2 min(u, 1-u))) (smooth, monotone, s(1/2) = 0), and x1 = 2 sqrt(y) - 1
+// from sqrt(y) = sqrt(nu / (max(lambda, 0) + nu)) in (0, 1].
 __device__ __forceinline__ float mlp_feature_u(float u) {
   const float v = fminf(u, 1.0f - u);
   const float s = sqrtf(fmaxf(-2.0f * __logf(2.0f * v), 0.0f));
   return (u < 0.5f ? -s : s) * (1.0f / 3.0f);
 }
-__device__ __forceinline__ float mlp_feature_lam(float lam) {
-  return fminf(fmaxf(__logf(fmaxf(lam, 1e-30f)) * 0.25f, -1.0f), 1.0f);
-}
+__device__ __forceinline__ float mlp_sqrt_y(float lam, float nu) { return sqrtf(nu / (fmaxf(lam, 0.0f) + nu)); }
+__device__ __forceinline__ float mlp_feature_y(float sy) { return fmaf(2.0f, sy, -1.0f); }
 
 // Stage FP32 parameters (global) into shared memory; W2 rounded to BF16.
 __device__ __forceinline__ void mlp_stage(const float *__restrict__ p, MlpSmem &s) {
@@ -181,7 +189,7 @@ __device__ __forceinline__ float mlp_gather_output(const MlpSmem &s, float (&par
   return v + s.b3;
 }
 
-// Full forward for the warp: lane's sample (x0, x1) -> output.  hs: this
+// Full forward for the warp: lane's sample (x0, x1) -> N(x0, x1).  hs: this
 // warp's [32][kHPad] BF16 tile in shared memory.  All 32 lanes must call.
 __device__ __forceinline__ float mlp_forward_warp(const MlpSmem &s, float x0, float x1, __nv_bfloat16 *hs) {
   mlp_layer1(s, x0, x1, hs);

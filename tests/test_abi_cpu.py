@@ -220,3 +220,19 @@ def test_ncx2_tables_build_across_nu(P, orc):
         assert t.info()[0] == nu
     c = P.Ncx2Table(100.0, 16, 16, 1).coefficients()
     assert abs(orc.ncx2_poly_rmse(c, 100.0, 100.0) - 0.161) <= 0.0006
+
+
+def test_surrogate_load_rejects_bad_files(P, tmp_path):
+    """aicdf_surrogate_load refuses a missing file, a foreign file and a
+    truncated one before it creates anything (no device needed)."""
+    L = P.lib()
+    h = C.c_void_p()
+    assert L.aicdf_surrogate_load(os.fsencode(str(tmp_path / "none.bin")), C.byref(h)) == P.ERR_ARG
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a surrogate file at all")
+    assert L.aicdf_surrogate_load(os.fsencode(str(bad)), C.byref(h)) == P.ERR_ARG
+    short = tmp_path / "short.bin"
+    short.write_bytes(b"AICDFSG1" + np.float64(0.889).tobytes() + np.int32(4417).tobytes() + b"\0" * 100)
+    assert L.aicdf_surrogate_load(os.fsencode(str(short)), C.byref(h)) == P.ERR_ARG
+    assert not h.value
+    assert L.aicdf_surrogate_save(None, os.fsencode(str(bad))) == P.ERR_ARG

@@ -76,12 +76,22 @@ def test_ncx2_targets_match_oracle(P, orc):
         assert abs(ph[i] - ref) <= 1e-5 * (1 + abs(ref)), (i, ph[i], ref)
 
 
-def _features(u, lam):
+def _sqrt_y(lam, nu=NU_CFG):
+    return np.sqrt(nu / (np.maximum(lam, 0.0) + nu))
+
+
+def _features(u, lam, nu=NU_CFG):
+    """The network's inputs as aicdf.h defines them: s(u)/3 and 2 sqrt(y) - 1."""
     v = np.minimum(u, 1 - u)
     s = np.sqrt(np.maximum(-2 * np.log(2 * v), 0.0))
     x0 = np.where(u < 0.5, -s, s) / 3.0
-    x1 = np.clip(np.log(np.maximum(lam, 1e-30)) / 4.0, -1, 1)
+    x1 = 2 * _sqrt_y(lam, nu) - 1
     return np.stack([x0, x1], axis=1)
+
+
+def _compose(orc, u, lam, nn, nu=NU_CFG):
+    """P~ = Phi^{-1}(u) + sqrt(y) N from the network output N (oracle Phi^{-1})."""
+    return orc.phiinv(np.asarray(u, dtype=np.float32)) + _sqrt_y(lam, nu) * nn
 
 
 def _random_params(rng):
@@ -113,9 +123,13 @@ def test_mlp_forward_matches_oracle(P, orc):
     out = torch.zeros(n, device="cuda")
     s.eval(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), out)
     got = out.cpu().numpy().astype(np.float64)
-    ref = orc.mlp_forward(_oracle_params(p), _features(u.astype(np.float64), lam.astype(np.float64)))
+    nn = orc.mlp_forward(_oracle_params(p), _features(u.astype(np.float64), lam.astype(np.float64)))
+    ref = _compose(orc, u, lam.astype(np.float64), nn)
+    z = orc.phiinv(u)
+    # the network's error scaled by sqrt(y), and the FP32 inverse's 1e-6 relative
+    sy = _sqrt_y(lam.astype(np.float64))
     err = np.abs(got - ref)
-    assert np.all(err <= 0.03 + 0.01 * np.abs(ref)), err.max()
+    assert np.all(err <= sy * (0.03 + 0.01 * np.abs(nn)) + 2e-6 * np.abs(z) + 1e-6), err.max()
     assert math.sqrt(np.mean(err ** 2)) <= 0.01
 
 
@@ -132,8 +146,9 @@ def test_mlp_gradient_matches_oracle(P, orc):
     g = torch.zeros(4418, device="cuda")
     s.grad(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), torch.from_numpy(tgt).cuda(), g)
     got = g.cpu().numpy().astype(np.float64)
-    loss, ref = orc.mlp_grad(_oracle_params(p), _features(u.astype(np.float64), lam.astype(np.float64)),
-                             tgt.astype(np.float64))
+    # the network's own target g = (P - Phi^{-1}(u)) / sqrt(y) for the P targets given
+    gt = (tgt.astype(np.float64) - orc.phiinv(u)) / _sqrt_y(lam.astype(np.float64))
+    loss, ref = orc.mlp_grad(_oracle_params(p), _features(u.astype(np.float64), lam.astype(np.float64)), gt)
     assert got[4417] / n == pytest.approx(loss, rel=0.05)
     offs = {"W1": (0, 128), "b1": (128, 192), "W2": (192, 4288), "b2": (4288, 4352), "w3": (4352, 4416),
             "b3": (4416, 4417)}
@@ -154,7 +169,7 @@ def trained(P):
     lam = torch.empty(n, device="cuda")
     p = torch.empty(n, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    P.ncx2_targets(NU_CFG, n, u, lam, p, st, seed=11, tag=1)
+    P.ncx2_targets(NU_CFG, n, u, lam, p, st, seed=11, tag=1, loglam_lo=-6.0, loglam_hi=7.0)
     s = P.Surrogate(NU_CFG, seed=3)
     loss = torch.zeros(1, device="cuda")
     s.train(u, lam, p, batch=8192, epochs=48, lr=3e-3, lr_final=3e-5, loss=loss)
@@ -187,8 +202,8 @@ def test_training_beats_the_gaussian_limit(P, trained):
     sel = np.log(lam.cpu().numpy()) > 2.0
     reg = (math.sqrt(np.mean(e_mlp[sel] ** 2)), math.sqrt(np.mean(e_gauss[sel] ** 2)))
     assert math.isfinite(last_loss) and last_loss < 0.01, last_loss
-    assert rmse_mlp < rmse_gauss / 4, (rmse_mlp, rmse_gauss, reg)
-    assert reg[0] < reg[1] / 2, (rmse_mlp, rmse_gauss, reg)
+    assert rmse_mlp < rmse_gauss / 20, (rmse_mlp, rmse_gauss, reg)
+    assert reg[0] < reg[1] / 10, (rmse_mlp, rmse_gauss, reg)
 
 
 def test_cir_exact_mean_and_surrogate_gain(P, trained):
@@ -278,5 +293,176 @@ def test_eval_ragged_tiles(P, orc, n):
     assert np.all(np.isinf(got[n:]))
     assert np.all(np.isfinite(got[:n]))
     idx = np.unique(np.concatenate([np.arange(min(n, 300)), rng.integers(0, n, 200), [n - 1]]))
-    ref = orc.mlp_forward(_oracle_params(p), _features(u[idx].astype(np.float64), lam[idx].astype(np.float64)))
-    assert np.all(np.abs(got[idx] - ref) <= 0.03 + 0.01 * np.abs(ref))
+    nn = orc.mlp_forward(_oracle_params(p), _features(u[idx].astype(np.float64), lam[idx].astype(np.float64)))
+    ref = _compose(orc, u[idx], lam[idx].astype(np.float64), nn)
+    sy = _sqrt_y(lam[idx].astype(np.float64))
+    assert np.all(np.abs(got[idx] - ref) <= sy * (0.03 + 0.01 * np.abs(nn)) + 2e-6 * np.abs(ref) + 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Learned CIR paths step by step against the oracle's network (Section 5.2)
+R_TANH, R_BF16 = 2.0 ** -10.9, 2.0 ** -9                 # tanh.approx.f32 relative error; BF16 rounding
+
+
+def _plumbing_params(rng):
+    """Weights for the path test: the inputs move P~ by O(0.3) through the
+    64 x 64 layer, whose small weights keep the GPU's BF16 / tanh.approx
+    error -- the bound below -- near 1e-3."""
+    p = np.zeros(4417, dtype=np.float32)
+    p[0:128] = rng.uniform(-1.5, 1.5, 128)
+    p[128:192] = rng.uniform(-0.5, 0.5, 64)
+    p[192:4288] = rng.uniform(-0.05, 0.05, 4096)
+    p[4288:4352] = rng.uniform(-0.3, 0.3, 64)
+    p[4352:4416] = rng.uniform(-0.5, 0.5, 64)
+    p[4416] = 0.1
+    return p
+
+
+def _net_layers(q, x0, x1):
+    """The network in FP64 (W2 BF16-rounded as the GPU keeps it): output, the
+    layer activations, and dy/dx0, dy/dx1 -- used for the error bound only;
+    the path emulation takes its P~ from the oracle's mlp_forward."""
+    a1 = q["W1"] @ np.array([x0, x1]) + q["b1"]
+    t1 = np.tanh(a1)
+    z2 = q["W2"] @ t1 + q["b2"]
+    h2 = np.tanh(z2)
+    y = float(q["w3"] @ h2 + q["b3"][0])
+    g = (q["w3"] * (1 - h2 ** 2)) @ q["W2"] * (1 - t1 ** 2)   # dy/da1
+    return y, t1, h2, float(g @ q["W1"][:, 0]), float(g @ q["W1"][:, 1])
+
+
+def _net_error_bound(q, t1, h2, dydx0, dydx1, s):
+    """Error of the GPU's P~ against the FP64 network at one evaluation, as
+    (sd, wc).  sd: the rounding errors of the GPU network -- layer-1
+    activations from tanh.approx (relative 2^-10.9) rounded to BF16 (2^-9),
+    tanh.approx again after the 64 x 64 product -- taken as independent and
+    uniform within their bounds and propagated linearly (standard deviation).
+    wc: worst-case terms -- FP32 accumulation, and the inputs' FP32 error: the
+    feature sqrt(-2 ln 2v) takes __logf (absolute error ~2^-21 near 1), which
+    moves s by min(dL / s, sqrt(2 dL))."""
+    var_h1 = (R_BF16 ** 2 + R_TANH ** 2) / 3.0 * t1 ** 2
+    var_z2 = (q["W2"] ** 2) @ var_h1
+    var_h2 = (1 - h2 ** 2) ** 2 * var_z2 + R_TANH ** 2 / 3.0 * h2 ** 2
+    sd = math.sqrt(float((q["w3"] ** 2) @ var_h2))
+    dL = 2.0 ** -21
+    ds = min(dL / s, math.sqrt(2 * dL)) if s > 0 else math.sqrt(2 * dL)
+    wc = (2.0 ** -18 * float(np.abs(q["w3"]) @ (np.abs(q["W2"]) @ np.abs(t1))) +
+          2.0 ** -20 * (float(np.abs(q["w3"]) @ np.abs(h2)) + abs(float(q["b3"][0]))) +
+          abs(dydx0) * (ds / 3 + 1e-7) + abs(dydx1) * 2.0 ** -21)
+    return sd, wc
+
+
+def _surrogate_step(orc, qd, nu, cc, e, u, x, feature_power=0.5):
+    """One learned transition as aicdf.h defines it: lambda = max(X, 0) e / c,
+    sqrt(y) = sqrt(nu / (lambda + nu)), features (s(u)/3, 2 sqrt(y) - 1), N from
+    the oracle network, P~ = Phi^{-1}(u) + sqrt(y) N, X' = c max(h + 2 sqrt(h) P~,
+    0).  Returns X' and the (sd, worst-case) parts of its error from this
+    evaluation.  feature_power != 1/2 plants a wrong input (y^p for sqrt(y))."""
+    lam = max(x, 0.0) * e / cc
+    sy = math.sqrt(nu / (lam + nu))
+    v = min(u, 1.0 - u)
+    s = math.sqrt(max(-2.0 * math.log(2.0 * v), 0.0))
+    x0 = (-s if u < 0.5 else s) / 3.0
+    x1 = 2.0 * (nu / (lam + nu)) ** feature_power - 1.0
+    nn = float(orc.mlp_forward(qd, np.array([[x0, x1]]))[0])
+    y, t1, h2, d0, d1 = _net_layers(qd, x0, x1)
+    assert abs(y - nn) <= 1e-12 * (1 + abs(nn))          # the bound describes the oracle's own network
+    sd, wc = _net_error_bound(qd, t1, h2, d0, d1, s)
+    z = orc.phiinv_f64(u)
+    pt = z + sy * nn
+    sd, wc = sy * sd, sy * (wc + abs(d1) * 1e-6) + 2e-6 * abs(z)   # FP32 sqrt(y); the FP32 inverse, 1e-6 rel.
+    h = lam + nu
+    k = 2.0 * cc * math.sqrt(h)
+    return cc * max(h + 2.0 * math.sqrt(h) * pt, 0.0), k * sd, k * wc
+
+
+def _emulate_surrogate_path(orc, qd, prm_q, level, p, seed, tag, feature_power=0.5):
+    """Exact and learned CIR path of 2^level steps from the same uniforms, with
+    the error of the learned one carried along: sd' = sqrt((L sd)^2 + sd_new^2)
+    and wc' = L wc + wc_new + FP32 rounding of the step, L the step map's
+    sensitivity to X (central difference of the FP64 map at the same u).
+    Returns X^_T, X~_T and the band 6 sd + 1.5 wc."""
+    q = prm_q
+    nu = 4 * q["kappa"] * q["theta"] / q["sigma"] ** 2
+    hstep = q["T"] / 2 ** level
+    e = math.exp(-q["kappa"] * hstep)
+    cc = q["sigma"] ** 2 * (-math.expm1(-q["kappa"] * hstep)) / (4 * q["kappa"])
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    xe = q["X0"]
+    xa = float(np.float32(q["X0"]))
+    sd = wc = 0.0
+    for s in range(2 ** level):
+        w = int(orc.philox4([s // 4, p & 0xFFFFFFFF, p >> 32, tag], key, 32)[s % 4])
+        u = orc.u01(w)
+        lam_e = xe * e / cc
+        xe = cc * (orc.ncx2_ppf(u, nu, lam_e) if u <= 0.5 else orc.ncx2_isf(1.0 - u, nu, lam_e))
+        xn, sd_new, wc_new = _surrogate_step(orc, qd, nu, cc, e, u, xa, feature_power)
+        d = max(1e-9, 1e-4 * abs(xa))
+        lo = max(xa - d, 0.0)
+        L = abs(_surrogate_step(orc, qd, nu, cc, e, u, xa + d, feature_power)[0] -
+                _surrogate_step(orc, qd, nu, cc, e, u, lo, feature_power)[0]) / (xa + d - lo)
+        sd = math.sqrt((L * sd) ** 2 + sd_new ** 2)
+        wc = L * wc + wc_new + 8 * 2.0 ** -24 * (abs(xn) + cc * (nu + max(xa, 0) * e / cc))
+        xa = xn
+    return xe, xa, 6 * sd + 1.5 * wc + 1e-9
+
+
+@pytest.mark.parametrize("level", [0, 2, 4, 6])
+def test_cir_surrogate_paths_match_oracle_network(P, orc, level):
+    """aicdf_cir_level SURROGATE and DIFF paths, one at a time, against the
+    step-by-step restatement above with the oracle's FP64 network (BF16 W2),
+    at the CIR configuration (nu = 0.889), levels 0..6 (lambda from near 0 at
+    X0 = 0.0005 to ~e^6 at level 6 from X0 = 0.3).  The emulation with a wrong
+    input (y for sqrt(y)) is checked to fall outside the tolerance, so the band
+    is tight enough to see such a mistake."""
+    import torch
+    rng = np.random.default_rng(17)
+    params = _plumbing_params(rng)
+    qd = _oracle_params(params)
+    s = P.Surrogate(NU_CFG, seed=0)
+    s.set_params(params)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    seed, tag = 9, 4
+    caught = 0
+    for X0 in (0.04, 0.0005, 0.3):
+        q = dict(kappa=0.5, theta=0.04, sigma=0.3, X0=X0, T=1.0)
+        prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=X0, T=1.0, K=0.0, mu=0.0, sigma=0.3,
+                           kappa=0.5, theta=0.04, discount=1.0)
+        for p in ((0, 5, 77777) if level < 6 else (3,)):
+            xe, xa, band = _emulate_surrogate_path(orc, qd, q, level, p, seed, tag)
+            got = {}
+            for kind in (P.CIR_EXACT, P.CIR_SURROGATE, P.CIR_DIFF):
+                P.cir_level(prm, s, level, kind, 1, sums, ws, st, path_offset=p, seed=seed, tag=tag)
+                got[kind] = sums[0].item()
+            assert st.item() == 0
+            assert band <= 0.02 * (abs(xa) + 0.04), (level, X0, p, band, xa)   # well inside the scale of X
+            assert got[P.CIR_EXACT] == pytest.approx(xe, rel=1e-6, abs=1e-12)
+            assert abs(got[P.CIR_SURROGATE] - xa) <= band, (level, X0, p, got[P.CIR_SURROGATE], xa, band)
+            assert abs(got[P.CIR_DIFF] - (xe - xa)) <= band + 1e-6 * abs(xe), (level, X0, p)
+            # the same path with y fed for sqrt(y) (a plausible slip) leaves the band
+            _, xb, _ = _emulate_surrogate_path(orc, qd, q, level, p, seed, tag, feature_power=1.0)
+            caught += abs(xb - xa) > 3 * band
+    assert caught >= 3, caught
+
+
+def test_save_and_load_round_trip(P, orc, tmp_path):
+    """aicdf_surrogate_save / _load: the loaded handle has the same nu and
+    weights and evaluates to the same bits."""
+    import torch
+    rng = np.random.default_rng(23)
+    s = P.Surrogate(NU_CFG, seed=0)
+    s.set_params(_random_params(rng))
+    path = str(tmp_path / "sur.bin")
+    s.save(path)
+    t = P.Surrogate.load(path)
+    assert t.nu == NU_CFG
+    assert np.array_equal(s.get_params(), t.get_params())
+    n = 4096
+    u = torch.from_numpy(orc.uniforms(3, 0, n)).cuda()
+    lam = torch.from_numpy(np.exp(rng.uniform(-6, 7, n)).astype(np.float32)).cuda()
+    a, b = torch.zeros(n, device="cuda"), torch.ones(n, device="cuda")
+    s.eval(u, lam, a)
+    t.eval(u, lam, b)
+    assert torch.equal(a, b)
