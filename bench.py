@@ -624,6 +624,7 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     L_max = 12
     nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=L_max, n_pilot=2000)
     regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=L_max, n_pilot=2000)
+    adaptive = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_ADAPTIVE, seed=6, L_max=L_max, n_pilot=2000)
     Lp = max(r.L for r in nested[:n_plain])
     plain = P.mlmc_run_sets(sets[:n_plain], tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=Lp, seed=3)
     res["L_max"] = L_max
@@ -644,8 +645,11 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
                                               default=0.0)
         return out
 
-    for name, rr in (("nested", nested), ("regular", regular), ("plain_exact_subset", plain)):
+    for name, rr in (("nested", nested), ("regular", regular), ("adaptive", adaptive), ("plain_exact_subset", plain)):
         res[name] = summary(rr)
+    res["adaptive"]["exact_levels"] = sum(sum(r.exact_level[l] for l in range(r.L + 1)) for r in adaptive)
+    res["adaptive"]["nested_levels"] = sum(sum(1 - r.exact_level[l] for l in range(r.L + 1)) for r in adaptive)
+    res["speedup_adaptive_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / adaptive[0].gpu_ms
     # where the nested estimator's work goes: per level, the median over sets of
     # log2 Var(four-way) / Var(two-way), and the per-step costs of the kinds
     import math as _m
@@ -668,10 +672,11 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
         wss = torch.empty(P.mlmc_run_sets_workspace_bytes(len(ss)), dtype=torch.uint8, device=dev)
         n16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_NESTED, seed=4, L_max=L_max + 4, n_pilot=2000)
         r16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_REGULAR, seed=5, L_max=L_max + 4, n_pilot=2000)
+        a16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_ADAPTIVE, seed=9, L_max=L_max + 4, n_pilot=2000)
         feller = sorted(2 * sw["kappa"][i] * sw["theta"][i] / sw["sigma"][i] ** 2 for i in slow)
         res["slow_class"] = {"sets": len(slow), "feller_ratio_median": feller[len(feller) // 2],
                              "feller_ratio_max": feller[-1], "L_max": L_max + 4,
-                             "nested": summary(n16), "regular": summary(r16)}
+                             "nested": summary(n16), "regular": summary(r16), "adaptive": summary(a16)}
     res["plain_exact_fixed_L"] = Lp
     plain_all_ms = plain[0].gpu_ms * n_sets / n_plain
     res["plain_exact_gpu_ms_scaled"] = plain_all_ms
@@ -694,9 +699,10 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     res = {}
     nested = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_NESTED, seed=1)
     regular = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_REGULAR, seed=2)
+    adaptive = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_ADAPTIVE, seed=1)
     L = nested.L
     plain = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=L, seed=3)
-    for name, r in (("nested", nested), ("regular", regular), ("plain_exact", plain)):
+    for name, r in (("nested", nested), ("regular", regular), ("adaptive", adaptive), ("plain_exact", plain)):
         # fine path-steps per term slot (slot 0: APPROX2 / EXACT2 / PLAIN, slot 1: CORR4)
         steps = [sum(r.paths[l][k] * ((1 << l) + 1 if l > 0 else 1) for l in range(r.L + 1)) for k in range(2)]
         res[name] = {"estimate": r.estimate, "rmse_est": (r.variance + r.bias ** 2) ** 0.5,

@@ -472,7 +472,12 @@ aicdf_status aicdf_cir_level_table(const aicdf_sde_params *params, aicdf_ncx2_ta
 typedef enum {
   AICDF_EST_NESTED = 0,   /* theta~ : per level APPROX2 + CORR4 terms (independent streams) */
   AICDF_EST_REGULAR = 1,  /* theta^ : per level EXACT2 terms                              */
-  AICDF_EST_PLAIN = 2     /* plain Monte Carlo with exact variates at the finest level     */
+  AICDF_EST_PLAIN = 2,    /* plain Monte Carlo with exact variates at the finest level     */
+  AICDF_EST_ADAPTIVE = 3  /* per level the cheaper of the nested pair and an EXACT2 term:
+                             the pair is piloted; where (sqrt(V2 c2) + sqrt(V4 c4))^2 >
+                             V2 c_exact2 (Section 4.1's cost model) it is dropped and an
+                             EXACT2 term on its own stream replaces it (a library
+                             extension of the paper's nested estimator)                 */
 } aicdf_estimator;
 
 #define AICDF_MAX_LEVELS 24
@@ -508,10 +513,13 @@ typedef struct {
   double var[AICDF_MAX_LEVELS][2];
   double kurt[AICDF_MAX_LEVELS][2];     /* kurtosis E(Y-EY)^4 / Var(Y)^2 of the term          */
   double cost_ns[AICDF_MAX_LEVELS][2];  /* measured device ns per path                     */
+  int exact_level[AICDF_MAX_LEVELS];    /* AICDF_EST_ADAPTIVE: 1 where level l uses an EXACT2
+                                           term (slot 0) in place of the nested pair         */
 } aicdf_mlmc_result;
 
 /* Run one estimator to RMSE opts->eps.  Each term draws uniforms from its own
- * Philox stream (tag = 1 + 64*estimator + 2*l + t), extending the stream with
+ * Philox stream (tag = 1 + 64*estimator + 2*l + t; an adaptive estimator's
+ * EXACT2 replacement at level l: 1 + 64*estimator + 42 + l), extending the stream with
  * path_offset as more paths are added, so the result is reproducible from the
  * seed.  Path counts follow the optimal allocation of Section 4.1 from the
  * measured variances and per-path device times.  A term whose share f of

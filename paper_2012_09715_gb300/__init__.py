@@ -48,7 +48,7 @@ class SdeParams(C.Structure):
                 ("discount", C.c_double)]
 
 
-EST_NESTED, EST_REGULAR, EST_PLAIN = 0, 1, 2
+EST_NESTED, EST_REGULAR, EST_PLAIN, EST_ADAPTIVE = 0, 1, 2, 3
 MAX_LEVELS = 24
 
 
@@ -64,7 +64,7 @@ class MlmcResult(C.Structure):
                 ("converged", C.c_int), ("n_terms", C.c_int), ("launches", C.c_int),
                 ("paths", (C.c_uint64 * 2) * MAX_LEVELS), ("mean", (C.c_double * 2) * MAX_LEVELS),
                 ("var", (C.c_double * 2) * MAX_LEVELS), ("kurt", (C.c_double * 2) * MAX_LEVELS),
-                ("cost_ns", (C.c_double * 2) * MAX_LEVELS)]
+                ("cost_ns", (C.c_double * 2) * MAX_LEVELS), ("exact_level", C.c_int * MAX_LEVELS)]
 
     def as_dict(self):
         L, t = self.L, self.n_terms
@@ -74,7 +74,7 @@ class MlmcResult(C.Structure):
                 "launches": self.launches,
                 "levels": [{"l": l, "paths": list(self.paths[l])[:t], "mean": list(self.mean[l])[:t],
                             "var": list(self.var[l])[:t], "kurt": list(self.kurt[l])[:t],
-                            "cost_ns": list(self.cost_ns[l])[:t]}
+                            "cost_ns": list(self.cost_ns[l])[:t], "exact_level": bool(self.exact_level[l])}
                            for l in lv]}
 
 

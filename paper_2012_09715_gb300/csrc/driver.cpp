@@ -25,6 +25,7 @@ namespace {
 
 struct Term {
   int level = 0, kind = 0, slot = 0;
+  bool active = true;  // false: a nested pair the adaptive estimator replaced by an exact term
   uint32_t tag = 0;
   uint64_t n = 0;
   double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
@@ -83,6 +84,22 @@ std::vector<double> variance_shares(const std::vector<double> &v, const std::vec
       if (m[i] > 0.0) f[i] = v[i] / m[i] / tot;
   return f;
 }
+
+// The adaptive estimator (Section 4.1's cost model applied per level): the
+// nested pair of level l -- the approximate two-way term (variance V2, cost
+// c2 per path) and the four-way correction (V4, c4) -- needs total work
+// (sqrt(V2 c2) + sqrt(V4 c4))^2 / eps'^2 for a given variance share, the exact
+// two-way term about V2 ce / eps'^2 (its variance is the approximate one's up
+// to the approximation error).  The pair stays where it is cheaper.
+bool nested_pays(const Term &t2, const Term &t4, double c2, double c4, double ce) {
+  const double v2 = t2.var(), v4 = t4.var();
+  const double nested = std::sqrt(v2 * c2) + std::sqrt(v4 * c4);
+  return nested * nested <= v2 * ce;
+}
+
+// Philox stream of the exact term that replaces level l's nested pair (tags
+// 1 + 64 est + 2 l + t are the pairs'; these follow them, below 256).
+uint32_t exact_level_tag(int est, int l) { return 1u + 64u * (uint32_t)est + 42u + (uint32_t)l; }
 
 // Pilot paths of a new multilevel term at level l: n at levels <= L_min,
 // halved for each level above (at least 128).  The optimal counts of level
@@ -171,7 +188,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
   if (!(o->eps > 0.0) || o->L_min < 0 || o->L_max < o->L_min || o->L_max >= AICDF_MAX_LEVELS ||
       o->L_max > 20 || o->fixed_L >= AICDF_MAX_LEVELS || o->fixed_L > 20)
     return AICDF_ERR_ARG;
-  if (o->estimator < AICDF_EST_NESTED || o->estimator > AICDF_EST_PLAIN) return AICDF_ERR_ARG;
+  if (o->estimator < AICDF_EST_NESTED || o->estimator > AICDF_EST_ADAPTIVE) return AICDF_ERR_ARG;
   if (o->estimator == AICDF_EST_PLAIN && o->fixed_L < 0) return AICDF_ERR_ARG;
   if (workspace_bytes < aicdf_mlmc_run_workspace_bytes() || ((uintptr_t)workspace_dev % 256))
     return AICDF_ERR_ARG;
@@ -187,11 +204,13 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
 
   const int est = o->estimator;
   std::vector<int> kinds;
-  if (est == AICDF_EST_NESTED) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
+  if (est == AICDF_EST_NESTED || est == AICDF_EST_ADAPTIVE) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
   else if (est == AICDF_EST_REGULAR) kinds = {AICDF_KIND_EXACT2};
   else kinds = {AICDF_KIND_PLAIN};
+  std::vector<int> cal = kinds;
+  if (est == AICDF_EST_ADAPTIVE) cal.push_back(AICDF_KIND_EXACT2);
   double kind_ns[5] = {0, 0, 0, 0, 0};
-  for (int k : kinds) {
+  for (int k : cal) {
     aicdf_status s = step_cost_ns(params, approx, k, w, lvl_ws, cal_sums, st, &kind_ns[k]);
     if (s != AICDF_OK) return s;
   }
@@ -256,7 +275,26 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     std::vector<uint64_t> add(terms.size(), 0);
     for (size_t i = first; i < terms.size(); ++i)
       add[i] = level_pilot(terms[i].kind == AICDF_KIND_CORR4 ? pilot4 : pilot, terms[i].level, o->L_min, est);
-    return run_round(add);
+    aicdf_status rs = run_round(add);
+    if (rs != AICDF_OK || est != AICDF_EST_ADAPTIVE) return rs;
+    // adaptive: the new levels whose nested pair does not pay get an exact term
+    const size_t last = terms.size();
+    for (size_t i = first; i + 1 < last; i += 2) {
+      Term &t2 = terms[i], &t4 = terms[i + 1];
+      if (nested_pays(t2, t4, cost(t2), cost(t4), kind_ns[AICDF_KIND_EXACT2] * (double)((1u << t2.level) + 1)))
+        continue;
+      t2.active = t4.active = false;
+      Term t;
+      t.level = t2.level;
+      t.kind = AICDF_KIND_EXACT2;
+      t.slot = 0;
+      t.tag = exact_level_tag(est, t2.level);
+      terms.push_back(t);
+    }
+    if (terms.size() == last) return AICDF_OK;
+    std::vector<uint64_t> add2(terms.size(), 0);
+    for (size_t i = last; i < terms.size(); ++i) add2[i] = level_pilot(pilot, terms[i].level, o->L_min, est);
+    return run_round(add2);
   };
 
   aicdf_status s = AICDF_OK;
@@ -275,7 +313,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     // optimal counts for the current terms (Section 4.1)
     std::vector<double> v, c, m(terms.size());
     for (auto &t : terms) {
-      v.push_back(t.var());
+      v.push_back(t.active ? t.var() : 0.0);  // a replaced pair gets no more paths
       c.push_back(cost(t));
     }
     double total = 0.0;
@@ -302,7 +340,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     auto level_mean = [&](int l) {
       double mm = 0.0;
       for (auto &t : terms)
-        if (t.level == l) mm += t.mean();
+        if (t.level == l && t.active) mm += t.mean();
       return mm;
     };
     const double a2 = std::pow(2.0, alpha);
@@ -328,6 +366,7 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
   if (s != AICDF_OK) return s;
   double estv = 0.0, var = 0.0;
   for (auto &t : terms) {
+    if (!t.active) continue;
     estv += t.mean();
     var += t.n ? t.var() / (double)t.n : 0.0;
     r->paths[t.level][t.slot] = t.n;
@@ -335,12 +374,13 @@ extern "C" aicdf_status aicdf_mlmc_run(const aicdf_sde_params *params, aicdf_tab
     r->var[t.level][t.slot] = t.var();
     r->kurt[t.level][t.slot] = t.kurt();
     r->cost_ns[t.level][t.slot] = cost(t);
+    if (t.kind == AICDF_KIND_EXACT2 && est == AICDF_EST_ADAPTIVE) r->exact_level[t.level] = 1;
   }
   r->estimate = estv;
   r->variance = var;
   r->L = L;
   r->converged = converged ? 1 : 0;
-  r->n_terms = est == AICDF_EST_NESTED ? 2 : 1;
+  r->n_terms = (est == AICDF_EST_NESTED || est == AICDF_EST_ADAPTIVE) ? 2 : 1;
   r->gpu_ms = gpu_ms;
   r->launches = launches;
   r->wall_ms =
@@ -375,7 +415,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
   if (!(o->eps > 0.0) || o->L_min < 0 || o->L_max < o->L_min || o->L_max >= AICDF_MAX_LEVELS ||
       o->L_max > 20 || o->fixed_L >= AICDF_MAX_LEVELS || o->fixed_L > 20)
     return AICDF_ERR_ARG;
-  if (o->estimator < AICDF_EST_NESTED || o->estimator > AICDF_EST_PLAIN) return AICDF_ERR_ARG;
+  if (o->estimator < AICDF_EST_NESTED || o->estimator > AICDF_EST_ADAPTIVE) return AICDF_ERR_ARG;
   if (o->estimator == AICDF_EST_PLAIN && o->fixed_L < 0) return AICDF_ERR_ARG;
   if (workspace_bytes < aicdf_mlmc_run_sets_workspace_bytes(n_sets) || ((uintptr_t)workspace_dev % 256))
     return AICDF_ERR_ARG;
@@ -390,16 +430,18 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
 
   const int est = o->estimator;
   std::vector<int> kinds;
-  if (est == AICDF_EST_NESTED) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
+  if (est == AICDF_EST_NESTED || est == AICDF_EST_ADAPTIVE) kinds = {AICDF_KIND_APPROX2, AICDF_KIND_CORR4};
   else if (est == AICDF_EST_REGULAR) kinds = {AICDF_KIND_EXACT2};
   else kinds = {AICDF_KIND_PLAIN};
+  std::vector<int> cal = kinds;
+  if (est == AICDF_EST_ADAPTIVE) cal.push_back(AICDF_KIND_EXACT2);
   // calibrated per-step costs, per (model, scheme) of the sets (cached per process)
   std::map<std::pair<int, int>, std::vector<double>> kind_ns;
   for (int s = 0; s < n_sets; ++s) {
     const auto key = std::make_pair(sets[s].model, sets[s].scheme);
     if (kind_ns.count(key)) continue;
     std::vector<double> ns(5, 0.0);
-    for (int k : kinds) {
+    for (int k : cal) {
       aicdf_status rc = step_cost_ns(&sets[s], approx, k, w, lvl_ws, cal_sums, st, &ns[k]);
       if (rc != AICDF_OK) return rc;
     }
@@ -486,6 +528,38 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
         add[s].push_back(level_pilot(t.kind == AICDF_KIND_CORR4 ? pilot4 : pilot, l, o->L_min, est));
       }
   };
+  // adaptive: after a pilot round, each set's new levels whose nested pair
+  // does not pay (nested_pays) get an exact term instead, piloted in one more
+  // launch; first[s] = the set's first term of that round
+  auto adapt = [&](const std::vector<size_t> &first) -> aicdf_status {
+    if (est != AICDF_EST_ADAPTIVE) return AICDF_OK;
+    std::vector<std::vector<uint64_t>> add2(n_sets);
+    bool any = false;
+    for (int s = 0; s < n_sets; ++s) {
+      std::vector<Term> &T = S[s].terms;
+      const size_t last = T.size();
+      const double ce_step = kind_ns[std::make_pair(sets[s].model, sets[s].scheme)][AICDF_KIND_EXACT2];
+      for (size_t i = first[s]; i + 1 < last; i += 2) {
+        if (!nested_pays(T[i], T[i + 1], cost(s, T[i]), cost(s, T[i + 1]),
+                         ce_step * (double)((1u << T[i].level) + 1)))
+          {
+            T[i].active = T[i + 1].active = false;
+            Term t;
+            t.level = T[i].level;
+            t.kind = AICDF_KIND_EXACT2;
+            t.slot = 0;
+            t.tag = ((uint32_t)s << 8) + exact_level_tag(est, t.level);
+            T.push_back(t);
+          }
+      }
+      add2[s].assign(T.size(), 0);
+      for (size_t i = last; i < T.size(); ++i) {
+        add2[s][i] = level_pilot(pilot, T[i].level, o->L_min, est);
+        any = true;
+      }
+    }
+    return any ? run_round(add2) : AICDF_OK;
+  };
   std::vector<std::vector<uint64_t>> add(n_sets);
   for (int s = 0; s < n_sets; ++s) {
     if (est == AICDF_EST_PLAIN) {
@@ -497,6 +571,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     }
   }
   aicdf_status rc = run_round(add);
+  if (rc == AICDF_OK) rc = adapt(std::vector<size_t>(n_sets, 0));
   const double eps = o->eps;
   const double alpha = o->weak_order > 0.0 ? o->weak_order : 1.0;
   const double a2 = std::pow(2.0, alpha);
@@ -509,7 +584,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       any = true;
       std::vector<double> v, c, m(S[s].terms.size());
       for (auto &t : S[s].terms) {
-        v.push_back(t.var());
+        v.push_back(t.active ? t.var() : 0.0);  // a replaced pair gets no more paths
         c.push_back(cost(s, t));
       }
       double total = 0.0;
@@ -531,7 +606,9 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     if (rc != AICDF_OK) break;
     // bias test per set; sets that need more levels get them, piloted in one launch
     bool grow = false;
+    std::vector<size_t> first(n_sets);
     for (int s = 0; s < n_sets; ++s) {
+      first[s] = S[s].terms.size();
       add[s].assign(S[s].terms.size(), 0);
       SetState &q = S[s];
       if (!q.active) continue;
@@ -543,7 +620,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       auto level_mean = [&](int l) {
         double mm = 0.0;
         for (auto &t : q.terms)
-          if (t.level == l) mm += t.mean();
+          if (t.level == l && t.active) mm += t.mean();
         return mm;
       };
       double bias = std::fabs(level_mean(q.L)) / (a2 - 1.0);
@@ -565,6 +642,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       grow = true;
     }
     if (grow) rc = run_round(add);
+    if (grow && rc == AICDF_OK) rc = adapt(first);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -576,6 +654,7 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
     std::memset(r, 0, sizeof(*r));
     double estv = 0.0, var = 0.0;
     for (auto &t : S[s].terms) {
+      if (!t.active) continue;
       estv += t.mean();
       var += t.n ? t.var() / (double)t.n : 0.0;
       r->paths[t.level][t.slot] = t.n;
@@ -583,13 +662,14 @@ extern "C" aicdf_status aicdf_mlmc_run_sets(const aicdf_sde_params *sets, int n_
       r->var[t.level][t.slot] = t.var();
       r->kurt[t.level][t.slot] = t.kurt();
       r->cost_ns[t.level][t.slot] = cost(s, t);
+      if (t.kind == AICDF_KIND_EXACT2 && est == AICDF_EST_ADAPTIVE) r->exact_level[t.level] = 1;
     }
     r->estimate = estv;
     r->variance = var;
     r->bias = S[s].bias;
     r->L = S[s].L;
     r->converged = S[s].converged ? 1 : 0;
-    r->n_terms = est == AICDF_EST_NESTED ? 2 : 1;
+    r->n_terms = (est == AICDF_EST_NESTED || est == AICDF_EST_ADAPTIVE) ? 2 : 1;
     r->gpu_ms = gpu_ms;
     r->wall_ms = wall_ms;
     r->launches = launches;

@@ -90,9 +90,11 @@ struct ApproxTable<AICDF_PWC> {
 struct PathConsts {
   // GBM: fine increment factor g0 + g1 Z + g2 Z^2, coarse c0 + c1 S + c2 S^2
   float g0, g1, g2, c0, c1, c2;
-  // CIR: fine   kdt (theta - X) + sig_sdt sqrt|X| Z + mq (Z^2 - 1)
-  //      coarse 2 kdt (theta - X) + sig_sdt sqrt|X| S + mq (S^2 - 2)
-  float kdt, theta, sig_sdt, mq;
+  // CIR: fine   kdt (theta - X) + Z (sig_sdt sqrt|X| + mq Z) - mq
+  //      coarse 2 kdt (theta - X) + S (sig_sdt sqrt|X| + mq S) - 2 mq
+  // (the noise term sigma sqrt|X| dW + mq (dW^2 / dt - 1) written as one
+  // product and one add: mq = 0 for Euler-Maruyama)
+  float kdt, kdt2, theta, sig_sdt, mq, mq2;
 };
 
 // (all products and differences rounded separately, _rn intrinsics: the
@@ -114,6 +116,8 @@ __device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   p.theta = a.theta;
   p.sig_sdt = p.g1;
   p.mq = mil ? __fmul_rn(__fmul_rn(0.25f, s2), dt) : 0.f;
+  p.kdt2 = __fmul_rn(2.0f, p.kdt);
+  p.mq2 = __fmul_rn(2.0f, p.mq);
   return p;
 }
 
@@ -131,7 +135,7 @@ template <int MODEL>
 __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.g2, z, p.g1), z, p.g0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(p.kdt, p.theta - x, fmaf(p.sig_sdt * r, z, p.mq * fmaf(z, z, -1.0f)));
+  const float inc = fmaf(p.kdt, p.theta - x, fmaf(z, fmaf(p.mq, z, p.sig_sdt * r), -p.mq));
   return x + inc;
 }
 
@@ -139,7 +143,7 @@ template <int MODEL>
 __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.c2, s, p.c1), s, p.c0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(2.0f * p.kdt, p.theta - x, fmaf(p.sig_sdt * r, s, p.mq * fmaf(s, s, -2.0f)));
+  const float inc = fmaf(p.kdt2, p.theta - x, fmaf(s, fmaf(p.mq, s, p.sig_sdt * r), -p.mq2));
   return x + inc;
 }
 

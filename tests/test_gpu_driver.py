@@ -25,7 +25,7 @@ def _bs():
     return norm.cdf(d1) - math.exp(-r) * norm.cdf(d1 - s)
 
 
-@pytest.mark.parametrize("estimator", ["EST_NESTED", "EST_REGULAR"])
+@pytest.mark.parametrize("estimator", ["EST_NESTED", "EST_REGULAR", "EST_ADAPTIVE"])
 def test_driver_reaches_rmse(P, estimator):
     import torch
     tl = P.table_build(P.PWL, 15)
@@ -71,7 +71,7 @@ def test_driver_sets_single_set_equals_run(P):
     prm = P.sde_params()
     ws = torch.empty(max(P.mlmc_run_workspace_bytes(), P.mlmc_run_sets_workspace_bytes(1)), dtype=torch.uint8,
                      device="cuda")
-    for est in (P.EST_NESTED, P.EST_REGULAR):
+    for est in (P.EST_NESTED, P.EST_REGULAR, P.EST_ADAPTIVE):
         r = P.mlmc_run(prm, tl, 5e-4, ws, estimator=est, seed=4)
         (q,) = P.mlmc_run_sets([prm], tl, 5e-4, ws, estimator=est, seed=4)
         assert q.estimate == r.estimate and q.variance == r.variance and q.L == r.L
@@ -101,3 +101,29 @@ def test_driver_sets_many_cir_sets(P):
         ests.append(r.estimate - prm.theta)
     assert len(set(ests)) == len(ests)  # no two sets share a stream
     assert res[0].launches == res[-1].launches >= 2
+
+
+def test_adaptive_keeps_the_pair_where_it_pays(P):
+    """The adaptive estimator (per level the cheaper of the nested pair and the
+    exact two-way term by the Section 4.1 cost model).  With the piecewise
+    linear table the GBM call's four-way variance is ~2^-14 of the two-way
+    one, so the nested pair stays at every level.  With the two-interval
+    piecewise constant table (Z^E = +-0.80, squared L2 error 1 - 2/pi) the
+    four-way variance is of the two-way one's order and the pair never pays:
+    every level runs an exact two-way term on its own stream -- which is then
+    the regular estimator on other streams -- and the estimate stays within
+    its error of the Black-Scholes price."""
+    import torch
+    ws = torch.empty(P.mlmc_run_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    eps = 2e-4
+    for table, want_exact in ((P.table_build(P.PWL, 15), False), (P.table_build(P.PWC, 2), True)):
+        r = P.mlmc_run(P.sde_params(), table, eps, ws, estimator=P.EST_ADAPTIVE, seed=6)
+        d = r.as_dict()
+        assert r.converged and r.variance <= eps * eps / 2 * 1.05
+        assert all(lv["exact_level"] == want_exact for lv in d["levels"]), d["levels"]
+        for lv in d["levels"]:
+            if want_exact:
+                assert lv["paths"][1] == 0 and lv["paths"][0] > 0
+            else:
+                assert 0 < lv["paths"][1] <= lv["paths"][0]
+        assert abs(r.estimate - _bs()) <= 4 * math.sqrt(r.variance) + eps / math.sqrt(2)
