@@ -7,9 +7,9 @@
 // and every second step the coarse states advance with the pairwise sums
 // (Section 4.1: coarse Wiener increments are pairwise sums of the fine
 // ones).  The payoff difference Y of the requested estimator kind and its
-// powers Y^2, Y^3, Y^4 are accumulated per thread in FP32 over a chunk of
-// paths and flushed to FP64 (Y, Y^2) or to compensated FP32 sums (Y^3, Y^4)
-// (FP64 issues at a small fraction of the FP32 rate on this GPU); warps
+// powers Y^2, Y^3, Y^4 are accumulated per thread in FP32, Y and Y^2 over a
+// chunk of paths flushed to FP64 (FP64 issues at a small fraction of the
+// FP32 rate on this GPU), Y^3 and Y^4 over all the thread's paths; warps
 // reduce in FP64 by shuffles, blocks write one FP64 partial each, and a
 // second one-block kernel adds the partials in a fixed order, so the sums
 // are deterministic.
@@ -272,25 +272,67 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
 }
 
 // sums[5 t + {0..4}] = (sum Y, sum Y^2, sum Y^3, sum Y^4, n) of term t from
-// its slots, in slot order.
-__global__ void k_reduce_terms(const Moments *__restrict__ partials, const int *__restrict__ slot_begin,
-                               const double *__restrict__ counts, int n_terms,
-                               double *__restrict__ sums) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_terms) return;
-  Moments m{0.0, 0.0, 0.0, 0.0};
-  for (int s = slot_begin[t]; s < slot_begin[t + 1]; ++s) {
-    const Moments p = partials[s];
-    m.s1 += p.s1;
-    m.s2 += p.s2;
-    m.s3 += p.s3;
-    m.s4 += p.s4;
-  }
+// its slots.  One term may own thousands of slots (the driver's level-0 terms
+// hold about half of a round's tiles), and a serial FP64 chain over them, four
+// adds per slot at ~64 cycles each, took longer than the path kernel; so P
+// lanes (a power of two, at most 32) share each term: lane j adds slots j,
+// j + P, ..., and an xor butterfly over the P lanes finishes the sums.  P is
+// fixed by the plan, so the order of every add is too.
+__device__ __forceinline__ void add_moments(Moments &m, const Moments &p) {
+  m.s1 += p.s1;
+  m.s2 += p.s2;
+  m.s3 += p.s3;
+  m.s4 += p.s4;
+}
+__device__ __forceinline__ void write_term_sums(double *sums, int t, const Moments &m, double count) {
   sums[kSumsPerTerm * t + 0] = m.s1;
   sums[kSumsPerTerm * t + 1] = m.s2;
   sums[kSumsPerTerm * t + 2] = m.s3;
   sums[kSumsPerTerm * t + 3] = m.s4;
-  sums[kSumsPerTerm * t + 4] = counts[t];
+  sums[kSumsPerTerm * t + 4] = count;
+}
+
+__global__ void __launch_bounds__(256) k_reduce_terms(const Moments *__restrict__ partials,
+                                                      const int *__restrict__ slot_begin,
+                                                      const double *__restrict__ counts, int n_terms,
+                                                      int log2_lanes, double *__restrict__ sums) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int P = 1 << log2_lanes, t = g >> log2_lanes, j = g & (P - 1);
+  Moments m{0.0, 0.0, 0.0, 0.0};
+  if (t < n_terms)
+    for (int s = slot_begin[t] + j; s < slot_begin[t + 1]; s += P) add_moments(m, partials[s]);
+  for (int o = P >> 1; o > 0; o >>= 1) {  // every lane of the warp takes part (P divides 32)
+    m.s1 += __shfl_xor_sync(FULL_MASK, m.s1, o);
+    m.s2 += __shfl_xor_sync(FULL_MASK, m.s2, o);
+    m.s3 += __shfl_xor_sync(FULL_MASK, m.s3, o);
+    m.s4 += __shfl_xor_sync(FULL_MASK, m.s4, o);
+  }
+  if (t < n_terms && j == 0) write_term_sums(sums, t, m, counts[t]);
+}
+
+// The same with a block of 256 threads per term, for terms of more than 256
+// slots.
+__global__ void __launch_bounds__(256) k_reduce_terms_block(const Moments *__restrict__ partials,
+                                                            const int *__restrict__ slot_begin,
+                                                            const double *__restrict__ counts,
+                                                            double *__restrict__ sums) {
+  __shared__ Moments s_red[256 / 32];
+  const int t = blockIdx.x;
+  Moments m{0.0, 0.0, 0.0, 0.0};
+  for (int s = slot_begin[t] + (int)threadIdx.x; s < slot_begin[t + 1]; s += blockDim.x) add_moments(m, partials[s]);
+  const Moments r = block_reduce_moments(m, s_red);
+  if (threadIdx.x == 0) write_term_sums(sums, t, r, counts[t]);
+}
+
+// Lanes per term for the term reduction of a plan: log2 P with P the least
+// power of two giving each lane at most 8 slots, or -1 for a block per term.
+int reduce_lanes_log2(const std::vector<int> &slot_begin) {
+  int most = 0;
+  for (size_t t = 0; t + 1 < slot_begin.size(); ++t) most = std::max(most, slot_begin[t + 1] - slot_begin[t]);
+  if (most > 256) return -1;
+  int lg = 0;
+  while (lg < 5 && (8 << lg) < most) ++lg;
+  return lg;
 }
 
 using BatchFn = void (*)(BatchArgs);
@@ -314,6 +356,7 @@ struct Plan {
   aicdf_schedule sched;
   std::vector<BatchItem> items;  // dispatch order (largest tiles first)
   std::vector<int> slot_begin;   // n_terms + 1
+  int reduce_log2 = 0;           // lanes per term of the term reduction (log2; -1: a block)
   // workspace layout (byte offsets)
   size_t off_counter, off_items, off_specs, off_slots, off_counts, off_partials, bytes;
   // graph captured for this plan and the pointers it was captured with
@@ -403,6 +446,7 @@ static Plan *get_plan(aicdf_batch_s *b, const aicdf_schedule &s) {
     }
   }
   p->slot_begin[nt] = (int)slot;
+  p->reduce_log2 = reduce_lanes_log2(p->slot_begin);
   std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &x, const Tile &y) { return x.cost > y.cost; });
   p->items.reserve(tiles.size());
   for (auto &x : tiles) p->items.push_back(x.it);
@@ -526,8 +570,15 @@ static aicdf_status record_batch(aicdf_batch_s *b, Plan *p, void *ws, double *su
   cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   k<<<grid, threads, 0, st>>>(a);
   const int nt = (int)b->terms.size();
-  k_reduce_terms<<<(nt + 255) / 256, 256, 0, st>>>(a.partials, reinterpret_cast<const int *>(w + p->off_slots),
-                                                   reinterpret_cast<const double *>(w + p->off_counts), nt, sums);
+  const int *slots = reinterpret_cast<const int *>(w + p->off_slots);
+  const double *counts = reinterpret_cast<const double *>(w + p->off_counts);
+  if (p->reduce_log2 < 0) {
+    k_reduce_terms_block<<<nt, 256, 0, st>>>(a.partials, slots, counts, sums);
+  } else {
+    const long long threads = (long long)nt << p->reduce_log2;
+    k_reduce_terms<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a.partials, slots, counts, nt, p->reduce_log2,
+                                                                     sums);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error((int)e);

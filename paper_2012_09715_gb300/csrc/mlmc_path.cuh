@@ -154,49 +154,38 @@ struct __align__(16) Moments {
   double s1, s2, s3, s4;  // sum Y, sum Y^2, sum Y^3, sum Y^4
 };
 
-// s + x with the rounding error carried in c (Kahan's compensated sum), each
-// operation rounded on its own (_rn intrinsics are never contracted).
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-  const float y = __fsub_rn(x, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
-}
-
-// Per-thread power sums of Y: FP32 over chunks of about 16 paths.  At each
-// chunk's end the sums of Y and Y^2 are added to FP64 accumulators (FP64 runs
-// at 1/64 of the FP32 rate on this GPU: a warp's FP64 add holds its
-// sub-partition's FP64 unit for ~64 cycles), and those of Y^3 and Y^4 to
-// FP32 running sums with Kahan compensation (relative error ~2^-24 per chunk
-// sum, no FP64 work per chunk), in a fixed order per thread.  add() is FP32
-// only; flush() is called by the loops below once per chunk, outside the
-// per-path body, so that the FP64 adds are never if-converted into predicated
-// instructions issued for every path (predicated-off FP64 instructions still
-// occupy the FP64 unit).  Lanes past the end of their range add zero (valid =
-// false), which keeps every lane's chunking and the control flow warp-uniform.
+// Per-thread power sums of Y: FP32 over chunks of about 16 paths for Y and
+// Y^2, each chunk added to FP64 accumulators (FP64 runs at 1/64 of the FP32
+// rate on this GPU: a warp's FP64 add holds its sub-partition's FP64 unit for
+// ~64 cycles), in a fixed order per thread.  Y^3 and Y^4, which only serve the
+// kurtosis of a term, are FP32 running sums over the thread's k paths (two
+// registers, no per-chunk work; relative error at most (k-1) 2^-24 and
+// typically sqrt(k) 2^-24: ~4e-6 at the few thousand paths per thread of a
+// 10^9-path level launch).  add() is FP32 only; flush() is
+// called by the loops below once per chunk, outside the per-path body, so
+// that the FP64 adds are never if-converted into predicated instructions
+// issued for every path (predicated-off FP64 instructions still occupy the
+// FP64 unit).  Lanes past the end of their range add zero (valid = false),
+// which keeps every lane's chunking and the control flow warp-uniform.
 struct PathSums {
-  float f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f;  // current chunk
+  float f1 = 0.f, f2 = 0.f;  // current chunk
+  float f3 = 0.f, f4 = 0.f;  // running sums of Y^3, Y^4
   double d1 = 0.0, d2 = 0.0;
-  float k3 = 0.f, c3 = 0.f, k4 = 0.f, c4 = 0.f;  // compensated running sums of Y^3, Y^4
   __device__ __forceinline__ void add(float y, bool valid) {
     y = valid ? y : 0.0f;
     f1 = __fadd_rn(f1, y);
-    f2 = fmaf(y, y, f2);
     const float y2 = __fmul_rn(y, y);
+    f2 = __fadd_rn(f2, y2);
     f3 = fmaf(y2, y, f3);
     f4 = fmaf(y2, y2, f4);
   }
   __device__ __forceinline__ void flush() {
     d1 += (double)f1;
     d2 += (double)f2;
-    kahan_add(k3, c3, f3);
-    kahan_add(k4, c4, f4);
-    f1 = f2 = f3 = f4 = 0.f;
+    f1 = f2 = 0.f;
   }
   // the thread's totals (call after the last flush)
-  __device__ __forceinline__ Moments total() const {
-    return Moments{d1, d2, (double)k3 - (double)c3, (double)k4 - (double)c4};
-  }
+  __device__ __forceinline__ Moments total() const { return Moments{d1, d2, (double)f3, (double)f4}; }
 };
 
 constexpr int kChunkPaths = 16;  // paths per thread between FP64 flushes
@@ -372,43 +361,70 @@ template <class GroupFn>
 __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, uint64_t first, uint64_t stride,
                                            GroupFn group, PathSums &acc) {
   const int sh = 2 - level, G = 4 >> level;
+  const bool four = level == 0;  // G = 4, else G = 2
   const uint64_t q0 = p0 >> sh, ng = ((p0 + n - 1) >> sh) - q0 + 1;
+  // Groups wholly inside the range: all but a first group that starts before
+  // p0 and a last one that runs past p0 + n.  The warp's groups base ..
+  // base + 31 (base a multiple of 32) are all inside iff base + 32 <= qb and
+  // not (base = 0 with a partial first group).
+  const bool head = (p0 & (uint64_t)(G - 1)) != 0;
+  const uint64_t qb = ng - (((p0 + n) & (uint64_t)(G - 1)) ? 1 : 0);
   const int lane = threadIdx.x & 31;
   chunked_loop(first, ng, stride, kChunkPaths / G, acc, [&](uint64_t base) {
     const uint64_t qi = base + lane, q = q0 + qi;
     float y[4];
     group(q, y);
+    if (base + 32 <= qb && (base != 0 || !head)) {  // warp-uniform
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const uint64_t p = (q << sh) + (uint64_t)g;
-      if (g < G) acc.add(y[g], qi < ng && p >= p0 && p < p0 + n);  // G is uniform
+      for (int g = 0; g < 4; ++g)
+        if (g < 2 || four) acc.add(y[g], true);
+    } else {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint64_t p = (q << sh) + (uint64_t)g;
+        if (g < 2 || four) acc.add(y[g], qi < ng && p >= p0 && p < p0 + n);
+      }
     }
   });
 }
 
 // FP64 block reduction of the four sums; result valid in thread 0.  Ends with
-// a barrier so that s_red may be reused right away.
+// a barrier so that s_red may be reused right away.  A warp's FP64 add holds
+// its sub-partition's FP64 unit for ~64 cycles whatever the number of active
+// lanes, so the warp stage keeps every lane's add useful: the first exchange
+// (lanes L, L^16) leaves the lower half with (sum Y, sum Y^2) and the upper
+// half with (sum Y^3, sum Y^4) of the two lanes, the second (L, L^8) one sum
+// per group of 8 lanes (group k: sum Y^(k+1)) of four lanes, and three xor
+// rounds within each group finish it: 6 FP64 adds per warp instead of 20 for
+// four separate shuffle trees.  Warp 0 then adds the warps' sums the same way
+// (lane 8k + w holds sum k of warp w).  The order of every add is fixed by
+// lane and warp indices, so the result is deterministic.
 template <int NW>
 __device__ __forceinline__ Moments block_reduce_moments(Moments m, Moments (&s_red)[NW]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m.s1 += __shfl_down_sync(FULL_MASK, m.s1, o);
-    m.s2 += __shfl_down_sync(FULL_MASK, m.s2, o);
-    m.s3 += __shfl_down_sync(FULL_MASK, m.s3, o);
-    m.s4 += __shfl_down_sync(FULL_MASK, m.s4, o);
-  }
+  static_assert(NW <= 8, "at most 8 warps");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) s_red[warp] = m;
+  const bool hi = (lane & 16) != 0, mid = (lane & 8) != 0;
+  // lanes L, L^16: keep (s1, s2) below 16, (s3, s4) above
+  const double r1 = __shfl_xor_sync(FULL_MASK, hi ? m.s1 : m.s3, 16);
+  const double r2 = __shfl_xor_sync(FULL_MASK, hi ? m.s2 : m.s4, 16);
+  const double a = (hi ? m.s3 : m.s1) + r1, b = (hi ? m.s4 : m.s2) + r2;
+  // lanes L, L^8: keep a below 8 (within the half), b above
+  double c = (mid ? b : a) + __shfl_xor_sync(FULL_MASK, mid ? a : b, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+  double *red = reinterpret_cast<double *>(s_red);  // [warp][4]
+  if ((lane & 7) == 0) red[4 * warp + (lane >> 3)] = c;
   __syncthreads();
   Moments t{0.0, 0.0, 0.0, 0.0};
-  if (threadIdx.x == 0) {
-    const int nw = (int)(blockDim.x >> 5);
-    for (int w = 0; w < nw; ++w) {
-      t.s1 += s_red[w].s1;
-      t.s2 += s_red[w].s2;
-      t.s3 += s_red[w].s3;
-      t.s4 += s_red[w].s4;
-    }
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5), w = lane & 7;
+    double v = w < nw ? red[4 * w + (lane >> 3)] : 0.0;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    t.s1 = v;
+    t.s2 = __shfl_sync(FULL_MASK, v, 8);
+    t.s3 = __shfl_sync(FULL_MASK, v, 16);
+    t.s4 = __shfl_sync(FULL_MASK, v, 24);
   }
   __syncthreads();
   return t;

@@ -98,8 +98,9 @@ def test_level_sums_within_3se(P, orc, env, level, kind):
     assert abs(g[1] - o[1]) <= 1e-4 * o[1] + 8 * math.sqrt(o[1]) * d + 1e-12
     # sum Y^3 and sum Y^4: a per-path error of at most D (the per-path parity
     # bound) moves y^3 by <= 3 y^2 D + 3 |y| D^2 + D^3 and y^4 by <= 4 |y|^3 D +
-    # 6 y^2 D^2 + ..., with sum |y|^3 <= sqrt(sum y^2 sum y^4); the FP32 chunk
-    # sums and their compensated total add ~1e-6 of sum |y|^k
+    # 6 y^2 D^2 + ..., with sum |y|^3 <= sqrt(sum y^2 sum y^4); the FP32
+    # running sums add at most (paths per thread) 2^-24 of sum |y|^k (one or
+    # two paths per thread here)
     D = 4 * (2 ** level + 2) * 2.0 ** -23 * 2.0
     abs3 = math.sqrt(o[1] * o[3])
     assert abs(g[2] - o[2]) <= 1e-5 * abs3 + 3 * D * o[1] + 3 * D * D * math.sqrt(n * o[1]) + n * D ** 3 + 1e-30
