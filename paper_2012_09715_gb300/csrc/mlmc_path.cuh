@@ -90,11 +90,13 @@ struct ApproxTable<AICDF_PWC> {
 struct PathConsts {
   // GBM: fine increment factor g0 + g1 Z + g2 Z^2, coarse c0 + c1 S + c2 S^2
   float g0, g1, g2, c0, c1, c2;
-  // CIR: fine   kdt (theta - X) + Z (sig_sdt sqrt|X| + mq Z) - mq
-  //      coarse 2 kdt (theta - X) + S (sig_sdt sqrt|X| + mq S) - 2 mq
-  // (the noise term sigma sqrt|X| dW + mq (dW^2 / dt - 1) written as one
-  // product and one add: mq = 0 for Euler-Maruyama)
-  float kdt, kdt2, theta, sig_sdt, mq, mq2;
+  // CIR: fine   Z (sig_sdt sqrt|X| + mq Z) + (nkdt X + dc1)
+  //      coarse S (sig_sdt sqrt|X| + mq S) + (nkdt2 X + dc2)
+  // with nkdt = -kappa h, dc1 = kappa h theta - mq (coarse: twice each): the
+  // drift kappa (theta - X) h and the Milstein term's -mq in one FMA, the noise
+  // sigma sqrt|X| dW + mq dW^2 / h in two (mq = 0 for Euler-Maruyama).  The
+  // constants' rounding is relative to the drift per step, not to X.
+  float nkdt, nkdt2, dc1, dc2, sig_sdt, mq;
 };
 
 // (all products and differences rounded separately, _rn intrinsics: the
@@ -112,12 +114,13 @@ __device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   p.c0 = __fsub_rn(__fmul_rn(2.0f, mdt), mil ? __fmul_rn(2.0f, hs2) : 0.f);
   p.c1 = p.g1;
   p.c2 = mil ? hs2 : 0.f;
-  p.kdt = __fmul_rn(a.kappa, dt);
-  p.theta = a.theta;
+  const float kdt = __fmul_rn(a.kappa, dt), kth = __fmul_rn(kdt, a.theta);
   p.sig_sdt = p.g1;
   p.mq = mil ? __fmul_rn(__fmul_rn(0.25f, s2), dt) : 0.f;
-  p.kdt2 = __fmul_rn(2.0f, p.kdt);
-  p.mq2 = __fmul_rn(2.0f, p.mq);
+  p.nkdt = -kdt;
+  p.nkdt2 = __fmul_rn(-2.0f, kdt);
+  p.dc1 = __fsub_rn(kth, p.mq);
+  p.dc2 = __fmul_rn(2.0f, p.dc1);
   return p;
 }
 
@@ -135,7 +138,7 @@ template <int MODEL>
 __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.g2, z, p.g1), z, p.g0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(p.kdt, p.theta - x, fmaf(z, fmaf(p.mq, z, p.sig_sdt * r), -p.mq));
+  const float inc = fmaf(z, fmaf(p.mq, z, p.sig_sdt * r), fmaf(p.nkdt, x, p.dc1));
   return x + inc;
 }
 
@@ -143,7 +146,7 @@ template <int MODEL>
 __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts &p) {
   if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.c2, s, p.c1), s, p.c0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(p.kdt2, p.theta - x, fmaf(s, fmaf(p.mq, s, p.sig_sdt * r), -p.mq2));
+  const float inc = fmaf(s, fmaf(p.mq, s, p.sig_sdt * r), fmaf(p.nkdt2, x, p.dc2));
   return x + inc;
 }
 

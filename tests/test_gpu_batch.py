@@ -72,6 +72,41 @@ def test_batch_matches_level_kernel(P, method):
         assert got[i, 3] == pytest.approx(ref[3], rel=4e-6, abs=1e-30)
 
 
+@pytest.mark.parametrize("slots", [1, 5, 9, 17, 33, 65, 129, 256, 257, 600])
+def test_term_reduction_widths(P, slots):
+    """The term sums come from a term's tile partials, added by P = 1 .. 32
+    lanes per term (at most 8 tiles a lane) or by a block for terms of more
+    than 256 tiles; the widest term of a plan sets the form.  A level-0 term
+    of `slots` tiles of 256 paths (the last one ragged) beside two small terms
+    must give the level kernel's sums in every form, and the same bits on a
+    graph replay."""
+    import torch
+    table = P.table_build(P.PWL, 15)
+    sets = [P.sde_params()]
+    n = slots * 256 - 77
+    terms = [P.BatchTerm(0, 0, P.KIND_APPROX2, 11, n, 5), P.BatchTerm(0, 0, P.KIND_CORR4, 12, 300, 7),
+             P.BatchTerm(0, 3, P.KIND_APPROX2, 13, 200, 0)]
+    b = P.Batch(sets, terms, table, seed=17)
+    sched = P.Schedule(256, 128, 0, 0)
+    sums = torch.zeros(P.SUMS * len(terms), dtype=torch.float64, device="cuda")
+    ws = torch.empty(b.workspace_bytes(sched), dtype=torch.uint8, device="cuda")
+    b.run(sched, sums, ws)
+    got = sums.cpu().numpy().reshape(-1, P.SUMS).copy()
+    b.run(sched, sums, ws)  # graph replay
+    assert np.array_equal(got, sums.cpu().numpy().reshape(-1, P.SUMS))
+    assert b.info(sched)[0] >= slots
+    lws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    ls = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    for i, t in enumerate(terms):
+        ref = _level_sums(P, sets[0], table, t, lws, ls, 17)
+        assert got[i, 4] == t.n_paths
+        scale = math.sqrt(t.n_paths * ref[1]) + 1e-30
+        assert abs(got[i, 0] - ref[0]) <= 2e-6 * scale, (i, got[i], ref)
+        assert got[i, 1] == pytest.approx(ref[1], rel=2e-6, abs=1e-30)
+        assert abs(got[i, 2] - ref[2]) <= 4e-6 * math.sqrt(ref[1] * ref[3]) + 1e-30, (i, got[i], ref)
+        assert got[i, 3] == pytest.approx(ref[3], rel=4e-6, abs=1e-30)
+
+
 def test_batch_deterministic_across_replays_and_schedules(P):
     import torch
     table = P.table_build(P.PWL, 15)
