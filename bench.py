@@ -641,6 +641,9 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
                 for k in range(2):
                     t[k] += r.paths[l][k] * r.cost_ns[l][k] * 1e-6
         out["modelled_ms_by_slot"] = t
+        steps = sum(r.paths[l][k] << l for r in rr for l in range(r.L + 1) for k in range(2))
+        out["fine_path_steps"] = steps
+        out["path_steps_per_s"] = steps / (rr[0].gpu_ms * 1e-3) if rr[0].gpu_ms > 0 else None
         out["unconverged_max_rmse_est"] = max(((r.variance + r.bias ** 2) ** 0.5 for r in rr if not r.converged),
                                               default=0.0)
         return out

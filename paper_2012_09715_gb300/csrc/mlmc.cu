@@ -52,23 +52,10 @@ __global__ void __launch_bounds__(kLevelThreads)
   __shared__ Moments s_red[kLevelThreads / 32];
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
   const PathConsts pc = make_path_consts(a.ps);
-  const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
   PathSums acc;
-  if (a.ps.level < 2) {  // warp-uniform: groups of paths share a Philox call
-    sum_groups(a.path_offset, a.n_paths, a.ps.level, first, stride,
-               [&](uint64_t q, float (&y)[4]) {
-                 group_y_level<NE, NA, AP, MODEL, false>(a.ps, pc, ap, a.keys, q, y);
-               },
-               acc);
-  } else {
-    chunked_loop(first, a.n_paths, stride, kChunkPaths, acc, [&](uint64_t base) {
-      const uint64_t i = base + lane;
-      const float y = path_y<NE, NA, AP, MODEL>(a.ps, pc, ap, a.keys, a.path_offset + i);
-      acc.add(y, i < a.n_paths);
-    });
-  }
+  term_sums_scheme<NE, NA, AP, MODEL, false>(a.ps, pc, ap, a.keys, a.path_offset, a.n_paths, first, stride, acc);
   const Moments t = block_reduce_moments(acc.total(), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
@@ -245,7 +232,6 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
   __shared__ Moments s_red[256 / 32];
   __shared__ int s_item;
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
-  const int lane = threadIdx.x & 31;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
@@ -261,9 +247,8 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
                  [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); }, acc);
     } else {
       chunked_loop(threadIdx.x & ~31u, item.count, blockDim.x, kChunkPaths, acc, [&](uint64_t base) {
-        const uint32_t i = (uint32_t)base + lane;
-        const float y = path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i);
-        acc.add(y, i < item.count);
+        const uint32_t i = (uint32_t)base + (threadIdx.x & 31);
+        acc.add(path_y_any<AP, V16>(ps, pc, ap, a.keys, item.begin + i), i < item.count);
       });
     }
     const Moments t = block_reduce_moments(acc.total(), s_red);

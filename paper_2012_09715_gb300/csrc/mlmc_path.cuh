@@ -134,19 +134,22 @@ __device__ __forceinline__ float cir_sqrt_abs(float x) {
   return r;
 }
 
-template <int MODEL>
+// MIL: Milstein.  The Euler-Maruyama forms leave out the Z^2 terms, whose
+// constants are zero there: fmaf(0, z, c) = c for finite z, so both forms give
+// the same bits and EM saves one FMA per fine and per coarse step.
+template <int MODEL, bool MIL>
 __device__ __forceinline__ float step_fine(float x, float z, const PathConsts &p) {
-  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.g2, z, p.g1), z, p.g0), x);
+  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(MIL ? fmaf(p.g2, z, p.g1) : p.g1, z, p.g0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(z, fmaf(p.mq, z, p.sig_sdt * r), fmaf(p.nkdt, x, p.dc1));
+  const float inc = fmaf(z, MIL ? fmaf(p.mq, z, p.sig_sdt * r) : p.sig_sdt * r, fmaf(p.nkdt, x, p.dc1));
   return x + inc;
 }
 
-template <int MODEL>
+template <int MODEL, bool MIL>
 __device__ __forceinline__ float step_coarse(float x, float s, const PathConsts &p) {
-  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(fmaf(p.c2, s, p.c1), s, p.c0), x);
+  if (MODEL == AICDF_MODEL_GBM) return fmaf(x, fmaf(MIL ? fmaf(p.c2, s, p.c1) : p.c1, s, p.c0), x);
   const float r = cir_sqrt_abs(x);
-  const float inc = fmaf(s, fmaf(p.mq, s, p.sig_sdt * r), fmaf(p.nkdt2, x, p.dc2));
+  const float inc = fmaf(s, MIL ? fmaf(p.mq, s, p.sig_sdt * r) : p.sig_sdt * r, fmaf(p.nkdt2, x, p.dc2));
   return x + inc;
 }
 
@@ -235,14 +238,14 @@ __device__ __forceinline__ float path_result(const PathSpec &a, bool coarse, flo
 // Y of one path at level >= 2 (path p owns the Philox calls (s/4, p, tag)).
 // All 32 lanes of a warp must call it together (the PWL approximation
 // shuffles across the warp).  V16: the approximate variate is rounded to FP16
-// before use (FP16 approximate variates).
-template <bool NE, bool NA, int AP, int MODEL, bool V16 = false>
+// before use (FP16 approximate variates); MIL: Milstein steps.
+template <bool NE, bool NA, int AP, int MODEL, bool V16, bool MIL>
 __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
                                         const ApproxTable<AP> &ap, const PhiloxKeys &keys,
                                         uint64_t p) {
   const int nfine = 1 << a.level;
   float xfe = a.X0, xce = a.X0, xfa = a.X0, xca = a.X0;
-  float se = 0.f, sa = 0.f;  // pair sums of fine variates
+  float se = 0.f, sa = 0.f;  // pair sums of fine variates (set at even steps)
   const uint32_t plo = (uint32_t)p, phi = (uint32_t)(p >> 32);
   for (int s4 = 0; s4 < nfine; s4 += 4) {
     const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), plo, phi, a.tag), keys);
@@ -251,20 +254,18 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
     for (int t = 0; t < 4; ++t) {
       if (NE) {
         const float ze = phiinv_f32_word(w[t]);
-        xfe = step_fine<MODEL>(xfe, ze, pc);
-        se += ze;
+        xfe = step_fine<MODEL, MIL>(xfe, ze, pc);
+        se = (t & 1) ? se + ze : ze;
       }
       if (NA) {
         float za = ap(w[t]);
         if (V16) za = __half2float(__float2half_rn(za));
-        xfa = step_fine<MODEL>(xfa, za, pc);
-        sa += za;
+        xfa = step_fine<MODEL, MIL>(xfa, za, pc);
+        sa = (t & 1) ? sa + za : za;
       }
       if (t & 1) {
-        if (NE) xce = step_coarse<MODEL>(xce, se, pc);
-        if (NA) xca = step_coarse<MODEL>(xca, sa, pc);
-        se = 0.f;
-        sa = 0.f;
+        if (NE) xce = step_coarse<MODEL, MIL>(xce, se, pc);
+        if (NA) xca = step_coarse<MODEL, MIL>(xca, sa, pc);
       }
     }
   }
@@ -275,7 +276,7 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
 // G = 4 >> LEVEL paths: group q (paths q G .. q G + G - 1) uses the call
 // (0, q, tag), path q G + g taking words g 2^LEVEL .. g 2^LEVEL + 2^LEVEL - 1.
 // y[g] = Y of path q G + g.  All 32 lanes must call it together.
-template <bool NE, bool NA, int AP, int MODEL, bool V16, int LEVEL>
+template <bool NE, bool NA, int AP, int MODEL, bool V16, bool MIL, int LEVEL>
 __device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
                                         const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
   constexpr int NF = 1 << LEVEL, G = 4 >> LEVEL;
@@ -290,69 +291,21 @@ __device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc,
       const uint32_t x = w[g * NF + s];
       if (NE) {
         const float ze = phiinv_f32_word(x);
-        xfe = step_fine<MODEL>(xfe, ze, pc);
-        se += ze;
+        xfe = step_fine<MODEL, MIL>(xfe, ze, pc);
+        se = s ? se + ze : ze;
       }
       if (NA) {
         float za = ap(x);
         if (V16) za = __half2float(__float2half_rn(za));
-        xfa = step_fine<MODEL>(xfa, za, pc);
-        sa += za;
+        xfa = step_fine<MODEL, MIL>(xfa, za, pc);
+        sa = s ? sa + za : za;
       }
     }
     if (LEVEL == 1) {
-      if (NE) xce = step_coarse<MODEL>(xce, se, pc);
-      if (NA) xca = step_coarse<MODEL>(xca, sa, pc);
+      if (NE) xce = step_coarse<MODEL, MIL>(xce, se, pc);
+      if (NA) xca = step_coarse<MODEL, MIL>(xca, sa, pc);
     }
     y[g] = path_result<NE, NA>(a, LEVEL == 1, xfe, xce, xfa, xca);
-  }
-}
-
-template <bool NE, bool NA, int AP, int MODEL, bool V16>
-__device__ __forceinline__ void group_y_level(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
-                                              const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
-  if (a.level == 0) group_y<NE, NA, AP, MODEL, V16, 0>(a, pc, ap, keys, q, y);
-  else group_y<NE, NA, AP, MODEL, V16, 1>(a, pc, ap, keys, q, y);
-}
-
-// Runtime dispatch on (kind, model) for kernels that mix terms; the branch is
-// uniform across the block, outside the path loop.
-template <int AP, bool V16>
-__device__ __forceinline__ float path_y_any(const PathSpec &a, const PathConsts &pc,
-                                            const ApproxTable<AP> &ap, const PhiloxKeys &keys,
-                                            uint64_t p) {
-  const bool gbm = a.model == AICDF_MODEL_GBM;
-  switch (a.kind) {
-    case AICDF_KIND_CORR4:
-      return gbm ? path_y<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
-                 : path_y<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
-    case AICDF_KIND_EXACT2:
-    case AICDF_KIND_PLAIN:
-      return gbm ? path_y<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
-                 : path_y<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
-    default:
-      return gbm ? path_y<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
-                 : path_y<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
-  }
-}
-
-template <int AP, bool V16>
-__device__ __forceinline__ void group_y_any(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
-                                            const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
-  const bool gbm = a.model == AICDF_MODEL_GBM;
-  switch (a.kind) {
-    case AICDF_KIND_CORR4:
-      if (gbm) group_y_level<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
-      else group_y_level<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
-      break;
-    case AICDF_KIND_EXACT2:
-    case AICDF_KIND_PLAIN:
-      if (gbm) group_y_level<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
-      else group_y_level<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
-      break;
-    default:
-      if (gbm) group_y_level<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
-      else group_y_level<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
   }
 }
 
@@ -389,6 +342,103 @@ __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, u
       }
     }
   });
+}
+
+// Sums of Y over the paths [p0, p0 + n) of one term into acc: levels 0 and 1
+// by groups of paths sharing a Philox call, finer levels one path per lane;
+// `first` (warp-aligned) and `stride` lay the paths over the launch.  All 32
+// lanes of a warp must call it together.
+template <bool NE, bool NA, int AP, int MODEL, bool V16, bool MIL>
+__device__ __forceinline__ void term_sums(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                          const PhiloxKeys &keys, uint64_t p0, uint64_t n, uint64_t first,
+                                          uint64_t stride, PathSums &acc) {
+  if (a.level < 2) {  // warp-uniform
+    sum_groups(p0, n, a.level, first, stride,
+               [&](uint64_t q, float (&y)[4]) {
+                 if (a.level == 0) group_y<NE, NA, AP, MODEL, V16, MIL, 0>(a, pc, ap, keys, q, y);
+                 else group_y<NE, NA, AP, MODEL, V16, MIL, 1>(a, pc, ap, keys, q, y);
+               },
+               acc);
+  } else {
+    const int lane = threadIdx.x & 31;
+    chunked_loop(first, n, stride, kChunkPaths, acc, [&](uint64_t base) {
+      const uint64_t i = base + lane;
+      acc.add(path_y<NE, NA, AP, MODEL, V16, MIL>(a, pc, ap, keys, p0 + i), i < n);
+    });
+  }
+}
+
+// term_sums with the scheme taken at run time (a uniform branch outside the
+// path loops).
+template <bool NE, bool NA, int AP, int MODEL, bool V16>
+__device__ __forceinline__ void term_sums_scheme(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                                 const PhiloxKeys &keys, uint64_t p0, uint64_t n, uint64_t first,
+                                                 uint64_t stride, PathSums &acc) {
+  if (a.scheme == AICDF_SCHEME_MILSTEIN)
+    term_sums<NE, NA, AP, MODEL, V16, true>(a, pc, ap, keys, p0, n, first, stride, acc);
+  else
+    term_sums<NE, NA, AP, MODEL, V16, false>(a, pc, ap, keys, p0, n, first, stride, acc);
+}
+
+// Y of one path (level >= 2) or of one group of paths (levels 0, 1), with the
+// kind, model and scheme taken at run time, for kernels that mix terms: the
+// branches are uniform across the block, and the path loops stay one loop.
+template <bool NE, bool NA, int AP, int MODEL, bool V16>
+__device__ __forceinline__ float path_y_scheme(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                               const PhiloxKeys &keys, uint64_t p) {
+  return a.scheme == AICDF_SCHEME_MILSTEIN ? path_y<NE, NA, AP, MODEL, V16, true>(a, pc, ap, keys, p)
+                                           : path_y<NE, NA, AP, MODEL, V16, false>(a, pc, ap, keys, p);
+}
+
+template <int AP, bool V16>
+__device__ __forceinline__ float path_y_any(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                            const PhiloxKeys &keys, uint64_t p) {
+  const bool gbm = a.model == AICDF_MODEL_GBM;
+  switch (a.kind) {
+    case AICDF_KIND_CORR4:
+      return gbm ? path_y_scheme<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y_scheme<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+    case AICDF_KIND_EXACT2:
+    case AICDF_KIND_PLAIN:
+      return gbm ? path_y_scheme<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y_scheme<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+    default:
+      return gbm ? path_y_scheme<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, p)
+                 : path_y_scheme<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, p);
+  }
+}
+
+template <bool NE, bool NA, int AP, int MODEL, bool V16>
+__device__ __forceinline__ void group_y_scheme(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                               const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  const bool mil = a.scheme == AICDF_SCHEME_MILSTEIN;
+  if (a.level == 0) {
+    if (mil) group_y<NE, NA, AP, MODEL, V16, true, 0>(a, pc, ap, keys, q, y);
+    else group_y<NE, NA, AP, MODEL, V16, false, 0>(a, pc, ap, keys, q, y);
+  } else {
+    if (mil) group_y<NE, NA, AP, MODEL, V16, true, 1>(a, pc, ap, keys, q, y);
+    else group_y<NE, NA, AP, MODEL, V16, false, 1>(a, pc, ap, keys, q, y);
+  }
+}
+
+template <int AP, bool V16>
+__device__ __forceinline__ void group_y_any(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                            const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  const bool gbm = a.model == AICDF_MODEL_GBM;
+  switch (a.kind) {
+    case AICDF_KIND_CORR4:
+      if (gbm) group_y_scheme<true, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_scheme<true, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+      break;
+    case AICDF_KIND_EXACT2:
+    case AICDF_KIND_PLAIN:
+      if (gbm) group_y_scheme<true, false, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_scheme<true, false, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+      break;
+    default:
+      if (gbm) group_y_scheme<false, true, AP, AICDF_MODEL_GBM, V16>(a, pc, ap, keys, q, y);
+      else group_y_scheme<false, true, AP, AICDF_MODEL_CIR, V16>(a, pc, ap, keys, q, y);
+  }
 }
 
 // FP64 block reduction of the four sums; result valid in thread 0.  Ends with
