@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(kCirThreads)
     const uint64_t p = a.path_offset + i;
     double xe = a.X0;
     float xa = a.X0;
+    const PhiloxPath pp = philox_path((uint32_t)p, (uint32_t)(p >> 32), a.keys);
     for (int s4 = 0; s4 < nsteps && (active || APPROX == 1); s4 += 4) {
-      const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), (uint32_t)p, (uint32_t)(p >> 32), a.tag), a.keys);
+      const uint4 r = philox_path_call((uint32_t)(s4 >> 2), a.tag, pp, a.keys);
       const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {

@@ -235,6 +235,33 @@ __device__ __forceinline__ float path_result(const PathSpec &a, bool coarse, flo
   }
 }
 
+// Philox4x32-10 calls (j, plo, phi, tag) of one path.  Round 0 multiplies the
+// path-constant word phi and the call index j; round 1 multiplies round 0's
+// x (a path constant) and z (which depends on j and the tag only, the same on
+// every lane of a warp).  So the path-constant halves of both rounds are taken
+// once per path here, and a call redoes only the j-dependent products
+// (warp-uniform) and rounds 2..9.  Same words as philox().
+struct PhiloxPath {
+  uint32_t y1;      // round 0: lo(M1 phi)
+  uint32_t hx, lx;  // round 1: hi / lo (M0 x1), x1 = hi(M1 phi) ^ plo ^ k0[0]
+};
+__device__ __forceinline__ PhiloxPath philox_path(uint32_t plo, uint32_t phi, const PhiloxKeys &k) {
+  const uint64_t p1 = (uint64_t)PHILOX_M1 * phi;
+  const uint32_t x1 = (uint32_t)(p1 >> 32) ^ plo ^ k.k0[0];
+  const uint64_t q0 = (uint64_t)PHILOX_M0 * x1;
+  return PhiloxPath{(uint32_t)p1, (uint32_t)(q0 >> 32), (uint32_t)q0};
+}
+__device__ __forceinline__ uint4 philox_path_call(uint32_t j, uint32_t tag, const PhiloxPath &pp,
+                                                  const PhiloxKeys &k) {
+  const uint64_t p0 = (uint64_t)PHILOX_M0 * j;
+  const uint32_t z1 = (uint32_t)(p0 >> 32) ^ tag ^ k.k1[0], w1 = (uint32_t)p0;
+  const uint64_t q1 = (uint64_t)PHILOX_M1 * z1;
+  uint4 c = make_uint4((uint32_t)(q1 >> 32) ^ pp.y1 ^ k.k0[1], (uint32_t)q1, pp.hx ^ w1 ^ k.k1[1], pp.lx);
+#pragma unroll
+  for (int r = 2; r < 10; ++r) c = philox_round(c, k.k0[r], k.k1[r]);
+  return c;
+}
+
 // Y of one path at level >= 2 (path p owns the Philox calls (s/4, p, tag)).
 // All 32 lanes of a warp must call it together (the PWL approximation
 // shuffles across the warp).  V16: the approximate variate is rounded to FP16
@@ -246,9 +273,9 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
   const int nfine = 1 << a.level;
   float xfe = a.X0, xce = a.X0, xfa = a.X0, xca = a.X0;
   float se = 0.f, sa = 0.f;  // pair sums of fine variates (set at even steps)
-  const uint32_t plo = (uint32_t)p, phi = (uint32_t)(p >> 32);
+  const PhiloxPath pp = philox_path((uint32_t)p, (uint32_t)(p >> 32), keys);
   for (int s4 = 0; s4 < nfine; s4 += 4) {
-    const uint4 r = philox(make_uint4((uint32_t)(s4 >> 2), plo, phi, a.tag), keys);
+    const uint4 r = philox_path_call((uint32_t)(s4 >> 2), a.tag, pp, keys);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
