@@ -147,15 +147,31 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def _time_device(fn, steps, warmup, stream):
+def _time_device(fn, steps, warmup, stream, per_step=True):
+    """Device time of `steps` calls of fn after `warmup` untimed ones: (total ms
+    between events recorded on `stream` before the first and after the last
+    call, per-call ms).  per_step: an event pair around every call; otherwise
+    the calls run back to back, as a caller's loop would issue them, and each
+    is credited total / steps (the pairs cost the headline kernel ~2%: each
+    splits the stream, so a launch cannot be set up under its predecessor).
+    The device is idle when t0 is recorded, so the host's time to issue the
+    first call is counted once in the total."""
     import torch
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    if not per_step:
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        total = t0.elapsed_time(t1)
+        return total, [total / steps] * steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     t0.record(stream)
     for i in range(steps):
         starts[i].record(stream)
@@ -222,7 +238,9 @@ def cpu_baseline(budget_s: float = 12.0, chunk: int = 1 << 20):
 
 
 def sampler_sweep(P, tl, dev, stream):
-    """Bandwidth sweep of the PWL sampler, 2^16 .. 2^30 samples (FP32 out)."""
+    """Bandwidth sweep of the PWL sampler, 2^16 .. 2^30 samples (FP32 out),
+    each launch timed by its own event pair: below ~2^22 samples that is the
+    latency of one call (launch included), not the back-to-back rate."""
     import torch
     res = {}
     for lg in (16, 18, 20, 22, 24, 26, 28, 30):
@@ -990,7 +1008,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        total_ms, per = _time_device(step, args.steps, args.warmup, stream)
+        total_ms, per = _time_device(step, args.steps, args.warmup, stream, per_step=False)
     total_ms = _max_over_ranks(total_ms, dist, dev)
     ms = total_ms / args.steps
     value = _whole_job_gsamples(world, N_SAMPLES, args.steps, total_ms)
@@ -1037,12 +1055,12 @@ def main():
             "exact_lib_f32": lambda: P.sample(None, P.EXACT_LIB, out, seed=seed, stream=stream),
         }
         for name, fn in variants.items():
-            tot, _ = _time_device(fn, max(5, args.steps // 2), 3, stream)
+            tot, _ = _time_device(fn, max(5, args.steps // 2), 3, stream, per_step=False)
             extras[name + "_gsamples_per_s"] = N_SAMPLES * max(5, args.steps // 2) / (tot / 1e3) / 1e9
         # u -> x mode: caller uniforms in HBM (8 B/sample moved: 4 read + 4 written)
         uin = torch.rand(N_SAMPLES, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
         tot, per = _time_device(lambda: P.sample(tl, P.PWL, out, u=uin, stream=stream), max(5, args.steps // 2), 3,
-                                stream)
+                                stream, per_step=False)
         extras["pwl_input_f32_gsamples_per_s"] = N_SAMPLES / (statistics.mean(per) / 1e3) / 1e9
         extras["pwl_input_f32_hbm_frac"] = 8.0 * N_SAMPLES / (statistics.mean(per) / 1e3) / 1e9 / peak
         del uin
