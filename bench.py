@@ -748,8 +748,9 @@ def oracle_host(P, tl, dev, budget_s: float = 2.0):
     host cores; the GPU's aicdf_mlmc_level on 2^21 paths), and exact
     non-central chi^2 quantiles/s (the oracle's FP64 root finder in one
     thread; the GPU's aicdf_ncx2_ppf on 2^20), nu = 0.889, log lambda ~
-    U(-4, 4).  Each oracle leg runs a bounded number of paths or quantiles
-    (about budget_s seconds), stated in the result."""
+    U(-4, 4), and the fixed-work batched CIR sweep on the first sets, scaled
+    to all 4096.  Each oracle leg runs a bounded number of paths or quantiles
+    (about budget_s seconds, twice that for the sweep), stated in the result."""
     import os
     import numpy as np
     import torch
@@ -782,6 +783,30 @@ def oracle_host(P, tl, dev, budget_s: float = 2.0):
         gpu = m * steps / (statistics.mean(per) / 1e3)
         res[name] = {"host_fine_steps_per_s": host, "host_paths": n, "gpu_fine_steps_per_s": gpu,
                      "gpu_over_host": gpu / host}
+    # the fixed-work batched sweep (4096 CIR sets x levels 0..7 x two kinds) on
+    # the host: the oracle's path loops over the first sets' terms, about
+    # 2 budget_s of them, scaled to all sets by fine path-steps
+    from paper_2012_09715_gb300 import inputs
+    sw = inputs.sweep_sets(4096, seed=0)
+    n2, n4 = inputs.sweep_counts(sw["n_base"], levels=8)
+    lv = np.arange(8)
+    all_steps = int(((n2 + n4) << lv[None, :]).sum())
+    t0, done, s = time.perf_counter(), 0, 0
+    while s < 4096 and time.perf_counter() - t0 < 2 * budget_s:
+        osp = oracle.sde_params(model=oracle.MODEL_CIR, payoff=oracle.PAYOFF_X, X0=float(sw["X0"][s]), T=1.0, K=0.0,
+                                mu=0.0, sigma=float(sw["sigma"][s]), kappa=float(sw["kappa"][s]),
+                                theta=float(sw["theta"][s]), discount=1.0)
+        for l in range(8):
+            for kind, n in ((oracle.KIND_APPROX2, int(n2[s, l])), (oracle.KIND_CORR4, int(n4[s, l]))):
+                oracle.mlmc_level(osp, (a32, b32), l, kind, n, seed=0, tag=2 * (8 * s + l) + 1 + kind)
+                done += n << l
+        s += 1
+    dt = time.perf_counter() - t0
+    res["sweep_fixed_work"] = {"host_sets": s, "host_s": dt, "host_fine_steps_per_s": done / dt,
+                               "all_sets_fine_path_steps": all_steps,
+                               "host_ms_all_sets_scaled": all_steps / (done / dt) * 1e3,
+                               "note": f"oracle on the first {s} of 4096 sets ({done} fine path-steps), "
+                                       f"scaled to all sets by fine path-steps"}
     nu = 8.0 / 9.0
     rng = np.random.default_rng(3)
     u = oracle.uniforms(5, 0, 1 << 20).astype(np.float32)
