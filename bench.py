@@ -457,12 +457,17 @@ def cir_table(P, dev, stream, n_eval: int = 1 << 22):
     return res
 
 
-def _nested_vs_exact(run, eps, n0=1 << 12):
+def _nested_vs_exact(run, eps, n0=1 << 12, n0c=1 << 10):
     """E[P] to RMSE eps (a) with exact transitions only and (b) with the nested
     estimator E[P~] + E[P^ - P~] (Section 5.2), the paths of (b) split by the
     optimal allocation (Section 4.1) from pilot variances and timed pilot
     costs.  run(kind, n, offset, tag) -> (sums, gpu_ms) for kind in 'exact',
-    'approx', 'diff'.  Wall times include the pilots."""
+    'approx', 'diff'.  The correction's pilot is n0c paths (its optimal count
+    is a few hundred: variance 2^-14 or less of the approximate term's at ~40x
+    the cost per path), and it keeps at least (k - 1)(4 f)^2 paths, k its
+    pilot kurtosis and f its share of the estimator variance, so that its
+    variance estimate cannot move the RMSE by more than ~25% of that share.
+    Wall times include the pilots."""
     import math
     import time as _t
     res = {"eps": eps, "pilot_paths": n0}
@@ -476,19 +481,26 @@ def _nested_vs_exact(run, eps, n0=1 << 12):
                     "var": var, "ns_per_path": 1e6 * pms / n0}
     w0 = _t.perf_counter()
     pa, ta = run("approx", n0, 0, 2)
-    pc, tc = run("diff", n0, 0, 3)
+    pc, tc = run("diff", n0c, 0, 3)
     va = pa[1] / n0 - (pa[0] / n0) ** 2
-    vc = max(pc[1] / n0 - (pc[0] / n0) ** 2, 1e-300)
-    ca, cc = ta / n0, tc / n0
+    mc1 = pc[0] / n0c
+    vc = max(pc[1] / n0c - mc1 ** 2, 1e-300)
+    c4 = pc[3] / n0c - 4 * mc1 * pc[2] / n0c + 6 * mc1 ** 2 * pc[1] / n0c - 3 * mc1 ** 4
+    kurt = max(c4, 0.0) / vc ** 2
+    ca, cc = ta / n0, tc / n0c
     k = (math.sqrt(va * ca) + math.sqrt(vc * cc)) / eps ** 2
     na = max(n0, int(math.ceil(k * math.sqrt(va / ca))))
-    nc = max(n0, int(math.ceil(k * math.sqrt(vc / cc))))
+    nc = max(n0c, int(math.ceil(k * math.sqrt(vc / cc))))
+    share = (vc / nc) / (va / na + vc / nc)
+    nc = max(nc, int(math.ceil((kurt - 1.0) * (4.0 * share) ** 2)))
     a2, ma = run("approx", na - n0, n0, 2) if na > n0 else (pa * 0, 0.0)
-    c2, mc = run("diff", nc - n0, n0, 3) if nc > n0 else (pc * 0, 0.0)
+    c2, mc = run("diff", nc - n0c, n0c, 3) if nc > n0c else (pc * 0, 0.0)
     sa, sc = pa + a2, pc + c2
     est = sa[0] / na + sc[0] / nc
     rmse = math.sqrt(va / na + vc / nc)
+    res["correction_pilot_paths"] = n0c
     res["nested"] = {"estimate": est, "rmse_est": rmse, "paths_approx": na, "paths_correction": nc,
+                     "correction_pilot_kurtosis": kurt,
                      "gpu_ms": ta + tc + ma + mc, "wall_ms": 1e3 * (_t.perf_counter() - w0),
                      "log2_var_ratio": math.log2(vc / va), "cost_ratio_diff_over_approx": cc / ca}
     res["speedup_gpu"] = res["exact"]["gpu_ms"] / res["nested"]["gpu_ms"]
