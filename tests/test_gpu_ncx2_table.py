@@ -155,6 +155,33 @@ def test_cir_table_variance_drop(P):
         assert r[(3, level)] < r[(1, level)] - 5.0, r
 
 
+@pytest.mark.parametrize("deg", [1, 3])
+def test_cir_nested_estimator_is_unbiased(P, deg):
+    """Section 5.2's nested estimator E[X~_T] + E[X^_T - X~_T] on independent
+    streams targets E[X^_T] = theta + (X0 - theta) e^{-kappa T} = 1 for the
+    paper's set, whatever the table's error: within 4 standard errors of 1
+    at two seeds, with the table term alone off by its approximation bias only
+    (far below the table's own per-path error)."""
+    import torch
+    prm, q = _cir_params(P, "paper")
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t = P.Ncx2Table(2.0, 16, 16, deg)
+    na, nc, level = 1 << 21, 1 << 14, 3
+    for seed in (2, 5):
+        m, v = {}, {}
+        for kind, n, tag in ((P.CIR_TABLE, na, 2), (P.CIR_DIFF_TABLE, nc, 3)):
+            P.cir_level_table(prm, t, level, kind, n, sums, ws, st, seed=seed, tag=tag)
+            s = sums.cpu().numpy()
+            m[kind], v[kind] = s[0] / n, s[1] / n - (s[0] / n) ** 2
+        assert st.item() == 0
+        nested = m[P.CIR_TABLE] + m[P.CIR_DIFF_TABLE]
+        se = math.sqrt(v[P.CIR_TABLE] / na + v[P.CIR_DIFF_TABLE] / nc)
+        assert abs(nested - 1.0) <= 4 * se, (seed, nested, se)
+        assert abs(m[P.CIR_DIFF_TABLE]) <= 4 * math.sqrt(v[P.CIR_DIFF_TABLE] / nc) + 1e-3
+
+
 @pytest.mark.parametrize("kind", ["CIR_TABLE", "CIR_EXACT", "CIR_DIFF_TABLE"])
 def test_cir_small_terms_cover_each_path_once(P, kind):
     """Terms below 4 x 32 paths per SM run with fewer active lanes per warp
