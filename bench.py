@@ -1105,8 +1105,19 @@ def main():
         extras["pwl_over_exact_lib"] = value / world / extras["exact_lib_f32_gsamples_per_s"]
         # the small piecewise-constant configuration: 2^20 samples (launch-latency bound)
         small = torch.empty(1 << 20, dtype=torch.float32, device=dev)
-        tot, _ = _time_device(lambda: P.sample(tc, P.PWC, small, seed=seed, stream=stream), 50, 5, stream)
+        tot, _ = _time_device(lambda: P.sample(tc, P.PWC, small, seed=seed, stream=stream), 50, 5, stream,
+                              per_step=False)
         extras["pwc_2p20_gsamples_per_s"] = (1 << 20) * 50 / (tot / 1e3) / 1e9
+        # the same 50 calls captured once as a CUDA graph and replayed (no host
+        # launch cost per call: the device rate of the small configuration)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cs = torch.cuda.current_stream()
+            for _ in range(50):
+                P.sample(tc, P.PWC, small, seed=seed, stream=cs)
+        tot, _ = _time_device(g.replay, 5, 2, stream, per_step=False)
+        extras["pwc_2p20_graph_gsamples_per_s"] = (1 << 20) * 50 * 5 / (tot / 1e3) / 1e9
+        del g
         del out16, small
         del out
         for name, fn in (("mlmc", lambda: mlmc_time_to_rmse(P, tl, dev)),

@@ -95,6 +95,7 @@ aicdf_status launch_sample(const SampleArgs &a, int method, int out_dtype, int s
   KernelFn k = select_kernel(method, out_dtype, src, vec);
   const int E = vec ? (out_dtype == AICDF_F32 ? 4 : 8) : 1;
   int waves = 1;
+  uint64_t per_thread = 1;  // output units a thread takes per grid-stride step
   if (src == SRC_PHILOX && vec) {
     // 32-bit index variant when counters and element indices stay below 2^32
     // (a warp chunk spans at most 128 vectors)
@@ -103,13 +104,15 @@ aicdf_status launch_sample(const SampleArgs &a, int method, int out_dtype, int s
     if ((nvec + 128) * (uint64_t)E < lim && (a.offset >> 2) + (nvec + 128) * (uint64_t)(E / 4) < lim) {
       k = out_dtype == AICDF_F32 ? select_philox32<AICDF_F32>(method) : select_philox32<AICDF_F16>(method);
       waves = 4;  // several resident-block waves even out the end of the grid-stride loop
+      per_thread = out_dtype == AICDF_F32 ? 4 : 2;  // vectors of a lane's warp chunk
     }
   }
   const uint64_t units = (a.n + E - 1) / E;
   const int threads = 256;
-  // SMs x resident blocks of this kernel x waves (grid-stride inside)
+  // SMs x resident blocks of this kernel x waves (grid-stride inside); small
+  // launches get one chunk per warp, so no block starts with nothing to do
   const uint64_t cap = (uint64_t)sm_count() * resident_blocks((const void *)k, threads) * waves;
-  uint64_t blocks = (units + threads - 1) / threads;
+  uint64_t blocks = (units + threads * per_thread - 1) / (threads * per_thread);
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k<<<(unsigned)blocks, threads, 0, stream>>>(a);
