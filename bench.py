@@ -708,8 +708,9 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
         a16 = P.mlmc_run_sets(ss, tl, eps, wss, estimator=P.EST_ADAPTIVE, seed=9, L_max=L_max + 4, n_pilot=2000)
         feller = sorted(2 * sw["kappa"][i] * sw["theta"][i] / sw["sigma"][i] ** 2 for i in slow)
         res["slow_class"] = {"sets": len(slow), "feller_ratio_median": feller[len(feller) // 2],
-                             "feller_ratio_max": feller[-1], "L_max": L_max + 4,
-                             "nested": summary(n16), "regular": summary(r16), "adaptive": summary(a16)}
+                             "feller_ratio_min": feller[0], "feller_ratio_max": feller[-1], "L_max": L_max + 4,
+                             "nested": summary(n16), "regular": summary(r16), "adaptive": summary(a16),
+                             "exact_transition": _exact_transition_mc(P, dev, ss, eps)}
     res["plain_exact_fixed_L"] = Lp
     plain_all_ms = plain[0].gpu_ms * n_sets / n_plain
     res["plain_exact_gpu_ms_scaled"] = plain_all_ms
@@ -718,6 +719,59 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     res["speedup_vs_plain_exact_gpu"] = plain_all_ms / nested[0].gpu_ms
     res["speedup_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / nested[0].gpu_ms
     return res
+
+
+def _exact_transition_mc(P, dev, sets, eps):
+    """The call on X_T with X_T drawn in one step from its exact non-central
+    chi^2 law (Section 5: X_T = c C^{-1}_nu(U; X0 e^{-kappa T}/c), h = T), which
+    has no time bias, per set to RMSE eps: (a) plain Monte Carlo with the exact
+    draws; (b) the nested estimator of Section 5.2 with the approximation that
+    needs no table per nu, the Gaussian limit P~ = Phi^{-1}(U): E[X~_T] +
+    E[X^_T - X~_T], paths split by the optimal allocation from pilots
+    (_nested_vs_exact).  Device time of all launches; the payoff-X mean of the
+    exact draws is checked against theta + (X0 - theta) e^{-kappa T}."""
+    import math
+    import torch
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kinds = {"exact": P.CIR_EXACT, "approx": P.CIR_GAUSS, "diff": P.CIR_DIFF_GAUSS}
+    out = {"exact": {"gpu_ms": 0.0, "paths": 0}, "nested_gauss": {"gpu_ms": 0.0, "paths": 0, "conv": 0}}
+    worst_z, nus, ratios = 0.0, [], []
+    for k, prm in enumerate(sets):
+        nus.append(4 * prm.kappa * prm.theta / prm.sigma ** 2)
+
+        def run(kind, n, off, tag, payoff=P.PAYOFF_CALL):
+            q = P.sde_params(model=P.MODEL_CIR, payoff=payoff, X0=prm.X0, T=prm.T, K=prm.K, mu=0.0,
+                             sigma=prm.sigma, kappa=prm.kappa, theta=prm.theta, discount=1.0)
+            e0.record()
+            P.cir_level(q, None, 0, kinds[kind], n, sums, ws, st, path_offset=off, seed=31 + k, tag=tag)
+            e1.record()
+            torch.cuda.synchronize()
+            return sums.cpu().numpy().copy(), e0.elapsed_time(e1)
+
+        r = _nested_vs_exact(run, eps)
+        out["exact"]["gpu_ms"] += r["exact"]["gpu_ms"]
+        out["exact"]["paths"] += r["exact"]["paths"]
+        out["nested_gauss"]["gpu_ms"] += r["nested"]["gpu_ms"]
+        out["nested_gauss"]["paths"] += r["nested"]["paths_approx"] + r["nested"]["paths_correction"]
+        out["nested_gauss"]["conv"] += int(r["nested"]["rmse_est"] <= eps * 1.001)
+        ratios.append(r["nested"]["log2_var_ratio"])
+        n0 = 1 << 12
+        sx, _ = run("exact", n0, 0, 7, P.PAYOFF_X)
+        mx = sx[0] / n0
+        vx = max(sx[1] / n0 - mx * mx, 1e-300)
+        ex = prm.theta + (prm.X0 - prm.theta) * math.exp(-prm.kappa * prm.T)
+        worst_z = max(worst_z, abs(mx - ex) / math.sqrt(vx / n0))
+    ratios.sort()
+    out["exact"]["converged"] = len(sets)
+    out["nested_gauss"]["converged"] = out["nested_gauss"].pop("conv")
+    out["nested_gauss"]["median_log2_var_ratio"] = ratios[len(ratios) // 2]
+    out.update({"sets": len(sets), "nu_min": min(nus), "nu_max": max(nus),
+                "root_finder_status": int(st.item()), "payoff_x_check_max_abs_z": worst_z,
+                "note": "one exact non-central chi^2 step per path (no time bias)"})
+    return out
 
 
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
