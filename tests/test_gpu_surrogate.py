@@ -57,6 +57,37 @@ def test_ncx2_ppf_matches_oracle(P, orc):
             assert np.allclose(got[:3], -2 * np.log1p(-us[:3].astype(np.float64)), rtol=1e-10)
 
 
+@pytest.mark.parametrize("nu", [0.03, 0.1, 0.3])
+def test_ncx2_ppf_small_nu(P, orc, nu):
+    """Small nu (the slow-decay CIR sets): the law's spike at 0 holds a large
+    share of the mass at values below 1e-20; every quantile above that agrees
+    with the oracle to 1e-8 relative, and the deeper ones are 0 or agree (a
+    CIR step multiplies them by c ~ 1e-2: far below the resolution of X)."""
+    import torch
+    rng = np.random.default_rng(4)
+    us = np.concatenate([orc.uniforms(9, 0, 400), (10.0 ** -np.arange(2, 12)).astype(np.float32)]).astype(np.float32)
+    lam = np.exp(rng.uniform(-7.0, 4.6, us.size))
+    lam[:20] = 0.0
+    out = torch.zeros(us.size, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.ncx2_ppf(torch.from_numpy(us).cuda(), torch.from_numpy(lam).cuda(), nu, out, st)
+    got = out.cpu().numpy()
+    ref = np.array([orc.ncx2_ppf(float(u), nu, float(l)) for u, l in zip(us, lam)])
+    assert np.all(np.isfinite(got)) and np.all(got >= 0.0)
+    big = ref > 1e-20
+    assert big.sum() > us.size // 4
+    assert np.allclose(got[big], ref[big], rtol=1e-8, atol=0.0), np.max(np.abs(got[big] / ref[big] - 1))
+    assert np.all((got[~big] == 0.0) | (np.abs(got[~big] - ref[~big]) <= 1e-8 * ref[~big]) | (got[~big] <= 1e-20))
+    # monotone in u at fixed lambda wherever the quantile is above 1e-20
+    u_sorted = np.sort(np.concatenate([us[:50], us[-10:]]))
+    l_d = torch.full((u_sorted.size,), 0.5, dtype=torch.float64, device="cuda")
+    o2 = torch.zeros(u_sorted.size, dtype=torch.float64, device="cuda")
+    P.ncx2_ppf(torch.from_numpy(u_sorted).cuda(), l_d, nu, o2, st)
+    q = o2.cpu().numpy()
+    q = q[q > 1e-20]
+    assert np.all(np.diff(q) >= 0.0)
+
+
 def test_ncx2_targets_match_oracle(P, orc):
     import torch
     n = 4096
