@@ -636,7 +636,8 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     """C5 to a target RMSE: the 4096 CIR sets of the sweep (truncated
     Euler-Maruyama, X0 = theta) priced as calls with K = theta (a payoff with a
     time bias), every set to RMSE eps through aicdf_mlmc_run_sets (levels <= 12)
-    -- nested (PWL + exact correction) and regular MLMC over all sets; plain
+    -- nested (PWL + exact correction), adaptive, nested with the piecewise
+    cubic table, and regular MLMC over all sets; plain
     Monte Carlo with exact variates at the finest level nested MLMC needed, run
     on the first n_plain sets and scaled to all sets by the set count."""
     import torch
@@ -655,6 +656,11 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
     nested = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=1, L_max=L_max, n_pilot=2000)
     regular = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_REGULAR, seed=2, L_max=L_max, n_pilot=2000)
     adaptive = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_ADAPTIVE, seed=6, L_max=L_max, n_pilot=2000)
+    # the nested estimator with the piecewise cubic table: four-way variances
+    # ~2^-22 of the two-way ones instead of ~2^-11, at a dearer approximate step
+    tc3 = P.table_build(P.PWP, 15, 3)
+    P.mlmc_run_sets(sets[:64], tc3, 1e-3, ws, estimator=P.EST_NESTED, seed=99, L_max=12)  # calibration warm-up
+    nested_cubic = P.mlmc_run_sets(sets, tc3, eps, ws, estimator=P.EST_NESTED, seed=7, L_max=L_max, n_pilot=2000)
     Lp = max(r.L for r in nested[:n_plain])
     plain = P.mlmc_run_sets(sets[:n_plain], tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=Lp, seed=3)
     res["L_max"] = L_max
@@ -678,8 +684,11 @@ def sweep_time_to_rmse(P, dev, eps: float = 1e-4, n_sets: int = 4096, n_plain: i
                                               default=0.0)
         return out
 
-    for name, rr in (("nested", nested), ("regular", regular), ("adaptive", adaptive), ("plain_exact_subset", plain)):
+    for name, rr in (("nested", nested), ("regular", regular), ("adaptive", adaptive),
+                     ("nested_cubic", nested_cubic), ("plain_exact_subset", plain)):
         res[name] = summary(rr)
+    res["nested_cubic"]["step_cost_ratio_approx2_over_exact2"] = nested_cubic[0].cost_ns[5][0] / regular[0].cost_ns[5][0]
+    res["speedup_nested_cubic_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / nested_cubic[0].gpu_ms
     res["adaptive"]["exact_levels"] = sum(sum(r.exact_level[l] for l in range(r.L + 1)) for r in adaptive)
     res["adaptive"]["nested_levels"] = sum(sum(1 - r.exact_level[l] for l in range(r.L + 1)) for r in adaptive)
     res["speedup_adaptive_vs_regular_mlmc_gpu"] = regular[0].gpu_ms / adaptive[0].gpu_ms
