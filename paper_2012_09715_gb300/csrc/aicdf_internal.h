@@ -10,11 +10,13 @@
 
 struct aicdf_table_s {
   uint32_t magic;
-  int method;                 // AICDF_PWC or AICDF_PWL
-  int n;                      // PWC: number of intervals; PWL: K
-  int construction;           // PWC constant construction
-  std::vector<double> c0, c1; // FP64 coefficients (PWC: constants; PWL: alpha, beta)
-  std::vector<float> f0, f1;  // the same rounded to FP32 (what the kernels use)
+  int method;                 // AICDF_PWC, AICDF_PWL or AICDF_PWP
+  int n;                      // PWC: number of intervals; PWL, PWP: K
+  int construction;           // PWC constant construction; PWP: degree
+  std::vector<double> c0, c1; // FP64 coefficients (PWC: constants; PWL: alpha, beta;
+                              // PWP: [row][power] in each row's local variable s)
+  std::vector<float> f0, f1;  // the same rounded to FP32 (PWC, PWL: what the kernels use)
+  std::vector<float> fv;      // PWP: each row of f0 re-expanded in v (what the kernels use)
 };
 
 constexpr uint32_t AICDF_TABLE_MAGIC = 0x41494344u;  // "AICD"

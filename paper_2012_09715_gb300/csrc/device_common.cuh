@@ -147,12 +147,15 @@ __device__ __forceinline__ float pwl_eval_t(float t, const PwlRows &c) {
 __device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) { return pwl_eval_t(u - 0.5f, c); }
 
 // ---------------------------------------------------------------------------
-// Piecewise polynomial (degree <= 3) on the dyadic intervals, Horner's rule in
-// the local variable s: the fraction of v's significand on I_k = [2^-(k+1),
-// 2^-k) (exactly (v - a)/(b - a)), and v 2^K on the singular interval.  Lane L
+// Piecewise polynomial (degree <= 3) on the dyadic intervals.  The table's
+// rows are polynomials in the local variable s of each interval (the fraction
+// of v's significand on I_k = [2^-(k+1), 2^-k), s = 2^(k+1) v - 1; s = 2^K v on
+// the singular interval); the kernels receive each row re-expanded in v itself
+// (d_j, built on the host from the FP32 s-coefficients in FP64), so that one
+// Horner pass in v needs neither s nor a test for the singular row.  Lane L
 // holds the 4 coefficients of row min(30 - L, K), as for the linear table.
 struct PwpRows {
-  float c0, c1, c2, c3;
+  float c0, c1, c2, c3;  // d_0 .. d_3 of the lane's row
 };
 
 __device__ __forceinline__ PwpRows pwp_lane_rows(const float *tab, int K) {  // tab: [4 powers][16 rows]
@@ -161,33 +164,26 @@ __device__ __forceinline__ PwpRows pwp_lane_rows(const float *tab, int K) {  // 
 }
 
 // v in [0, 1/2]; lane = 30 - row; all 32 lanes must call.
-__device__ __forceinline__ float pwp_eval_v(float v, uint32_t lane, bool singular, float scale_k,
-                                            const PwpRows &c) {
+__device__ __forceinline__ float pwp_eval_v(float v, uint32_t lane, const PwpRows &c) {
   const float a0 = __shfl_sync(0xffffffffu, c.c0, lane);
   const float a1 = __shfl_sync(0xffffffffu, c.c1, lane);
   const float a2 = __shfl_sync(0xffffffffu, c.c2, lane);
   const float a3 = __shfl_sync(0xffffffffu, c.c3, lane);
-  const float frac = __uint_as_float((__float_as_uint(v) & 0x7FFFFFu) | 0x3F800000u) - 1.0f;
-  const float s = singular ? v * scale_k : frac;
-  return fmaf(fmaf(fmaf(a3, s, a2), s, a1), s, a0);
+  return fmaf(fmaf(fmaf(a3, v, a2), v, a1), v, a0);
 }
 
-// Grid uniforms: lane = biased exponent e of v (mod 32), singular when e <= 126 - K.
-__device__ __forceinline__ float pwp_eval_t(float t, const PwpRows &c, uint32_t e_sing, float scale_k) {
+// Grid uniforms: lane = biased exponent e of v (mod 32).
+__device__ __forceinline__ float pwp_eval_t(float t, const PwpRows &c) {
   const float v = 0.5f - fabsf(t);
-  const uint32_t e = __float_as_uint(v) >> 23;
-  const float z = pwp_eval_v(v, e, e <= e_sing, scale_k, c);
+  const float z = pwp_eval_v(v, __float_as_uint(v) >> 23, c);
   return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
 }
-__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c, uint32_t e_sing, float scale_k) {
-  return pwp_eval_t(u - 0.5f, c, e_sing, scale_k);
-}
+__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c) { return pwp_eval_t(u - 0.5f, c); }
 
 // The same for a word x: equals pwp_eval_grid(u01(x), ...).
-__device__ __forceinline__ float pwp_eval_word(uint32_t x, const PwpRows &c, uint32_t e_sing, float scale_k) {
+__device__ __forceinline__ float pwp_eval_word(uint32_t x, const PwpRows &c) {
   const float v = v01(x);
-  const uint32_t e = __float_as_uint(v) >> 23;
-  const float z = pwp_eval_v(v, e, e <= e_sing, scale_k, c);
+  const float z = pwp_eval_v(v, __float_as_uint(v) >> 23, c);
   return __uint_as_float(__float_as_uint(z) ^ (x & 0x80000000u));
 }
 
@@ -195,12 +191,12 @@ __device__ __forceinline__ float pwp_eval_word(uint32_t x, const PwpRows &c, uin
 // taken in unsigned arithmetic as in pwl_eval: a set sign bit (u = -0, or the
 // NaN / out-of-range inputs whose result the caller discards) wraps 126 - e
 // past K, so -0 lands on the singular row like +0.
-__device__ __forceinline__ float pwp_eval(float u, const PwpRows &c, uint32_t K, float scale_k) {
+__device__ __forceinline__ float pwp_eval(float u, const PwpRows &c, uint32_t K) {
   const bool lower = u < 0.5f;
   const float v = lower ? u : 1.0f - u;
   const uint32_t e = __float_as_uint(v) >> 23;
   const uint32_t row = min(126u - e, K);
-  const float z = pwp_eval_v(v, 30u - row, row == K, scale_k, c);
+  const float z = pwp_eval_v(v, 30u - row, c);
   return lower ? z : -z;
 }
 

@@ -155,7 +155,7 @@ aicdf_status pack_table(aicdf_table approx, float *tab, int *ntab) {
   } else if (approx->method == AICDF_PWP) {
     if (approx->n > 15) return AICDF_ERR_UNSUPPORTED;
     for (int j = 0; j < 4; ++j)
-      for (int r = 0; r < 16; ++r) tab[16 * j + r] = approx->f0[4 * std::min(r, approx->n) + j];
+      for (int r = 0; r < 16; ++r) tab[16 * j + r] = approx->fv[4 * std::min(r, approx->n) + j];
   } else {
     if (approx->n > 1024) return AICDF_ERR_UNSUPPORTED;
     for (int i = 0; i < approx->n; ++i) tab[i] = approx->f0[i];

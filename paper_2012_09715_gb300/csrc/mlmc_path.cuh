@@ -54,14 +54,8 @@ struct ApproxTable<AICDF_PWL> {
 template <>
 struct ApproxTable<AICDF_PWP> {
   PwpRows rows;
-  uint32_t e_sing;
-  float scale_k;
-  __device__ ApproxTable(const float *tab, int ntab, float *) {
-    rows = pwp_lane_rows(tab, ntab);
-    e_sing = 126u - (uint32_t)ntab;
-    scale_k = __int_as_float((127 + ntab) << 23);  // 2^K
-  }
-  __device__ __forceinline__ float operator()(uint32_t x) const { return pwp_eval_word(x, rows, e_sing, scale_k); }
+  __device__ ApproxTable(const float *tab, int ntab, float *) { rows = pwp_lane_rows(tab, ntab); }
+  __device__ __forceinline__ float operator()(uint32_t x) const { return pwp_eval_word(x, rows); }
 };
 
 template <>

@@ -51,9 +51,8 @@ aicdf_status prepare_sample_args(aicdf_table table, int method, SampleArgs *a) {
     if (method == AICDF_PWP) {
       if (table->n > 15) return AICDF_ERR_UNSUPPORTED;
       for (int j = 0; j < 4; ++j)
-        for (int r = 0; r < 16; ++r) a->tab[16 * j + r] = table->f0[4 * std::min(r, table->n) + j];
+        for (int r = 0; r < 16; ++r) a->tab[16 * j + r] = table->fv[4 * std::min(r, table->n) + j];
       a->ntab = table->n;
-      a->nf = std::ldexp(1.0f, table->n);  // 2^K: scale of the singular interval
     } else if (method == AICDF_PWC) {
       if (table->n > 1024) return AICDF_ERR_UNSUPPORTED;
       for (int i = 0; i < table->n; ++i) a->tab[i] = table->f0[i];

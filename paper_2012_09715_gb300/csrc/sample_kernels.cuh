@@ -85,19 +85,15 @@ template <int SRC>
 struct Approx<AICDF_PWP, SRC> {
   PwpRows rows;
   uint32_t K;
-  uint32_t e_sing;
-  float scale_k;
   __device__ Approx(const SampleArgs &a, float *) {
     rows = pwp_lane_rows(a.tab, a.ntab);
     K = (uint32_t)a.ntab;
-    e_sing = 126u - (uint32_t)a.ntab;
-    scale_k = a.nf;  // 2^K
   }
-  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_word(x, rows, e_sing, scale_k); }
-  __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K, scale_k); }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_word(x, rows); }
+  __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const {
-    return pwp_eval_t(tbits<B>(m), rows, e_sing, scale_k);
+    return pwp_eval_t(tbits<B>(m), rows);
   }
 };
 

@@ -152,6 +152,33 @@ static aicdf_status build_pwp(aicdf_table_s *t, int K, int deg) {
   return AICDF_OK;
 }
 
+// The kernels' form of a polynomial table: row k's polynomial p(s) = sum_i
+// c_i s^i, with c_i its FP32 coefficients, rewritten in v = min(u, 1 - u):
+// s = alpha v + beta (alpha = 2^(k+1), beta = -1 on I_k = [2^-(k+1), 2^-k);
+// alpha = 2^K, beta = 0 on the singular row K), so
+// d_j = alpha^j sum_{i >= j} C(i, j) beta^(i - j) c_i, in FP64, rounded once
+// to FP32.  The polynomial is the same up to that rounding; its terms d_j v^j
+// stay within a small factor of the row's values because alpha v lies in
+// [1, 2) on a regular interval.
+static void pwp_rows_in_v(aicdf_table_s *t) {
+  static const double binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+  const int K = t->n;
+  t->fv.assign(t->f0.size(), 0.0f);
+  for (int r = 0; r <= K; ++r) {
+    const double alpha = std::ldexp(1.0, r == K ? K : r + 1), beta = r == K ? 0.0 : -1.0;
+    double ap = 1.0;  // alpha^j
+    for (int j = 0; j < 4; ++j) {
+      double d = 0.0, bp = 1.0;  // beta^(i - j)
+      for (int i = j; i < 4; ++i) {
+        d += binom[i][j] * bp * (double)t->f0[4 * r + i];
+        bp *= beta;
+      }
+      t->fv[4 * r + j] = (float)(ap * d);
+      ap *= alpha;
+    }
+  }
+}
+
 extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, aicdf_table *out) {
   if (!out) return AICDF_ERR_ARG;
   *out = nullptr;
@@ -180,6 +207,7 @@ extern "C" aicdf_status aicdf_table_build(int method, int n, int construction, a
   }
   t->f0.assign(t->c0.begin(), t->c0.end());
   t->f1.assign(t->c1.begin(), t->c1.end());
+  if (method == AICDF_PWP) pwp_rows_in_v(t);
   *out = t;
   return AICDF_OK;
 }

@@ -13,6 +13,8 @@ Section 3.2 and Algorithm 1 at every interval edge the grid can reach:
   and equal to the FP16 rounding of the oracle's FP32-rounded value wherever
   the two FP32 results agree.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -93,16 +95,29 @@ def test_pwp_every_grid_point(P, orc, grid, deg):
     c32 = t.coefficients()[0].astype(np.float32)
     ref = orc.sample_pwp(c32, grid)
     z = _run(P, t, P.PWP, grid, torch.float32)
-    # Horner's rule in FP32 rounds each of its FMAs once: at most ~3 * 2^-24 of
-    # the row's sum |c_j| on top of the 2-ulp band (see test_gpu_pwp.py)
-    rows = np.abs(c32.reshape(-1, 4).astype(np.float64)).sum(axis=1)
+    # the kernels evaluate each row re-expanded in v, d_j = alpha^j sum_{i>=j}
+    # C(i, j) beta^(i-j) c_j (s = alpha v + beta), by Horner's rule in FP32:
+    # the rounding of the d_j and of each FMA is at most ~3 * 2^-24 of
+    # sum_j |d_j| v^j, on top of the 2-ulp band (see test_gpu_pwp.py)
+    c = c32.reshape(-1, 4).astype(np.float64)
+    K = c.shape[0] - 1
+    d = np.zeros_like(c)
+    for r in range(K + 1):
+        alpha, beta = (2.0 ** K, 0.0) if r == K else (2.0 ** (r + 1), -1.0)
+        for j in range(4):
+            d[r, j] = alpha ** j * sum(math.comb(i, j) * beta ** (i - j) * c[r, i] for i in range(j, 4))
     v = np.minimum(grid, 1 - grid).astype(np.float64)
-    k = np.minimum(np.floor(-np.log2(v)).astype(int), 15)
-    bound = 2 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) + 4 * 2.0 ** -24 * rows[k]
+    k = np.minimum(np.floor(-np.log2(v)).astype(int), K)
+    dk = np.abs(d)[k]
+    dv = dk[:, 0] + v * (dk[:, 1] + v * (dk[:, 2] + v * dk[:, 3]))
+    bound = (2 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+             + 4 * 2.0 ** -24 * (np.abs(c).sum(axis=1)[k] + dv))
     err = np.abs(z.astype(np.float64) - ref)
     assert np.all(err <= bound), (deg, int((err > bound).sum()))
     same = float(np.mean(z == ref.astype(np.float32)))
     print(f"piecewise polynomial degree {deg}: {same:.4f} of the grid bit-equal to the oracle")
-    assert same > 0.5, same
+    # the oracle evaluates the s form in FP64, the kernels the v form in FP32:
+    # about a third of the grid rounds to the same FP32 value
+    assert same > 0.25, same
     z16 = _run(P, t, P.PWP, grid, torch.float16)
     assert np.array_equal(z16, z.astype(np.float16))
