@@ -103,9 +103,12 @@ typedef enum { AICDF_F32 = 0, AICDF_F16 = 1 } aicdf_dtype;
  *                      the FP32 exponent bits, one FMA, restore the sign
  *                      (u = 1/2 gives -0, as the piecewise linear C
  *                      listing of Section 3.3 does)
- *   method AICDF_PWP : the piecewise polynomial of the table's interval
- *                      (Horner's rule in the local variable s), sign restored
- *                      as for PWL
+ *   method AICDF_PWP : the piecewise polynomial of the table's interval,
+ *                      evaluated by Horner's rule in v = min(u, 1 - u) on the
+ *                      row re-expanded in v (FP64, rounded once to FP32;
+ *                      the same polynomial up to that rounding: within
+ *                      ~3 2^-24 sum_j |d_j| v^j of the s form), sign
+ *                      restored as for PWL
  *   method AICDF_EXACT     : the library's FP32 Phi^{-1} (max rel. error < 1e-6)
  *   method AICDF_EXACT_LIB : CUDA's normcdfinvf, for comparison
  * Uniforms: if u_dev != NULL, u_i = u_dev[i] (FP32, any value; u outside
