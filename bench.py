@@ -954,9 +954,10 @@ def run_reference(args):
 
 def profile_mlmc_kinds(model: str = "gbm"):
     """One level launch per estimator kind (Euler-Maruyama, level 6, 2^20
-    paths): APPROX2, EXACT2, CORR4 in that order.  GBM: the call of the GBM
-    configuration.  CIR: a set from the middle of the batched sweep's ranges
-    (kappa 1, theta 0.05, sigma 0.3, X0 = K = theta), truncated scheme."""
+    paths): APPROX2, EXACT2, CORR4 in that order, then APPROX2 and CORR4 with
+    the piecewise cubic table.  GBM: the call of the GBM configuration.  CIR: a
+    set from the middle of the batched sweep's ranges (kappa 1, theta 0.05,
+    sigma 0.3, X0 = K = theta), truncated scheme."""
     import torch
     import paper_2012_09715_gb300 as P
     from paper_2012_09715_gb300 import build as B
@@ -971,6 +972,9 @@ def profile_mlmc_kinds(model: str = "gbm"):
                            kappa=1.0, theta=0.05, discount=1.0)
     for kind in (P.KIND_APPROX2, P.KIND_EXACT2, P.KIND_CORR4):
         P.mlmc_level(prm, tl, 6, kind, 1 << 20, sums, ws, seed=1, tag=3)
+    tc = P.table_build(P.PWP, 15, 3)
+    for kind in (P.KIND_APPROX2, P.KIND_CORR4):
+        P.mlmc_level(prm, tc, 6, kind, 1 << 20, sums, ws, seed=1, tag=3)
     torch.cuda.synchronize()
     print(sums.cpu().numpy())
 
