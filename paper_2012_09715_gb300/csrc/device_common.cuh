@@ -152,51 +152,39 @@ __device__ __forceinline__ float pwl_eval_grid(float u, const PwlRows &c) { retu
 // of v's significand on I_k = [2^-(k+1), 2^-k), s = 2^(k+1) v - 1; s = 2^K v on
 // the singular interval); the kernels receive each row re-expanded in v itself
 // (d_j, built on the host from the FP32 s-coefficients in FP64), so that one
-// Horner pass in v needs neither s nor a test for the singular row.  Lane L
-// holds the 4 coefficients of row min(30 - L, K), as for the linear table.
-struct PwpRows {
-  float c0, c1, c2, c3;  // d_0 .. d_3 of the lane's row
-};
-
-__device__ __forceinline__ PwpRows pwp_lane_rows(const float *tab, int K) {  // tab: [4 powers][16 rows]
-  const int r = min(max(30 - (int)(threadIdx.x & 31), 0), K);
-  return PwpRows{tab[r], tab[16 + r], tab[32 + r], tab[48 + r]};
+// Horner pass in v needs neither s nor a test for the singular row.  The rows
+// are staged in shared memory for one 16-byte load per variate (four
+// coefficients; four shuffles of lane-held rows cost more): entry i < 512
+// holds row min(126 - i, K) (unsigned, so every i > 126 -- v >= 1, a set sign
+// bit, NaN -- takes the singular row K, and -0 lands there like +0), indexed
+// by the top 9 bits of v (its sign and biased exponent).  tab: [4 powers][16
+// rows].  All threads of the block must call the stager.
+constexpr int kPwpStagedRows = 512;
+__device__ __forceinline__ void pwp_stage_rows(const float *tab, int K, float4 *rows) {
+  for (int i = threadIdx.x; i < kPwpStagedRows; i += blockDim.x) {
+    const int r = (int)min(126u - (uint32_t)i, (uint32_t)K);
+    rows[i] = make_float4(tab[r], tab[16 + r], tab[32 + r], tab[48 + r]);
+  }
+  __syncthreads();
 }
-
-// v in [0, 1/2]; lane = 30 - row; all 32 lanes must call.
-__device__ __forceinline__ float pwp_eval_v(float v, uint32_t lane, const PwpRows &c) {
-  const float a0 = __shfl_sync(0xffffffffu, c.c0, lane);
-  const float a1 = __shfl_sync(0xffffffffu, c.c1, lane);
-  const float a2 = __shfl_sync(0xffffffffu, c.c2, lane);
-  const float a3 = __shfl_sync(0xffffffffu, c.c3, lane);
-  return fmaf(fmaf(fmaf(a3, v, a2), v, a1), v, a0);
+__device__ __forceinline__ float pwp_horner(float v, const float4 *rows) {
+  const float4 d = rows[__float_as_uint(v) >> 23];
+  return fmaf(fmaf(fmaf(d.w, v, d.z), v, d.y), v, d.x);
 }
-
-// Grid uniforms: lane = biased exponent e of v (mod 32).
-__device__ __forceinline__ float pwp_eval_t(float t, const PwpRows &c) {
-  const float v = 0.5f - fabsf(t);
-  const float z = pwp_eval_v(v, __float_as_uint(v) >> 23, c);
-  return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
-}
-__device__ __forceinline__ float pwp_eval_grid(float u, const PwpRows &c) { return pwp_eval_t(u - 0.5f, c); }
-
-// The same for a word x: equals pwp_eval_grid(u01(x), ...).
-__device__ __forceinline__ float pwp_eval_word(uint32_t x, const PwpRows &c) {
-  const float v = v01(x);
-  const float z = pwp_eval_v(v, __float_as_uint(v) >> 23, c);
+// The library's uniform of word x (v and the sign straight from the bits).
+__device__ __forceinline__ float pwp_staged_word(uint32_t x, const float4 *rows) {
+  const float z = pwp_horner(v01(x), rows);
   return __uint_as_float(__float_as_uint(z) ^ (x & 0x80000000u));
 }
-
-// Any FP32 u (caller uniforms): reflection by 1 - u, capped row.  The row is
-// taken in unsigned arithmetic as in pwl_eval: a set sign bit (u = -0, or the
-// NaN / out-of-range inputs whose result the caller discards) wraps 126 - e
-// past K, so -0 lands on the singular row like +0.
-__device__ __forceinline__ float pwp_eval(float u, const PwpRows &c, uint32_t K) {
+// Grid uniforms, t = u - 1/2 (exact).
+__device__ __forceinline__ float pwp_staged_t(float t, const float4 *rows) {
+  const float z = pwp_horner(0.5f - fabsf(t), rows);
+  return __uint_as_float(__float_as_uint(z) ^ (~__float_as_uint(t) & 0x80000000u));
+}
+// Any FP32 u (caller uniforms): reflection by 1 - u.
+__device__ __forceinline__ float pwp_staged(float u, const float4 *rows) {
   const bool lower = u < 0.5f;
-  const float v = lower ? u : 1.0f - u;
-  const uint32_t e = __float_as_uint(v) >> 23;
-  const uint32_t row = min(126u - e, K);
-  const float z = pwp_eval_v(v, 30u - row, c);
+  const float z = pwp_horner(lower ? u : 1.0f - u, rows);
   return lower ? z : -z;
 }
 

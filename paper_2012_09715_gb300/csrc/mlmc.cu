@@ -48,7 +48,7 @@ constexpr int kMaxLevelBlocks = 4096;
 template <bool NE, bool NA, int AP, int MODEL>
 __global__ void __launch_bounds__(kLevelThreads)
     k_mlmc_level(const __grid_constant__ LevelArgs a, Moments *__restrict__ partials) {
-  __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
+  __shared__ __align__(16) float s_tab[AP == AICDF_PWC ? 1024 : AP == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   __shared__ Moments s_red[kLevelThreads / 32];
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);
   const PathConsts pc = make_path_consts(a.ps);
@@ -228,7 +228,7 @@ struct BatchArgs {
 
 template <int AP, bool V16>
 __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ BatchArgs a) {
-  __shared__ float s_tab[AP == AICDF_PWC ? 1024 : 1];
+  __shared__ __align__(16) float s_tab[AP == AICDF_PWC ? 1024 : AP == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   __shared__ Moments s_red[256 / 32];
   __shared__ int s_item;
   const ApproxTable<AP> ap(a.tab, a.ntab, s_tab);

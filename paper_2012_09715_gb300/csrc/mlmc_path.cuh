@@ -53,9 +53,13 @@ struct ApproxTable<AICDF_PWL> {
 
 template <>
 struct ApproxTable<AICDF_PWP> {
-  PwpRows rows;
-  __device__ ApproxTable(const float *tab, int ntab, float *) { rows = pwp_lane_rows(tab, ntab); }
-  __device__ __forceinline__ float operator()(uint32_t x) const { return pwp_eval_word(x, rows); }
+  const float4 *rows;  // kPwpStagedRows rows in shared memory
+  __device__ ApproxTable(const float *tab, int ntab, float *smem) {
+    float4 *r = reinterpret_cast<float4 *>(smem);
+    pwp_stage_rows(tab, ntab, r);
+    rows = r;
+  }
+  __device__ __forceinline__ float operator()(uint32_t x) const { return pwp_staged_word(x, rows); }
 };
 
 template <>

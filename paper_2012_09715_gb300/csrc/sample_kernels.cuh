@@ -83,17 +83,17 @@ struct Approx<AICDF_PWL, SRC> {
 
 template <int SRC>
 struct Approx<AICDF_PWP, SRC> {
-  PwpRows rows;
-  uint32_t K;
-  __device__ Approx(const SampleArgs &a, float *) {
-    rows = pwp_lane_rows(a.tab, a.ntab);
-    K = (uint32_t)a.ntab;
+  const float4 *rows;  // kPwpStagedRows rows in shared memory
+  __device__ Approx(const SampleArgs &a, float *smem) {
+    float4 *r = reinterpret_cast<float4 *>(smem);
+    pwp_stage_rows(a.tab, a.ntab, r);
+    rows = r;
   }
-  __device__ __forceinline__ float word(uint32_t x) const { return pwp_eval_word(x, rows); }
-  __device__ __forceinline__ float operator()(float u) const { return pwp_eval(u, rows, K); }
+  __device__ __forceinline__ float word(uint32_t x) const { return pwp_staged_word(x, rows); }
+  __device__ __forceinline__ float operator()(float u) const { return pwp_staged(u, rows); }
   template <int B>
   __device__ __forceinline__ float cell(uint32_t m) const {
-    return pwp_eval_t(tbits<B>(m), rows);
+    return pwp_staged_t(tbits<B>(m), rows);
   }
 };
 
@@ -155,7 +155,7 @@ __device__ __forceinline__ void store_one(__half *out, uint64_t e, float z) {
 // SRC_INPUT: u 16-byte aligned.
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
+  __shared__ __align__(16) float smem[METHOD == AICDF_PWC ? 2048 : METHOD == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) k_sample_vec(const __grid_constant__ Samp
 // multiply and logic pipes, and those products were ~6% of its multiply work.
 template <int METHOD, int OUT>
 __global__ void __launch_bounds__(256, 3) k_sample_philox32(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
+  __shared__ __align__(16) float smem[METHOD == AICDF_PWC ? 2048 : METHOD == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -347,7 +347,7 @@ __device__ __forceinline__ void call_samples(const Approx<METHOD, SRC_PHILOX> &f
 // q x 32 + L (q < NC) interleaved, and each q writes one contiguous span.
 template <int METHOD, int OUT, int B>
 __global__ void __launch_bounds__(256) k_sample_bits(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
+  __shared__ __align__(16) float smem[METHOD == AICDF_PWC ? 2048 : METHOD == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256) k_sample_bits(const __grid_constant__ Sam
 // its call; only for ragged or unaligned requests).
 template <int METHOD, int OUT, int B>
 __global__ void __launch_bounds__(256) k_sample_bits_scalar(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
+  __shared__ __align__(16) float smem[METHOD == AICDF_PWC ? 2048 : METHOD == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   const Approx<METHOD, SRC_PHILOX> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_sample_bits_scalar(const __grid_constan
 // Scalar kernel for unaligned pointers or an offset not divisible by 4.
 template <int METHOD, int OUT, int SRC>
 __global__ void __launch_bounds__(256) k_sample_scalar(const __grid_constant__ SampleArgs a) {
-  __shared__ float smem[METHOD == AICDF_PWC ? 2048 : 1];
+  __shared__ __align__(16) float smem[METHOD == AICDF_PWC ? 2048 : METHOD == AICDF_PWP ? 4 * kPwpStagedRows : 1];
   const Approx<METHOD, SRC> f(a, smem);
   using T = typename std::conditional<OUT == AICDF_F32, float, __half>::type;
   T *out = reinterpret_cast<T *>(a.out);
