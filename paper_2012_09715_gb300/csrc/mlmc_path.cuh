@@ -236,9 +236,10 @@ __device__ __forceinline__ float path_result(const PathSpec &a, bool coarse, flo
 // Philox4x32-10 calls (j, plo, phi, tag) of one path.  The first Philox round
 // multiplies the path-constant word phi and the call index j; the second
 // multiplies the first's x (a path constant) and z (which depends on j and the
-// tag only, the same on every lane of a warp).  So the path-constant halves of both rounds are taken
-// once per path here, and a call redoes only the j-dependent products
-// (warp-uniform) and the remaining eight rounds.  Same words as philox().
+// tag only, the same on every lane of a warp).  So the path-constant halves
+// of both rounds are taken once per path here, and a call redoes only the
+// j-dependent products (warp-uniform) and the remaining eight rounds.  Same
+// words as philox().
 struct PhiloxPath {
   uint32_t y1;      // first round: lo(M1 phi)
   uint32_t hx, lx;  // second round: hi / lo (M0 x1), x1 = hi(M1 phi) ^ plo ^ k0[0]
