@@ -2,6 +2,8 @@
 estimators reach the target RMSE around the Black-Scholes price."""
 import math
 
+import numpy as np
+
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -78,17 +80,20 @@ def test_driver_sets_single_set_equals_run(P):
         assert [list(q.paths[l]) for l in range(r.L + 1)] == [list(r.paths[l]) for l in range(r.L + 1)]
 
 
-def test_driver_sets_many_cir_sets(P):
+@pytest.mark.parametrize("table", ["PWL", "PWP3"])
+def test_driver_sets_many_cir_sets(P, table):
     """64 CIR sets (truncated Euler-Maruyama, X0 = theta): E[X_T] = theta at every
     level, so each set's estimate is within 4 of its own standard deviations of
-    theta; every set converges, and sets of one run use their own streams."""
+    theta; every set converges, and sets of one run use their own streams.  The
+    same with the piecewise cubic table (whose rows the kernels read in v), where
+    the four-way terms' variance is ~2^-20 of the two-way terms'."""
     import torch
     from paper_2012_09715_gb300 import inputs
     sw = inputs.sweep_sets(64, seed=3)
     sets = [P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=float(sw["X0"][i]), T=1.0, K=0.0, mu=0.0,
                          sigma=float(sw["sigma"][i]), kappa=float(sw["kappa"][i]), theta=float(sw["theta"][i]),
                          discount=1.0) for i in range(64)]
-    tl = P.table_build(P.PWL, 15)
+    tl = P.table_build(P.PWL, 15) if table == "PWL" else P.table_build(P.PWP, 15, 3)
     ws = torch.empty(P.mlmc_run_sets_workspace_bytes(len(sets)), dtype=torch.uint8, device="cuda")
     eps = 1e-3
     res = P.mlmc_run_sets(sets, tl, eps, ws, estimator=P.EST_NESTED, seed=7)
@@ -101,6 +106,9 @@ def test_driver_sets_many_cir_sets(P):
         ests.append(r.estimate - prm.theta)
     assert len(set(ests)) == len(ests)  # no two sets share a stream
     assert res[0].launches == res[-1].launches >= 2
+    if table == "PWP3":
+        ratios = [r.var[l][1] / r.var[l][0] for r in res for l in range(1, r.L + 1) if r.var[l][0] > 0]
+        assert np.median(ratios) < 2.0 ** -15, np.median(ratios)
 
 
 def test_adaptive_keeps_the_pair_where_it_pays(P):
