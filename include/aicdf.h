@@ -158,7 +158,12 @@ aicdf_status aicdf_sample_bits(aicdf_table table, int method, int bits, uint64_t
 /* ===================================================================== */
 typedef enum { AICDF_MODEL_GBM = 0, AICDF_MODEL_CIR = 1 } aicdf_model;
 typedef enum { AICDF_SCHEME_EM = 0, AICDF_SCHEME_MILSTEIN = 1 } aicdf_scheme;
-typedef enum { AICDF_PAYOFF_X = 0, AICDF_PAYOFF_CALL = 1 } aicdf_payoff;
+/* Payoffs P of a path: X_T; discount (X_T - K)^+; ASIAN: discount times the
+ * arithmetic average of the path's 2^level post-step values X_1 .. X_N, the
+ * path-dependent functional of Section 5.2 (accepted by the CIR per-step
+ * calls aicdf_cir_level and aicdf_cir_level_table only; the level kernels
+ * return AICDF_ERR_ARG for it). */
+typedef enum { AICDF_PAYOFF_X = 0, AICDF_PAYOFF_CALL = 1, AICDF_PAYOFF_ASIAN = 2 } aicdf_payoff;
 /* Level estimator kinds.  With P^ (exact variates) and P~ (approximate
  * variates from the same uniforms), fine level l and coarse level l-1
  * (P_{-1} := 0):

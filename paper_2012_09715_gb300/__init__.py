@@ -24,7 +24,7 @@ Z_E, Z_C, Z_I, Z_V = 0, 1, 2, 3
 F32, F16 = 0, 1
 MODEL_GBM, MODEL_CIR = 0, 1
 SCHEME_EM, SCHEME_MILSTEIN = 0, 1
-PAYOFF_X, PAYOFF_CALL = 0, 1
+PAYOFF_X, PAYOFF_CALL, PAYOFF_ASIAN = 0, 1, 2
 KIND_APPROX2, KIND_CORR4, KIND_EXACT2, KIND_PLAIN, KIND_PLAIN_APPROX = range(5)
 SUMS = 5  # AICDF_SUMS_PER_TERM: (sum Y, sum Y^2, sum Y^3, sum Y^4, n) per term
 

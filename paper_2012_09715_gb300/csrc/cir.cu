@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(kCirThreads)
     const uint64_t i = base + lane;
     const bool active = (uint64_t)lane < L && i < a.n_paths;
     const uint64_t p = a.path_offset + i;
-    double xe = a.X0;
-    float xa = a.X0;
+    double xe = a.X0, se = 0.0;  // the path and (ASIAN) the sum of its post-step values
+    float xa = a.X0, sa = 0.f;
     const PhiloxPath pp = philox_path((uint32_t)p, (uint32_t)(p >> 32), a.keys);
     for (int s4 = 0; s4 < nsteps && (active || APPROX == 1); s4 += 4) {
       const uint4 r = philox_path_call((uint32_t)(s4 >> 2), a.tag, pp, a.keys);
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kCirThreads)
           if (EXACT) {
             const double lam = xe * a.e / a.c;
             xe = a.c * ncx2_ppf((double)u, a.nu, lam, &st);
+            se += xe;
           }
           if (APPROX != 0) {
             const float lam = fmaxf(xa, 0.f) * ratio;
@@ -99,14 +100,19 @@ __global__ void __launch_bounds__(kCirThreads)
             }
             const float h = lam + nuf;
             xa = cf * fmaxf(fmaf(2.0f * sqrtf(h), pt, h), 0.f);
+            sa += xa;
           }
         }
       }
     }
     float y;
-    const float pe = a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf((float)xe - a.K, 0.f)
-                                                   : a.discount * (float)xe;
-    const float pa = a.payoff == AICDF_PAYOFF_CALL ? a.discount * fmaxf(xa - a.K, 0.f) : a.discount * xa;
+    const float inv_n = 1.0f / (float)nsteps;  // exact: nsteps is a power of two
+    const float pe = a.payoff == AICDF_PAYOFF_CALL    ? a.discount * fmaxf((float)xe - a.K, 0.f)
+                     : a.payoff == AICDF_PAYOFF_ASIAN ? a.discount * ((float)se * inv_n)
+                                                      : a.discount * (float)xe;
+    const float pa = a.payoff == AICDF_PAYOFF_CALL    ? a.discount * fmaxf(xa - a.K, 0.f)
+                     : a.payoff == AICDF_PAYOFF_ASIAN ? a.discount * (sa * inv_n)
+                                                      : a.discount * xa;
     if (EXACT && APPROX != 0) y = pe - pa;
     else if (EXACT) y = pe;
     else y = pa;
@@ -146,7 +152,8 @@ static aicdf_status cir_setup(const aicdf_sde_params *prm, int level, uint64_t n
   if (!sums_dev || ((uintptr_t)sums_dev % 8) || !status_dev) return AICDF_ERR_ARG;
   if (!workspace_dev || ((uintptr_t)workspace_dev % 16) || workspace_bytes < aicdf_mlmc_level_workspace_bytes())
     return AICDF_ERR_ARG;
-  if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL) return AICDF_ERR_ARG;
+  if (prm->payoff != AICDF_PAYOFF_X && prm->payoff != AICDF_PAYOFF_CALL && prm->payoff != AICDF_PAYOFF_ASIAN)
+    return AICDF_ERR_ARG;
   if (!(prm->kappa > 0.0) || !(prm->theta > 0.0) || !(prm->sigma > 0.0) || !(prm->T > 0.0) ||
       !(prm->X0 >= 0.0) || !std::isfinite(prm->X0 + prm->T + prm->K + prm->discount))
     return AICDF_ERR_DOMAIN;

@@ -152,6 +152,9 @@ def test_mlmc_argument_validation_without_gpu(P):
     bad = P.sde_params(T=0.0)
     assert call(bad, 3, P.KIND_CORR4, 10) == P.ERR_DOMAIN
     assert L.aicdf_mlmc_level(None, t.handle, 3, 1, 10, 0, 0, 1, fake, fake, ws_bytes, None) == P.ERR_ARG
+    # the path average is for the CIR per-step calls only; unknown payoffs everywhere
+    assert call(P.sde_params(payoff=P.PAYOFF_ASIAN), 3, P.KIND_CORR4, 10) == P.ERR_ARG
+    assert call(P.sde_params(payoff=3), 3, P.KIND_CORR4, 10) == P.ERR_ARG
 
 
 def test_pwp_table_matches_oracle(P, orc):
@@ -207,6 +210,10 @@ def test_ncx2_table_argument_validation(P):
     call = lambda tab, kind: L.aicdf_cir_level_table(C.byref(prm), tab.handle, 3, kind, 10, 0, 0, 1, fake, fake,
                                                      ws, fake, None)
     assert call(t, P.CIR_SURROGATE) == P.ERR_ARG
+    bad = P.sde_params(model=P.MODEL_CIR, payoff=3, X0=1.0, T=1.0, mu=0.0, sigma=1.0, kappa=0.5, theta=1.0,
+                       discount=1.0)
+    assert L.aicdf_cir_level_table(C.byref(bad), t.handle, 3, P.CIR_TABLE, 10, 0, 0, 1, fake, fake, ws, fake,
+                                   None) == P.ERR_ARG
     assert call(P.Ncx2Table(1.0, 16, 16, 1), P.CIR_DIFF_TABLE) == P.ERR_DOMAIN
     assert L.aicdf_cir_level(C.byref(prm), None, 3, P.CIR_TABLE, 10, 0, 0, 1, fake, fake, ws, fake, None) == P.ERR_ARG
 

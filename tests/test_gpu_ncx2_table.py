@@ -6,6 +6,9 @@
 * CIR paths: single paths (n_paths = 1) equal a step-by-step restatement with
   the oracle's functions (exact quantile in FP64; tabulated steps in FP64 from
   the same FP32 table) to 1e-4 relative after 2^level steps.
+* Path average (the ASIAN payoff, Section 5.2's path-dependent functional):
+  single paths against the same restatement; the exact mean against its
+  closed form; the correction's variance share matches the terminal value's.
 * Variance: with the paper's CIR parameters the exact-minus-table difference
   has the share of the exact variance that the tables' Table 5 RMSE predicts
   (Section 5.2; see test_cir_table_variance_drop).
@@ -74,20 +77,23 @@ CIR_SETS = {
 }
 
 
-def _cir_params(P, name):
+def _cir_params(P, name, payoff=None):
     q = CIR_SETS[name]
-    return P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X, X0=q["X0"], T=q["T"], mu=0.0, sigma=q["sigma"],
+    return P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_X if payoff is None else payoff, X0=q["X0"], T=q["T"], mu=0.0, sigma=q["sigma"],
                         kappa=q["kappa"], theta=q["theta"], discount=1.0), q
 
 
-def _emulate_path(orc, q, c, level, p, seed, tag):
-    """Exact and tabulated CIR path of 2^level steps (Section 5.2 per-step law)."""
+def _emulate_path(orc, q, c, level, p, seed, tag, average=False):
+    """Exact and tabulated CIR path of 2^level steps (Section 5.2 per-step law):
+    the values at T, or with average=True the means of the post-step values
+    X_1 .. X_N (the path-average functional)."""
     nu = 4 * q["kappa"] * q["theta"] / q["sigma"] ** 2
     h = q["T"] / 2 ** level
     e = math.exp(-q["kappa"] * h)
     cc = q["sigma"] ** 2 * (-math.expm1(-q["kappa"] * h)) / (4 * q["kappa"])
     key = [seed & 0xFFFFFFFF, seed >> 32]
     xe = xa = q["X0"]
+    se = sa = 0.0
     for s in range(2 ** level):
         w = int(orc.philox4([s // 4, p & 0xFFFFFFFF, p >> 32, tag], key, 32)[s % 4])
         u = orc.u01(w)
@@ -95,6 +101,9 @@ def _emulate_path(orc, q, c, level, p, seed, tag):
         xe = cc * (orc.ncx2_ppf(u, nu, lam_e) if u <= 0.5 else orc.ncx2_isf(1.0 - u, nu, lam_e))
         lam_a = max(xa, 0.0) * e / cc
         xa = cc * max(orc.ncx2_poly_ppf(c, nu, u, lam_a), 0.0)
+        se, sa = se + xe, sa + xa
+    if average:
+        return se / 2 ** level, sa / 2 ** level
     return xe, xa
 
 
@@ -119,6 +128,92 @@ def test_cir_table_paths_match_restatement(P, orc, name, deg):
             assert got[P.CIR_EXACT] == pytest.approx(xe, rel=1e-6, abs=1e-9)
             assert got[P.CIR_TABLE] == pytest.approx(xa, rel=1e-4, abs=1e-6)
             assert got[P.CIR_DIFF_TABLE] == pytest.approx(xe - xa, abs=1e-4 * abs(xa) + 1e-6)
+
+
+@pytest.mark.parametrize("deg", [1, 3])
+def test_cir_table_asian_paths_match_restatement(P, orc, deg):
+    """The path-average payoff (the mean of X_1 .. X_N) of the exact path, the
+    tabulated path and their difference, path by path against the oracle."""
+    import torch
+    prm, q = _cir_params(P, "paper", payoff=P.PAYOFF_ASIAN)
+    t = P.Ncx2Table(2.0, 16, 16, deg)
+    c = _c32(t)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for level in (0, 1, 3, 5):
+        for p in (0, 31, 987654321):
+            ae, aa = _emulate_path(orc, q, c, level, p, seed=9, tag=2, average=True)
+            if level == 0:   # one step: the average is the terminal value
+                assert (ae, aa) == _emulate_path(orc, q, c, level, p, seed=9, tag=2)
+            got = {}
+            for kind in (P.CIR_EXACT, P.CIR_TABLE, P.CIR_DIFF_TABLE):
+                P.cir_level_table(prm, t, level, kind, 1, sums, ws, st, path_offset=p, seed=9, tag=2)
+                got[kind] = sums[0].item()
+            assert st.item() == 0
+            assert got[P.CIR_EXACT] == pytest.approx(ae, rel=1e-6, abs=1e-9)
+            assert got[P.CIR_TABLE] == pytest.approx(aa, rel=1e-4, abs=1e-6)
+            assert got[P.CIR_DIFF_TABLE] == pytest.approx(ae - aa, abs=1e-4 * abs(aa) + 1e-6)
+
+
+def test_cir_asian_exact_mean_closed_form(P):
+    """The exact transitions keep the CIR mean E[X_t] = theta + (X0 - theta)
+    e^{-kappa t}, so the path average over t_n = n h (n = 1 .. N) has mean
+    theta + (X0 - theta) (1/N) sum_n e^{-kappa n h}: within 4 standard errors
+    at levels 0, 2 and 5 from X0 = 2 (theta = 1, nu = 2)."""
+    import torch
+    kappa, theta, sigma, X0, T = 0.5, 1.0, 1.0, 2.0, 1.0
+    prm = P.sde_params(model=P.MODEL_CIR, payoff=P.PAYOFF_ASIAN, X0=X0, T=T, mu=0.0, sigma=sigma,
+                       kappa=kappa, theta=theta, discount=1.0)
+    t = P.Ncx2Table(2.0, 16, 16, 1)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n = 1 << 16
+    for level in (0, 2, 5):
+        N = 2 ** level
+        h = T / N
+        mean = theta + (X0 - theta) * sum(math.exp(-kappa * k * h) for k in range(1, N + 1)) / N
+        P.cir_level_table(prm, t, level, P.CIR_EXACT, n, sums, ws, st, seed=21, tag=4)
+        s = sums.cpu().numpy()
+        assert st.item() == 0 and s[4] == n
+        m, var = s[0] / n, s[1] / n - (s[0] / n) ** 2
+        assert abs(m - mean) < 4 * math.sqrt(var / n), (level, m, mean, math.sqrt(var / n))
+
+
+def test_cir_asian_variance_structure_matches_terminal(P):
+    """Section 5.2: a path-dependent functional keeps the variance structure of
+    the terminal value.  Each step error is carried forward with the factor
+    ~e^{-kappa (t - t_n)} into every later X_t, so the average's correction
+    variance relative to its own variance is, like the terminal's, flat in h
+    and of the same order: the log2 ratios of the two payoffs agree within a
+    few units at levels 1 and 4, for the linear and the cubic table alike."""
+    import torch
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n = 1 << 16
+    r = {}
+    for deg in (1, 3):
+        t = P.Ncx2Table(2.0, 16, 16, deg)
+        for payoff in (P.PAYOFF_X, P.PAYOFF_ASIAN):
+            prm, _ = _cir_params(P, "paper", payoff=payoff)
+            for level in (1, 4):
+                v = {}
+                for kind in (P.CIR_EXACT, P.CIR_DIFF_TABLE):
+                    P.cir_level_table(prm, t, level, kind, n, sums, ws, st, seed=11, tag=1)
+                    s = sums.cpu().numpy()
+                    v[kind] = s[1] / n - (s[0] / n) ** 2
+                assert st.item() == 0
+                r[(deg, payoff, level)] = math.log2(v[P.CIR_DIFF_TABLE] / v[P.CIR_EXACT])
+    print({k: round(x, 2) for k, x in r.items()})
+    for deg in (1, 3):
+        for level in (1, 4):
+            assert abs(r[(deg, P.PAYOFF_ASIAN, level)] - r[(deg, P.PAYOFF_X, level)]) < 3.0, r
+        # flat in h for the average too
+        assert abs(r[(deg, P.PAYOFF_ASIAN, 4)] - r[(deg, P.PAYOFF_ASIAN, 1)]) < 3.0, r
+    for level in (1, 4):
+        assert r[(3, P.PAYOFF_ASIAN, level)] < r[(1, P.PAYOFF_ASIAN, level)] - 5.0, r
 
 
 def test_cir_table_variance_drop(P):
