@@ -786,8 +786,9 @@ def _exact_transition_mc(P, dev, sets, eps):
 def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     """GBM European call (S0 = K = 1, r = 0.05, sigma = 0.2, T = 1), Euler-Maruyama:
     wall time to RMSE eps of nested MLMC (PWL + exact correction), regular MLMC
-    (exact variates) and plain Monte Carlo with exact variates at the finest
-    level the nested run chose -- all on this GPU, through aicdf_mlmc_run."""
+    (exact variates), nested MLMC on the piecewise cubic table, and plain Monte
+    Carlo with exact variates at the finest level the nested run chose -- all
+    on this GPU, through aicdf_mlmc_run."""
     import torch
     ws = torch.empty(P.mlmc_run_workspace_bytes(), dtype=torch.uint8, device=dev)
     prm = P.sde_params()
@@ -796,9 +797,15 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     nested = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_NESTED, seed=1)
     regular = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_REGULAR, seed=2)
     adaptive = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_ADAPTIVE, seed=1)
+    # the same nested estimator on the piecewise cubic table (Section 3.4 with
+    # degree 3): its four-way corrections are far smaller
+    tc3 = P.table_build(P.PWP, 15, 3)
+    P.mlmc_run(prm, tc3, 1e-3, ws, estimator=P.EST_NESTED, seed=99)   # calibration warm-up
+    nested_cubic = P.mlmc_run(prm, tc3, eps, ws, estimator=P.EST_NESTED, seed=4)
     L = nested.L
     plain = P.mlmc_run(prm, tl, eps, ws, estimator=P.EST_PLAIN, fixed_L=L, seed=3)
-    for name, r in (("nested", nested), ("regular", regular), ("adaptive", adaptive), ("plain_exact", plain)):
+    for name, r in (("nested", nested), ("regular", regular), ("adaptive", adaptive), ("nested_cubic", nested_cubic),
+                    ("plain_exact", plain)):
         # fine path-steps per term slot (slot 0: APPROX2 / EXACT2 / PLAIN, slot 1: CORR4)
         steps = [sum(r.paths[l][k] * ((1 << l) + 1 if l > 0 else 1) for l in range(r.L + 1)) for k in range(2)]
         res[name] = {"estimate": r.estimate, "rmse_est": (r.variance + r.bias ** 2) ** 0.5,
@@ -813,6 +820,9 @@ def mlmc_time_to_rmse(P, tl, dev, eps: float = 1e-4):
     res["speedup_vs_regular_mlmc_wall"] = regular.wall_ms / nested.wall_ms
     res["speedup_vs_plain_exact_gpu"] = plain.gpu_ms / nested.gpu_ms
     res["speedup_vs_regular_mlmc_gpu"] = regular.gpu_ms / nested.gpu_ms
+    res["speedup_nested_cubic_vs_regular_mlmc_gpu"] = regular.gpu_ms / nested_cubic.gpu_ms
+    res["step_ns"]["approx2_cubic"] = nested_cubic.cost_ns[0][0] / 2
+    res["step_ns"]["corr4_cubic"] = nested_cubic.cost_ns[0][1] / 2
     return res
 
 

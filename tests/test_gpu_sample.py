@@ -258,3 +258,30 @@ def test_full_size_sampled_parity(P, tabs, orc):
     h = out16[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
     r16 = ref.astype(np.float32).astype(np.float16).astype(np.float64)
     assert np.all(np.abs(h - r16) <= np.spacing(np.abs(r16).astype(np.float16)).astype(np.float64))
+
+
+@pytest.mark.parametrize("method,offset", [("pwl", 0), ("pwl", 5), ("pwc", 2)])
+def test_sweep_maximum_size_sampled_parity(P, tabs, orc, method, offset):
+    """The largest size of the benchmark's size sweep, 2^30 FP32 samples
+    (4 GiB), at an aligned and two unaligned stream offsets, checked on
+    sampled outputs including both ends."""
+    import torch
+    tl, tc, a, b, q = tabs
+    n = 1 << 30
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    if method == "pwl":
+        P.sample(tl, P.PWL, out, seed=7, offset=offset)
+    else:
+        P.sample(tc, P.PWC, out, seed=7, offset=offset)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 16000), np.arange(600), np.arange(n - 600, n)]))
+    u = np.array([orc.uniforms(7, offset + int(i), 1)[0] for i in idx], dtype=np.float32)
+    z = out[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    del out
+    if method == "pwl":
+        ref, _ = orc.sample_pwl(a, b, u)
+        _assert_pwl(z, ref)
+    else:
+        ref, _ = orc.sample_pwc(q, u)
+        assert np.array_equal(z, ref)
