@@ -989,6 +989,28 @@ def profile_mlmc_kinds(model: str = "gbm"):
     print(sums.cpu().numpy())
 
 
+def profile_mlmc_level0():
+    """One level launch per estimator kind at level 0 (one step a path, four
+    paths per Philox call; GBM call of the GBM configuration, Euler-Maruyama,
+    2^26 paths): APPROX2, EXACT2, CORR4; then APPROX2 at level 1 (2^25 paths)
+    and level 2 (2^24 paths)."""
+    import torch
+    import paper_2012_09715_gb300 as P
+    from paper_2012_09715_gb300 import build as B
+    B.build()
+    P.lib()
+    tl = P.table_build(P.PWL, 15)
+    ws = torch.empty(P.mlmc_level_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sums = torch.zeros(P.SUMS, dtype=torch.float64, device="cuda")
+    prm = P.sde_params()
+    n = 1 << 26
+    for level, kind in ((0, P.KIND_APPROX2), (0, P.KIND_EXACT2), (0, P.KIND_CORR4), (1, P.KIND_APPROX2),
+                        (2, P.KIND_APPROX2)):
+        P.mlmc_level(prm, tl, level, kind, n >> level, sums, ws, seed=1, tag=1)
+    torch.cuda.synchronize()
+    print(sums.cpu().numpy())
+
+
 def profile_kernels():
     """One representative launch of each kernel family besides the headline
     sampler, in this order: truncated 16-bit PWL sampling (2^26 FP32), exact
@@ -1080,13 +1102,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n-log2", type=int, default=28, help="workload size (profiling runs only)")
-    ap.add_argument("--profile-case", choices=["mlmc_kinds", "mlmc_kinds_cir", "kernels", "cir_small"], default=None,
+    ap.add_argument("--profile-case", choices=["mlmc_kinds", "mlmc_kinds_cir", "mlmc_level0", "kernels", "cir_small"],
+                    default=None,
                     help="run one fixed launch sequence for an ncu capture and exit (no timing line)")
     args = ap.parse_args()
     if args.profile_case == "mlmc_kinds":
         return profile_mlmc_kinds()
     if args.profile_case == "mlmc_kinds_cir":
         return profile_mlmc_kinds("cir")
+    if args.profile_case == "mlmc_level0":
+        return profile_mlmc_level0()
     if args.profile_case == "kernels":
         return profile_kernels()
     if args.profile_case == "cir_small":

@@ -196,7 +196,8 @@ typedef struct {
  * estimators, plus the third and fourth power sums from which the term's
  * kurtosis (the reliability of its variance estimate) follows.  Sums of Y and
  * Y^2 are exact FP64 sums of per-chunk FP32 partial sums (chunks of ~16 paths
- * per thread); those of Y^3 and Y^4 are FP32 running sums over each thread's
+ * per thread, ~32 at levels 0 and 1, each chunk's FP32 sum within 31 2^-24
+ * of its sum of |Y|); those of Y^3 and Y^4 are FP32 running sums over each thread's
  * k paths, reduced across threads in FP64 (relative error at most (k-1) 2^-24,
  * typically sqrt(k) 2^-24, with k = n_paths / (resident threads) -- ~4e-6 for
  * a 10^9-path level; |Y| below ~1e-9 underflows Y^4 in FP32). */

@@ -95,6 +95,10 @@ struct PathConsts {
   // sigma sqrt|X| dW + mq dW^2 / h in two (mq = 0 for Euler-Maruyama).  The
   // constants' rounding is relative to the drift per step, not to X.
   float nkdt, nkdt2, dc1, dc2, sig_sdt, mq;
+  // payoff discount * max(X - pk, pfloor): the call has (K, 0); P = X has
+  // (0, NaN), since X - 0 is X and fmaxf returns its other operand for a NaN
+  // one (a NaN X stays NaN), so both payoffs are one branch-free form
+  float pk, pfloor;
 };
 
 // (all products and differences rounded separately, _rn intrinsics: the
@@ -119,6 +123,9 @@ __device__ __forceinline__ PathConsts make_path_consts(const PathSpec &a) {
   p.nkdt2 = __fmul_rn(-2.0f, kdt);
   p.dc1 = __fsub_rn(kth, p.mq);
   p.dc2 = __fmul_rn(2.0f, p.dc1);
+  const bool call = a.payoff == AICDF_PAYOFF_CALL;
+  p.pk = call ? a.K : 0.0f;
+  p.pfloor = call ? 0.0f : __int_as_float(0x7fffffff);
   return p;
 }
 
@@ -192,7 +199,8 @@ struct PathSums {
   __device__ __forceinline__ Moments total() const { return Moments{d1, d2, (double)f3, (double)f4}; }
 };
 
-constexpr int kChunkPaths = 16;  // paths per thread between FP64 flushes
+constexpr int kChunkPaths = 16;       // paths per thread between FP64 flushes
+constexpr int kGroupChunkPaths = 32;  // the same at levels 0 and 1 (one or two steps a path)
 
 // for (b = first; b < end; b += stride) body(b), in chunks of `per_chunk`
 // iterations with acc.flush() after each chunk.  first, end and stride are
@@ -212,18 +220,20 @@ __device__ __forceinline__ void chunked_loop(uint64_t first, uint64_t end, uint6
 // never contracts into FMAs, so that Y of a path is the same bits in every
 // kernel that inlines this code (the four-way Y is a small difference of
 // nearly equal payoffs, where one contraction changes it visibly).
-__device__ __forceinline__ float payoff(const PathSpec &a, float x) {
-  return a.payoff == AICDF_PAYOFF_CALL ? __fmul_rn(a.discount, fmaxf(__fsub_rn(x, a.K), 0.0f))
-                                       : __fmul_rn(a.discount, x);
+__device__ __forceinline__ float payoff(const PathSpec &a, const PathConsts &pc, float x) {
+  return __fmul_rn(a.discount, fmaxf(__fsub_rn(x, pc.pk), pc.pfloor));
 }
 
 // Y of a path from its final fine / coarse states (exact e, approximate a).
-template <bool NE, bool NA>
-__device__ __forceinline__ float path_result(const PathSpec &a, bool coarse, float xfe, float xce, float xfa,
-                                             float xca) {
-  const float pfe = NE ? payoff(a, xfe) : 0.f, pfa = NA ? payoff(a, xfa) : 0.f;
-  const float pce = (NE && coarse) ? payoff(a, xce) : 0.f;
-  const float pca = (NA && coarse) ? payoff(a, xca) : 0.f;
+// Without a coarse path (level 0) every kind of a given (NE, NA) gives the
+// same Y (a zero coarse payoff subtracts exactly), so no test of the kind.
+template <bool NE, bool NA, bool COARSE>
+__device__ __forceinline__ float path_result(const PathSpec &a, const PathConsts &pc, float xfe, float xce,
+                                             float xfa, float xca) {
+  const float pfe = NE ? payoff(a, pc, xfe) : 0.f, pfa = NA ? payoff(a, pc, xfa) : 0.f;
+  if constexpr (!COARSE) return (NE && NA) ? __fsub_rn(pfe, pfa) : NE ? pfe : pfa;
+  const float pce = NE ? payoff(a, pc, xce) : 0.f;
+  const float pca = NA ? payoff(a, pc, xca) : 0.f;
   switch (a.kind) {
     case AICDF_KIND_APPROX2: return __fsub_rn(pfa, pca);
     case AICDF_KIND_CORR4: return __fsub_rn(__fsub_rn(pfe, pfa), __fsub_rn(pce, pca));
@@ -295,7 +305,7 @@ __device__ __forceinline__ float path_y(const PathSpec &a, const PathConsts &pc,
       }
     }
   }
-  return path_result<NE, NA>(a, true, xfe, xce, xfa, xca);
+  return path_result<NE, NA, true>(a, pc, xfe, xce, xfa, xca);
 }
 
 // Levels 0 and 1 have 1 or 2 fine steps per path, so one Philox call serves
@@ -331,19 +341,21 @@ __device__ __forceinline__ void group_y(const PathSpec &a, const PathConsts &pc,
       if (NE) xce = step_coarse<MODEL, MIL>(xce, se, pc);
       if (NA) xca = step_coarse<MODEL, MIL>(xca, sa, pc);
     }
-    y[g] = path_result<NE, NA>(a, LEVEL == 1, xfe, xce, xfa, xca);
+    y[g] = path_result<NE, NA, LEVEL == 1>(a, pc, xfe, xce, xfa, xca);
   }
 }
 
 // Sums over the paths [p0, p0 + n) of a term at level 0 or 1 by groups of
 // G = 4 >> level: group-stride loop over the groups that meet the range,
 // starting at group index `first` with stride `stride` (warp-aligned), into
-// acc.  GROUP(q, y) fills y.
-template <class GroupFn>
+// acc.  GROUP(q, y) fills y.  LV >= 0 fixes the level at compile time
+// (the level kernel); LV = -1 takes `level` at run time (the batched kernel).
+template <int LV = -1, class GroupFn>
 __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, uint64_t first, uint64_t stride,
                                            GroupFn group, PathSums &acc) {
-  const int sh = 2 - level, G = 4 >> level;
-  const bool four = level == 0;  // G = 4, else G = 2
+  const int lv = LV >= 0 ? LV : level;
+  const int sh = 2 - lv, G = 4 >> lv;
+  const bool four = lv == 0;  // G = 4, else G = 2
   const uint64_t q0 = p0 >> sh, ng = ((p0 + n - 1) >> sh) - q0 + 1;
   // Groups wholly inside the range: all but a first group that starts before
   // p0 and a last one that runs past p0 + n.  The warp's groups base ..
@@ -352,7 +364,7 @@ __device__ __forceinline__ void sum_groups(uint64_t p0, uint64_t n, int level, u
   const bool head = (p0 & (uint64_t)(G - 1)) != 0;
   const uint64_t qb = ng - (((p0 + n) & (uint64_t)(G - 1)) ? 1 : 0);
   const int lane = threadIdx.x & 31;
-  chunked_loop(first, ng, stride, kChunkPaths / G, acc, [&](uint64_t base) {
+  chunked_loop(first, ng, stride, kGroupChunkPaths / G, acc, [&](uint64_t base) {
     const uint64_t qi = base + lane, q = q0 + qi;
     float y[4];
     group(q, y);
@@ -378,13 +390,14 @@ template <bool NE, bool NA, int AP, int MODEL, bool V16, bool MIL>
 __device__ __forceinline__ void term_sums(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
                                           const PhiloxKeys &keys, uint64_t p0, uint64_t n, uint64_t first,
                                           uint64_t stride, PathSums &acc) {
-  if (a.level < 2) {  // warp-uniform
-    sum_groups(p0, n, a.level, first, stride,
-               [&](uint64_t q, float (&y)[4]) {
-                 if (a.level == 0) group_y<NE, NA, AP, MODEL, V16, MIL, 0>(a, pc, ap, keys, q, y);
-                 else group_y<NE, NA, AP, MODEL, V16, MIL, 1>(a, pc, ap, keys, q, y);
-               },
-               acc);
+  if (a.level == 0) {  // warp-uniform
+    sum_groups<0>(p0, n, 0, first, stride,
+                  [&](uint64_t q, float (&y)[4]) { group_y<NE, NA, AP, MODEL, V16, MIL, 0>(a, pc, ap, keys, q, y); },
+                  acc);
+  } else if (a.level == 1) {
+    sum_groups<1>(p0, n, 1, first, stride,
+                  [&](uint64_t q, float (&y)[4]) { group_y<NE, NA, AP, MODEL, V16, MIL, 1>(a, pc, ap, keys, q, y); },
+                  acc);
   } else {
     const int lane = threadIdx.x & 31;
     chunked_loop(first, n, stride, kChunkPaths, acc, [&](uint64_t base) {
