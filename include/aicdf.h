@@ -402,7 +402,10 @@ aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const float *u_dev, c
  * lr_final; the last batch's L goes to *loss_dev.  One epoch's launches are
  * captured as a CUDA graph and replayed per epoch (the step sizes come from a
  * device step counter), so the call must not itself be made during a stream
- * capture. */
+ * capture.  The samples' network inputs and g_i are formed once per call into
+ * a device buffer of 16 bytes a sample that the surrogate keeps (and grows for
+ * a larger n) until aicdf_surrogate_destroy; should that allocation fail, every
+ * gradient launch forms them itself, with the same result. */
 aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
                                    const float *target_dev, size_t n, size_t batch, int epochs,
                                    float lr, float lr_final, float *loss_dev, aicdf_stream_t stream);

@@ -192,11 +192,40 @@ __device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
   return a;
 }
 
+// Programmatic dependent launch, used between the training graph's gradient
+// and Adam launches: a kernel launched with the programmatic-serialization
+// attribute may start while its predecessor is still running.  pdl_wait()
+// returns once the predecessor grid has completed and its writes are visible
+// (at once for a kernel launched without the attribute); after
+// pdl_launch_dependents() in every CTA the successor may start its prologue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// A training sample's network inputs and target: (x0, x1, g) of (u, lambda,
+// target) -- the features of mlp_device.cuh and g = (target - Phi^{-1}(u)) /
+// sqrt(y).  The training loop computes them once per call into a float4 per
+// sample (w unused) instead of once per epoch inside the gradient kernel.
+__device__ __forceinline__ float3 train_features(float ui, float li, float ti, float nu) {
+  const float sy = mlp_sqrt_y(li, nu);
+  return make_float3(mlp_feature_u(ui), mlp_feature_y(sy), (ti - phiinv_f32(ui)) / sy);
+}
+
+__global__ void k_mlp_features(const float *__restrict__ u, const float *__restrict__ lam,
+                               const float *__restrict__ target, uint64_t n, float nu, float4 *__restrict__ feat) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const float3 f = train_features(u[i], lam[i], target[i], nu);
+    feat[i] = make_float4(f.x, f.y, f.z, 0.f);
+  }
+}
+
+// FEAT: the samples' (x0, x1, g) come from feat (k_mlp_features); otherwise
+// from u, lam and target here.
+template <bool FEAT>
 __global__ void __launch_bounds__(kTrainThreads)
     k_mlp_train(const float *__restrict__ params, const __nv_bfloat16 *__restrict__ w2c,
                 const float *__restrict__ u, const float *__restrict__ lam, const float *__restrict__ target,
-                uint64_t begin, uint64_t count, float scale, float *__restrict__ partial, float nu,
-                long long *__restrict__ step_count) {
+                const float4 *__restrict__ feat, uint64_t begin, uint64_t count, float scale,
+                float *__restrict__ partial, float nu, long long *__restrict__ step_count) {
   extern __shared__ __align__(1024) unsigned char tr_raw[];
   MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(tr_raw + ((1024 - (tc_smem(tr_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -204,14 +233,34 @@ __global__ void __launch_bounds__(kTrainThreads)
   unsigned char *w2k = reinterpret_cast<unsigned char *>(s.w2k), *w2t = reinterpret_cast<unsigned char *>(s.w2t);
   unsigned char *h1 = reinterpret_cast<unsigned char *>(s.h1), *dz2 = reinterpret_cast<unsigned char *>(s.dz2);
   unsigned char *dz2t = reinterpret_cast<unsigned char *>(s.dz2t), *h1t = reinterpret_cast<unsigned char *>(s.h1t);
-  // ---- W2 and W2^T (BF16, canonical, adjacent) by one bulk copy; the zero
-  // rows of dZ2^T and the FP32 vectors by the threads
+  if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTrainCols);
+  // ---- this thread's sample (inputs no launch writes), before the wait for
+  // the previous Adam step
+  const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + m;
+  const bool ok = m_idx < count;
+  const uint64_t i = begin + m_idx;
+  float3 f = make_float3(0.f, 0.f, 0.f);  // (x0, x1, g); g is the network's own target
+  if (ok) {
+    if constexpr (FEAT) {
+      const float4 q = feat[i];
+      f = make_float3(q.x, q.y, q.z);
+    } else {
+      f = train_features(u[i], lam[i], target[i], nu);
+    }
+  }
+  const float x0 = f.x, x1 = f.y, tg = f.z;
+  for (int c = tid; c < (kTcRows - kH) * kTcRows / 8; c += blockDim.x)  // rows 64..127 of dZ2^T
+    *reinterpret_cast<uint4 *>(dz2t + (size_t)(kH / 8) * 2048 + 16 * (size_t)c) = make_uint4(0u, 0u, 0u, 0u);
+  // the Adam step after this one may start (it waits for these partials); the
+  // parameters, W2 and the step counter below come from the Adam step before
+  pdl_launch_dependents();
+  pdl_wait();
+  // ---- W2 and W2^T (BF16, canonical, adjacent) by one bulk copy; the FP32
+  // vectors by the threads
   if (tid == 0) {
     tc_mbar_init(tc_smem(&s.wbar), 1);
     tc_bulk_g2s(tc_smem(w2k), w2c, 2 * kW2cBytes, tc_smem(&s.wbar));
   }
-  for (int c = tid; c < (kTcRows - kH) * kTcRows / 8; c += blockDim.x)  // rows 64..127 of dZ2^T
-    *reinterpret_cast<uint4 *>(dz2t + (size_t)(kH / 8) * 2048 + 16 * (size_t)c) = make_uint4(0u, 0u, 0u, 0u);
   for (int c = tid; c < 2 * kH; c += blockDim.x) s.w1[c] = params[kOffW1 + c];
   for (int c = tid; c < kH; c += blockDim.x) {
     s.b1[c] = params[kOffB1 + c];
@@ -222,18 +271,9 @@ __global__ void __launch_bounds__(kTrainThreads)
     s.b3 = params[kOffB3];
     tc_mbar_init(tc_smem(&s.mbar), 1);
   }
-  if (warp == 0) tc_alloc(tc_smem(&s.tmem), kTrainCols);
-  // ---- layer 1: this thread's 32 units of H1 (BF16), by rows and by columns
-  const uint64_t m_idx = (uint64_t)blockIdx.x * kTcRows + m;
-  const bool ok = m_idx < count;
-  const uint64_t i = begin + m_idx;
   if (step_count && blockIdx.x == 0 && tid == 0) *step_count += 1;  // the Adam kernel after this reads it
-  const float ui = ok ? u[i] : 0.5f;
-  const float sy = ok ? mlp_sqrt_y(lam[i], nu) : 1.f;
-  const float x0 = ok ? mlp_feature_u(ui) : 0.f;
-  const float x1 = ok ? mlp_feature_y(sy) : 0.f;
-  const float tg = ok ? (target[i] - phiinv_f32(ui)) / sy : 0.f;  // g: the network's own target
   __syncthreads();  // vectors staged
+  // ---- layer 1: this thread's 32 units of H1 (BF16), by rows and by columns
 #pragma unroll
   for (int j = 0; j < kHalf / 8; ++j) {
     uint32_t w[4];
@@ -361,16 +401,21 @@ __global__ void __launch_bounds__(kTrainThreads)
     if (tid < kH) out[kOffW1 + 2 * tid + 1] = a;
   }
   // ---- dW2 rows n = TMEM lanes 0..63 (warps 0, 1 and 4, 5 for the two
-  // column halves); every warp runs the warp-collective loads
+  // column halves; every warp runs the warp-collective loads), staged in
+  // `red` (free again after the last column sum) so that the 64 x 64 block
+  // goes out in coalesced rows: a lane's own row is 256 bytes from its
+  // neighbour's, and stored directly every warp store touched 32 sectors
 #pragma unroll
   for (int c = 0; c < kHalf; c += 16) {
     float d[16];
     if (done) tc_ld16(tmem + 128 + lane_base + (uint32_t)(c0 + c), d);
     if (m < kH) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) out[kOffW2 + m * kH + c0 + c + q] = done ? d[q] : __int_as_float(0x7fc00000);
+      for (int q = 0; q < 16; ++q) s.red[m][c0 + c + q] = done ? d[q] : __int_as_float(0x7fc00000);
     }
   }
+  __syncthreads();
+  for (int i = tid; i < kH * kH; i += kTrainThreads) out[kOffW2 + i] = s.red[i / kH][i % kH];
   // ---- sums of dy (gradient of b3) and err^2 over the samples (first half
   // of the threads), in a fixed order
   if (hf == 0) {
@@ -411,9 +456,29 @@ __device__ __forceinline__ float sum_partials(const float *__restrict__ partial,
   return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-// Sum per-block gradients in a fixed order and take one Adam step (one thread
-// per parameter, in small blocks so that the summing spreads over many SMs).
+// The same sum with the eight chains on eight lanes (lane q sums blocks q,
+// q + 8, ...), combined by xor shuffles in the pairing above, so the result is
+// the same bits while each lane waits for one round of loads instead of eight.
+// All lanes of the warp call it; every lane of an aligned 8-lane group gets
+// the sum (lanes with valid = false add nothing but take part).
+__device__ __forceinline__ float sum_partials_lanes(const float *__restrict__ partial, int nblocks, int p, int q,
+                                                    bool valid) {
+  float a = 0.f;
+  if (valid) {
+#pragma unroll 8
+    for (int b = q; b < nblocks; b += 8) a += partial[(size_t)b * kGradSlots + p];
+  }
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  a += __shfl_xor_sync(0xffffffffu, a, 2);
+  a += __shfl_xor_sync(0xffffffffu, a, 4);
+  return a;
+}
+
+// Sum per-block gradients in a fixed order and take one Adam step: eight
+// lanes per parameter (and per the loss slot), in small blocks so that the
+// summing spreads over many SMs.
 constexpr int kAdamThreads = 64;
+constexpr int kAdamBlocks = ((kLossSlot + 1) * 8 + kAdamThreads - 1) / kAdamThreads;
 
 // The step size and bias corrections of a scheduled Adam step come from the
 // device step counter (advanced by the gradient kernel before it): step st
@@ -432,16 +497,21 @@ __global__ void __launch_bounds__(kAdamThreads)
                __nv_bfloat16 *__restrict__ w2c, const float *__restrict__ partial, int nblocks, float lr,
                float b1, float b2, float eps, float bc1, float bc2, float *__restrict__ loss_out,
                float loss_scale, const long long *__restrict__ step_count, AdamSched sch) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0 && loss_out) *loss_out = sum_partials(partial, nblocks, kLossSlot) * loss_scale;
-  if (p > kOffB3) return;
+  pdl_launch_dependents();  // the next gradient launch may set up; it waits for these parameters
+  pdl_wait();               // the partials of the gradient launch before
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, q = threadIdx.x & 7;
+  const float gsum = sum_partials_lanes(partial, nblocks, p, q, p <= kLossSlot);
+  if (q != 0 || p > kLossSlot) return;
+  if (p == kLossSlot) {
+    if (loss_out) *loss_out = gsum * loss_scale;
+    return;
+  }
   if (sch.on) {
     const float st = (float)*step_count;
     lr = sch.lr0 * exp2f(sch.log2_ratio * (st - 1.0f - (float)sch.base));
     bc1 = 1.0f - exp2f(st * sch.log2_b1);
     bc2 = 1.0f - exp2f(st * sch.log2_b2);
   }
-  const float gsum = sum_partials(partial, nblocks, p);
   const float m = b1 * m1[p] + (1.f - b1) * gsum;
   const float v = b2 * m2[p] + (1.f - b2) * gsum * gsum;
   m1[p] = m;
@@ -512,6 +582,8 @@ struct aicdf_surrogate_s {
   float *partial = nullptr;  // per-block gradient partials
   int partial_blocks = 0;
   int *status = nullptr;
+  float4 *feat = nullptr;    // training samples' (x0, x1, g), aicdf_surrogate_train
+  size_t feat_n = 0;
   long long *d_step = nullptr;  // Adam steps taken, on the device (scheduled training reads it)
   long long step = 0;           // the same on the host
 };
@@ -595,6 +667,7 @@ extern "C" void aicdf_surrogate_destroy(aicdf_surrogate s) {
   cudaFree(s->m1);
   cudaFree(s->m2);
   cudaFree(s->partial);
+  cudaFree(s->feat);
   cudaFree(s->status);
   cudaFree(s->d_step);
   s->magic = 0;
@@ -705,8 +778,10 @@ static aicdf_status prepare_train_grad(aicdf_surrogate_s *s, int blocks) {
   aicdf_status rc = ensure_partials(s, blocks);
   if (rc != AICDF_OK) return rc;
   static const cudaError_t attr =  // opt in to > 48 KB of dynamic shared memory once
-      cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
-  return attr == cudaSuccess ? AICDF_OK : cuda_fail();
+      cudaFuncSetAttribute(k_mlp_train<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+  static const cudaError_t attr_f =
+      cudaFuncSetAttribute(k_mlp_train<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+  return attr == cudaSuccess && attr_f == cudaSuccess ? AICDF_OK : cuda_fail();
 }
 
 // The gradient kernel over samples [begin, begin + count); step_count (may be
@@ -717,8 +792,9 @@ static aicdf_status launch_train_grad(aicdf_surrogate_s *s, const float *u, cons
   const int blocks = (int)((count + kTcRows - 1) / kTcRows);
   aicdf_status rc = prepare_train_grad(s, blocks);
   if (rc != AICDF_OK) return rc;
-  k_mlp_train<<<blocks, kTrainThreads, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, begin, count,
-                                                   1.0f / (float)count, s->partial, (float)s->nu, step_count);
+  k_mlp_train<false><<<blocks, kTrainThreads, kTrainSmem, st>>>(s->params, s->w2c, u, lam, target, nullptr,
+                                                                begin, count, 1.0f / (float)count, s->partial,
+                                                                (float)s->nu, step_count);
   *blocks_out = blocks;
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
 }
@@ -750,10 +826,28 @@ extern "C" aicdf_status aicdf_surrogate_train_step(aicdf_surrogate s, const floa
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.f - (float)std::pow((double)b1, (double)s->step);
   const float bc2 = 1.f - (float)std::pow((double)b2, (double)s->step);
-  k_mlp_adam<<<(kOffB3 + kAdamThreads) / kAdamThreads, kAdamThreads, 0, st>>>(
+  k_mlp_adam<<<kAdamBlocks, kAdamThreads, 0, st>>>(
       s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, b1, b2, 1e-8f, bc1, bc2, loss_dev, 1.0f / (float)n,
       s->d_step, AdamSched{0, 0.f, 0.f, 0, 0.f, 0.f});
   return cudaGetLastError() == cudaSuccess ? AICDF_OK : cuda_fail();
+}
+
+// Kernel launch with programmatic stream serialization when `pdl` is set (the
+// kernel must call pdl_wait() before it reads what its predecessor writes).
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, bool pdl,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, (KArgs)args...);
 }
 
 extern "C" aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_dev, const float *lam_dev,
@@ -769,6 +863,23 @@ extern "C" aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_
   const int blocks = (int)((batch + kTcRows - 1) / kTcRows);
   aicdf_status rc = prepare_train_grad(s, blocks);
   if (rc != AICDF_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The samples' features, once for all epochs (16 bytes a sample, kept by the
+  // surrogate); without room for them each gradient launch forms its own.
+  const size_t used = steps_per_epoch * batch;
+  if (s->feat_n < used) {
+    cudaFree(s->feat);
+    s->feat = nullptr;
+    s->feat_n = 0;
+    if (cudaMalloc(&s->feat, sizeof(float4) * used) == cudaSuccess) s->feat_n = used;
+    else (void)cudaGetLastError();  // clear the failed allocation; train without the buffer
+  }
+  const bool feat = s->feat != nullptr;
+  if (feat) {
+    const int grid = (int)std::min<uint64_t>((used + 255) / 256, (uint64_t)sm_count() * 8);
+    k_mlp_features<<<grid, 256, 0, st>>>(u_dev, lam_dev, target_dev, used, (float)s->nu, s->feat);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail();
+  }
   // One epoch -- a gradient launch and an Adam launch per batch -- is captured
   // as a CUDA graph and replayed once per epoch: the launches run back to back
   // with no host in between.  The step size and bias corrections of each step
@@ -784,19 +895,27 @@ extern "C" aicdf_status aicdf_surrogate_train(aicdf_surrogate s, const float *u_
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     rc = AICDF_ERR_CUDA;
   } else {
-    for (size_t b = 0; b < steps_per_epoch; ++b) {
-      k_mlp_train<<<blocks, kTrainThreads, kTrainSmem, cap>>>(s->params, s->w2c, u_dev, lam_dev, target_dev,
-                                                          b * batch, batch, 1.0f / (float)batch, s->partial,
-                                                          (float)s->nu, s->d_step);
-      k_mlp_adam<<<(kOffB3 + kAdamThreads) / kAdamThreads, kAdamThreads, 0, cap>>>(
-          s->params, s->m1, s->m2, s->w2c, s->partial, blocks, lr, 0.9f, 0.999f, 1e-8f, 1.f, 1.f,
-          b + 1 == steps_per_epoch ? loss_dev : nullptr, 1.0f / (float)batch, s->d_step, sch);
+    // each launch after the first may start under the tail of the one before
+    // (programmatic dependent launch; the kernels wait where they read it)
+    cudaError_t e = cudaSuccess;
+    for (size_t b = 0; b < steps_per_epoch && e == cudaSuccess; ++b) {
+      e = launch_pdl(feat ? k_mlp_train<true> : k_mlp_train<false>, blocks, kTrainThreads, kTrainSmem, cap, b > 0,
+                     (const float *)s->params, (const __nv_bfloat16 *)s->w2c, feat ? nullptr : u_dev,
+                     feat ? nullptr : lam_dev, feat ? nullptr : target_dev, (const float4 *)s->feat,
+                     (uint64_t)(b * batch), (uint64_t)batch, 1.0f / (float)batch, s->partial, (float)s->nu,
+                     s->d_step);
+      if (e == cudaSuccess)
+        e = launch_pdl(k_mlp_adam, kAdamBlocks, kAdamThreads, 0, cap, true, s->params,
+                       s->m1, s->m2, s->w2c, (const float *)s->partial, blocks, lr, 0.9f, 0.999f, 1e-8f, 1.f, 1.f,
+                       b + 1 == steps_per_epoch ? loss_dev : (float *)nullptr, 1.0f / (float)batch,
+                       (const long long *)s->d_step, sch);
     }
-    if (cudaStreamEndCapture(cap, &g) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = AICDF_ERR_CUDA;
+    if (cudaStreamEndCapture(cap, &g) != cudaSuccess || e != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      rc = AICDF_ERR_CUDA;
   }
   if (rc == AICDF_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) rc = AICDF_ERR_CUDA;
   for (int e = 0; e < epochs && rc == AICDF_OK; ++e)
-    if (cudaGraphLaunch(exec, (cudaStream_t)stream) != cudaSuccess) rc = AICDF_ERR_CUDA;
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = AICDF_ERR_CUDA;
   if (rc != AICDF_OK) set_cuda_error((int)cudaGetLastError());
   // the launches are queued on the caller's stream; the graph may go once they are
   if (exec) cudaGraphExecDestroy(exec);
