@@ -191,6 +191,35 @@ def test_mlp_gradient_matches_oracle(P, orc):
             assert cos > 0.995, (name, cos)
 
 
+def test_scheduled_training_equals_step_by_step(P):
+    """aicdf_surrogate_train (features formed once per call, the epoch's
+    gradient and Adam launches replayed as one graph and chained by
+    programmatic dependent launch) against the same four Adam steps taken one
+    call at a time (features formed in the gradient kernel, plain launches),
+    from the same initial weights at a constant step size.  The two differ only
+    in how the bias corrections 1 - b^t are rounded (host against device), a
+    relative 1e-6 of each step."""
+    import torch
+    n, b = 4 * 8192, 8192
+    u, lam, p = (torch.empty(n, device="cuda") for _ in range(3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.ncx2_targets(NU_CFG, n, u, lam, p, st, seed=21, tag=1, loglam_lo=-6.0, loglam_hi=7.0)
+    s1, s2 = P.Surrogate(NU_CFG, seed=5), P.Surrogate(NU_CFG, seed=5)
+    p0 = s1.get_params()
+    assert np.array_equal(p0, s2.get_params())
+    l1, l2 = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    s1.train(u, lam, p, batch=b, epochs=1, lr=1e-3, lr_final=1e-3, loss=l1)
+    for k in range(n // b):
+        s2.train_step(u[k * b:(k + 1) * b], lam[k * b:(k + 1) * b], p[k * b:(k + 1) * b], 1e-3, loss=l2)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    a1, a2 = s1.get_params().astype(np.float64), s2.get_params().astype(np.float64)
+    moved = np.abs(a1 - p0)
+    assert np.median(moved) > 1e-4          # four steps of ~lr each moved the weights
+    assert np.max(np.abs(a1 - a2)) <= 1e-6, np.max(np.abs(a1 - a2))
+    assert l1.item() == pytest.approx(l2.item(), rel=1e-3)
+
+
 @pytest.fixture(scope="module")
 def trained(P):
     """Surrogate trained on 2^20 exact targets (the benchmark trains on 2^22)."""
