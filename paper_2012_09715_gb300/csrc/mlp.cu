@@ -156,7 +156,7 @@ struct MlpTrainSmem {
   __nv_bfloat16 dz2[kTcRows * kH];      // dZ2 [m][n]: A of dH1
   __nv_bfloat16 dz2t[kTcRows * kTcRows];  // dZ2^T [n][m], rows 64..127 zero: A of dW2
   __nv_bfloat16 h1t[kH * kTcRows];      // H1^T [k][m]: B of dW2
-  float red[kTcRows][2 * kH + 1];       // column sums, two 64-wide quantities per pass (pitch 129)
+  float red[kTcRows][3 * kH + 1];       // column sums, up to three 64-wide quantities a pass (pitch 193)
   float psum[2][2 * kH];                // the two row halves of a pass's column sums
   float ypart[2][kTcRows];              // the two halves of each sample's output
   float w1[2 * kH], b1[kH], b2[kH], w3[kH], b3;
@@ -166,6 +166,7 @@ struct MlpTrainSmem {
 };
 static_assert(offsetof(MlpTrainSmem, w2t) == offsetof(MlpTrainSmem, w2k) + kW2cBytes, "W2 tiles not adjacent");
 constexpr size_t kTrainSmem = sizeof(MlpTrainSmem) + 1024;
+static_assert(kTrainSmem <= 227u * 1024u, "training CTA exceeds the 227 KB of shared memory a CTA may opt in to");
 
 // byte offset of (r, k) in a canonical K-major tile with K = 128
 __device__ __forceinline__ uint32_t canon_off128(int r, int k) {
@@ -188,6 +189,25 @@ __device__ __forceinline__ float train_colsum(MlpTrainSmem &s, int ncols) {
   }
   __syncthreads();
   const float a = (rh == 0 && c < ncols) ? s.psum[0][c] + s.psum[1][c] : 0.f;
+  __syncthreads();
+  return a;
+}
+
+// Column sums of red[0..127][c] for all c < 3 kH in a fixed order: thread c
+// sums its column over the 128 rows as eight interleaved partial sums.  The
+// caller has filled red and passed a barrier; one barrier inside, so red may be
+// refilled after.
+__device__ __forceinline__ float train_colsum_wide(MlpTrainSmem &s) {
+  const int c = threadIdx.x;
+  float a = 0.f;
+  if (c < 3 * kH) {
+    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < kTcRows / 8; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] += s.red[8 * r + q][c];
+    a = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+  }
   __syncthreads();
   return a;
 }
@@ -387,18 +407,13 @@ __global__ void __launch_bounds__(kTrainThreads)
   for (int c = 0; c < kHalf; ++c) {
     s.red[m][c0 + c] = dz1[c];
     s.red[m][kH + c0 + c] = dz1[c] * x0;
+    s.red[m][2 * kH + c0 + c] = dz1[c] * x1;
   }
   __syncthreads();
   {
-    const float a = train_colsum(s, 2 * kH);  // gradient of b1, then of W1[., 0]
-    if (tid < kTcRows) out[tid < kH ? kOffB1 + tid : kOffW1 + 2 * (tid - kH)] = a;
-  }
-#pragma unroll
-  for (int c = 0; c < kHalf; ++c) s.red[m][c0 + c] = dz1[c] * x1;
-  __syncthreads();
-  {
-    const float a = train_colsum(s, kH);  // gradient of W1[., 1]
-    if (tid < kH) out[kOffW1 + 2 * tid + 1] = a;
+    const float a = train_colsum_wide(s);  // gradients of b1, W1[., 0] and W1[., 1] in one pass
+    if (tid < 3 * kH)
+      out[tid < kH ? kOffB1 + tid : tid < 2 * kH ? kOffW1 + 2 * (tid - kH) : kOffW1 + 2 * (tid - 2 * kH) + 1] = a;
   }
   // ---- dW2 rows n = TMEM lanes 0..63 (warps 0, 1 and 4, 5 for the two
   // column halves; every warp runs the warp-collective loads), staged in
