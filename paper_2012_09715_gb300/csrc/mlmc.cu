@@ -242,7 +242,11 @@ __global__ void __launch_bounds__(256) k_mlmc_batch(const __grid_constant__ Batc
     const PathSpec ps = a.specs[item.term];
     const PathConsts pc = make_path_consts(ps);
     PathSums acc;
-    if (ps.level < 2) {  // block-uniform: groups of paths share a Philox call
+    if (ps.level == 0 && ps.kind == AICDF_KIND_APPROX2) {  // block-uniform: the driver's bulk term
+      sum_groups<0>(item.begin, item.count, 0, threadIdx.x & ~31u, blockDim.x,
+                    [&](uint64_t q, float (&y)[4]) { group_y_kind<false, true, AP, V16, 0>(ps, pc, ap, a.keys, q, y); },
+                    acc);
+    } else if (ps.level < 2) {  // groups of paths share a Philox call
       sum_groups(item.begin, item.count, ps.level, threadIdx.x & ~31u, blockDim.x,
                  [&](uint64_t q, float (&y)[4]) { group_y_any<AP, V16>(ps, pc, ap, a.keys, q, y); }, acc);
     } else {

@@ -447,17 +447,27 @@ __device__ __forceinline__ float path_y_any(const PathSpec &a, const PathConsts 
   }
 }
 
-template <bool NE, bool NA, int AP, int MODEL, bool V16>
+// LEVEL >= 0 fixes the level at compile time; -1 takes it from a.level.
+template <bool NE, bool NA, int AP, int MODEL, bool V16, int LEVEL = -1>
 __device__ __forceinline__ void group_y_scheme(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
                                                const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
   const bool mil = a.scheme == AICDF_SCHEME_MILSTEIN;
-  if (a.level == 0) {
+  if (LEVEL == 0 || (LEVEL < 0 && a.level == 0)) {
     if (mil) group_y<NE, NA, AP, MODEL, V16, true, 0>(a, pc, ap, keys, q, y);
     else group_y<NE, NA, AP, MODEL, V16, false, 0>(a, pc, ap, keys, q, y);
   } else {
     if (mil) group_y<NE, NA, AP, MODEL, V16, true, 1>(a, pc, ap, keys, q, y);
     else group_y<NE, NA, AP, MODEL, V16, false, 1>(a, pc, ap, keys, q, y);
   }
+}
+
+// group_y_any with the kind's (NE, NA), and optionally the level, fixed by
+// the caller (the model and scheme still taken at run time).
+template <bool NE, bool NA, int AP, bool V16, int LEVEL = -1>
+__device__ __forceinline__ void group_y_kind(const PathSpec &a, const PathConsts &pc, const ApproxTable<AP> &ap,
+                                             const PhiloxKeys &keys, uint64_t q, float (&y)[4]) {
+  if (a.model == AICDF_MODEL_GBM) group_y_scheme<NE, NA, AP, AICDF_MODEL_GBM, V16, LEVEL>(a, pc, ap, keys, q, y);
+  else group_y_scheme<NE, NA, AP, AICDF_MODEL_CIR, V16, LEVEL>(a, pc, ap, keys, q, y);
 }
 
 template <int AP, bool V16>
